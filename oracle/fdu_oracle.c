@@ -1,0 +1,996 @@
+/*
+ * fdu_oracle.c -- plain, slow, single-threaded FP64 reference of the
+ * unstructured-mesh finite difference method of Zhen, Qu & Cai
+ * ("A Novel Finite Difference Method for Euler Equations in 2D
+ * Unstructured Meshes", arXiv 2102.12933).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library.  It shares no
+ * code, header, table or helper with the CUDA path.
+ *
+ * What it computes, in the paper's order:
+ *   - Euler state, fluxes and equation of state (Section 2.1, Eq. 1);
+ *   - the edge list and, per edge, the 1D curvilinear stencil of six
+ *     vertices (Section 2.3.1, Fig. weno1d-tri) with its arc-length
+ *     coordinate along Catmull-Rom curves (Section 2.3.1, Fig. curve_sten);
+ *   - fifth-order non-uniform WENO interpolation of characteristic variables
+ *     to the edge midpoint (Appendix, Eqs. u0-u2, C_K, smoothness
+ *     indicators and nonlinear weights), then a Riemann flux projected on
+ *     the edge direction (Section 2.3.1);
+ *   - one- and two-level divergence stencils (Section 2.2.2) and the
+ *     least-squares flux divergence by the SVD pseudo-inverse
+ *     (Section 2.2.1, Eqs. ef, eg, eLinearSystem and the a1+b2 weights);
+ *   - third-order TVD Runge-Kutta (Section 3, Shu & Osher).
+ *
+ * Readings where the paper is silent (stencil-walk rule, curve tangents,
+ * arc-length quadrature, Riemann solver, characteristic average, positivity
+ * fallback, time step) are marked "Reading:" below.
+ *
+ * Parity status: every function here is pinned by the CPU tests
+ * (polynomial reproduction, closed forms, exactness, convergence rates,
+ * the paper's stencil figure and counts).  The stencil-walk rule, the
+ * Catmull-Rom parametrisation, the Roe solver and the Roe average used
+ * for characteristics are readings: the tests pin their properties, not
+ * printed values.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OM_OK 0
+#define OM_ERR_ARG -1
+#define OM_ERR_MESH -2
+#define OM_ERR_STENCIL -3
+#define OM_ERR_RANK -4
+#define OM_ERR_NONPHYSICAL -7
+#define OM_ERR_NOMEM -8
+
+static char om_err[512];
+static int fail(int code, const char *msg) {
+    snprintf(om_err, sizeof om_err, "%s", msg);
+    return code;
+}
+const char *om_last_error(void) { return om_err; }
+
+/* ------------------------------------------------------------------ */
+/* Mesh                                                               */
+/* ------------------------------------------------------------------ */
+typedef struct om_mesh {
+    int64_t nv, nt, ne;
+    double Lx, Ly, gamma;
+    int degree, levels;
+    double *xy;       /* [nv][2] */
+    int32_t *edge;    /* [ne][2], v0 < v1, sorted lexicographically */
+    double *nrm;      /* [ne][2] unit(x_v1 - x_v0) */
+    double *mid;      /* [ne][2] midpoint, x_v0 + d/2 */
+    int64_t *adj_off; /* [nv+1] */
+    int32_t *adj;     /* neighbour ids, ascending per vertex */
+    int32_t *adj_e;   /* edge id of (v, adj) */
+    int32_t *sten;    /* [ne][6]  L3 L2 L1 R1 R2 R3 */
+    double *xi;       /* [ne][6]  normalised curve coordinates */
+    int32_t *ghost;   /* [nv] donor id for ghost vertices, -1 for real ones (NULL = none) */
+    /* divergence stencils (CSR over vertices) */
+    int64_t *dv_off;
+    int32_t *dv_id;
+    int64_t *de_off;
+    int32_t *de_id;
+    /* LSQ weights, aligned with dv_id / de_id */
+    double *wf, *wg, *we;
+    uint8_t *has_w;   /* [nv] weights computed for this vertex */
+} om_mesh;
+
+static void disp(const om_mesh *m, int64_t a, int64_t b, double d[2]) {
+    d[0] = m->xy[2 * b] - m->xy[2 * a];
+    d[1] = m->xy[2 * b + 1] - m->xy[2 * a + 1];
+    if (m->Lx > 0) d[0] -= m->Lx * rint(d[0] / m->Lx);
+    if (m->Ly > 0) d[1] -= m->Ly * rint(d[1] / m->Ly);
+}
+
+static int cmp_pair(const void *p, const void *q) {
+    const int32_t *a = (const int32_t *)p, *b = (const int32_t *)q;
+    if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;
+    if (a[1] != b[1]) return a[1] < b[1] ? -1 : 1;
+    return 0;
+}
+static int cmp_i32(const void *p, const void *q) {
+    int32_t a = *(const int32_t *)p, b = *(const int32_t *)q;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* edge id of the undirected pair (a, b), or -1 */
+static int64_t find_edge(const om_mesh *m, int32_t a, int32_t b) {
+    for (int64_t k = m->adj_off[a]; k < m->adj_off[a + 1]; ++k)
+        if (m->adj[k] == b) return m->adj_e[k];
+    return -1;
+}
+static int is_adjacent(const om_mesh *m, int32_t a, int32_t b) { return find_edge(m, a, b) >= 0; }
+
+/* ------------------------------------------------------------------ */
+/* 1D curvilinear stencil (Section 2.3.1, Fig. weno1d-tri)            */
+/* Reading: from the current vertex c, reached along direction d,     */
+/* take the unused neighbour q with the largest cosine                */
+/* d.(x_q - x_c)/(|d||x_q - x_c|); cosines within 1e-12 of the best   */
+/* so far do not replace it (neighbours scanned in ascending id, so   */
+/* near-ties go to the smaller id).  The cosine must be positive.     */
+/* ------------------------------------------------------------------ */
+static int walk_step(const om_mesh *m, int32_t prev, int32_t cur, const int32_t *used, int nused, int32_t *next) {
+    double d[2], e[2];
+    disp(m, prev, cur, d);
+    double dn = sqrt(d[0] * d[0] + d[1] * d[1]);
+    int32_t best = -1;
+    double sbest = 0;
+    for (int64_t k = m->adj_off[cur]; k < m->adj_off[cur + 1]; ++k) {
+        int32_t q = m->adj[k];
+        int skip = 0;
+        for (int u = 0; u < nused; ++u) skip |= (used[u] == q);
+        if (skip) continue;
+        disp(m, cur, q, e);
+        double en = sqrt(e[0] * e[0] + e[1] * e[1]);
+        double s = (d[0] * e[0] + d[1] * e[1]) / (dn * en);
+        if (best < 0 || s > sbest + 1e-12) {
+            best = q;
+            sbest = s;
+        }
+    }
+    if (best < 0 || !(sbest > 0)) return OM_ERR_STENCIL;
+    *next = best;
+    return OM_OK;
+}
+
+int om_walk_edge(const om_mesh *m, int64_t k, int32_t s[6]) {
+    int32_t v0 = m->edge[2 * k], v1 = m->edge[2 * k + 1];
+    int32_t used[6] = {v0, v1};
+    int n = 2;
+    int32_t r2, r3, l2, l3;
+    /* right side first (from v1, away from v0), then left (from v0, away from v1) */
+    if (walk_step(m, v0, v1, used, n, &r2)) return OM_ERR_STENCIL;
+    used[n++] = r2;
+    if (walk_step(m, v1, r2, used, n, &r3)) return OM_ERR_STENCIL;
+    used[n++] = r3;
+    if (walk_step(m, v1, v0, used, n, &l2)) return OM_ERR_STENCIL;
+    used[n++] = l2;
+    if (walk_step(m, v0, l2, used, n, &l3)) return OM_ERR_STENCIL;
+    s[0] = l3; s[1] = l2; s[2] = v0; s[3] = v1; s[4] = r2; s[5] = r3;
+    return OM_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Curve coordinate (Section 2.3.1, Fig. curve_sten).                 */
+/* Reading: each side is two cubic Hermite segments.  Tangent at the  */
+/* middle-edge end: the middle edge direction (pointing away from the */
+/* edge) scaled by the first segment's chord; at the inner vertex the */
+/* Catmull-Rom tangent (P2 - P0)/2; at the far end the last chord.    */
+/* Arc length: 16-point Gauss-Legendre on each segment.  The 1D       */
+/* coordinate is arc length from the edge midpoint, divided by the    */
+/* middle edge length.                                                */
+/* ------------------------------------------------------------------ */
+static double gl_t[16], gl_w[16];
+static int gl_ready = 0;
+
+/* Gauss-Legendre nodes on [0,1] by Newton iteration on P_16 */
+static void gl_init(void) {
+    const int n = 16;
+    for (int i = 0; i < n; ++i) {
+        double x = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        {
+            double p0 = 1, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1);
+        }
+        gl_t[i] = 0.5 * (1 - x);
+        gl_w[i] = 1.0 / ((1 - x * x) * dp * dp); /* 2/((1-x^2)P'^2) on [-1,1], halved */
+    }
+    gl_ready = 1;
+}
+
+/* arc length of the cubic Hermite segment P0 -> P1 with tangents m0, m1 */
+static double hermite_length(const double P0[2], const double P1[2], const double m0[2], const double m1[2]) {
+    if (!gl_ready) gl_init();
+    double s = 0;
+    for (int g = 0; g < 16; ++g) {
+        double t = gl_t[g];
+        double h00 = 6 * t * t - 6 * t, h10 = 3 * t * t - 4 * t + 1, h01 = -6 * t * t + 6 * t, h11 = 3 * t * t - 2 * t;
+        double dx = h00 * P0[0] + h10 * m0[0] + h01 * P1[0] + h11 * m1[0];
+        double dy = h00 * P0[1] + h10 * m0[1] + h01 * P1[1] + h11 * m1[1];
+        s += gl_w[g] * sqrt(dx * dx + dy * dy);
+    }
+    return s;
+}
+
+/* lengths along one side: A = middle-edge end, B, C = next two vertices,
+ * O = the other end of the middle edge.  Returns s(A,B), s(B,C). */
+static void side_lengths(const double O[2], const double A[2], const double B[2], const double C[2], double *sAB,
+                         double *sBC) {
+    double dir[2] = {A[0] - O[0], A[1] - O[1]};
+    double dl = sqrt(dir[0] * dir[0] + dir[1] * dir[1]);
+    double cab = sqrt((B[0] - A[0]) * (B[0] - A[0]) + (B[1] - A[1]) * (B[1] - A[1]));
+    double mA[2] = {dir[0] / dl * cab, dir[1] / dl * cab};
+    double mB[2] = {0.5 * (C[0] - A[0]), 0.5 * (C[1] - A[1])};
+    double mC[2] = {C[0] - B[0], C[1] - B[1]};
+    *sAB = hermite_length(A, B, mA, mB);
+    *sBC = hermite_length(B, C, mB, mC);
+}
+
+/* P[6][2] = L3 L2 L1 R1 R2 R3 as unwrapped points -> xi[6] */
+int om_curve_coords(const double *P, double *xi) {
+    const double *L3 = P, *L2 = P + 2, *L1 = P + 4, *R1 = P + 6, *R2 = P + 8, *R3 = P + 10;
+    double ell = sqrt((R1[0] - L1[0]) * (R1[0] - L1[0]) + (R1[1] - L1[1]) * (R1[1] - L1[1]));
+    if (!(ell > 0)) return fail(OM_ERR_MESH, "zero-length middle edge");
+    double sR1, sR2, sL1, sL2;
+    side_lengths(L1, R1, R2, R3, &sR1, &sR2);
+    side_lengths(R1, L1, L2, L3, &sL1, &sL2);
+    xi[2] = -0.5;
+    xi[3] = 0.5;
+    xi[1] = -0.5 - sL1 / ell;
+    xi[0] = xi[1] - sL2 / ell;
+    xi[4] = 0.5 + sR1 / ell;
+    xi[5] = xi[4] + sR2 / ell;
+    return OM_OK;
+}
+
+static int stencil_points(const om_mesh *m, const int32_t s[6], double P[12]) {
+    double d[2];
+    /* unwrap along the stencil, L1 at the origin */
+    P[4] = 0; P[5] = 0;
+    disp(m, s[2], s[1], d); P[2] = d[0]; P[3] = d[1];
+    disp(m, s[1], s[0], d); P[0] = P[2] + d[0]; P[1] = P[3] + d[1];
+    disp(m, s[2], s[3], d); P[6] = d[0]; P[7] = d[1];
+    disp(m, s[3], s[4], d); P[8] = P[6] + d[0]; P[9] = P[7] + d[1];
+    disp(m, s[4], s[5], d); P[10] = P[8] + d[0]; P[11] = P[9] + d[1];
+    return OM_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Non-uniform WENO5 (Appendix)                                        */
+/* x[5] = x_{i-2}..x_{i+2} with (x_i + x_{i+1})/2 = 0; u[5] the values */
+/* ------------------------------------------------------------------ */
+/* Eqs. u0-u2: the three sub-stencil interpolants evaluated at 0 */
+void om_substencil_coeffs(const double *x, double *lag /*[9]*/) {
+    double xm2 = x[0], xm1 = x[1], x0 = x[2], xp1 = x[3], xp2 = x[4];
+    double d0 = (xm1 - xm2) * (x0 - xm2) * (x0 - xm1);
+    lag[0] = xm1 * x0 * (x0 - xm1) / d0;
+    lag[1] = -xm2 * x0 * (x0 - xm2) / d0;
+    lag[2] = xm2 * xm1 * (xm1 - xm2) / d0;
+    double d1 = (x0 - xm1) * (xp1 - xm1) * (xp1 - x0);
+    lag[3] = x0 * xp1 * (xp1 - x0) / d1;
+    lag[4] = -xm1 * xp1 * (xp1 - xm1) / d1;
+    lag[5] = x0 * xm1 * (x0 - xm1) / d1;
+    double d2 = (xp1 - x0) * (xp2 - x0) * (xp2 - xp1);
+    lag[6] = xp1 * xp2 * (xp2 - xp1) / d2;
+    lag[7] = -x0 * xp2 * (xp2 - x0) / d2;
+    lag[8] = xp1 * x0 * (xp1 - x0) / d2;
+}
+
+/* Eq. C_K: linear (optimal) weights */
+void om_linear_weights(const double *x, double *C /*[3]*/) {
+    double xm2 = x[0], xm1 = x[1], xp1 = x[3], xp2 = x[4];
+    C[0] = xp1 * xp2 / ((xp1 - xm2) * (xp2 - xm2));
+    C[1] = -xm2 * (-xm2 - xm1 + xp1 + xp2) * xp2 / ((xp1 - xm2) * (xp2 - xm2) * (xp2 - xm1));
+    C[2] = xm2 * xm1 / ((xp2 - xm2) * (xp2 - xm1));
+}
+
+/* Eq. S5: the degree-4 interpolant over all five points, evaluated at 0,
+ * as a plain Lagrange product (used by the tests only). */
+void om_s5_coeffs(const double *x, double *l /*[5]*/) {
+    for (int k = 0; k < 5; ++k) {
+        double num = 1, den = 1;
+        for (int m = 0; m < 5; ++m) {
+            if (m == k) continue;
+            num *= (0 - x[m]);
+            den *= (x[k] - x[m]);
+        }
+        l[k] = num / den;
+    }
+}
+
+/* Smoothness indicator of a quadratic through (p[3], q[3]) on [a, b]:
+ * sum_{l=1,2} int_a^b dx^{2l-1} (d^l u/dx^l)^2 dx with dx = b - a. */
+static double smoothness(const double *p, const double *q, double a, double b) {
+    double A = 0, B = 0; /* u'(0) and u'' of the interpolating quadratic */
+    for (int j = 0; j < 3; ++j) {
+        double pa = p[(j + 1) % 3], pb = p[(j + 2) % 3];
+        double D = (p[j] - pa) * (p[j] - pb);
+        A += q[j] * (-(pa + pb)) / D;
+        B += q[j] * 2.0 / D;
+    }
+    double dx = b - a;
+    double i1 = A * A * (b - a) + A * B * (b * b - a * a) + B * B * (b * b * b - a * a * a) / 3.0;
+    double i2 = B * B * (b - a);
+    return dx * i1 + dx * dx * dx * i2;
+}
+
+/* Left-state interpolation at 0 (mode 0: nonlinear weights, 1: linear). */
+double om_nuweno(const double *x, const double *u, double eps, int mode) {
+    double lag[9], C[3], ut[3], beta[3];
+    om_substencil_coeffs(x, lag);
+    om_linear_weights(x, C);
+    for (int k = 0; k < 3; ++k) {
+        ut[k] = lag[3 * k] * u[k] + lag[3 * k + 1] * u[k + 1] + lag[3 * k + 2] * u[k + 2];
+        beta[k] = smoothness(x + k, u + k, x[2], x[3]);
+    }
+    if (mode == 1) return C[0] * ut[0] + C[1] * ut[1] + C[2] * ut[2];
+    double alpha[3], sa = 0;
+    for (int k = 0; k < 3; ++k) {
+        alpha[k] = C[k] / (beta[k] + eps); /* p = 1 */
+        sa += alpha[k];
+    }
+    double r = 0;
+    for (int k = 0; k < 3; ++k) r += alpha[k] / sa * ut[k];
+    return r;
+}
+
+/* ------------------------------------------------------------------ */
+/* Euler (Section 2.1) and the Riemann flux                            */
+/* ------------------------------------------------------------------ */
+static double pressure(const double *w, double g) {
+    return (g - 1.0) * (w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0]);
+}
+static void flux_fg(const double *w, double g, double *f, double *gg) {
+    double rho = w[0], u = w[1] / rho, v = w[2] / rho, p = pressure(w, g);
+    f[0] = rho * u; f[1] = rho * u * u + p; f[2] = rho * u * v; f[3] = (w[3] + p) * u;
+    gg[0] = rho * v; gg[1] = rho * v * u; gg[2] = rho * v * v + p; gg[3] = (w[3] + p) * v;
+}
+
+/* Roe average of a and b, then the right eigenvectors of dF_n/dw as
+ * columns (order: q_n - c, q_n (entropy), q_n (shear), q_n + c) and the
+ * eigenvalues.  Reading: the paper names neither the average nor the
+ * eigenvector normalisation. */
+static int roe_eigen(const double *a, const double *b, const double *n, double g, double R[4][4], double lam[4], double *cout) {
+    double ra = a[0], rb = b[0];
+    if (!(ra > 0) || !(rb > 0)) return OM_ERR_NONPHYSICAL;
+    double ua = a[1] / ra, va = a[2] / ra, ub = b[1] / rb, vb = b[2] / rb;
+    double Ha = (a[3] + pressure(a, g)) / ra, Hb = (b[3] + pressure(b, g)) / rb;
+    double sa = sqrt(ra), sb = sqrt(rb);
+    double u = (sa * ua + sb * ub) / (sa + sb);
+    double v = (sa * va + sb * vb) / (sa + sb);
+    double H = (sa * Ha + sb * Hb) / (sa + sb);
+    double q2 = u * u + v * v;
+    double c2 = (g - 1.0) * (H - 0.5 * q2);
+    if (!(c2 > 0)) return OM_ERR_NONPHYSICAL;
+    double c = sqrt(c2);
+    double nx = n[0], ny = n[1];
+    double qn = u * nx + v * ny, qt = -u * ny + v * nx;
+    double col[4][4] = {
+        {1, u - c * nx, v - c * ny, H - c * qn},
+        {1, u, v, 0.5 * q2},
+        {0, -ny, nx, qt},
+        {1, u + c * nx, v + c * ny, H + c * qn},
+    };
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) R[i][j] = col[j][i];
+    lam[0] = qn - c; lam[1] = qn; lam[2] = qn; lam[3] = qn + c;
+    if (cout) *cout = c;
+    return OM_OK;
+}
+
+/* Gauss-Jordan inverse with partial pivoting (a plain library-style step) */
+static int inverse4(double A[4][4], double X[4][4]) {
+    double M[4][8];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 8; ++j) M[i][j] = j < 4 ? A[i][j] : (j - 4 == i);
+    for (int col = 0; col < 4; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < 4; ++i)
+            if (fabs(M[i][col]) > fabs(M[piv][col])) piv = i;
+        if (M[piv][col] == 0) return -1;
+        if (piv != col)
+            for (int j = 0; j < 8; ++j) { double t = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = t; }
+        double inv = 1.0 / M[col][col];
+        for (int j = 0; j < 8; ++j) M[col][j] *= inv;
+        for (int i = 0; i < 4; ++i) {
+            if (i == col) continue;
+            double f = M[i][col];
+            for (int j = 0; j < 8; ++j) M[i][j] -= f * M[col][j];
+        }
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) X[i][j] = M[i][j + 4];
+    return 0;
+}
+
+/* exported for the tests: R (row-major 4x4) and its inverse */
+int om_eigvec(const double *a, const double *b, const double *n, double gamma, double *Rout, double *Lout, double *lam) {
+    double R[4][4], L[4][4];
+    int st = roe_eigen(a, b, n, gamma, R, lam, NULL);
+    if (st) return fail(st, "non-physical state in eigenvectors");
+    if (inverse4(R, L)) return fail(OM_ERR_NONPHYSICAL, "singular eigenvector matrix");
+    memcpy(Rout, R, sizeof R);
+    memcpy(Lout, L, sizeof L);
+    return OM_OK;
+}
+
+/* Reading (the paper does not name the solver for its method; Roe is the
+ * one it pairs with WENO for WCNS in Section 3.2): Roe flux with Harten's
+ * entropy fix |l| -> (l^2 + d^2)/(2d) for |l| < d, d = 0.1 c. */
+int om_roe_flux(const double *wl, const double *wr, const double *n, double g, double *out) {
+    double R[4][4], L[4][4], lam[4], c;
+    int st = roe_eigen(wl, wr, n, g, R, lam, &c);
+    if (st) return st;
+    if (inverse4(R, L)) return OM_ERR_NONPHYSICAL;
+    double fl[4], gl[4], fr[4], gr[4];
+    flux_fg(wl, g, fl, gl);
+    flux_fg(wr, g, fr, gr);
+    double dw[4], al[4];
+    for (int i = 0; i < 4; ++i) dw[i] = wr[i] - wl[i];
+    for (int k = 0; k < 4; ++k) {
+        al[k] = 0;
+        for (int j = 0; j < 4; ++j) al[k] += L[k][j] * dw[j];
+    }
+    double delta = 0.1 * c;
+    for (int k = 0; k < 4; ++k) {
+        double a = fabs(lam[k]);
+        if (a < delta) a = (lam[k] * lam[k] + delta * delta) / (2 * delta);
+        lam[k] = a;
+    }
+    for (int i = 0; i < 4; ++i) {
+        double diss = 0;
+        for (int k = 0; k < 4; ++k) diss += lam[k] * al[k] * R[i][k];
+        double fn_l = n[0] * fl[i] + n[1] * gl[i];
+        double fn_r = n[0] * fr[i] + n[1] * gr[i];
+        out[i] = 0.5 * (fn_l + fn_r) - 0.5 * diss;
+    }
+    return OM_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Edge flux: characteristic NU-WENO5 + Roe (Section 2.3.1, Appendix)  */
+/* Reading: characteristics at the Roe average of the two edge end     */
+/* states; the right state uses the mirrored stencil.  Positivity      */
+/* reading: if an interpolated density or pressure is not positive,    */
+/* the edge falls back to the end states (first order) and is counted. */
+/* ------------------------------------------------------------------ */
+static int edge_flux(const om_mesh *m, const double *w, int64_t k, double eps, double *r, int *fallback) {
+    const int32_t *s = m->sten + 6 * k;
+    const double *xi = m->xi + 6 * k;
+    const double *W[6];
+    for (int i = 0; i < 6; ++i) W[i] = w + 4 * (int64_t)s[i];
+    const double *n = m->nrm + 2 * k;
+    double R[4][4], L[4][4], lam[4];
+    int st = roe_eigen(W[2], W[3], n, m->gamma, R, lam, NULL);
+    if (st) return st;
+    if (inverse4(R, L)) return OM_ERR_NONPHYSICAL;
+    double ch[6][4];
+    for (int i = 0; i < 6; ++i)
+        for (int f = 0; f < 4; ++f) {
+            ch[i][f] = 0;
+            for (int j = 0; j < 4; ++j) ch[i][f] += L[f][j] * W[i][j];
+        }
+    double xl[5] = {xi[0], xi[1], xi[2], xi[3], xi[4]};
+    double xr[5] = {-xi[5], -xi[4], -xi[3], -xi[2], -xi[1]};
+    double cl[4], cr[4];
+    for (int f = 0; f < 4; ++f) {
+        double ul[5] = {ch[0][f], ch[1][f], ch[2][f], ch[3][f], ch[4][f]};
+        double ur[5] = {ch[5][f], ch[4][f], ch[3][f], ch[2][f], ch[1][f]};
+        cl[f] = om_nuweno(xl, ul, eps, 0);
+        cr[f] = om_nuweno(xr, ur, eps, 0);
+    }
+    double wl[4], wr[4];
+    for (int i = 0; i < 4; ++i) {
+        wl[i] = 0;
+        wr[i] = 0;
+        for (int f = 0; f < 4; ++f) {
+            wl[i] += R[i][f] * cl[f];
+            wr[i] += R[i][f] * cr[f];
+        }
+    }
+    *fallback = 0;
+    if (!(wl[0] > 0) || !(wr[0] > 0) || !(pressure(wl, m->gamma) > 0) || !(pressure(wr, m->gamma) > 0)) {
+        memcpy(wl, W[2], sizeof wl);
+        memcpy(wr, W[3], sizeof wr);
+        *fallback = 1;
+    }
+    return om_roe_flux(wl, wr, n, m->gamma, r);
+}
+
+/* ------------------------------------------------------------------ */
+/* Divergence stencils (Section 2.2.2)                                 */
+/* one-level(O): N(O), the edges at O and the edges between members of  */
+/* N(O).  two-level(O): union of one-level(j), j in N(O), minus O.      */
+/* ------------------------------------------------------------------ */
+typedef struct { int32_t *a; int64_t n, cap; } ivec;
+static int ivec_push(ivec *v, int32_t x) {
+    if (v->n == v->cap) {
+        int64_t c = v->cap ? 2 * v->cap : 64;
+        int32_t *p = (int32_t *)realloc(v->a, c * sizeof(int32_t));
+        if (!p) return -1;
+        v->a = p;
+        v->cap = c;
+    }
+    v->a[v->n++] = x;
+    return 0;
+}
+static void ivec_sort_unique(ivec *v) {
+    if (!v->n) return;
+    qsort(v->a, v->n, sizeof(int32_t), cmp_i32);
+    int64_t o = 1;
+    for (int64_t i = 1; i < v->n; ++i)
+        if (v->a[i] != v->a[o - 1]) v->a[o++] = v->a[i];
+    v->n = o;
+}
+
+static void one_level(const om_mesh *m, int32_t c, ivec *V, ivec *E) {
+    for (int64_t k = m->adj_off[c]; k < m->adj_off[c + 1]; ++k) {
+        int32_t a = m->adj[k];
+        ivec_push(V, a);
+        ivec_push(E, m->adj_e[k]);
+        /* ring edges: a-b with both a, b neighbours of c */
+        for (int64_t q = m->adj_off[a]; q < m->adj_off[a + 1]; ++q) {
+            int32_t b = m->adj[q];
+            if (b != c && is_adjacent(m, c, b)) ivec_push(E, m->adj_e[q]);
+        }
+    }
+}
+
+static int build_div_stencils(om_mesh *m) {
+    ivec V = {0}, E = {0};
+    int64_t nvtot = 0, netot = 0;
+    int64_t *voff = (int64_t *)calloc(m->nv + 1, sizeof(int64_t));
+    int64_t *eoff = (int64_t *)calloc(m->nv + 1, sizeof(int64_t));
+    ivec allV = {0}, allE = {0};
+    for (int32_t o = 0; o < m->nv; ++o) {
+        V.n = 0;
+        E.n = 0;
+        if (m->ghost && m->ghost[o] >= 0) {
+            voff[o + 1] = nvtot;
+            eoff[o + 1] = netot;
+            continue;
+        }
+        if (m->levels == 1) {
+            one_level(m, o, &V, &E);
+        } else {
+            for (int64_t k = m->adj_off[o]; k < m->adj_off[o + 1]; ++k) one_level(m, m->adj[k], &V, &E);
+        }
+        ivec_sort_unique(&V);
+        ivec_sort_unique(&E);
+        for (int64_t i = 0; i < V.n; ++i)
+            if (V.a[i] != o) { ivec_push(&allV, V.a[i]); ++nvtot; }
+        for (int64_t i = 0; i < E.n; ++i) { ivec_push(&allE, E.a[i]); ++netot; }
+        voff[o + 1] = nvtot;
+        eoff[o + 1] = netot;
+    }
+    free(V.a);
+    free(E.a);
+    m->dv_off = voff;
+    m->de_off = eoff;
+    m->dv_id = allV.a ? allV.a : (int32_t *)malloc(4);
+    m->de_id = allE.a ? allE.a : (int32_t *)malloc(4);
+    m->wf = (double *)calloc(nvtot + 1, sizeof(double));
+    m->wg = (double *)calloc(nvtot + 1, sizeof(double));
+    m->we = (double *)calloc(netot + 1, sizeof(double));
+    m->has_w = (uint8_t *)calloc(m->nv, 1);
+    return OM_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Least squares (Section 2.2.1): A^+ by one-sided Jacobi SVD          */
+/* ------------------------------------------------------------------ */
+/* monomials of p(x,y) in the paper's order: x, y, x^2, xy, y^2, x^3, ... */
+static int monomials(int degree, double x, double y, double *p) {
+    int c = 0;
+    for (int d = 1; d <= degree; ++d)
+        for (int i = d; i >= 0; --i) p[c++] = pow(x, i) * pow(y, d - i);
+    return c;
+}
+
+/* pseudo-inverse rows of A (m x n, column-major in A[j*m + i]) via
+ * one-sided Jacobi: A = U S V^T, A^+ = V S^-1 U^T.  Returns rows r0 and r1
+ * of A^+ summed into out[m].  Fails when sigma_min/sigma_max <= 1e-13. */
+static int pinv_rows_sum(double *A, int m, int n, int r0, int r1, double *out) {
+    double *V = (double *)calloc((size_t)n * n, sizeof(double));
+    for (int j = 0; j < n; ++j) V[j * n + j] = 1;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        int rot = 0;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double al = 0, be = 0, ga = 0;
+                for (int i = 0; i < m; ++i) {
+                    al += A[p * m + i] * A[p * m + i];
+                    be += A[q * m + i] * A[q * m + i];
+                    ga += A[p * m + i] * A[q * m + i];
+                }
+                if (fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+                rot = 1;
+                double zeta = (be - al) / (2 * ga);
+                double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1 + zeta * zeta));
+                double cs = 1 / sqrt(1 + t * t), sn = cs * t;
+                for (int i = 0; i < m; ++i) {
+                    double x = A[p * m + i], y = A[q * m + i];
+                    A[p * m + i] = cs * x - sn * y;
+                    A[q * m + i] = sn * x + cs * y;
+                }
+                for (int i = 0; i < n; ++i) {
+                    double x = V[p * n + i], y = V[q * n + i];
+                    V[p * n + i] = cs * x - sn * y;
+                    V[q * n + i] = sn * x + cs * y;
+                }
+            }
+        if (!rot) break;
+    }
+    double smax = 0, smin = INFINITY;
+    double *sig = (double *)malloc(n * sizeof(double));
+    for (int j = 0; j < n; ++j) {
+        double s = 0;
+        for (int i = 0; i < m; ++i) s += A[j * m + i] * A[j * m + i];
+        sig[j] = sqrt(s);
+        if (sig[j] > smax) smax = sig[j];
+        if (sig[j] < smin) smin = sig[j];
+    }
+    if (!(smin > 1e-13 * smax)) {
+        free(V);
+        free(sig);
+        return OM_ERR_RANK;
+    }
+    for (int i = 0; i < m; ++i) out[i] = 0;
+    for (int j = 0; j < n; ++j) {
+        /* column j of U is A[:,j]/sig_j; row r of A^+ = sum_j V[r][j]/sig_j U[:,j]^T */
+        double c = (V[j * n + r0] + V[j * n + r1]) / (sig[j] * sig[j]);
+        for (int i = 0; i < m; ++i) out[i] += c * A[j * m + i];
+    }
+    free(V);
+    free(sig);
+    return OM_OK;
+}
+
+static int lsq_vertex(om_mesh *m, int32_t o) {
+    int64_t v0 = m->dv_off[o], J = m->dv_off[o + 1] - v0;
+    int64_t e0 = m->de_off[o], K = m->de_off[o + 1] - e0;
+    int M = m->degree * (m->degree + 3) / 2, n = 2 * M;
+    int rows = (int)(2 * J + K);
+    if (rows < n) return fail(OM_ERR_RANK, "divergence stencil has fewer conditions than unknowns");
+    /* scale: monomials of degree d are evaluated at (x/h, y/h); the scaled
+     * problem has A' = A S with S = diag(h^d), so the rows of A^+ for the
+     * degree-1 unknowns a1 and b2 are those of A'^+ divided by h (exact for
+     * full column rank). */
+    double h = 0;
+    for (int64_t j = 0; j < J; ++j) {
+        double d[2];
+        disp(m, o, m->dv_id[v0 + j], d);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1]);
+        if (r > h) h = r;
+    }
+    double *A = (double *)calloc((size_t)rows * n, sizeof(double));
+    double p[64];
+    for (int64_t j = 0; j < J; ++j) {
+        double d[2];
+        disp(m, o, m->dv_id[v0 + j], d);
+        monomials(m->degree, d[0] / h, d[1] / h, p);
+        for (int c = 0; c < M; ++c) {
+            A[c * rows + 2 * j] = p[c];
+            A[(M + c) * rows + 2 * j + 1] = p[c];
+        }
+    }
+    for (int64_t k = 0; k < K; ++k) {
+        int32_t e = m->de_id[e0 + k];
+        /* edge midpoint relative to o: o -> v0 of the edge, plus half the edge */
+        double d[2], de[2];
+        disp(m, o, m->edge[2 * e], d);
+        disp(m, m->edge[2 * e], m->edge[2 * e + 1], de);
+        double mx = d[0] + 0.5 * de[0], my = d[1] + 0.5 * de[1];
+        monomials(m->degree, mx / h, my / h, p);
+        for (int c = 0; c < M; ++c) {
+            A[c * rows + 2 * J + k] = m->nrm[2 * e] * p[c];
+            A[(M + c) * rows + 2 * J + k] = m->nrm[2 * e + 1] * p[c];
+        }
+    }
+    double *wd = (double *)malloc(rows * sizeof(double));
+    int st = pinv_rows_sum(A, rows, n, 0, M + 1, wd);
+    free(A);
+    if (st) {
+        free(wd);
+        return fail(OM_ERR_RANK, "rank-deficient least-squares system");
+    }
+    for (int64_t j = 0; j < J; ++j) {
+        m->wf[v0 + j] = wd[2 * j] / h;
+        m->wg[v0 + j] = wd[2 * j + 1] / h;
+    }
+    for (int64_t k = 0; k < K; ++k) m->we[e0 + k] = wd[2 * J + k] / h;
+    free(wd);
+    m->has_w[o] = 1;
+    return OM_OK;
+}
+
+int om_build_weights(om_mesh *m, const uint8_t *mask) {
+    for (int32_t o = 0; o < m->nv; ++o) {
+        if (mask && !mask[o]) continue;
+        if (m->ghost && m->ghost[o] >= 0) continue;
+        if (m->has_w[o]) continue;
+        int st = lsq_vertex(m, o);
+        if (st) return st;
+    }
+    return OM_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Mesh construction                                                   */
+/* ------------------------------------------------------------------ */
+void om_destroy(om_mesh *m) {
+    if (!m) return;
+    free(m->xy); free(m->edge); free(m->nrm); free(m->mid);
+    free(m->adj_off); free(m->adj); free(m->adj_e);
+    free(m->sten); free(m->xi); free(m->ghost);
+    free(m->dv_off); free(m->dv_id); free(m->de_off); free(m->de_id);
+    free(m->wf); free(m->wg); free(m->we); free(m->has_w);
+    free(m);
+}
+
+/* ghost: [nv] donor ids (-1 for real vertices) or NULL.  On a periodic
+ * mesh every edge must have a 1D stencil.  On an open mesh, edges whose
+ * walk runs into the boundary are marked with sten = -1; a residual that
+ * needs such an edge fails with OM_ERR_STENCIL. */
+int om_create(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, double Lx, double Ly, int degree,
+              int levels, double gamma, const int32_t *ghost, om_mesh **out) {
+    if (!xy || !tri || nv < 3 || nt < 1 || degree < 1 || degree > 6 || levels < 1 || levels > 2 || !out)
+        return fail(OM_ERR_ARG, "bad argument");
+    om_mesh *m = (om_mesh *)calloc(1, sizeof(om_mesh));
+    m->nv = nv; m->nt = nt; m->Lx = Lx; m->Ly = Ly; m->gamma = gamma; m->degree = degree; m->levels = levels;
+    m->xy = (double *)malloc(nv * 2 * sizeof(double));
+    memcpy(m->xy, xy, nv * 2 * sizeof(double));
+    if (ghost) {
+        m->ghost = (int32_t *)malloc(nv * sizeof(int32_t));
+        memcpy(m->ghost, ghost, nv * sizeof(int32_t));
+    }
+    /* edges: unique undirected triangle sides, (min id, max id), sorted */
+    int32_t *pairs = (int32_t *)malloc(nt * 6 * sizeof(int32_t));
+    for (int64_t t = 0; t < nt; ++t)
+        for (int s = 0; s < 3; ++s) {
+            int32_t a = tri[3 * t + s], b = tri[3 * t + (s + 1) % 3];
+            if (a < 0 || a >= nv || b < 0 || b >= nv || a == b) {
+                free(pairs);
+                om_destroy(m);
+                return fail(OM_ERR_MESH, "triangle with a bad vertex id");
+            }
+            pairs[6 * t + 2 * s] = a < b ? a : b;
+            pairs[6 * t + 2 * s + 1] = a < b ? b : a;
+        }
+    qsort(pairs, nt * 3, 2 * sizeof(int32_t), cmp_pair);
+    int64_t ne = 0;
+    for (int64_t i = 0; i < nt * 3; ++i)
+        if (ne == 0 || cmp_pair(pairs + 2 * i, pairs + 2 * (ne - 1)) != 0) {
+            pairs[2 * ne] = pairs[2 * i];
+            pairs[2 * ne + 1] = pairs[2 * i + 1];
+            ++ne;
+        }
+    m->ne = ne;
+    m->edge = (int32_t *)malloc(ne * 2 * sizeof(int32_t));
+    memcpy(m->edge, pairs, ne * 2 * sizeof(int32_t));
+    free(pairs);
+    /* adjacency, ascending neighbour ids */
+    m->adj_off = (int64_t *)calloc(nv + 1, sizeof(int64_t));
+    for (int64_t k = 0; k < ne; ++k) {
+        m->adj_off[m->edge[2 * k] + 1]++;
+        m->adj_off[m->edge[2 * k + 1] + 1]++;
+    }
+    for (int64_t v = 0; v < nv; ++v) m->adj_off[v + 1] += m->adj_off[v];
+    m->adj = (int32_t *)malloc(2 * ne * sizeof(int32_t));
+    m->adj_e = (int32_t *)malloc(2 * ne * sizeof(int32_t));
+    int64_t *fill = (int64_t *)malloc(nv * sizeof(int64_t));
+    for (int64_t v = 0; v < nv; ++v) fill[v] = m->adj_off[v];
+    for (int64_t k = 0; k < ne; ++k) {
+        int32_t a = m->edge[2 * k], b = m->edge[2 * k + 1];
+        m->adj[fill[a]] = b; m->adj_e[fill[a]++] = (int32_t)k;
+        m->adj[fill[b]] = a; m->adj_e[fill[b]++] = (int32_t)k;
+    }
+    free(fill);
+    for (int64_t v = 0; v < nv; ++v) {
+        /* insertion sort of (neighbour, edge) by neighbour id */
+        for (int64_t i = m->adj_off[v] + 1; i < m->adj_off[v + 1]; ++i) {
+            int32_t a = m->adj[i], e = m->adj_e[i];
+            int64_t j = i - 1;
+            while (j >= m->adj_off[v] && m->adj[j] > a) {
+                m->adj[j + 1] = m->adj[j];
+                m->adj_e[j + 1] = m->adj_e[j];
+                --j;
+            }
+            m->adj[j + 1] = a;
+            m->adj_e[j + 1] = e;
+        }
+    }
+    /* edge geometry */
+    m->nrm = (double *)malloc(ne * 2 * sizeof(double));
+    m->mid = (double *)malloc(ne * 2 * sizeof(double));
+    for (int64_t k = 0; k < ne; ++k) {
+        double d[2];
+        disp(m, m->edge[2 * k], m->edge[2 * k + 1], d);
+        double l = sqrt(d[0] * d[0] + d[1] * d[1]);
+        if (!(l > 0)) {
+            om_destroy(m);
+            return fail(OM_ERR_MESH, "zero-length edge");
+        }
+        m->nrm[2 * k] = d[0] / l;
+        m->nrm[2 * k + 1] = d[1] / l;
+        m->mid[2 * k] = m->xy[2 * m->edge[2 * k]] + 0.5 * d[0];
+        m->mid[2 * k + 1] = m->xy[2 * m->edge[2 * k] + 1] + 0.5 * d[1];
+    }
+    /* 1D stencils and curve coordinates */
+    m->sten = (int32_t *)malloc(ne * 6 * sizeof(int32_t));
+    m->xi = (double *)malloc(ne * 6 * sizeof(double));
+    for (int64_t k = 0; k < ne; ++k) {
+        int32_t *s = m->sten + 6 * k;
+        if (om_walk_edge(m, k, s) != OM_OK) {
+            if (Lx > 0 && Ly > 0) {
+                om_destroy(m);
+                return fail(OM_ERR_STENCIL, "1D stencil walk found no forward neighbour");
+            }
+            for (int i = 0; i < 6; ++i) s[i] = -1;
+            for (int i = 0; i < 6; ++i) m->xi[6 * k + i] = 0;
+            continue;
+        }
+        double P[12];
+        stencil_points(m, s, P);
+        om_curve_coords(P, m->xi + 6 * k);
+    }
+    build_div_stencils(m);
+    *out = m;
+    return OM_OK;
+}
+
+int64_t om_num_edges(const om_mesh *m) { return m->ne; }
+void om_get_edges(const om_mesh *m, int32_t *e) { memcpy(e, m->edge, m->ne * 2 * sizeof(int32_t)); }
+void om_get_normals(const om_mesh *m, double *n) { memcpy(n, m->nrm, m->ne * 2 * sizeof(double)); }
+void om_get_stencils(const om_mesh *m, int32_t *s, double *xi) {
+    if (s) memcpy(s, m->sten, m->ne * 6 * sizeof(int32_t));
+    if (xi) memcpy(xi, m->xi, m->ne * 6 * sizeof(double));
+}
+void om_div_sizes(const om_mesh *m, int64_t *nvert, int64_t *nedge) {
+    *nvert = m->dv_off[m->nv];
+    *nedge = m->de_off[m->nv];
+}
+void om_get_div(const om_mesh *m, int64_t *voff, int32_t *vid, double *wf, double *wg, int64_t *eoff, int32_t *eid,
+                double *we) {
+    memcpy(voff, m->dv_off, (m->nv + 1) * sizeof(int64_t));
+    memcpy(eoff, m->de_off, (m->nv + 1) * sizeof(int64_t));
+    memcpy(vid, m->dv_id, m->dv_off[m->nv] * sizeof(int32_t));
+    memcpy(eid, m->de_id, m->de_off[m->nv] * sizeof(int32_t));
+    if (wf) memcpy(wf, m->wf, m->dv_off[m->nv] * sizeof(double));
+    if (wg) memcpy(wg, m->wg, m->dv_off[m->nv] * sizeof(double));
+    if (we) memcpy(we, m->we, m->de_off[m->nv] * sizeof(double));
+}
+
+/* ------------------------------------------------------------------ */
+/* Residual (Section 2.2.1): dw/dt = -(a1 + b2) per component          */
+/* ------------------------------------------------------------------ */
+/* r[ne][4] for edges with emask[k] (NULL = all) */
+int om_edge_fluxes(const om_mesh *m, const double *w, double eps, const uint8_t *emask, double *r, int64_t *nfallback) {
+    int64_t nf = 0;
+    for (int64_t k = 0; k < m->ne; ++k) {
+        if (emask && !emask[k]) continue;
+        if (m->sten[6 * k] < 0) return fail(OM_ERR_STENCIL, "an edge in a divergence stencil has no 1D stencil");
+        int fb = 0;
+        int st = edge_flux(m, w, k, eps, r + 4 * k, &fb);
+        if (st) return fail(st, "non-physical state in an edge flux");
+        nf += fb;
+    }
+    if (nfallback) *nfallback = nf;
+    return OM_OK;
+}
+
+/* ghost fill (transmissive reading): ghost vertices copy their donor */
+void om_fill_ghosts(const om_mesh *m, double *w) {
+    if (!m->ghost) return;
+    for (int64_t v = 0; v < m->nv; ++v)
+        if (m->ghost[v] >= 0) memcpy(w + 4 * v, w + 4 * (int64_t)m->ghost[v], 4 * sizeof(double));
+}
+
+/* dwdt[nv][4] at vertices with vmask[v] (NULL = all real vertices);
+ * w must already hold the ghost states.  The edge fluxes needed are
+ * computed from scratch. */
+int om_residual(om_mesh *m, const double *w, double eps, const uint8_t *vmask, double *dwdt, int64_t *nfallback) {
+    int st = om_build_weights(m, vmask);
+    if (st) return st;
+    uint8_t *emask = (uint8_t *)calloc(m->ne, 1);
+    for (int64_t o = 0; o < m->nv; ++o) {
+        if (vmask && !vmask[o]) continue;
+        for (int64_t i = m->de_off[o]; i < m->de_off[o + 1]; ++i) emask[m->de_id[i]] = 1;
+    }
+    double *r = (double *)calloc(m->ne * 4, sizeof(double));
+    st = om_edge_fluxes(m, w, eps, emask, r, nfallback);
+    if (st) { free(emask); free(r); return st; }
+    for (int64_t o = 0; o < m->nv; ++o) {
+        if (vmask && !vmask[o]) continue;
+        if (m->ghost && m->ghost[o] >= 0) { for (int c = 0; c < 4; ++c) dwdt[4 * o + c] = 0; continue; }
+        double f0[4], g0[4], fj[4], gj[4];
+        flux_fg(w + 4 * o, m->gamma, f0, g0);
+        double div[4] = {0, 0, 0, 0};
+        for (int64_t i = m->dv_off[o]; i < m->dv_off[o + 1]; ++i) {
+            flux_fg(w + 4 * (int64_t)m->dv_id[i], m->gamma, fj, gj);
+            for (int c = 0; c < 4; ++c) div[c] += m->wf[i] * (fj[c] - f0[c]) + m->wg[i] * (gj[c] - g0[c]);
+        }
+        for (int64_t i = m->de_off[o]; i < m->de_off[o + 1]; ++i) {
+            int32_t e = m->de_id[i];
+            for (int c = 0; c < 4; ++c)
+                div[c] += m->we[i] * (r[4 * e + c] - (m->nrm[2 * e] * f0[c] + m->nrm[2 * e + 1] * g0[c]));
+        }
+        for (int c = 0; c < 4; ++c) dwdt[4 * o + c] = -div[c];
+    }
+    free(emask);
+    free(r);
+    return OM_OK;
+}
+
+/* SSP-RK3 stage combination (Shu & Osher), stage = 1, 2, 3:
+ *   1: out = wn + dt L
+ *   2: out = 3/4 wn + 1/4 (ws + dt L)
+ *   3: out = 1/3 wn + 2/3 (ws + dt L)                                  */
+void om_stage_combine(int64_t n, int stage, const double *wn, const double *ws, const double *L, double dt,
+                      double *out) {
+    for (int64_t i = 0; i < n; ++i) {
+        if (stage == 1) out[i] = wn[i] + dt * L[i];
+        else if (stage == 2) out[i] = 0.75 * wn[i] + 0.25 * (ws[i] + dt * L[i]);
+        else out[i] = (1.0 / 3.0) * wn[i] + (2.0 / 3.0) * (ws[i] + dt * L[i]);
+    }
+}
+
+/* one SSP-RK3 step in place on w[nv][4] */
+int om_rk3_step(om_mesh *m, double *w, double dt, double eps, int64_t *nfallback) {
+    int64_t n = m->nv * 4, nf = 0, f;
+    double *wn = (double *)malloc(n * sizeof(double));
+    double *L = (double *)malloc(n * sizeof(double));
+    double *ws = (double *)malloc(n * sizeof(double));
+    memcpy(wn, w, n * sizeof(double));
+    memcpy(ws, w, n * sizeof(double));
+    int st = OM_OK;
+    for (int stage = 1; stage <= 3 && st == OM_OK; ++stage) {
+        om_fill_ghosts(m, ws);
+        st = om_residual(m, ws, eps, NULL, L, &f);
+        nf += f;
+        if (st) break;
+        om_stage_combine(n, stage, wn, ws, L, dt, ws);
+        if (m->ghost)
+            for (int64_t v = 0; v < m->nv; ++v)
+                if (m->ghost[v] >= 0) memcpy(ws + 4 * v, wn + 4 * v, 4 * sizeof(double));
+    }
+    if (st == OM_OK) {
+        om_fill_ghosts(m, ws);
+        memcpy(w, ws, n * sizeof(double));
+    }
+    free(wn); free(L); free(ws);
+    if (nfallback) *nfallback = nf;
+    return st;
+}
+
+/* Reading (the paper uses a CFL number without defining it):
+ * dt = cfl * min over real vertices of h_v / (|u_v| + c_v), h_v the
+ * shortest edge at v. */
+double om_max_dt(const om_mesh *m, const double *w, double cfl) {
+    double best = INFINITY;
+    for (int64_t v = 0; v < m->nv; ++v) {
+        if (m->ghost && m->ghost[v] >= 0) continue;
+        double h = INFINITY;
+        for (int64_t k = m->adj_off[v]; k < m->adj_off[v + 1]; ++k) {
+            double d[2];
+            disp(m, v, m->adj[k], d);
+            double l = sqrt(d[0] * d[0] + d[1] * d[1]);
+            if (l < h) h = l;
+        }
+        const double *s = w + 4 * v;
+        double u = s[1] / s[0], vv = s[2] / s[0];
+        double c = sqrt(m->gamma * pressure(s, m->gamma) / s[0]);
+        double dt = h / (sqrt(u * u + vv * vv) + c);
+        if (dt < best) best = dt;
+    }
+    return cfl * best;
+}
+
+/* smoothness indicators beta_0..2 of the left-state sub-stencils (tests) */
+void om_smoothness_all(const double *x, const double *u, double *beta) {
+    for (int k = 0; k < 3; ++k) beta[k] = smoothness(x + k, u + k, x[2], x[3]);
+}

@@ -1,0 +1,228 @@
+"""Seeded synthetic inputs: triangle meshes and initial states.
+
+This module is shared by the CUDA path's tests and benchmark and by the
+oracle's tests.  It holds none of the method's arithmetic: it only draws
+meshes (jittered lattices split on random diagonals) and evaluates the
+initial conditions of the paper's test problems (isentropic vortex,
+Section 3.1; 2D Riemann problem; 2D Sod problem, Section 3.2).
+
+Every generator takes an explicit seed and uses numpy's PCG64
+(``numpy.random.default_rng``), so both sides of a parity test see the
+same bytes.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+@dataclass
+class Mesh:
+    """A triangle mesh as plain arrays (original vertex ids)."""
+
+    xy: np.ndarray  # [nv, 2] float64
+    tri: np.ndarray  # [nt, 3] int32, counter-clockwise
+    Lx: float  # periodic length in x (0 = not periodic)
+    Ly: float  # periodic length in y (0 = not periodic)
+    n: int = 0  # lattice size it was drawn from (informational)
+    h: float = 0.0  # lattice spacing (informational)
+
+    @property
+    def nv(self) -> int:
+        return int(self.xy.shape[0])
+
+    @property
+    def nt(self) -> int:
+        return int(self.tri.shape[0])
+
+
+def _signed_areas(xy, tri, Lx, Ly):
+    a = xy[tri[:, 0]]
+    b = xy[tri[:, 1]] - a
+    c = xy[tri[:, 2]] - a
+    if Lx > 0:
+        b[:, 0] -= Lx * np.rint(b[:, 0] / Lx)
+        c[:, 0] -= Lx * np.rint(c[:, 0] / Lx)
+    if Ly > 0:
+        b[:, 1] -= Ly * np.rint(b[:, 1] / Ly)
+        c[:, 1] -= Ly * np.rint(c[:, 1] / Ly)
+    return 0.5 * (b[:, 0] * c[:, 1] - b[:, 1] * c[:, 0])
+
+
+def torus_lattice(n: int, L: float = 10.0, jitter: float = 0.2, seed: int = 1001,
+                  random_diagonals: bool = True, origin: float = 0.0) -> Mesh:
+    """n x n vertices on the periodic square [origin, origin+L)^2.
+
+    Vertex (i, j) has id j*n + i and sits at (origin + i*h, origin + j*h),
+    h = L/n, moved by U(-jitter*h, +jitter*h) in x and y independently.
+    Each lattice quad is split on a Bernoulli(1/2) diagonal (or always on
+    the (i,j)-(i+1,j+1) diagonal when ``random_diagonals`` is False).
+    """
+    if n < 4:
+        raise ValueError("torus lattice needs n >= 4")
+    rng = np.random.default_rng(seed)
+    h = L / n
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    xy = np.stack([origin + ii.ravel() * h, origin + jj.ravel() * h], axis=1).astype(np.float64)
+    if jitter > 0:
+        xy += rng.uniform(-jitter * h, jitter * h, size=xy.shape)
+    diag = rng.integers(0, 2, size=n * n) if random_diagonals else np.zeros(n * n, np.int64)
+    i = ii.ravel()
+    j = jj.ravel()
+    a = j * n + i
+    b = j * n + (i + 1) % n
+    c = ((j + 1) % n) * n + (i + 1) % n
+    d = ((j + 1) % n) * n + i
+    t0 = np.where(diag[:, None] == 0, np.stack([a, b, c], 1), np.stack([a, b, d], 1))
+    t1 = np.where(diag[:, None] == 0, np.stack([a, c, d], 1), np.stack([b, c, d], 1))
+    tri = np.concatenate([t0, t1], 0).astype(np.int32)
+    m = Mesh(xy=xy, tri=tri, Lx=L, Ly=L, n=n, h=h)
+    if np.any(_signed_areas(xy, tri, L, L) <= 0):
+        raise ValueError("jittered lattice produced a non-positive triangle")
+    return m
+
+
+def box_lattice(n: int, ghost_layers: int = 0, jitter: float = 0.2, seed: int = 1003) -> Mesh:
+    """Lattice on [0,1]^2 with n points per side (spacing h = 1/(n-1)).
+
+    ``ghost_layers`` extra lattice layers are added outside the unit
+    square on every side.  Only vertices strictly inside the square are
+    jittered; vertices on the square's boundary and in the ghost layers
+    stay on the lattice.  Quads are split on Bernoulli(1/2) diagonals.
+    Vertex (i, j), i, j in [-g, n-1+g], has id (j+g)*m + (i+g), m = n+2g.
+    """
+    g = ghost_layers
+    h = 1.0 / (n - 1)
+    m = n + 2 * g
+    rng = np.random.default_rng(seed)
+    jj, ii = np.meshgrid(np.arange(-g, n + g), np.arange(-g, n + g), indexing="ij")
+    i = ii.ravel()
+    j = jj.ravel()
+    xy = np.stack([i * h, j * h], axis=1).astype(np.float64)
+    jit = rng.uniform(-jitter * h, jitter * h, size=xy.shape)
+    interior = (i > 0) & (i < n - 1) & (j > 0) & (j < n - 1)
+    xy[interior] += jit[interior]
+    diag = rng.integers(0, 2, size=(m - 1) * (m - 1))
+    qi, qj = np.meshgrid(np.arange(m - 1), np.arange(m - 1), indexing="xy")
+    qi = qi.ravel()
+    qj = qj.ravel()
+    a = qj * m + qi
+    b = qj * m + qi + 1
+    c = (qj + 1) * m + qi + 1
+    d = (qj + 1) * m + qi
+    t0 = np.where(diag[:, None] == 0, np.stack([a, b, c], 1), np.stack([a, b, d], 1))
+    t1 = np.where(diag[:, None] == 0, np.stack([a, c, d], 1), np.stack([b, c, d], 1))
+    tri = np.concatenate([t0, t1], 0).astype(np.int32)
+    mesh = Mesh(xy=xy, tri=tri, Lx=0.0, Ly=0.0, n=n, h=h)
+    if np.any(_signed_areas(xy, tri, 0.0, 0.0) <= 0):
+        raise ValueError("jittered box lattice produced a non-positive triangle")
+    return mesh
+
+
+def permute_vertices(mesh: Mesh, seed: int) -> tuple[Mesh, np.ndarray]:
+    """Return the same mesh with vertex ids shuffled, and the permutation.
+
+    ``perm[new_id] = old_id``.
+    """
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(mesh.nv)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(mesh.nv)
+    tri = inv[mesh.tri].astype(np.int32)
+    return Mesh(xy=mesh.xy[perm].copy(), tri=tri, Lx=mesh.Lx, Ly=mesh.Ly, n=mesh.n, h=mesh.h), perm
+
+
+# --------------------------------------------------------------------------
+# Initial conditions (primitive -> conservative records [nv][4] = rho, rho*u,
+# rho*v, rho*E with E = e + (u^2+v^2)/2 and p = (gamma-1) rho e, Section 2.1)
+# --------------------------------------------------------------------------
+
+def primitive_to_conservative(rho, u, v, p, gamma=GAMMA):
+    w = np.empty((np.size(rho), 4), np.float64)
+    w[:, 0] = rho
+    w[:, 1] = rho * u
+    w[:, 2] = rho * v
+    w[:, 3] = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return w
+
+
+def _min_image(d, L):
+    if L > 0:
+        return d - L * np.rint(d / L)
+    return d
+
+
+def isentropic_vortex(xy, L=10.0, beta=5.0, centre=(5.0, 5.0), t=0.0, gamma=GAMMA,
+                      u_inf=1.0, v_inf=1.0):
+    """Isentropic vortex of Section 3.1 (free stream rho=u=v=p=1).
+
+    At time t the exact solution is the initial vortex translated by
+    (u_inf*t, v_inf*t), wrapped into the periodic box of side L.
+    Distances use the minimum image.
+    """
+    xc = centre[0] + u_inf * t
+    yc = centre[1] + v_inf * t
+    xb = _min_image(xy[:, 0] - xc, L)
+    yb = _min_image(xy[:, 1] - yc, L)
+    r2 = xb * xb + yb * yb
+    rho = (1.0 - (gamma - 1.0) * beta * beta / (8.0 * gamma * math.pi ** 2) * np.exp(1.0 - r2)) ** (1.0 / (gamma - 1.0))
+    amp = beta / (2.0 * math.pi) * np.exp(0.5 * (1.0 - r2))
+    u = u_inf - amp * yb
+    v = v_inf + amp * xb
+    p = rho ** gamma
+    return primitive_to_conservative(rho, u, v, p, gamma)
+
+
+RIEMANN_2D_QUADRANTS = (
+    # (rho, u, v, p) for x>1/2,y>1/2 ; x<1/2,y>1/2 ; x<1/2,y<1/2 ; x>1/2,y<1/2
+    (1.5, 0.0, 0.0, 1.5),
+    (0.5323, 1.206, 0.0, 0.3),
+    (0.138, 1.206, 1.206, 0.029),
+    (0.5323, 0.0, 1.206, 0.3),
+)
+
+
+def riemann_2d(xy, gamma=GAMMA):
+    """Four-quadrant 2D Riemann problem on [0,1]^2, interface at x=y=1/2."""
+    x = xy[:, 0]
+    y = xy[:, 1]
+    q = np.where(x > 0.5, np.where(y > 0.5, 0, 3), np.where(y > 0.5, 1, 2))
+    tab = np.array(RIEMANN_2D_QUADRANTS)
+    s = tab[q]
+    return primitive_to_conservative(s[:, 0], s[:, 1], s[:, 2], s[:, 3], gamma)
+
+
+def sod_2d(xy, gamma=GAMMA):
+    """2D Sod problem of Section 3.2 on [-1,1]^2: (1,0,0,1) inside |x|,|y|<1/4."""
+    inside = (np.abs(xy[:, 0]) < 0.25) & (np.abs(xy[:, 1]) < 0.25)
+    rho = np.where(inside, 1.0, 0.125)
+    p = np.where(inside, 1.0, 0.1)
+    z = np.zeros_like(rho)
+    return primitive_to_conservative(rho, z, z, p, gamma)
+
+
+def vortex_case(n: int, seed: int = 1001, L: float = 10.0, beta: float = 5.0,
+                centre=(5.0, 5.0), jitter: float = 0.2, random_diagonals: bool = True):
+    """Periodic vortex workload: jittered torus lattice + vortex state."""
+    mesh = torus_lattice(n, L=L, jitter=jitter, seed=seed, random_diagonals=random_diagonals)
+    w0 = isentropic_vortex(mesh.xy, L=L, beta=beta, centre=centre)
+    return mesh, w0
+
+
+def batch_sizes(count: int = 64, lo: float = 5e3, hi: float = 2e5, seed: int = 2004):
+    """Log-uniform mesh sizes, vortex strengths in [1,5], centres in [3,7]^2."""
+    rng = np.random.default_rng(seed)
+    v = np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=count)))
+    n = np.maximum(8, np.rint(np.sqrt(v))).astype(int)
+    beta = rng.uniform(1.0, 5.0, size=count)
+    centres = rng.uniform(3.0, 7.0, size=(count, 2))
+    return n, beta, centres
+
+
+def random_state_perturbation(nv: int, scale: float, seed: int):
+    rng = np.random.default_rng(seed)
+    return scale * rng.standard_normal((nv, 4))

@@ -1,0 +1,462 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test pins one part of the oracle to something other than itself:
+closed forms on uniform points, polynomial reproduction, the paper's
+printed stencil figure and counts, analytic fluxes and eigen-relations,
+exactness of the least squares for polynomial fluxes, convergence rates,
+free-stream preservation and the RK3 stability polynomial.
+"""
+import json
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import golden
+from paper_2102_12933_gb300 import inputs
+
+G = 1.4
+UNIFORM = np.array([-2.5, -1.5, -0.5, 0.5, 1.5])
+
+
+def random_points(rng, jitter=0.45):
+    """x_{i-2..i+2} ordered, with (x_i + x_{i+1})/2 = 0 and x_{i+1} - x_i = 1."""
+    base = UNIFORM.copy()
+    while True:
+        x = base + rng.uniform(-jitter, jitter, size=5)
+        x[2], x[3] = -0.5, 0.5
+        if np.all(np.diff(x) > 0.05):
+            return x
+
+
+# ----------------------------------------------------------------- Appendix
+def test_uniform_substencils_match_classic_weno5():
+    """Eqs. u0-u2 on unit spacing reduce to the classical WENO5 midpoint interpolants."""
+    lag = oracle.substencil_coeffs(UNIFORM)
+    want = np.array([[3, -10, 15], [-1, 6, 3], [3, 6, -1]]) / 8.0
+    assert np.allclose(lag, want, atol=1e-15, rtol=0)
+
+
+def test_uniform_linear_weights():
+    """Eq. C_K on unit spacing gives (1, 10, 5)/16."""
+    assert np.allclose(oracle.linear_weights(UNIFORM), np.array([1, 10, 5]) / 16.0, atol=1e-15, rtol=0)
+
+
+def test_uniform_smoothness_closed_form():
+    """beta_k on unit spacing, from integrating the quadratic's derivatives over [x_i, x_{i+1}]."""
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        u = rng.standard_normal(5)
+        b = oracle.smoothness(UNIFORM, u)
+        a, bb, c, d, e = u
+        want = [
+            (a - 3 * bb + 2 * c) ** 2 + 13 / 12 * (a - 2 * bb + c) ** 2,
+            (d - c) ** 2 + 13 / 12 * (bb - 2 * c + d) ** 2,
+            (d - c) ** 2 + 13 / 12 * (c - 2 * d + e) ** 2,
+        ]
+        assert np.allclose(b, want, rtol=1e-13, atol=1e-14)
+
+
+def test_substencils_reproduce_quadratics():
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        x = random_points(rng)
+        q = rng.standard_normal(3)
+        u = q[0] + q[1] * x + q[2] * x * x
+        lag = oracle.substencil_coeffs(x)
+        for k in range(3):
+            assert abs(lag[k] @ u[k:k + 3] - q[0]) < 1e-12
+
+
+def test_linear_weights_reproduce_quartics_and_s5():
+    """The C_k of Eq. C_K combine the sub-stencils into the degree-4 interpolant of Eq. S5."""
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        x = random_points(rng)
+        C = oracle.linear_weights(x)
+        assert abs(C.sum() - 1) < 1e-13
+        assert np.all(C > 0)
+        lag = oracle.substencil_coeffs(x)
+        comb = np.zeros(5)
+        for k in range(3):
+            comb[k:k + 3] += C[k] * lag[k]
+        assert np.allclose(comb, oracle.s5_coeffs(x), atol=1e-12)
+        q = rng.standard_normal(5)
+        u = np.polyval(q[::-1], x)
+        assert abs(oracle.nuweno(x, u, linear=True) - q[0]) < 1e-11
+
+
+def test_s5_matches_numpy_polyfit():
+    rng = np.random.default_rng(4)
+    x = random_points(rng)
+    u = rng.standard_normal(5)
+    p = np.polyfit(x, u, 4)
+    assert abs(oracle.s5_coeffs(x) @ u - np.polyval(p, 0.0)) < 1e-11
+
+
+def test_nonlinear_weno_exact_for_quadratics():
+    rng = np.random.default_rng(5)
+    for eps in (1e-40, 1e-6, 1.0):
+        for _ in range(20):
+            x = random_points(rng)
+            q = rng.standard_normal(3)
+            u = q[0] + q[1] * x + q[2] * x * x
+            assert abs(oracle.nuweno(x, u, eps=eps) - q[0]) < 1e-12
+
+
+def test_nonlinear_weno_avoids_a_jump():
+    """Across a jump the sub-stencil containing it gets (almost) no weight."""
+    x = UNIFORM
+    u = np.array([1.0, 1.0, 1.0, 1.0, 0.0])  # jump between x_{i+1} and x_{i+2}
+    assert abs(oracle.nuweno(x, u) - 1.0) < 1e-12
+
+
+def _rate(hs, errs):
+    return np.polyfit(np.log(hs), np.log(errs), 1)[0]
+
+
+def test_e2_nonuniform_fifth_order_uniform_weno_degrades():
+    """Section 2.3.2: on points jittered by up to half the spacing NU-WENO5 stays
+    fifth order, while WENO5 that assumes uniform spacing drops to about first."""
+    rng = np.random.default_rng(6)
+    hs = [0.2, 0.1, 0.05, 0.025]
+    e_nu, e_u = [], []
+    samples = [(rng.uniform(0, 2 * math.pi), rng.uniform(-0.45, 0.45, 6)) for _ in range(200)]
+    for h in hs:
+        en = eu = 0.0
+        for x0, jit in samples:
+            pts = x0 + (np.arange(6) - 2.5) * h + jit * h
+            pts.sort()
+            mid = 0.5 * (pts[2] + pts[3])
+            x = pts[:5] - mid
+            u = np.sin(pts[:5])
+            en += abs(oracle.nuweno(x, u) - math.sin(mid))
+            eu += abs(oracle.nuweno(UNIFORM, u) - math.sin(mid))
+        e_nu.append(en / len(samples))
+        e_u.append(eu / len(samples))
+    assert _rate(hs, e_nu) > 4.5
+    assert _rate(hs, e_u) < 2.0
+
+
+def test_e3_refining_curve_fifth_order():
+    """Section 2.3.3 "refining" case on the printed curve nodes."""
+    pytest.importorskip("scipy")
+    from scipy.integrate import quad
+
+    g = json.load(open(golden("refining_curve_nodes.json")))
+    cx, cy = np.array(g["x"]), np.array(g["y"])
+    poly = np.polyfit(cx, cy, 5)
+    dpoly = np.polyder(poly)
+    speed = lambda t: math.sqrt(1.0 + np.polyval(dpoly, t) ** 2)
+    f = lambda t: math.sin(t) * math.cos(np.polyval(poly, t))
+
+    def arclen(a, b):
+        return quad(speed, a, b, epsabs=1e-14, epsrel=1e-14, limit=200)[0]
+
+    def point_at_arclength(t0, s):
+        lo, hi = t0, t0 + s  # speed >= 1, so the parameter advances by at most s
+        for _ in range(100):
+            mid = 0.5 * (lo + hi)
+            if arclen(t0, mid) < s:
+                lo = mid
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+    errs_nu, errs_lin, errs_u, hs = [], [], [], []
+    for N in (48, 96, 192):
+        t = np.linspace(cx[0], cx[-1], N)
+        s = np.concatenate([[0.0], np.cumsum([arclen(t[i], t[i + 1]) for i in range(N - 1)])])
+        en = el = eu = 0.0
+        cnt = 0
+        for i in range(2, N - 3, max(1, (N - 5) // 24)):
+            smid = 0.5 * (s[i] + s[i + 1])
+            tm = point_at_arclength(t[i], smid - s[i])
+            u = np.array([f(tt) for tt in t[i - 2:i + 3]])
+            x = s[i - 2:i + 3] - smid
+            en += abs(oracle.nuweno(x, u) - f(tm))
+            el += abs(oracle.nuweno(x, u, linear=True) - f(tm))
+            eu += abs(oracle.nuweno(UNIFORM, u) - f(tm))
+            cnt += 1
+        errs_nu.append(en / cnt)
+        errs_lin.append(el / cnt)
+        errs_u.append(eu / cnt)
+        hs.append(s[-1] / (N - 1))
+    # linear weights: the fifth-order interpolant (about 4.5 at these sizes);
+    # nonlinear weights with p = 1 lose about one order near the critical
+    # points of f along the curve (the classic smoothness-indicator effect)
+    assert _rate(hs, errs_lin) > 4.2
+    assert _rate(hs, errs_nu) > 3.7
+    assert _rate(hs, errs_u) < 2.5
+
+
+# ----------------------------------------------------------- curve coordinate
+def test_straight_stencil_arc_is_chord():
+    P = np.array([[-2.7, 0], [-1.4, 0], [-0.5, 0], [0.5, 0], [1.3, 0], [2.9, 0]])
+    xi = oracle.curve_coords(P)
+    assert np.allclose(xi, P[:, 0], atol=1e-14)
+
+
+def test_curve_coords_scale_and_rotation_invariant():
+    rng = np.random.default_rng(8)
+    P = np.cumsum(np.c_[rng.uniform(0.6, 1.4, 6), rng.uniform(-0.5, 0.5, 6)], axis=0)
+    xi = oracle.curve_coords(P)
+    th = 0.7
+    Rm = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+    xi2 = oracle.curve_coords(3.7 * P @ Rm.T + np.array([5.0, -2.0]))
+    assert np.allclose(xi, xi2, atol=1e-13)
+    # arc >= chord on each side
+    ell = np.linalg.norm(P[3] - P[2])
+    assert xi[1] <= -0.5 - np.linalg.norm(P[1] - P[2]) / ell + 1e-14
+    assert xi[4] >= 0.5 + np.linalg.norm(P[4] - P[3]) / ell - 1e-14
+
+
+def test_curve_arclength_converges_on_a_circle():
+    """Points on a circle: the curve's arc lengths approach the circle's as spacing shrinks."""
+    errs = []
+    for dth in (0.4, 0.2, 0.1):
+        th = (np.arange(6) - 2.5) * dth
+        P = np.c_[np.sin(th), 1 - np.cos(th)]
+        xi = oracle.curve_coords(P)
+        ell = np.linalg.norm(P[3] - P[2])
+        exact = (th - 0.0) / ell  # arc from the chord midpoint ~ along the circle
+        # compare the outer spacings (arc of one step = dth)
+        errs.append(abs((xi[5] - xi[4]) * ell - dth) + abs((xi[1] - xi[0]) * ell - dth))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 2e-3 * 0.1
+
+
+# ----------------------------------------------------------- stencils (2.2.2, 2.3.1)
+def test_stencil_walk_reproduces_paper_figure():
+    g = json.load(open(golden("weno1d_tri_figure.json")))
+    names = list(g["nodes"].keys())
+    idx = {n: i for i, n in enumerate(names)}
+    xy = np.array([g["nodes"][n] for n in names])
+    E = {tuple(sorted((idx[a], idx[b]))) for a, b in g["edges"]}
+    adj = {i: set() for i in range(len(names))}
+    for a, b in E:
+        adj[a].add(b)
+        adj[b].add(a)
+    tris = []
+    for a, b in E:
+        for c in adj[a] & adj[b]:
+            if c > b:
+                t = [a, b, c]
+                p = xy[t]
+                area = (p[1, 0] - p[0, 0]) * (p[2, 1] - p[0, 1]) - (p[1, 1] - p[0, 1]) * (p[2, 0] - p[0, 0])
+                tris.append(t if area > 0 else [a, c, b])
+    om = oracle.OracleMesh(xy, np.array(tris), 0.0, 0.0, degree=1, levels=1)
+    e = om.edges()
+    a, b = sorted((idx[g["red_edge"][0]], idx[g["red_edge"][1]]))
+    k = int(np.nonzero((e[:, 0] == a) & (e[:, 1] == b))[0][0])
+    s = om.walk(k)
+    # v0 = I (id 0), v1 = J6: L3 L2 | L1 R1 | R2 R3
+    assert [names[i] for i in s] == list(reversed(g["stencil_I_side"])) + ["I", "J6"] + g["stencil_J6_side"]
+
+
+def test_divergence_stencil_counts_regular_lattice():
+    """Section 2.2.2: one-level = N vertices and 2N edges (N = 6); two-level = 18
+    vertices and 42 edges, i.e. 78 conditions."""
+    m = inputs.torus_lattice(12, L=1.0, jitter=0.0, random_diagonals=False)
+    for levels, nvt, net in ((1, 6, 12), (2, 18, 42)):
+        om = oracle.OracleMesh(m.xy, m.tri, 1.0, 1.0, degree=2, levels=levels)
+        voff, vid, _, _, eoff, eid, _ = om.div_stencils()
+        assert np.all(np.diff(voff) == nvt)
+        assert np.all(np.diff(eoff) == net)
+        if levels == 2:
+            assert np.all(2 * np.diff(voff) + np.diff(eoff) == 78)
+
+
+def test_edges_and_stencil_ids_are_consistent():
+    m, _ = inputs.vortex_case(12, seed=3)
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly)
+    e = om.edges()
+    assert om.ne == 3 * m.nv  # triangulated torus: E = 3V
+    assert np.all(e[:, 0] < e[:, 1])
+    assert np.all(np.diff(e[:, 0].astype(np.int64) * m.nv + e[:, 1]) > 0)
+    s, xi = om.stencils()
+    assert np.all(s[:, 2] == e[:, 0]) and np.all(s[:, 3] == e[:, 1])
+    assert np.all(np.diff(xi, axis=1) > 0)
+    assert np.all(xi[:, 2] == -0.5) and np.all(xi[:, 3] == 0.5)
+    for row in s:
+        assert len(set(row.tolist())) == 6
+
+
+# ----------------------------------------------------------- least squares (2.2.1)
+def _geometry(m, om):
+    e = om.edges()
+    n = om.normals()
+    return e, n
+
+
+def _min_image(d, L):
+    return d - L * np.rint(d / L) if L > 0 else d
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 5])
+def test_lsq_divergence_exact_for_polynomials(degree):
+    """For fluxes that are polynomials of degree <= p around O, with exact edge
+    projections, a1 + b2 is the exact divergence at O."""
+    m = inputs.torus_lattice(12, L=1.0, jitter=0.2, seed=21)
+    om = oracle.OracleMesh(m.xy, m.tri, 1.0, 1.0, degree=degree, levels=2)
+    om.build_weights()
+    voff, vid, wf, wg, eoff, eid, we = om.div_stencils()
+    e, nrm = _geometry(m, om)
+    rng = np.random.default_rng(degree)
+    for o in range(0, m.nv, 7):
+        cf = rng.standard_normal((degree + 1, degree + 1))
+        cg = rng.standard_normal((degree + 1, degree + 1))
+
+        def P(c, x, y):
+            return sum(c[i, j] * x ** i * y ** j for i in range(degree + 1) for j in range(degree + 1 - i))
+
+        dv = _min_image(m.xy[vid[voff[o]:voff[o + 1]]] - m.xy[o], 1.0)
+        ee = eid[eoff[o]:eoff[o + 1]]
+        d0 = _min_image(m.xy[e[ee, 0]] - m.xy[o], 1.0)
+        de = _min_image(m.xy[e[ee, 1]] - m.xy[e[ee, 0]], 1.0)
+        mid = d0 + 0.5 * de
+        f0, g0 = cf[0, 0], cg[0, 0]
+        fj, gj = P(cf, dv[:, 0], dv[:, 1]), P(cg, dv[:, 0], dv[:, 1])
+        r = nrm[ee, 0] * P(cf, mid[:, 0], mid[:, 1]) + nrm[ee, 1] * P(cg, mid[:, 0], mid[:, 1])
+        div = (wf[voff[o]:voff[o + 1]] @ (fj - f0) + wg[voff[o]:voff[o + 1]] @ (gj - g0)
+               + we[eoff[o]:eoff[o + 1]] @ (r - nrm[ee, 0] * f0 - nrm[ee, 1] * g0))
+        exact = cf[1, 0] + cg[0, 1]
+        assert abs(div - exact) < 1e-9 * (1 + abs(exact))
+
+
+@pytest.mark.parametrize("degree,want", [(2, 1.8), (5, 4.5)])
+def test_e1_lsq_divergence_rate(degree, want):
+    """Section 2.2.3: divergence of (sin cos, cos sin) on refined periodic
+    unstructured meshes converges at about the polynomial degree."""
+    errs, hs = [], []
+    for n in (16, 32, 64):
+        l = 1.0
+        m = inputs.torus_lattice(n, L=l, jitter=0.2, seed=11)
+        om = oracle.OracleMesh(m.xy, m.tri, l, l, degree=degree)
+        om.build_weights()
+        voff, vid, wf, wg, eoff, eid, we = om.div_stencils()
+        e, nrm = _geometry(m, om)
+        F = lambda x, y: np.sin(2 * np.pi * x / l) * np.cos(2 * np.pi * y / l)
+        Gf = lambda x, y: np.cos(2 * np.pi * x / l) * np.sin(2 * np.pi * y / l)
+        xy = m.xy
+        f, g = F(xy[:, 0], xy[:, 1]), Gf(xy[:, 0], xy[:, 1])
+        mid = xy[e[:, 0]] + 0.5 * _min_image(xy[e[:, 1]] - xy[e[:, 0]], l)
+        r = nrm[:, 0] * F(mid[:, 0], mid[:, 1]) + nrm[:, 1] * Gf(mid[:, 0], mid[:, 1])
+        rows = np.repeat(np.arange(m.nv), np.diff(voff))
+        rowe = np.repeat(np.arange(m.nv), np.diff(eoff))
+        div = np.bincount(rows, wf * (f[vid] - f[rows]) + wg * (g[vid] - g[rows]), minlength=m.nv)
+        div += np.bincount(rowe, we * (r[eid] - nrm[eid, 0] * f[rowe] - nrm[eid, 1] * g[rowe]), minlength=m.nv)
+        exact = 4 * np.pi / l * np.cos(2 * np.pi * xy[:, 0] / l) * np.cos(2 * np.pi * xy[:, 1] / l)
+        errs.append(np.mean(np.abs(div - exact)))
+        hs.append(l / n)
+    assert _rate(hs, errs) > want
+
+
+# ----------------------------------------------------------- Euler, Riemann
+def _flux_n(w, n):
+    rho, mu, mv, E = w
+    u, v = mu / rho, mv / rho
+    p = (G - 1) * (E - 0.5 * rho * (u * u + v * v))
+    qn = u * n[0] + v * n[1]
+    return np.array([rho * qn, mu * qn + p * n[0], mv * qn + p * n[1], (E + p) * qn])
+
+
+def _state(rho, u, v, p):
+    return inputs.primitive_to_conservative(np.array([rho]), np.array([u]), np.array([v]), np.array([p]))[0]
+
+
+def test_eigenvectors_diagonalise_flux_jacobian():
+    rng = np.random.default_rng(9)
+    for _ in range(10):
+        w = _state(rng.uniform(0.5, 2), rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.5, 2))
+        th = rng.uniform(0, 2 * np.pi)
+        n = np.array([np.cos(th), np.sin(th)])
+        R, Linv, lam = oracle.eigvec(w, w, n)
+        A = np.zeros((4, 4))
+        for j in range(4):
+            d = np.zeros(4)
+            d[j] = 1e-6
+            A[:, j] = (_flux_n(w + d, n) - _flux_n(w - d, n)) / 2e-6
+        assert np.allclose(A @ R, R * lam, atol=1e-7)
+        assert np.allclose(Linv @ R, np.eye(4), atol=1e-12)
+
+
+def test_roe_flux_consistency_symmetry_and_upwinding():
+    rng = np.random.default_rng(10)
+    n = np.array([0.6, 0.8])
+    for _ in range(10):
+        wl = _state(rng.uniform(0.5, 2), rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.5, 2))
+        wr = _state(rng.uniform(0.5, 2), rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(0.5, 2))
+        assert np.allclose(oracle.roe_flux(wl, wl, n), _flux_n(wl, n), atol=1e-13)
+        assert np.allclose(oracle.roe_flux(wl, wr, n), -oracle.roe_flux(wr, wl, -n), atol=1e-13)
+    # supersonic along +n: the flux is the left state's
+    wl = _state(1.0, 6 * 0.6, 6 * 0.8, 1.0)
+    wr = _state(0.9, 5.5 * 0.6, 5.5 * 0.8, 0.95)
+    assert np.allclose(oracle.roe_flux(wl, wr, n), _flux_n(wl, n), atol=1e-12)
+    assert np.allclose(oracle.roe_flux(wr, wl, -n), -_flux_n(wl, n), atol=1e-12)
+    # Roe property away from the entropy-fix band (all |lambda| >= 0.1 c):
+    # F(R) - F(L) = A_roe (R - L)
+    wl = _state(1.0, 0.3, 0.1, 1.0)
+    wr = _state(1.1, 0.35, 0.05, 1.2)
+    R, Linv, lam = oracle.eigvec(wl, wr, n)
+    c = (lam[3] - lam[0]) / 2
+    assert np.all(np.abs(lam) > 0.1 * c)
+    Aroe = R @ np.diag(lam) @ Linv
+    assert np.allclose(_flux_n(wr, n) - _flux_n(wl, n), Aroe @ (wr - wl), atol=1e-13)
+
+
+# ----------------------------------------------------------- residual, RK3
+def test_free_stream_preserved():
+    m, _ = inputs.vortex_case(20, seed=12)
+    one = np.ones(m.nv)
+    w = inputs.primitive_to_conservative(1.3 * one, 0.7 * one, -0.4 * one, 2.1 * one)
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly)
+    assert np.abs(om.residual(w)).max() < 1e-12
+
+
+def test_ssprk3_stability_polynomial():
+    for z in (-0.3, -1.0, -2.4, 0.5):
+        y = np.array([1.0])
+        dt = 1.0
+        lam = z
+        s1 = oracle.stage_combine(1, y, y, lam * y, dt)
+        s2 = oracle.stage_combine(2, y, s1, lam * s1, dt)
+        s3 = oracle.stage_combine(3, y, s2, lam * s2, dt)
+        assert abs(s3[0] - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-15
+
+
+@pytest.mark.parametrize("degree,want", [(2, 1.8), (3, 3.4)])
+def test_vortex_residual_rate_regular_meshes(degree, want):
+    """Section 3.1: on regular diagonalised meshes the residual converges to the
+    exact dw/dt of the translating vortex at the design rate (limited here by
+    the least-squares degree)."""
+    errs, hs = [], []
+    for n in (40, 80, 160):
+        m = inputs.torus_lattice(n, L=10.0, jitter=0.0, random_diagonals=False)
+        w0 = inputs.isentropic_vortex(m.xy)
+        d = 1e-5
+        ex = (inputs.isentropic_vortex(m.xy, t=d) - inputs.isentropic_vortex(m.xy, t=-d)) / (2 * d)
+        om = oracle.OracleMesh(m.xy, m.tri, 10.0, 10.0, degree=degree)
+        errs.append(np.mean(np.abs(om.residual(w0)[:, 0] - ex[:, 0])))
+        hs.append(10.0 / n)
+    assert _rate(hs, errs) > want
+
+
+def test_vortex_rk3_converges_in_time_and_space():
+    """A short SSP-RK3 run of the vortex tracks the exact translation; error
+    shrinks under refinement on regular meshes."""
+    errs = []
+    for n in (40, 80):
+        m = inputs.torus_lattice(n, L=10.0, jitter=0.0, random_diagonals=False)
+        w = inputs.isentropic_vortex(m.xy)
+        om = oracle.OracleMesh(m.xy, m.tri, 10.0, 10.0, degree=3)
+        dt = om.max_dt(w, 0.5)
+        T = 0.2
+        steps = int(math.ceil(T / dt))
+        dt = T / steps
+        for _ in range(steps):
+            w = om.rk3_step(w, dt)
+        ex = inputs.isentropic_vortex(m.xy, t=T)
+        errs.append(np.mean(np.abs(w[:, 0] - ex[:, 0])))
+    assert errs[1] < errs[0] / 4

@@ -1,0 +1,359 @@
+"""Benchmark of the residual + SSP-RK3 stage on one GB300 (or N replicas).
+
+One step = one SSP-RK3 time step = three (edge flux, divergence + stage)
+passes over the 250,000-vertex periodic isentropic-vortex mesh (jittered
+500x500 torus lattice split on random diagonals, two-level stencils,
+degree-2 least squares, NU-WENO5).  The headline is the FP64 path; the FP32
+residual path (FP64 state accumulation) is measured beside it with its
+error against FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica on its own GPU (the path has no exchange step); the
+time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "residual Mvertex/s FP64 vs FP32 at stated error, % HBM roofline; adjoint/fwd time"
+N_LATTICE = 500  # 250,000 vertices
+CFL = 0.5
+# FP64 operations per edge of the edge-flux kernel and per vertex of the
+# divergence + stage kernel (counted from the kernel source; FMA = 2).
+FLOP_EDGE64 = 827
+FLOP_DIV64_PER_VENTRY = 16
+FLOP_DIV64_PER_EENTRY = 8
+FLOP_DIV64_FIXED = 56
+FP64_PEAK_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), NVIDIA datasheet figure
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload():
+    from paper_2102_12933_gb300 import inputs
+
+    mesh, w0 = inputs.vortex_case(N_LATTICE, seed=1002)
+    return mesh, w0
+
+
+def _rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def time_oracle(steps: int, n_sample: int = 125):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: SSP-RK3
+    steps on a smaller mesh of the same family (one host core)."""
+    import oracle
+    from paper_2102_12933_gb300 import inputs
+
+    mesh, w = inputs.vortex_case(n_sample, seed=1002)
+    om = oracle.OracleMesh(mesh.xy, mesh.tri, mesh.Lx, mesh.Ly)
+    om.build_weights()
+    dt = om.max_dt(w, CFL)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        w = om.rk3_step(w, dt)
+    el = time.perf_counter() - t0
+    value = mesh.nv * 3 * steps / el / 1e6
+    sample = (f"{steps} SSP-RK3 step(s) of the single-threaded FP64 oracle on a {mesh.nv}-vertex mesh of the "
+              f"same family (jittered random-diagonal torus, vortex, two-level degree-2 stencils)")
+    return value, el, sample
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        time_oracle(1)
+    value, el, sample = time_oracle(args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mvertex/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * el / max(args.steps, 1), 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "periodic isentropic vortex, jittered random-diagonal torus lattice (oracle sample)",
+                   "sample_nv": 15625},
+        "cpu_baseline": {"value": round(value, 4), "unit": "Mvertex/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "Mvertex/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2102_12933_gb300 import fdu
+
+    ws_, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws_ > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    mesh, w0 = _workload()
+    t_build = time.perf_counter()
+    M = fdu.Mesh(mesh.xy, mesh.tri, mesh.Lx, mesh.Ly, device=local)
+    t_build = time.perf_counter() - t_build
+    info = M.info()
+    nv, ne = M.nv, M.ne
+    M.set_state(w0)
+    dt = M.max_dt(CFL)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed_steps(prec, k):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(k):
+            M.rk_step(dt, prec, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # ---------------- FP64 (headline)
+    for _ in range(args.warmup):
+        M.rk_step(dt, 64, stream=stream)
+    M.profile(True)
+    M.profile_read("edge", 64)
+    M.profile_read("div", 64)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms64 = timed_steps(64, args.steps)
+    clocks = sampler.stop()
+    edge_ms, edge_n = M.profile_read("edge", 64)
+    div_ms, div_n = M.profile_read("div", 64)
+    M.profile(False)
+    w64 = M.get_state()
+
+    # ---------------- FP32 residual path (FP64 accumulation), same steps from w0
+    M.set_state(w0)
+    for _ in range(args.warmup):
+        M.rk_step(dt, 32, stream=stream)
+    M.set_state(w0)
+    M.profile(True)
+    M.profile_read("edge", 32)
+    M.profile_read("div", 32)
+    ms32 = timed_steps(32, args.warmup + args.steps)
+    e32_ms, e32_n = M.profile_read("edge", 32)
+    d32_ms, d32_n = M.profile_read("div", 32)
+    M.profile(False)
+    w32 = M.get_state()
+    # reference FP64 state for the same number of steps
+    M.set_state(w0)
+    M.rk_steps(dt, args.warmup + args.steps, 64, stream=stream)
+    w64b = M.get_state()
+    err32 = {"rho": _rel_l2(w32[:, 0], w64b[:, 0]), "rhoE": _rel_l2(w32[:, 3], w64b[:, 3]),
+             "steps": args.warmup + args.steps}
+
+    # ---------------- end to end through the C-ABI with host buffers
+    host_in = np.ascontiguousarray(w0)
+    host_out = np.zeros_like(host_in)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        M.set_state(host_in)  # H2D of the step's input (host permutation to internal order)
+        M.rk_step(dt, 64)
+        M.get_state(out=host_out)  # D2H of the step's result (synchronises)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # ---------------- figures
+    stages = 3
+    value = ws_ * nv * stages * args.steps / (ms64 / 1e3) / 1e6
+    value32 = ws_ * nv * stages * (args.warmup + args.steps) / (ms32 / 1e3) / 1e6
+    e2e_value = ws_ * nv * stages * e2e_steps / e2e_s / 1e6
+    edge_avg_ms = edge_ms / max(edge_n, 1)
+    div_avg_ms = div_ms / max(div_n, 1)
+    achieved_tf = FLOP_EDGE64 * ne / (edge_avg_ms / 1e3) / 1e12
+    peaks = _peaks()
+    vnnz, ennz = info["div_vert_nnz"], info["div_edge_nnz"]
+    div_flops = FLOP_DIV64_PER_VENTRY * vnnz + FLOP_DIV64_PER_EENTRY * ennz + FLOP_DIV64_FIXED * nv
+    # FP32 kernels are HBM-bound: algorithmic bytes per launch
+    edge32_bytes = ne * (24 + 24 + 16) + nv * 16
+    div32_bytes = (vnnz * 12 + ennz * 8 + nv * 8) + nv * (32 + 32 + 32 + 32 + 16) + ne * 16 + nv * 32
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "Mvertex/s",
+        "n_gpus": ws_,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms64 / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": "periodic isentropic vortex (beta=5, centre (5,5)) on a 500x500 jittered random-diagonal "
+                        "torus lattice of [0,10]^2; two-level divergence stencils, degree-2 least squares, NU-WENO5, "
+                        "SSP-RK3, CFL 0.5; one step = 3 stages",
+            "nv": nv, "ne": ne, "stages_per_step": stages,
+            "l2": f"inputs larger than L2 (FP64 tables {info['table_bytes_f64'] / 1e9:.2f} GB streamed per stage)",
+            "parallelism": "replicas" if ws_ > 1 else "single GPU",
+            "host_build_s": round(t_build, 2),
+        },
+        "roofline": {
+            "kernel": "edge_flux_f64",
+            "bound": "alu",
+            "achieved": round(achieved_tf, 4),
+            "peak": FP64_PEAK_NOMINAL_TFLOPS,
+            "unit": "TFLOP/s",
+            "frac": round(achieved_tf / FP64_PEAK_NOMINAL_TFLOPS, 4),
+            "traffic": None,
+            "peak_source": "nominal GB300 FP64 rate (no FP64 figure in MEASURED_PEAKS.json)",
+            "flop_per_edge": FLOP_EDGE64,
+            "avg_launch_ms": round(edge_avg_ms, 4),
+            "share_of_step": round(edge_ms / ms64, 4) if ms64 > 0 else None,
+            "div_kernel": {"avg_launch_ms": round(div_avg_ms, 4),
+                           "achieved_tflops": round(div_flops / (div_avg_ms / 1e3) / 1e12, 4)},
+        },
+        "fp32": {
+            "value": round(value32, 3), "unit": "Mvertex/s", "speedup_vs_f64": round(value32 / value, 3),
+            "error_vs_f64": err32,
+            "edge_kernel": {"avg_launch_ms": round(e32_ms / max(e32_n, 1), 4),
+                            "achieved_gbs": round(edge32_bytes / (e32_ms / max(e32_n, 1) / 1e3) / 1e9, 1),
+                            "frac_hbm": round(edge32_bytes / (e32_ms / max(e32_n, 1) / 1e3) / 1e9 / hbm, 4)},
+            "div_kernel": {"avg_launch_ms": round(d32_ms / max(d32_n, 1), 4),
+                           "achieved_gbs": round(div32_bytes / (d32_ms / max(d32_n, 1) / 1e3) / 1e9, 1),
+                           "frac_hbm": round(div32_bytes / (d32_ms / max(d32_n, 1) / 1e3) / 1e9 / hbm, 4)},
+        },
+        "e2e": {"value": round(e2e_value, 3), "unit": "Mvertex/s", "h2d_bytes_per_step": nv * 32,
+                "d2h_bytes_per_step": nv * 32, "steps": e2e_steps},
+        "gpu_launches": 6 * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        v, el, sample = time_oracle(4)
+        line["cpu_baseline"] = {"value": round(v, 4), "unit": "Mvertex/s", "cores": 1, "kind": "oracle",
+                                "sample": sample, "seconds": round(el, 2)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    M.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

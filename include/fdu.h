@@ -1,0 +1,182 @@
+/*
+ * fdu.h -- C-ABI of the GB300 (sm_103a) residual and SSP-RK3 stage of the
+ * unstructured-mesh finite difference method for the 2D Euler equations
+ * (Zhen, Qu & Cai, arXiv 2102.12933).
+ *
+ * The calls follow the paper's statement of the problem: build the mesh
+ * and its stencils from vertices and triangles, set the state, evaluate
+ * the spatial residual dw/dt = -(df/dx + dg/dy) (Section 2.1, Eq. 1;
+ * Section 2.2.1), and advance one third-order TVD Runge-Kutta step
+ * (Section 3).
+ *
+ * Conventions common to every call
+ *   - Every call returns an fdu_status: FDU_OK (0) or a negative error
+ *     code.  No call aborts or exits.  fdu_last_error() returns a message
+ *     for the calling thread's last error.
+ *   - The library owns every object it creates; inputs are copied.
+ *     Outputs go to caller-owned buffers of the stated size.
+ *   - Vertex and edge ids in and out are ORIGINAL ids: vertex ids index
+ *     the caller's xy array; edge ids index the edge list of
+ *     fdu_get_edges (unique triangle sides (v0, v1), v0 < v1, sorted by
+ *     (v0, v1)).  Any internal renumbering stays internal.
+ *   - States are conservative records w[nv][4] = (rho, rho u, rho v,
+ *     rho E), row-major FP64, with E = e + (u^2 + v^2)/2 and
+ *     p = (gamma - 1) rho e (Section 2.1).
+ *   - A pointer flagged `on_device = 1` is a raw CUDA device pointer on
+ *     the mesh's device (for example torch.Tensor.data_ptr()); with
+ *     `on_device = 0` it is host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream are asynchronous on it unless
+ *     they return a host value or write host memory.
+ *   - Not thread-safe per mesh: serialise calls on one fdu_mesh.
+ */
+#ifndef FDU_H
+#define FDU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fdu_status;
+#define FDU_OK 0
+#define FDU_ERR_ARG (-1)            /* bad argument (null pointer, size, option) */
+#define FDU_ERR_MESH (-2)           /* bad mesh: bad ids, degenerate or inverted triangle */
+#define FDU_ERR_STENCIL (-3)        /* a 1D stencil walk found no forward neighbour */
+#define FDU_ERR_RANK_DEFICIENT (-4) /* least-squares system with too few conditions or rank loss */
+#define FDU_ERR_CUDA (-5)           /* a CUDA runtime call failed (message has the CUDA error) */
+#define FDU_ERR_TIMEOUT (-6)        /* a bounded device wait ran out */
+#define FDU_ERR_NONPHYSICAL (-7)    /* NaN, rho <= 0 or p <= 0 in a state */
+#define FDU_ERR_NODEVICE (-8)       /* the call needs device tables but the mesh is host-only */
+
+#define FDU_BC_PERIODIC 0
+#define FDU_BC_TRANSMISSIVE 1
+
+/* Options of fdu_mesh_create.  fdu_default_opts() fills the paper's
+ * settings: NU-WENO5 with eps = 1e-40 and p = 1 (Appendix), two-level
+ * divergence stencils (Section 3), gamma = 1.4 (Section 2.1). */
+typedef struct fdu_mesh_opts {
+    double Lx, Ly;      /* periodic lengths in x and y; 0 = not periodic */
+    double weno_eps;    /* epsilon of the nonlinear weights (FP64 path) */
+    double weno_eps32;  /* epsilon of the FP32 path (1e-40 is subnormal in FP32) */
+    double gamma;       /* ratio of specific heats */
+    int lsq_degree;     /* degree p of the least-squares polynomials, 1..6 */
+    int lsq_levels;     /* divergence stencil: 1 = one-level, 2 = two-level */
+    int bc;             /* FDU_BC_PERIODIC or FDU_BC_TRANSMISSIVE */
+    int renumber;       /* 1 = locality (Hilbert) renumbering of vertices and edges */
+    int device;         /* CUDA device ordinal; -1 = host tables only (no GPU use) */
+    int host_threads;   /* threads for host preprocessing; 0 = all cores */
+    const int32_t *ghost_donor; /* transmissive: [nv] donor vertex of each ghost, -1 for real vertices; NULL = none */
+} fdu_mesh_opts;
+
+typedef struct fdu_mesh fdu_mesh;
+
+typedef struct fdu_mesh_info {
+    int64_t nv, ne, nt;      /* vertices, edges, triangles */
+    int64_t n_real;          /* vertices that carry a residual (non-ghost) */
+    int64_t div_vert_nnz;    /* vertex entries over all divergence stencils */
+    int64_t div_edge_nnz;    /* edge entries over all divergence stencils */
+    int32_t J_min, J_max, K_min, K_max; /* stencil sizes (vertex, edge entries) */
+    int64_t device_bytes;    /* device memory held by the mesh */
+    int64_t table_bytes_f64; /* bytes of the FP64 residual's read-only tables */
+    int64_t table_bytes_f32; /* bytes of the FP32 residual's read-only tables */
+    int32_t sell_width;      /* SELL slice width of the divergence tables */
+    int32_t pad0;
+} fdu_mesh_info;
+
+/* Library version string and thread-local last error message. */
+const char *fdu_version(void);
+const char *fdu_last_error(void);
+
+/* Fill *opts with the defaults listed above (periodic lengths 0, device 0). */
+fdu_status fdu_default_opts(fdu_mesh_opts *opts);
+
+/* Build the mesh (Section 2.2.2, Section 2.3.1, Appendix, Section 2.2.1):
+ * unique edges; per edge the six-vertex 1D curvilinear stencil and its
+ * normalised arc-length coordinates; the non-uniform WENO5 coefficient
+ * tables; per vertex the divergence stencil and its least-squares weights
+ * (the a1 and b2 rows of the pseudo-inverse); all in FP64 on the host,
+ * then uploaded to the device unless opts->device = -1.
+ *   xy[nv][2] FP64 vertex coordinates; tri[nt][3] int32 vertex ids.
+ * Errors: FDU_ERR_ARG, FDU_ERR_MESH, FDU_ERR_STENCIL,
+ * FDU_ERR_RANK_DEFICIENT, FDU_ERR_CUDA.  On error *out is NULL. */
+fdu_status fdu_mesh_create(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts *opts,
+                           fdu_mesh **out);
+
+/* Free the mesh and its device memory (synchronises the device first). */
+fdu_status fdu_mesh_destroy(fdu_mesh *mesh);
+
+/* Sizes and stencil statistics. */
+fdu_status fdu_mesh_info_get(const fdu_mesh *mesh, fdu_mesh_info *out);
+
+/* Edge list e[ne][2] (original ids, v0 < v1, sorted). */
+fdu_status fdu_get_edges(const fdu_mesh *mesh, int32_t *e);
+
+/* Per edge (original edge order): the 1D stencil s[ne][6] = (L3, L2, L1 =
+ * v0, R1 = v1, R2, R3) in original vertex ids and its normalised
+ * coordinates xi[ne][6] (arc length from the edge midpoint divided by the
+ * edge length, so xi[.][2] = -1/2 and xi[.][3] = 1/2).  Either pointer
+ * may be NULL. */
+fdu_status fdu_get_edge_stencils(const fdu_mesh *mesh, int32_t *s, double *xi);
+
+/* Sizes of the divergence-stencil CSR. */
+fdu_status fdu_get_div_sizes(const fdu_mesh *mesh, int64_t *vert_nnz, int64_t *edge_nnz);
+
+/* Divergence stencils as CSR over original vertex ids, entries sorted by
+ * original id: vertex part voff[nv+1], vid[vert_nnz], weights wf, wg
+ * (multiplying f_j - f_O and g_j - g_O); edge part eoff[nv+1],
+ * eid[edge_nnz], weight we (multiplying r_k - n_k . (f_O, g_O)).
+ * Ghost vertices have empty rows.  Weight pointers may be NULL. */
+fdu_status fdu_get_div_stencils(const fdu_mesh *mesh, int64_t *voff, int32_t *vid, double *wf, double *wg,
+                                int64_t *eoff, int32_t *eid, double *we);
+
+/* Copy a state w[nv][4] into / out of the mesh (original vertex order). */
+fdu_status fdu_set_state(fdu_mesh *mesh, const double *w, int on_device, void *stream);
+fdu_status fdu_get_state(const fdu_mesh *mesh, double *w, int on_device, void *stream);
+
+/* Spatial residual dwdt[nv][4] = -(a1 + b2) per component of the current
+ * state (Section 2.2.1), with edge fluxes from characteristic NU-WENO5
+ * and a Roe flux (Section 2.3.1, Appendix).  precision = 64 computes in
+ * FP64; precision = 32 reads FP32 copies of the state and tables and
+ * computes in FP32.  Ghost vertices get 0.  With on_device = 0 the call
+ * synchronises `stream` before returning. */
+fdu_status fdu_residual(fdu_mesh *mesh, int precision, double *dwdt, int on_device, void *stream);
+
+/* dt = cfl * min over real vertices of h_v / (|u_v| + c_v), h_v the
+ * shortest edge at v, of the current state.  Synchronises `stream`. */
+fdu_status fdu_max_dt(fdu_mesh *mesh, double cfl, double *dt, void *stream);
+
+/* One SSP-RK3 step of the current state in place (Shu & Osher):
+ * w1 = w + dt L(w); w2 = 3/4 w + 1/4 (w1 + dt L(w1));
+ * w <- 1/3 w + 2/3 (w2 + dt L(w2)).  The state and the stage combination
+ * stay FP64 for both precisions; `precision` selects the residual.
+ * dt > 0 is required. */
+fdu_status fdu_rk_step(fdu_mesh *mesh, double dt, int precision, void *stream);
+
+/* n_steps SSP-RK3 steps, captured once into a CUDA graph per (precision,
+ * dt) and replayed. */
+fdu_status fdu_rk_steps(fdu_mesh *mesh, double dt, int precision, int n_steps, void *stream);
+
+/* Edges whose interpolated density or pressure was not positive and that
+ * fell back to the first-order end states, counted since the last reset
+ * (reset = 1 zeroes the counter after reading).  Synchronises `stream`. */
+fdu_status fdu_fallback_count(fdu_mesh *mesh, int64_t *count, int reset, void *stream);
+
+/* Kernel timing for measurement.  With enable = 1, every later
+ * fdu_residual / fdu_rk_step records a CUDA event pair around each
+ * edge-flux and divergence launch on the call's stream (CUDA-graph replays
+ * of fdu_rk_steps are not instrumented).  fdu_profile_read synchronises the
+ * recorded events and returns the summed device time (ms) and the launch
+ * count of one kernel kind: FDU_KERNEL_EDGE or FDU_KERNEL_DIV at
+ * precision 64 or 32; reset = 1 clears that kind's record. */
+#define FDU_KERNEL_EDGE 0
+#define FDU_KERNEL_DIV 1
+fdu_status fdu_profile(fdu_mesh *mesh, int enable);
+fdu_status fdu_profile_read(fdu_mesh *mesh, int kernel, int precision, double *total_ms, int64_t *launches,
+                            int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDU_H */

@@ -1,0 +1,664 @@
+// C-ABI of libfdu (declared in include/fdu.h): mesh object, device table
+// packing, stage sequencing and CUDA-graph replay of SSP-RK3 steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fdu.h"
+#include "fdu_internal.h"
+#include "fdu_kernels.cuh"
+
+using namespace fdu;
+
+namespace {
+
+thread_local std::string g_err;
+
+fdu_status set_err(fdu_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CK_LAUNCH()                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = cudaGetLastError();                                                     \
+        if (e_ != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct fdu_mesh {
+    HostTables T;
+    fdu_mesh_opts opts{};
+    int device = -1;
+    int64_t nv = 0, n_real = 0, n_ghost = 0, ne_act = 0, nslice = 0;
+    int64_t vert_nnz_sell = 0, edge_nnz_sell = 0;
+    int64_t device_bytes = 0, table_bytes_f64 = 0, table_bytes_f32 = 0;
+    std::vector<void *> allocs;
+    // tables
+    int32_t *sten = nullptr;          // [6][ne_act]
+    double *coef64 = nullptr;         // [44][ne_act]
+    float *coef32 = nullptr;          // [6][ne_act]
+    int64_t *slice_voff = nullptr, *slice_eoff = nullptr;
+    int32_t *svid = nullptr, *seid = nullptr;
+    double *swf64 = nullptr, *swg64 = nullptr, *swe64 = nullptr, *cfg64 = nullptr;
+    float *swf32 = nullptr, *swg32 = nullptr, *swe32 = nullptr, *cfg32 = nullptr;
+    int32_t *new2old = nullptr;       // [nv] internal -> original vertex
+    int32_t *donor = nullptr;         // [n_ghost] internal donor of each ghost
+    double *hmin = nullptr;           // [n_real]
+    // state
+    double *wn = nullptr, *ws = nullptr, *scratch = nullptr;  // [nv][4]
+    double *F64[3] = {nullptr, nullptr, nullptr};           // [nv][8]; F64[0] = fluxes of wn
+    float4 *F32[3] = {nullptr, nullptr, nullptr};           // [nv][2]
+    float4 *w32 = nullptr;                                  // [nv]
+    double *r64 = nullptr;                                  // [ne_act][4]
+    float4 *r32 = nullptr;                                  // [ne_act]
+    unsigned long long *counters = nullptr;                 // [0] fallbacks, [1] dt slot
+    bool f64_valid = false, f32_valid = false;              // F64[0] / (w32, F32[0]) describe wn
+    cudaStream_t own_stream = nullptr;
+    std::map<std::pair<int, double>, cudaGraphExec_t> graphs;
+    // kernel timing: event pairs per kind (0 edge64, 1 div64, 2 edge32, 3 div32)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev[4];
+    size_t prof_used[4] = {0, 0, 0, 0};
+
+    template <class T>
+    fdu_status alloc(T *&p, size_t count) {
+        p = nullptr;
+        if (count == 0) count = 1;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        allocs.push_back(q);
+        device_bytes += (int64_t)(count * sizeof(T));
+        p = static_cast<T *>(q);
+        return FDU_OK;
+    }
+    template <class T>
+    fdu_status upload(T *&p, const std::vector<T> &h) {
+        fdu_status st = alloc(p, h.size());
+        if (st) return st;
+        if (!h.empty()) CK(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return FDU_OK;
+    }
+    cudaStream_t stream(void *s) const { return s ? static_cast<cudaStream_t>(s) : own_stream; }
+    void release() {
+        if (device >= 0) {
+            cudaSetDevice(device);
+            cudaDeviceSynchronize();
+            for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+            graphs.clear();
+            for (auto &v : prof_ev)
+                for (cudaEvent_t e : v) cudaEventDestroy(e);
+            for (void *p : allocs) cudaFree(p);
+            allocs.clear();
+            if (own_stream) cudaStreamDestroy(own_stream);
+            own_stream = nullptr;
+        }
+    }
+};
+
+namespace {
+
+fdu_status need_device(const fdu_mesh *m) {
+    if (!m) return set_err(FDU_ERR_ARG, "null mesh");
+    if (m->device < 0) return set_err(FDU_ERR_NODEVICE, "mesh was built with device = -1 (host tables only)");
+    cudaError_t e = cudaSetDevice(m->device);
+    if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    return FDU_OK;
+}
+
+// Pack host tables into device layouts.
+fdu_status upload_tables(fdu_mesh *m) {
+    const HostTables &T = m->T;
+    const int64_t ne = m->ne_act, nv = m->nv, nr = m->n_real;
+    fdu_status st;
+    // 1D stencils and coefficient blocks, SoA over internal active edges
+    std::vector<int32_t> sten(6 * ne);
+    std::vector<double> coef((size_t)kEdgeCoef * ne);
+    std::vector<float> coef32(6 * ne);
+    for (int64_t e = 0; e < ne; ++e) {
+        const int64_t o = T.e_new2old[e];
+        for (int i = 0; i < 6; ++i) sten[i * ne + e] = T.v_old2new[T.sten[6 * o + i]];
+        for (int c = 0; c < kEdgeCoef; ++c) coef[(size_t)c * ne + e] = T.coef[(size_t)kEdgeCoef * o + c];
+        const double *xi = &T.xi[6 * o];
+        coef32[0 * ne + e] = (float)xi[0];
+        coef32[1 * ne + e] = (float)xi[1];
+        coef32[2 * ne + e] = (float)xi[4];
+        coef32[3 * ne + e] = (float)xi[5];
+        coef32[4 * ne + e] = (float)T.nrm[2 * o];
+        coef32[5 * ne + e] = (float)T.nrm[2 * o + 1];
+    }
+    if ((st = m->upload(m->sten, sten))) return st;
+    if ((st = m->upload(m->coef64, coef))) return st;
+    if ((st = m->upload(m->coef32, coef32))) return st;
+    // divergence tables, SELL-32 over internal real vertices
+    m->nslice = (nr + kSell - 1) / kSell;
+    std::vector<int64_t> svo(m->nslice + 1, 0), seo(m->nslice + 1, 0);
+    for (int64_t s = 0; s < m->nslice; ++s) {
+        int64_t mj = 0, mk = 0;
+        for (int64_t v = s * kSell; v < std::min(nr, (s + 1) * kSell); ++v) {
+            const int64_t o = T.v_new2old[v];
+            mj = std::max(mj, T.voff[o + 1] - T.voff[o]);
+            mk = std::max(mk, T.eoff[o + 1] - T.eoff[o]);
+        }
+        svo[s + 1] = svo[s] + mj * kSell;
+        seo[s + 1] = seo[s] + mk * kSell;
+    }
+    m->vert_nnz_sell = svo[m->nslice];
+    m->edge_nnz_sell = seo[m->nslice];
+    std::vector<int32_t> vid(m->vert_nnz_sell, 0), eid(m->edge_nnz_sell, 0);
+    std::vector<double> wf(m->vert_nnz_sell, 0.0), wg(m->vert_nnz_sell, 0.0), we(m->edge_nnz_sell, 0.0);
+    std::vector<double> cfg(2 * std::max<int64_t>(nr, 1), 0.0);
+    for (int64_t v = 0; v < nr; ++v) {
+        const int64_t o = T.v_new2old[v], s = v / kSell, lane = v % kSell;
+        const int64_t J = T.voff[o + 1] - T.voff[o], K = T.eoff[o + 1] - T.eoff[o];
+        const int64_t mj = (svo[s + 1] - svo[s]) / kSell, mk = (seo[s + 1] - seo[s]) / kSell;
+        double sf = 0, sg = 0, sx = 0, sy = 0;
+        for (int64_t j = 0; j < mj; ++j) {
+            const int64_t p = svo[s] + j * kSell + lane;
+            if (j < J) {
+                const int64_t q = T.voff[o] + j;
+                vid[p] = T.v_old2new[T.vid[q]];
+                wf[p] = T.wf[q];
+                wg[p] = T.wg[q];
+                sf += T.wf[q];
+                sg += T.wg[q];
+            } else {
+                vid[p] = (int32_t)v;  // padding: weight 0 on the vertex itself
+            }
+        }
+        for (int64_t k = 0; k < mk; ++k) {
+            const int64_t p = seo[s] + k * kSell + lane;
+            if (k < K) {
+                const int64_t q = T.eoff[o] + k;
+                const int32_t e = T.eid[q];
+                eid[p] = T.e_old2new[e];
+                we[p] = T.we[q];
+                sx += T.we[q] * T.nrm[2 * e];
+                sy += T.we[q] * T.nrm[2 * e + 1];
+            } else {
+                eid[p] = K > 0 ? T.e_old2new[T.eid[T.eoff[o]]] : 0;
+            }
+        }
+        cfg[v] = -(sf + sx);
+        cfg[nr + v] = -(sg + sy);
+    }
+    if ((st = m->upload(m->slice_voff, svo))) return st;
+    if ((st = m->upload(m->slice_eoff, seo))) return st;
+    if ((st = m->upload(m->svid, vid))) return st;
+    if ((st = m->upload(m->seid, eid))) return st;
+    if ((st = m->upload(m->swf64, wf))) return st;
+    if ((st = m->upload(m->swg64, wg))) return st;
+    if ((st = m->upload(m->swe64, we))) return st;
+    if ((st = m->upload(m->cfg64, cfg))) return st;
+    auto to32 = [](const std::vector<double> &a) { return std::vector<float>(a.begin(), a.end()); };
+    if ((st = m->upload(m->swf32, to32(wf)))) return st;
+    if ((st = m->upload(m->swg32, to32(wg)))) return st;
+    if ((st = m->upload(m->swe32, to32(we)))) return st;
+    if ((st = m->upload(m->cfg32, to32(cfg)))) return st;
+    if ((st = m->upload(m->new2old, T.v_new2old))) return st;
+    std::vector<int32_t> donor(std::max<int64_t>(m->n_ghost, 1), 0);
+    for (int64_t i = 0; i < m->n_ghost; ++i) donor[i] = T.v_old2new[T.ghost[T.v_new2old[nr + i]]];
+    if ((st = m->upload(m->donor, donor))) return st;
+    std::vector<double> hm(std::max<int64_t>(nr, 1), 0.0);
+    for (int64_t v = 0; v < nr; ++v) hm[v] = T.hmin[T.v_new2old[v]];
+    if ((st = m->upload(m->hmin, hm))) return st;
+    m->table_bytes_f64 = (int64_t)(sten.size() * 4 + coef.size() * 8 + (svo.size() + seo.size()) * 8 + vid.size() * 4 +
+                                   eid.size() * 4 + (wf.size() + wg.size() + we.size() + cfg.size()) * 8);
+    m->table_bytes_f32 = (int64_t)(sten.size() * 4 + coef32.size() * 4 + (svo.size() + seo.size()) * 8 +
+                                   vid.size() * 4 + eid.size() * 4 + (wf.size() + wg.size() + we.size() + cfg.size()) * 4);
+    // state and work buffers
+    if ((st = m->alloc(m->wn, 4 * nv))) return st;
+    if ((st = m->alloc(m->ws, 4 * nv))) return st;
+    if ((st = m->alloc(m->scratch, 4 * nv))) return st;
+    for (int i = 0; i < 3; ++i) {
+        if ((st = m->alloc(m->F64[i], 8 * nv))) return st;
+        if ((st = m->alloc(m->F32[i], 2 * nv))) return st;
+    }
+    if ((st = m->alloc(m->w32, nv))) return st;
+    if ((st = m->alloc(m->r64, 4 * ne))) return st;
+    if ((st = m->alloc(m->r32, ne))) return st;
+    if ((st = m->alloc(m->counters, 2))) return st;
+    CK(cudaMemset(m->counters, 0, 2 * sizeof(unsigned long long)));
+    CK(cudaMemset(m->wn, 0, 4 * nv * sizeof(double)));
+    return FDU_OK;
+}
+
+EdgeArgs edge_args(fdu_mesh *m, int prec, const void *w) {
+    EdgeArgs a{};
+    a.sten = m->sten;
+    a.coef = prec == 64 ? (const void *)m->coef64 : (const void *)m->coef32;
+    a.w = w;
+    a.r = prec == 64 ? (void *)m->r64 : (void *)m->r32;
+    a.ne = m->ne_act;
+    a.gamma = m->opts.gamma;
+    a.eps = prec == 64 ? m->opts.weno_eps : m->opts.weno_eps32;
+    a.fallback = m->counters;
+    return a;
+}
+
+DivArgs div_args(fdu_mesh *m, int prec, int fin) {
+    DivArgs a{};
+    a.n_real = m->n_real;
+    a.slice_voff = m->slice_voff;
+    a.slice_eoff = m->slice_eoff;
+    a.vid = m->svid;
+    a.eid = m->seid;
+    if (prec == 64) {
+        a.wf = m->swf64; a.wg = m->swg64; a.we = m->swe64; a.cfg = m->cfg64;
+        a.F = m->F64[fin]; a.r = m->r64;
+    } else {
+        a.wf = m->swf32; a.wg = m->swg32; a.we = m->swe32; a.cfg = m->cfg32;
+        a.F = m->F32[fin]; a.r = m->r32;
+    }
+    a.gamma = m->opts.gamma;
+    return a;
+}
+
+// Event pair around one launch of kernel kind k (nullptr when not profiling).
+cudaEvent_t *prof_pair(fdu_mesh *m, int kind, bool allowed) {
+    if (!m->prof_on || !allowed) return nullptr;
+    std::vector<cudaEvent_t> &v = m->prof_ev[kind];
+    const size_t i = m->prof_used[kind]++;
+    while (v.size() < 2 * (i + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        v.push_back(e);
+    }
+    return &v[2 * i];
+}
+
+template <class F>
+void timed(fdu_mesh *m, int kind, bool allowed, cudaStream_t s, F &&launch) {
+    cudaEvent_t *p = prof_pair(m, kind, allowed);
+    if (p) cudaEventRecord(p[0], s);
+    launch();
+    if (p) cudaEventRecord(p[1], s);
+}
+
+// Make F64[0] (or w32 and F32[0]) describe the current state wn.
+void ensure_fluxes(fdu_mesh *m, int prec, cudaStream_t s) {
+    if (prec == 64 && !m->f64_valid) {
+        launch_vertex_flux_f64(m->wn, m->F64[0], m->nv, m->opts.gamma, s);
+        m->f64_valid = true;
+    }
+    if (prec == 32 && !m->f32_valid) {
+        launch_vertex_flux_f32(m->wn, m->F32[0], m->w32, m->nv, m->opts.gamma, s);
+        m->f32_valid = true;
+    }
+}
+
+// One SSP-RK3 step: three (edge flux, divergence + stage) pairs.  Stage i
+// reads fluxes F[i-1] and writes F[i mod 3], so F[0] holds the fluxes of
+// the new state at the end and a captured step can be replayed as is.
+void enqueue_step(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaStream_t s, bool prof) {
+    const int fq = prec == 64 ? 4 : 2;  // 16-byte words of vertex fluxes per vertex
+    const int kd = prec == 64 ? 0 : 2;
+    for (int stage = 1; stage <= 3; ++stage) {
+        const double *win = stage == 1 ? m->wn : m->ws;
+        timed(m, kd, prof, s, [&] {
+            if (prec == 64) launch_edge_flux_f64(edge_args(m, 64, win), s);
+            else launch_edge_flux_f32(edge_args(m, 32, m->w32), s);
+        });
+        DivArgs a = div_args(m, prec, stage - 1);
+        a.wn = m->wn;
+        a.ws = win;
+        a.wout = stage == 3 ? m->wn : m->ws;
+        a.Fout = prec == 64 ? (void *)m->F64[stage % 3] : (void *)m->F32[stage % 3];
+        a.w32out = prec == 32 ? m->w32 : nullptr;
+        a.dt = dt;
+        a.dt_dev = dt_dev;
+        timed(m, kd + 1, prof, s, [&] {
+            if (prec == 64) launch_div_f64(a, stage, s);
+            else launch_div_f32(a, stage, s);
+        });
+        if (m->n_ghost > 0)
+            launch_ghost_fill(a.wout, a.Fout, fq, prec == 32 ? m->w32 : nullptr, m->donor, m->n_real, m->n_ghost, s);
+    }
+}
+
+}  // namespace
+
+// ====================================================================== C-ABI
+extern "C" {
+
+const char *fdu_version(void) { return "fdu 0.1 (sm_103a)"; }
+const char *fdu_last_error(void) { return g_err.c_str(); }
+
+fdu_status fdu_default_opts(fdu_mesh_opts *o) {
+    if (!o) return set_err(FDU_ERR_ARG, "null opts");
+    std::memset(o, 0, sizeof *o);
+    o->Lx = 0;
+    o->Ly = 0;
+    o->weno_eps = 1e-40;
+    o->weno_eps32 = 1e-30;
+    o->gamma = 1.4;
+    o->lsq_degree = 2;
+    o->lsq_levels = 2;
+    o->bc = FDU_BC_PERIODIC;
+    o->renumber = 1;
+    o->device = 0;
+    o->host_threads = 0;
+    o->ghost_donor = nullptr;
+    return FDU_OK;
+}
+
+fdu_status fdu_mesh_create(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts *opts,
+                           fdu_mesh **out) {
+    if (out) *out = nullptr;
+    if (!xy || !tri || !opts || !out) return set_err(FDU_ERR_ARG, "null argument");
+    if (nv < 3 || nt < 1 || nv > INT32_MAX / 2) return set_err(FDU_ERR_ARG, "bad vertex or triangle count");
+    if (opts->lsq_degree < 1 || opts->lsq_degree > 6 || opts->lsq_levels < 1 || opts->lsq_levels > 2)
+        return set_err(FDU_ERR_ARG, "lsq_degree must be 1..6 and lsq_levels 1..2");
+    if (!(opts->gamma > 1.0) || !(opts->weno_eps > 0) || !(opts->weno_eps32 > 0))
+        return set_err(FDU_ERR_ARG, "gamma must be > 1 and the WENO epsilons > 0");
+    if (opts->bc == FDU_BC_PERIODIC && !(opts->Lx > 0 && opts->Ly > 0))
+        return set_err(FDU_ERR_ARG, "periodic meshes need Lx > 0 and Ly > 0");
+    if (opts->bc == FDU_BC_TRANSMISSIVE && !opts->ghost_donor)
+        return set_err(FDU_ERR_ARG, "transmissive meshes need ghost_donor");
+    fdu_mesh *m = new (std::nothrow) fdu_mesh();
+    if (!m) return set_err(FDU_ERR_ARG, "out of host memory");
+    m->opts = *opts;
+    m->opts.ghost_donor = nullptr;
+    std::string err;
+    int st = build_host_tables(xy, nv, tri, nt, *opts, m->T, err);
+    if (st != FDU_OK) {
+        delete m;
+        return set_err(st, err);
+    }
+    m->nv = nv;
+    m->n_real = m->T.n_real;
+    m->n_ghost = nv - m->T.n_real;
+    m->ne_act = m->T.ne_active;
+    m->device = opts->device;
+    if (m->device >= 0) {
+        cudaError_t e = cudaSetDevice(m->device);
+        if (e == cudaSuccess) e = cudaStreamCreate(&m->own_stream);
+        if (e != cudaSuccess) {
+            delete m;
+            return set_err(FDU_ERR_CUDA, std::string("device setup: ") + cudaGetErrorString(e));
+        }
+        st = upload_tables(m);
+        if (st != FDU_OK) {
+            std::string keep = g_err;
+            m->release();
+            delete m;
+            return set_err(st, keep);
+        }
+    }
+    *out = m;
+    return FDU_OK;
+}
+
+fdu_status fdu_mesh_destroy(fdu_mesh *m) {
+    if (!m) return FDU_OK;
+    m->release();
+    delete m;
+    return FDU_OK;
+}
+
+fdu_status fdu_mesh_info_get(const fdu_mesh *m, fdu_mesh_info *out) {
+    if (!m || !out) return set_err(FDU_ERR_ARG, "null argument");
+    std::memset(out, 0, sizeof *out);
+    const HostTables &T = m->T;
+    out->nv = T.nv;
+    out->ne = T.ne;
+    out->nt = T.nt;
+    out->n_real = T.n_real;
+    out->div_vert_nnz = (int64_t)T.vid.size();
+    out->div_edge_nnz = (int64_t)T.eid.size();
+    int32_t jmin = INT32_MAX, jmax = 0, kmin = INT32_MAX, kmax = 0;
+    for (int64_t v = 0; v < T.nv; ++v) {
+        if (!T.ghost.empty() && T.ghost[v] >= 0) continue;
+        const int32_t J = (int32_t)(T.voff[v + 1] - T.voff[v]), K = (int32_t)(T.eoff[v + 1] - T.eoff[v]);
+        jmin = std::min(jmin, J); jmax = std::max(jmax, J);
+        kmin = std::min(kmin, K); kmax = std::max(kmax, K);
+    }
+    out->J_min = jmin; out->J_max = jmax; out->K_min = kmin; out->K_max = kmax;
+    out->device_bytes = m->device_bytes;
+    out->table_bytes_f64 = m->table_bytes_f64;
+    out->table_bytes_f32 = m->table_bytes_f32;
+    out->sell_width = kSell;
+    return FDU_OK;
+}
+
+fdu_status fdu_get_edges(const fdu_mesh *m, int32_t *e) {
+    if (!m || !e) return set_err(FDU_ERR_ARG, "null argument");
+    std::memcpy(e, m->T.edge.data(), m->T.edge.size() * sizeof(int32_t));
+    return FDU_OK;
+}
+
+fdu_status fdu_get_edge_stencils(const fdu_mesh *m, int32_t *s, double *xi) {
+    if (!m) return set_err(FDU_ERR_ARG, "null mesh");
+    if (s) std::memcpy(s, m->T.sten.data(), m->T.sten.size() * sizeof(int32_t));
+    if (xi) std::memcpy(xi, m->T.xi.data(), m->T.xi.size() * sizeof(double));
+    return FDU_OK;
+}
+
+fdu_status fdu_get_div_sizes(const fdu_mesh *m, int64_t *vn, int64_t *en) {
+    if (!m || !vn || !en) return set_err(FDU_ERR_ARG, "null argument");
+    *vn = (int64_t)m->T.vid.size();
+    *en = (int64_t)m->T.eid.size();
+    return FDU_OK;
+}
+
+fdu_status fdu_get_div_stencils(const fdu_mesh *m, int64_t *voff, int32_t *vid, double *wf, double *wg, int64_t *eoff,
+                                int32_t *eid, double *we) {
+    if (!m || !voff || !vid || !eoff || !eid) return set_err(FDU_ERR_ARG, "null argument");
+    const HostTables &T = m->T;
+    std::memcpy(voff, T.voff.data(), T.voff.size() * sizeof(int64_t));
+    std::memcpy(eoff, T.eoff.data(), T.eoff.size() * sizeof(int64_t));
+    std::memcpy(vid, T.vid.data(), T.vid.size() * sizeof(int32_t));
+    std::memcpy(eid, T.eid.data(), T.eid.size() * sizeof(int32_t));
+    if (wf) std::memcpy(wf, T.wf.data(), T.wf.size() * sizeof(double));
+    if (wg) std::memcpy(wg, T.wg.data(), T.wg.size() * sizeof(double));
+    if (we) std::memcpy(we, T.we.data(), T.we.size() * sizeof(double));
+    return FDU_OK;
+}
+
+fdu_status fdu_set_state(fdu_mesh *m, const double *w, int on_device, void *stream) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!w) return set_err(FDU_ERR_ARG, "null state");
+    cudaStream_t s = m->stream(stream);
+    if (on_device) {
+        launch_permute_rows(w, m->wn, m->new2old, m->nv, true, s);
+        CK_LAUNCH();
+    } else {
+        std::vector<double> h(4 * m->nv);
+        for (int64_t i = 0; i < m->nv; ++i) {
+            const double *src = w + 4 * (int64_t)m->T.v_new2old[i];
+            if (!(src[0] > 0) || !std::isfinite(src[1]) || !std::isfinite(src[2]) || !std::isfinite(src[3]))
+                return set_err(FDU_ERR_NONPHYSICAL, "state row " + std::to_string(m->T.v_new2old[i]) +
+                                                        " has rho <= 0 or a non-finite value");
+            std::memcpy(&h[4 * i], src, 4 * sizeof(double));
+        }
+        CK(cudaMemcpyAsync(m->wn, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (m->n_ghost > 0) {
+        launch_ghost_fill(m->wn, nullptr, 0, nullptr, m->donor, m->n_real, m->n_ghost, s);
+        CK_LAUNCH();
+    }
+    m->f64_valid = m->f32_valid = false;
+    return FDU_OK;
+}
+
+fdu_status fdu_get_state(const fdu_mesh *mc, double *w, int on_device, void *stream) {
+    fdu_mesh *m = const_cast<fdu_mesh *>(mc);
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!w) return set_err(FDU_ERR_ARG, "null state");
+    cudaStream_t s = m->stream(stream);
+    if (on_device) {
+        launch_permute_rows(m->wn, w, m->new2old, m->nv, false, s);
+        CK_LAUNCH();
+    } else {
+        launch_permute_rows(m->wn, m->scratch, m->new2old, m->nv, false, s);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(w, m->scratch, 4 * m->nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return FDU_OK;
+}
+
+fdu_status fdu_residual(fdu_mesh *m, int precision, double *dwdt, int on_device, void *stream) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!dwdt) return set_err(FDU_ERR_ARG, "null output");
+    if (precision != 64 && precision != 32) return set_err(FDU_ERR_ARG, "precision must be 64 or 32");
+    cudaStream_t s = m->stream(stream);
+    ensure_fluxes(m, precision, s);
+    double *out = on_device ? dwdt : m->scratch;
+    if (m->n_ghost > 0) CK(cudaMemsetAsync(out, 0, 4 * m->nv * sizeof(double), s));
+    const int kd = precision == 64 ? 0 : 2;
+    timed(m, kd, true, s, [&] {
+        if (precision == 64) launch_edge_flux_f64(edge_args(m, 64, m->wn), s);
+        else launch_edge_flux_f32(edge_args(m, 32, m->w32), s);
+    });
+    DivArgs a = div_args(m, precision, 0);
+    a.out = out;
+    a.out_map = m->new2old;
+    timed(m, kd + 1, true, s, [&] {
+        if (precision == 64) launch_div_f64(a, 0, s);
+        else launch_div_f32(a, 0, s);
+    });
+    CK_LAUNCH();
+    if (!on_device) {
+        CK(cudaMemcpyAsync(dwdt, m->scratch, 4 * m->nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return FDU_OK;
+}
+
+fdu_status fdu_max_dt(fdu_mesh *m, double cfl, double *dt, void *stream) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!dt || !(cfl > 0)) return set_err(FDU_ERR_ARG, "need cfl > 0 and an output pointer");
+    cudaStream_t s = m->stream(stream);
+    const unsigned long long inf_bits = 0x7FF0000000000000ull;
+    CK(cudaMemcpyAsync(m->counters + 1, &inf_bits, sizeof inf_bits, cudaMemcpyHostToDevice, s));
+    launch_max_dt(m->wn, m->hmin, m->n_real, m->opts.gamma, m->counters + 1, s);
+    CK_LAUNCH();
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, m->counters + 1, sizeof bits, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double v;
+    std::memcpy(&v, &bits, sizeof v);
+    if (!(v > 0) || !std::isfinite(v)) return set_err(FDU_ERR_NONPHYSICAL, "non-physical state in the time-step bound");
+    *dt = cfl * v;
+    return FDU_OK;
+}
+
+fdu_status fdu_rk_step(fdu_mesh *m, double dt, int precision, void *stream) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!(dt > 0) || !std::isfinite(dt)) return set_err(FDU_ERR_ARG, "dt must be positive and finite");
+    if (precision != 64 && precision != 32) return set_err(FDU_ERR_ARG, "precision must be 64 or 32");
+    cudaStream_t s = m->stream(stream);
+    ensure_fluxes(m, precision, s);
+    enqueue_step(m, precision, dt, nullptr, s, true);
+    CK_LAUNCH();
+    if (precision == 64) m->f32_valid = false;
+    else m->f64_valid = false;
+    return FDU_OK;
+}
+
+fdu_status fdu_rk_steps(fdu_mesh *m, double dt, int precision, int n_steps, void *stream) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!(dt > 0) || !std::isfinite(dt) || n_steps < 0) return set_err(FDU_ERR_ARG, "need dt > 0 and n_steps >= 0");
+    if (precision != 64 && precision != 32) return set_err(FDU_ERR_ARG, "precision must be 64 or 32");
+    if (n_steps == 0) return FDU_OK;
+    cudaStream_t s = m->stream(stream);
+    ensure_fluxes(m, precision, s);
+    CK_LAUNCH();
+    auto key = std::make_pair(precision, dt);
+    auto it = m->graphs.find(key);
+    if (it == m->graphs.end()) {
+        // capture on a blocking side stream (the legacy stream cannot be captured)
+        cudaStream_t cs = m->own_stream;
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, s));
+        CK(cudaStreamWaitEvent(cs, ev, 0));
+        CK(cudaEventDestroy(ev));
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(m, precision, dt, nullptr, cs, false);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        cudaGraphExec_t ge;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        it = m->graphs.emplace(key, ge).first;
+    }
+    for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(it->second, s));
+    if (precision == 64) m->f32_valid = false;
+    else m->f64_valid = false;
+    return FDU_OK;
+}
+
+fdu_status fdu_fallback_count(fdu_mesh *m, int64_t *count, int reset, void *stream) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!count) return set_err(FDU_ERR_ARG, "null output");
+    cudaStream_t s = m->stream(stream);
+    unsigned long long c = 0;
+    CK(cudaMemcpyAsync(&c, m->counters, sizeof c, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (reset) CK(cudaMemsetAsync(m->counters, 0, sizeof c, s));
+    *count = (int64_t)c;
+    return FDU_OK;
+}
+
+fdu_status fdu_profile(fdu_mesh *m, int enable) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    m->prof_on = enable != 0;
+    return FDU_OK;
+}
+
+fdu_status fdu_profile_read(fdu_mesh *m, int kernel, int precision, double *total_ms, int64_t *launches, int reset) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!total_ms || !launches || (kernel != FDU_KERNEL_EDGE && kernel != FDU_KERNEL_DIV) ||
+        (precision != 64 && precision != 32))
+        return set_err(FDU_ERR_ARG, "bad kernel kind, precision or output pointer");
+    const int kind = (precision == 64 ? 0 : 2) + kernel;
+    double tot = 0;
+    const size_t n = m->prof_used[kind];
+    for (size_t i = 0; i < n; ++i) {
+        cudaEvent_t a = m->prof_ev[kind][2 * i], b = m->prof_ev[kind][2 * i + 1];
+        CK(cudaEventSynchronize(b));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        tot += ms;
+    }
+    *total_ms = tot;
+    *launches = (int64_t)n;
+    if (reset) m->prof_used[kind] = 0;
+    return FDU_OK;
+}
+
+}  // extern "C"

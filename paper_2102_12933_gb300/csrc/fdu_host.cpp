@@ -1,0 +1,656 @@
+// Host preprocessing of libfdu, FP64, done once per static mesh
+// ("computed only once at the initial time for static meshes",
+// Section 2.2.1):
+//   - unique edge list and vertex adjacency;
+//   - per edge the six-vertex 1D curvilinear stencil (Section 2.3.1,
+//     Fig. weno1d-tri) and its normalised arc-length coordinates along
+//     Catmull-Rom curves (Section 2.3.1, Fig. curve_sten);
+//   - difference-form NU-WENO5 coefficient blocks (Appendix);
+//   - one- or two-level divergence stencils (Section 2.2.2) and their
+//     least-squares weights, the a1 and b2 rows of the pseudo-inverse
+//     (Section 2.2.1), here by Householder QR of the column-equilibrated
+//     system (equal to the SVD pseudo-inverse for full column rank);
+//   - a Hilbert-curve locality renumbering of vertices and edges.
+// Compiled with -ffp-contract=off so that the stencil walk's cosine
+// comparisons give the same bits on every host.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <thread>
+
+#include "fdu_internal.h"
+
+namespace fdu {
+namespace {
+
+struct Geo {
+    const double *xy;
+    double Lx, Ly;
+    inline void d(int64_t a, int64_t b, double out[2]) const {
+        double dx = xy[2 * b] - xy[2 * a];
+        double dy = xy[2 * b + 1] - xy[2 * a + 1];
+        if (Lx > 0) dx -= Lx * std::rint(dx / Lx);
+        if (Ly > 0) dy -= Ly * std::rint(dy / Ly);
+        out[0] = dx;
+        out[1] = dy;
+    }
+};
+
+// ---------------------------------------------------------------- edges
+int build_edges(const int32_t *tri, int64_t nt, int64_t nv, const Geo &g, HostTables &T, std::string &err) {
+    std::vector<uint64_t> keys;
+    keys.reserve(3 * nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        int32_t v[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
+        for (int s = 0; s < 3; ++s)
+            if (v[s] < 0 || v[s] >= nv) {
+                err = "triangle " + std::to_string(t) + " has a vertex id out of range";
+                return FDU_ERR_MESH;
+            }
+        if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) {
+            err = "triangle " + std::to_string(t) + " repeats a vertex";
+            return FDU_ERR_MESH;
+        }
+        double a[2], b[2];
+        g.d(v[0], v[1], a);
+        g.d(v[0], v[2], b);
+        if (!(a[0] * b[1] - a[1] * b[0] > 0)) {
+            err = "triangle " + std::to_string(t) + " is degenerate or clockwise";
+            return FDU_ERR_MESH;
+        }
+        for (int s = 0; s < 3; ++s) {
+            uint32_t p = (uint32_t)v[s], q = (uint32_t)v[(s + 1) % 3];
+            if (p > q) std::swap(p, q);
+            keys.push_back(((uint64_t)p << 32) | q);
+        }
+    }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    T.ne = (int64_t)keys.size();
+    T.edge.resize(2 * T.ne);
+    T.nrm.resize(2 * T.ne);
+    for (int64_t k = 0; k < T.ne; ++k) {
+        T.edge[2 * k] = (int32_t)(keys[k] >> 32);
+        T.edge[2 * k + 1] = (int32_t)(keys[k] & 0xffffffffu);
+        double d[2];
+        g.d(T.edge[2 * k], T.edge[2 * k + 1], d);
+        double l = std::sqrt(d[0] * d[0] + d[1] * d[1]);
+        if (!(l > 0)) {
+            err = "zero-length edge";
+            return FDU_ERR_MESH;
+        }
+        T.nrm[2 * k] = d[0] / l;
+        T.nrm[2 * k + 1] = d[1] / l;
+    }
+    // adjacency: (vertex, neighbour, edge) triples sorted by (vertex, neighbour)
+    std::vector<std::array<int32_t, 3>> trip(2 * T.ne);
+    for (int64_t k = 0; k < T.ne; ++k) {
+        trip[2 * k] = {T.edge[2 * k], T.edge[2 * k + 1], (int32_t)k};
+        trip[2 * k + 1] = {T.edge[2 * k + 1], T.edge[2 * k], (int32_t)k};
+    }
+    std::sort(trip.begin(), trip.end());
+    T.adj_off.assign(nv + 1, 0);
+    T.adj.resize(trip.size());
+    T.adj_edge.resize(trip.size());
+    for (size_t i = 0; i < trip.size(); ++i) {
+        T.adj_off[trip[i][0] + 1]++;
+        T.adj[i] = trip[i][1];
+        T.adj_edge[i] = trip[i][2];
+    }
+    for (int64_t v = 0; v < nv; ++v) T.adj_off[v + 1] += T.adj_off[v];
+    for (int64_t v = 0; v < nv; ++v)
+        if (T.adj_off[v + 1] - T.adj_off[v] < 2) {
+            err = "vertex " + std::to_string(v) + " has fewer than two neighbours";
+            return FDU_ERR_MESH;
+        }
+    return FDU_OK;
+}
+
+// ---------------------------------------------------------------- 1D stencil walk
+// Greedy "as smooth as possible" string (Section 2.3.1): from vertex c
+// reached along d, the unused neighbour with the largest cosine between d
+// and the next segment; a candidate replaces the best so far only if its
+// cosine is larger by more than 1e-12 (neighbours visited in ascending
+// original id); the winning cosine must be positive.
+bool next_vertex(const HostTables &T, const Geo &g, int32_t from, int32_t at, const int32_t *used, int nused,
+                 int32_t &out) {
+    double d[2];
+    g.d(from, at, d);
+    const double dlen = std::sqrt(d[0] * d[0] + d[1] * d[1]);
+    int32_t pick = -1;
+    double cbest = 0;
+    for (int64_t i = T.adj_off[at]; i < T.adj_off[at + 1]; ++i) {
+        const int32_t q = T.adj[i];
+        if (std::find(used, used + nused, q) != used + nused) continue;
+        double e[2];
+        g.d(at, q, e);
+        const double elen = std::sqrt(e[0] * e[0] + e[1] * e[1]);
+        const double c = (d[0] * e[0] + d[1] * e[1]) / (dlen * elen);
+        if (pick < 0 || c > cbest + 1e-12) {
+            pick = q;
+            cbest = c;
+        }
+    }
+    if (pick < 0 || !(cbest > 0)) return false;
+    out = pick;
+    return true;
+}
+
+bool walk(const HostTables &T, const Geo &g, int64_t k, int32_t s[6]) {
+    const int32_t a = T.edge[2 * k], b = T.edge[2 * k + 1];
+    int32_t used[6] = {a, b, -1, -1, -1, -1};
+    int32_t r2, r3, l2, l3;
+    if (!next_vertex(T, g, a, b, used, 2, r2)) return false;
+    used[2] = r2;
+    if (!next_vertex(T, g, b, r2, used, 3, r3)) return false;
+    used[3] = r3;
+    if (!next_vertex(T, g, b, a, used, 4, l2)) return false;
+    used[4] = l2;
+    if (!next_vertex(T, g, a, l2, used, 5, l3)) return false;
+    s[0] = l3; s[1] = l2; s[2] = a; s[3] = b; s[4] = r2; s[5] = r3;
+    return true;
+}
+
+// ---------------------------------------------------------------- arc length
+// 16-point Gauss-Legendre rule on [0, 1]; nodes from Newton's method on the
+// Legendre recurrence started at Tricomi's approximation.
+struct GaussLegendre16 {
+    double t[16], w[16];
+    GaussLegendre16() {
+        const int n = 16;
+        for (int i = 1; i <= n; ++i) {
+            double th = M_PI * (4.0 * i - 1.0) / (4.0 * n + 2.0);
+            double x = (1.0 - (n - 1.0) / (8.0 * n * n * n)) * std::cos(th);
+            double pn = 0, pd = 0;
+            for (int it = 0; it < 50; ++it) {
+                double pm = 1.0, p = x;
+                for (int m = 2; m <= n; ++m) {
+                    double pnew = ((2.0 * m - 1.0) * x * p - (m - 1.0) * pm) / m;
+                    pm = p;
+                    p = pnew;
+                }
+                pn = p;
+                pd = n * (pm - x * p) / (1.0 - x * x);
+                double step = pn / pd;
+                x -= step;
+                if (std::fabs(step) <= 4e-16) break;
+            }
+            {
+                double pm = 1.0, p = x;
+                for (int m = 2; m <= n; ++m) {
+                    double pnew = ((2.0 * m - 1.0) * x * p - (m - 1.0) * pm) / m;
+                    pm = p;
+                    p = pnew;
+                }
+                pd = n * (pm - x * p) / (1.0 - x * x);
+            }
+            t[i - 1] = 0.5 * (x + 1.0);
+            w[i - 1] = 1.0 / ((1.0 - x * x) * pd * pd);
+        }
+    }
+};
+const GaussLegendre16 &gl16() {
+    static const GaussLegendre16 q;
+    return q;
+}
+
+// length of the cubic Hermite segment p0 -> p1 with end tangents m0, m1
+double segment_length(const double p0[2], const double p1[2], const double m0[2], const double m1[2]) {
+    const GaussLegendre16 &q = gl16();
+    double len = 0;
+    for (int i = 0; i < 16; ++i) {
+        const double s = q.t[i];
+        // derivative of the Hermite basis
+        const double a = 6 * s * s - 6 * s;      // coefficient of p0 (and -p1)
+        const double b = 3 * s * s - 4 * s + 1;  // of m0
+        const double c = 3 * s * s - 2 * s;      // of m1
+        const double vx = a * (p0[0] - p1[0]) + b * m0[0] + c * m1[0];
+        const double vy = a * (p0[1] - p1[1]) + b * m0[1] + c * m1[1];
+        len += q.w[i] * std::sqrt(vx * vx + vy * vy);
+    }
+    return len;
+}
+
+// One side: start A at the middle edge (other end O), then B and C.  The
+// curve leaves A along O->A scaled by |B - A|, passes B with the
+// Catmull-Rom tangent (C - A)/2 and ends at C with tangent C - B.
+void side_arc(const double O[2], const double A[2], const double B[2], const double Cp[2], double &sAB, double &sBC) {
+    double u[2] = {A[0] - O[0], A[1] - O[1]};
+    const double ul = std::hypot(u[0], u[1]);
+    const double chord = std::hypot(B[0] - A[0], B[1] - A[1]);
+    const double tA[2] = {u[0] / ul * chord, u[1] / ul * chord};
+    const double tB[2] = {0.5 * (Cp[0] - A[0]), 0.5 * (Cp[1] - A[1])};
+    const double tC[2] = {Cp[0] - B[0], Cp[1] - B[1]};
+    sAB = segment_length(A, B, tA, tB);
+    sBC = segment_length(B, Cp, tB, tC);
+}
+
+void stencil_coordinates(const Geo &g, const int32_t s[6], double xi[6]) {
+    // unwrapped points, L1 at the origin
+    double P[6][2];
+    double d[2];
+    P[2][0] = 0; P[2][1] = 0;
+    g.d(s[2], s[3], d); P[3][0] = d[0]; P[3][1] = d[1];
+    g.d(s[3], s[4], d); P[4][0] = P[3][0] + d[0]; P[4][1] = P[3][1] + d[1];
+    g.d(s[4], s[5], d); P[5][0] = P[4][0] + d[0]; P[5][1] = P[4][1] + d[1];
+    g.d(s[2], s[1], d); P[1][0] = d[0]; P[1][1] = d[1];
+    g.d(s[1], s[0], d); P[0][0] = P[1][0] + d[0]; P[0][1] = P[1][1] + d[1];
+    const double ell = std::hypot(P[3][0], P[3][1]);
+    double r1, r2, l1, l2;
+    side_arc(P[2], P[3], P[4], P[5], r1, r2);
+    side_arc(P[3], P[2], P[1], P[0], l1, l2);
+    xi[2] = -0.5;
+    xi[3] = 0.5;
+    xi[4] = 0.5 + r1 / ell;
+    xi[5] = xi[4] + r2 / ell;
+    xi[1] = -0.5 - l1 / ell;
+    xi[0] = xi[1] - l2 / ell;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- NU-WENO5 coefficients
+// x[5] = x_{i-2..i+2}, origin at the midpoint of [x_i, x_{i+1}].
+// Sub-stencil k interpolates points x[k..k+2] by a quadratic (Appendix,
+// Eqs. u0-u2); its value, slope and curvature at 0 are written against
+// differences from the shared point x_i = x[2].  The linear weights follow
+// from their definition (the combination equals the degree-4 interpolant,
+// Eq. S5): only S0 holds x_{i-2} and only S2 holds x_{i+2}, so C_0 and C_2
+// are ratios of Lagrange values and C_1 = 1 - C_0 - C_2.
+void side_coefficients(const double x[5], double out[kSideCoef]) {
+    const double dx = x[3] - x[2];
+    const double curv = std::sqrt(13.0 / 12.0) * dx * dx;
+    // slot of each non-shared point per sub-stencil: local index -> slot
+    double val[3][3], der[3][3], sec[3][3];
+    for (int k = 0; k < 3; ++k) {
+        const double *p = x + k;
+        for (int j = 0; j < 3; ++j) {
+            const double pa = p[(j + 1) % 3], pb = p[(j + 2) % 3];
+            const double den = (p[j] - pa) * (p[j] - pb);
+            val[k][j] = pa * pb / den;
+            der[k][j] = -(pa + pb) / den;
+            sec[k][j] = 2.0 / den;
+        }
+    }
+    // non-shared local indices: k=0 -> (0,1), k=1 -> (0,2), k=2 -> (1,2)
+    const int nj[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int k = 0; k < 3; ++k)
+        for (int q = 0; q < 2; ++q) {
+            const int j = nj[k][q];
+            out[2 * k + q] = val[k][j];
+            out[6 + 2 * k + q] = dx * der[k][j];
+            out[12 + 2 * k + q] = curv * sec[k][j];
+        }
+    // degree-4 Lagrange weight at 0 of x[0] and x[4]
+    double l0 = 1, l4 = 1;
+    for (int m = 0; m < 5; ++m) {
+        if (m != 0) l0 *= (0.0 - x[m]) / (x[0] - x[m]);
+        if (m != 4) l4 *= (0.0 - x[m]) / (x[4] - x[m]);
+    }
+    const double c0 = l0 / val[0][0];
+    const double c2 = l4 / val[2][2];
+    out[18] = c0;
+    out[19] = 1.0 - c0 - c2;
+    out[20] = c2;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- divergence stencils
+void stencil_of(const HostTables &T, int32_t o, std::vector<int32_t> &V, std::vector<int32_t> &E) {
+    V.clear();
+    E.clear();
+    auto one_level = [&](int32_t c) {
+        const int64_t b = T.adj_off[c], e = T.adj_off[c + 1];
+        for (int64_t i = b; i < e; ++i) {
+            V.push_back(T.adj[i]);
+            E.push_back(T.adj_edge[i]);
+        }
+        // edges between two neighbours of c: merge the sorted neighbour lists
+        for (int64_t i = b; i < e; ++i) {
+            const int32_t a = T.adj[i];
+            int64_t p = T.adj_off[a], pe = T.adj_off[a + 1], q = b;
+            while (p < pe && q < e) {
+                if (T.adj[p] < T.adj[q]) ++p;
+                else if (T.adj[p] > T.adj[q]) ++q;
+                else {
+                    if (a < T.adj[p]) E.push_back(T.adj_edge[p]);
+                    ++p;
+                    ++q;
+                }
+            }
+        }
+    };
+    if (T.levels == 1) {
+        one_level(o);
+    } else {
+        for (int64_t i = T.adj_off[o]; i < T.adj_off[o + 1]; ++i) one_level(T.adj[i]);
+    }
+    std::sort(V.begin(), V.end());
+    V.erase(std::unique(V.begin(), V.end()), V.end());
+    V.erase(std::remove(V.begin(), V.end(), o), V.end());
+    std::sort(E.begin(), E.end());
+    E.erase(std::unique(E.begin(), E.end()), E.end());
+}
+
+// ---------------------------------------------------------------- least squares
+// Rows of the linear system (Section 2.2.1, Eq. eLinearSystem), unknowns
+// [a; b] with monomials ordered x, y, x^2, xy, y^2, ...  Columns are
+// scaled to unit norm, the scaled matrix is factorised A S = Q R by
+// Householder reflections, and the requested row sum of A^+ = S R^-1 Q^T
+// is Q R^-T S e (e = unit vectors of a1 and b2).
+int lsq_weights(const HostTables &T, const Geo &g, int32_t o, const int64_t vb, const int64_t nvj, const int64_t eb,
+                const int64_t nek, std::vector<double> &w_out, std::vector<double> &A, std::vector<double> &hv) {
+    const int p = T.degree;
+    const int M = p * (p + 3) / 2, n = 2 * M;
+    const int m = (int)(2 * nvj + nek);
+    if (m < n) return FDU_ERR_RANK_DEFICIENT;
+    A.assign((size_t)m * n, 0.0);  // column-major
+    double mono[64];
+    auto monos = [&](double x, double y) {
+        int c = 0;
+        for (int d = 1; d <= p; ++d) {
+            for (int i = d; i >= 0; --i) {
+                double v = 1;
+                for (int a = 0; a < i; ++a) v *= x;
+                for (int b = 0; b < d - i; ++b) v *= y;
+                mono[c++] = v;
+            }
+        }
+    };
+    for (int64_t j = 0; j < nvj; ++j) {
+        double d[2];
+        g.d(o, T.vid[vb + j], d);
+        monos(d[0], d[1]);
+        for (int c = 0; c < M; ++c) {
+            A[(size_t)c * m + 2 * j] = mono[c];
+            A[(size_t)(M + c) * m + 2 * j + 1] = mono[c];
+        }
+    }
+    for (int64_t k = 0; k < nek; ++k) {
+        const int32_t e = T.eid[eb + k];
+        double d0[2], de[2];
+        g.d(o, T.edge[2 * e], d0);
+        g.d(T.edge[2 * e], T.edge[2 * e + 1], de);
+        monos(d0[0] + 0.5 * de[0], d0[1] + 0.5 * de[1]);
+        const double nx = T.nrm[2 * e], ny = T.nrm[2 * e + 1];
+        for (int c = 0; c < M; ++c) {
+            A[(size_t)c * m + 2 * nvj + k] = nx * mono[c];
+            A[(size_t)(M + c) * m + 2 * nvj + k] = ny * mono[c];
+        }
+    }
+    // column equilibration
+    double scale[32];
+    for (int c = 0; c < n; ++c) {
+        double s = 0;
+        for (int i = 0; i < m; ++i) s += A[(size_t)c * m + i] * A[(size_t)c * m + i];
+        s = std::sqrt(s);
+        if (!(s > 0)) return FDU_ERR_RANK_DEFICIENT;
+        scale[c] = 1.0 / s;
+        for (int i = 0; i < m; ++i) A[(size_t)c * m + i] *= scale[c];
+    }
+    // Householder QR in place; reflector k stored in hv (length m-k) with beta
+    hv.assign((size_t)m * n, 0.0);
+    double beta[32], rdiag[32];
+    for (int k = 0; k < n; ++k) {
+        double *col = &A[(size_t)k * m];
+        double nrm2 = 0;
+        for (int i = k; i < m; ++i) nrm2 += col[i] * col[i];
+        const double nrm = std::sqrt(nrm2);
+        const double alpha = col[k] >= 0 ? -nrm : nrm;
+        double *v = &hv[(size_t)k * m];
+        for (int i = 0; i < m; ++i) v[i] = 0;
+        v[k] = col[k] - alpha;
+        for (int i = k + 1; i < m; ++i) v[i] = col[i];
+        double vv = 0;
+        for (int i = k; i < m; ++i) vv += v[i] * v[i];
+        beta[k] = vv > 0 ? 2.0 / vv : 0.0;
+        rdiag[k] = alpha;
+        for (int c = k; c < n; ++c) {
+            double *a = &A[(size_t)c * m];
+            double dot = 0;
+            for (int i = k; i < m; ++i) dot += v[i] * a[i];
+            dot *= beta[k];
+            for (int i = k; i < m; ++i) a[i] -= dot * v[i];
+        }
+    }
+    double rmax = 0, rmin = INFINITY;
+    for (int k = 0; k < n; ++k) {
+        rmax = std::max(rmax, std::fabs(rdiag[k]));
+        rmin = std::min(rmin, std::fabs(rdiag[k]));
+    }
+    if (!(rmin > 1e-13 * rmax)) return FDU_ERR_RANK_DEFICIENT;
+    // R^T y = S e  (R upper triangular, A now holds R in rows 0..n-1)
+    double y[32];
+    for (int c = 0; c < n; ++c) y[c] = 0;
+    y[0] = scale[0];
+    y[M + 1] += scale[M + 1];
+    for (int i = 0; i < n; ++i) {
+        double s = y[i];
+        for (int j = 0; j < i; ++j) s -= A[(size_t)i * m + j] * y[j];  // R[j][i] sits in column i, row j
+        y[i] = s / A[(size_t)i * m + i];
+    }
+    // w = Q [y; 0] = H_0 H_1 ... H_{n-1} [y; 0]
+    w_out.assign(m, 0.0);
+    for (int i = 0; i < n; ++i) w_out[i] = y[i];
+    for (int k = n - 1; k >= 0; --k) {
+        const double *v = &hv[(size_t)k * m];
+        double dot = 0;
+        for (int i = k; i < m; ++i) dot += v[i] * w_out[i];
+        dot *= beta[k];
+        for (int i = k; i < m; ++i) w_out[i] -= dot * v[i];
+    }
+    return FDU_OK;
+}
+
+// ---------------------------------------------------------------- Hilbert order
+uint64_t hilbert_index(uint32_t x, uint32_t y, int order) {
+    const uint32_t n = 1u << order;
+    uint64_t d = 0;
+    for (uint32_t s = n >> 1; s > 0; s >>= 1) {
+        const uint32_t rx = (x & s) ? 1u : 0u;
+        const uint32_t ry = (y & s) ? 1u : 0u;
+        d += (uint64_t)s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {  // rotate the quadrant
+            if (rx == 1) {
+                x = n - 1 - x;
+                y = n - 1 - y;
+            }
+            std::swap(x, y);
+        }
+    }
+    return d;
+}
+
+template <class F>
+void parallel_for(int64_t n, int threads, F &&f) {
+    if (threads <= 1 || n < 1024) {
+        f(0, n, 0);
+        return;
+    }
+    std::vector<std::thread> pool;
+    std::atomic<int64_t> next(0);
+    const int64_t chunk = 256;
+    for (int t = 0; t < threads; ++t)
+        pool.emplace_back([&, t] {
+            for (;;) {
+                int64_t b = next.fetch_add(chunk);
+                if (b >= n) break;
+                f(b, std::min(n, b + chunk), t);
+            }
+        });
+    for (auto &th : pool) th.join();
+}
+
+}  // namespace
+
+int build_host_tables(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts &o,
+                      HostTables &T, std::string &err) {
+    T.nv = nv;
+    T.nt = nt;
+    T.Lx = o.Lx;
+    T.Ly = o.Ly;
+    T.gamma = o.gamma;
+    T.degree = o.lsq_degree;
+    T.levels = o.lsq_levels;
+    T.xy.assign(xy, xy + 2 * nv);
+    T.ghost.clear();
+    T.n_real = nv;
+    if (o.ghost_donor) {
+        T.ghost.assign(o.ghost_donor, o.ghost_donor + nv);
+        T.n_real = 0;
+        for (int64_t v = 0; v < nv; ++v) {
+            if (T.ghost[v] >= nv || T.ghost[v] < -1 || (T.ghost[v] >= 0 && o.ghost_donor[T.ghost[v]] >= 0)) {
+                err = "ghost donor must be -1 or the id of a non-ghost vertex";
+                return FDU_ERR_ARG;
+            }
+            T.n_real += (T.ghost[v] < 0);
+        }
+    }
+    Geo g{T.xy.data(), T.Lx, T.Ly};
+    int st = build_edges(tri, nt, nv, g, T, err);
+    if (st) return st;
+    int threads = o.host_threads > 0 ? o.host_threads : (int)std::max(1u, std::thread::hardware_concurrency());
+    const bool periodic = T.Lx > 0 && T.Ly > 0;
+
+    // 1D stencils and coefficients
+    T.sten.assign(6 * T.ne, -1);
+    T.xi.assign(6 * T.ne, 0.0);
+    T.coef.assign((size_t)kEdgeCoef * T.ne, 0.0);
+    std::atomic<int64_t> bad(-1);
+    parallel_for(T.ne, threads, [&](int64_t b, int64_t e, int) {
+        for (int64_t k = b; k < e; ++k) {
+            int32_t *s = &T.sten[6 * k];
+            if (!walk(T, g, k, s)) {
+                for (int i = 0; i < 6; ++i) s[i] = -1;
+                bad.store(k);
+                continue;
+            }
+            double *xi = &T.xi[6 * k];
+            stencil_coordinates(g, s, xi);
+            double *c = &T.coef[(size_t)kEdgeCoef * k];
+            const double xl[5] = {xi[0], xi[1], xi[2], xi[3], xi[4]};
+            const double xr[5] = {-xi[5], -xi[4], -xi[3], -xi[2], -xi[1]};
+            side_coefficients(xl, c);
+            side_coefficients(xr, c + kSideCoef);
+            c[2 * kSideCoef] = T.nrm[2 * k];
+            c[2 * kSideCoef + 1] = T.nrm[2 * k + 1];
+        }
+    });
+    if (periodic && bad.load() >= 0) {
+        err = "1D stencil walk found no forward neighbour for edge " + std::to_string(bad.load());
+        return FDU_ERR_STENCIL;
+    }
+
+    // divergence stencils (serial: cheap) and weights (parallel)
+    T.voff.assign(nv + 1, 0);
+    T.eoff.assign(nv + 1, 0);
+    T.vid.clear();
+    T.eid.clear();
+    {
+        std::vector<int32_t> V, E;
+        for (int32_t v = 0; v < nv; ++v) {
+            if (T.ghost.empty() || T.ghost[v] < 0) {
+                stencil_of(T, v, V, E);
+                for (int32_t e : E)
+                    if (T.sten[6 * (int64_t)e] < 0) {
+                        err = "edge " + std::to_string(e) + " in the divergence stencil of vertex " +
+                              std::to_string(v) + " has no 1D stencil";
+                        return FDU_ERR_STENCIL;
+                    }
+                T.vid.insert(T.vid.end(), V.begin(), V.end());
+                T.eid.insert(T.eid.end(), E.begin(), E.end());
+            }
+            T.voff[v + 1] = (int64_t)T.vid.size();
+            T.eoff[v + 1] = (int64_t)T.eid.size();
+        }
+    }
+    T.wf.assign(T.vid.size(), 0.0);
+    T.wg.assign(T.vid.size(), 0.0);
+    T.we.assign(T.eid.size(), 0.0);
+    std::atomic<int64_t> rank_bad(-1);
+    parallel_for(nv, threads, [&](int64_t b, int64_t e, int) {
+        std::vector<double> w, A, hv;
+        for (int64_t v = b; v < e; ++v) {
+            if (!T.ghost.empty() && T.ghost[v] >= 0) continue;
+            const int64_t vb = T.voff[v], nvj = T.voff[v + 1] - vb;
+            const int64_t eb = T.eoff[v], nek = T.eoff[v + 1] - eb;
+            if (lsq_weights(T, g, (int32_t)v, vb, nvj, eb, nek, w, A, hv) != FDU_OK) {
+                rank_bad.store(v);
+                continue;
+            }
+            for (int64_t j = 0; j < nvj; ++j) {
+                T.wf[vb + j] = w[2 * j];
+                T.wg[vb + j] = w[2 * j + 1];
+            }
+            for (int64_t k = 0; k < nek; ++k) T.we[eb + k] = w[2 * nvj + k];
+        }
+    });
+    if (rank_bad.load() >= 0) {
+        err = "least-squares system of vertex " + std::to_string(rank_bad.load()) +
+              " has too few conditions or is rank deficient";
+        return FDU_ERR_RANK_DEFICIENT;
+    }
+
+    T.hmin.assign(nv, INFINITY);
+    for (int64_t k = 0; k < T.ne; ++k) {
+        double d[2];
+        g.d(T.edge[2 * k], T.edge[2 * k + 1], d);
+        const double l = std::sqrt(d[0] * d[0] + d[1] * d[1]);
+        T.hmin[T.edge[2 * k]] = std::min(T.hmin[T.edge[2 * k]], l);
+        T.hmin[T.edge[2 * k + 1]] = std::min(T.hmin[T.edge[2 * k + 1]], l);
+    }
+
+    // locality renumbering
+    T.v_new2old.resize(nv);
+    std::iota(T.v_new2old.begin(), T.v_new2old.end(), 0);
+    if (o.renumber) {
+        double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
+        for (int64_t v = 0; v < nv; ++v)
+            for (int c = 0; c < 2; ++c) {
+                lo[c] = std::min(lo[c], T.xy[2 * v + c]);
+                hi[c] = std::max(hi[c], T.xy[2 * v + c]);
+            }
+        const int order = 16;
+        const double span = std::max(hi[0] - lo[0], hi[1] - lo[1]);
+        const double scale = span > 0 ? ((1 << order) - 1) / span : 0;
+        std::vector<uint64_t> key(nv);
+        for (int64_t v = 0; v < nv; ++v) {
+            uint32_t ix = (uint32_t)((T.xy[2 * v] - lo[0]) * scale);
+            uint32_t iy = (uint32_t)((T.xy[2 * v + 1] - lo[1]) * scale);
+            key[v] = hilbert_index(ix, iy, order);
+        }
+        std::stable_sort(T.v_new2old.begin(), T.v_new2old.end(),
+                         [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    }
+    if (!T.ghost.empty())
+        std::stable_partition(T.v_new2old.begin(), T.v_new2old.end(), [&](int32_t v) { return T.ghost[v] < 0; });
+    T.v_old2new.resize(nv);
+    for (int64_t i = 0; i < nv; ++i) T.v_old2new[T.v_new2old[i]] = (int32_t)i;
+    T.e_new2old.resize(T.ne);
+    std::iota(T.e_new2old.begin(), T.e_new2old.end(), 0);
+    if (o.renumber) {
+        std::vector<uint64_t> key(T.ne);
+        for (int64_t k = 0; k < T.ne; ++k) {
+            uint32_t a = (uint32_t)T.v_old2new[T.edge[2 * k]], b = (uint32_t)T.v_old2new[T.edge[2 * k + 1]];
+            if (a > b) std::swap(a, b);
+            key[k] = ((uint64_t)a << 32) | b;
+        }
+        std::sort(T.e_new2old.begin(), T.e_new2old.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    }
+    {
+        std::vector<uint8_t> active(T.ne, 0);
+        for (int32_t e : T.eid) active[e] = 1;
+        T.ne_active = 0;
+        for (int64_t k = 0; k < T.ne; ++k) T.ne_active += active[k];
+        std::stable_partition(T.e_new2old.begin(), T.e_new2old.end(), [&](int32_t e) { return active[e] != 0; });
+    }
+    T.e_old2new.resize(T.ne);
+    for (int64_t i = 0; i < T.ne; ++i) T.e_old2new[T.e_new2old[i]] = (int32_t)i;
+    return FDU_OK;
+}
+
+}  // namespace fdu

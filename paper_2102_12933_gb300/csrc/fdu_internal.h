@@ -1,0 +1,55 @@
+// Internal host-side structures of libfdu (not part of the C-ABI).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fdu.h"
+
+namespace fdu {
+
+// Per-side coefficient block of the difference-form NU-WENO5 (21 values):
+//   value  A[k][2] : u~_k - u_c   = A[k][0]*d_a + A[k][1]*d_b
+//   slope  P[k][2] : dx u~_k'(0)  (same differences)
+//   curv   Q[k][2] : sqrt(13/12) dx^2 u~_k''
+//   linear C[3]
+// where the differences for sub-stencil k are taken against the shared
+// point x_i and use the slots (k=0: x_{i-2}, x_{i-1}), (k=1: x_{i-1},
+// x_{i+1}), (k=2: x_{i+1}, x_{i+2}).
+constexpr int kSideCoef = 21;
+constexpr int kEdgeCoef = 2 * kSideCoef + 2;  // left, right, normal (nx, ny)
+
+struct HostTables {
+    int64_t nv = 0, nt = 0, ne = 0, n_real = 0;
+    int64_t ne_active = 0;         // edges used by some divergence stencil (internal ids 0..ne_active-1)
+    double Lx = 0, Ly = 0, gamma = 1.4;
+    int degree = 2, levels = 2;
+    std::vector<double> xy;        // [nv][2]
+    std::vector<int32_t> ghost;    // [nv] donor or -1 (empty = no ghosts)
+    // original-id structures
+    std::vector<int32_t> edge;     // [ne][2] v0 < v1, sorted
+    std::vector<double> nrm;       // [ne][2]
+    std::vector<int64_t> adj_off;  // [nv+1]
+    std::vector<int32_t> adj;      // neighbour ids ascending
+    std::vector<int32_t> adj_edge; // edge id per adjacency entry
+    std::vector<int32_t> sten;     // [ne][6] (-1 when the edge has no stencil)
+    std::vector<double> xi;        // [ne][6]
+    std::vector<double> coef;      // [ne][kEdgeCoef] FP64 (edges without stencil: zeros)
+    std::vector<int64_t> voff, eoff; // [nv+1]
+    std::vector<int32_t> vid, eid;
+    std::vector<double> wf, wg, we;
+    std::vector<double> hmin;      // [nv] shortest edge at each vertex
+    // renumbering: internal order -> original and back.  Internal vertex
+    // order puts real vertices first (0..n_real-1), ghosts after; internal
+    // edge order puts active edges first.
+    std::vector<int32_t> v_new2old, v_old2new, e_new2old, e_old2new;
+};
+
+// Build every host table.  Returns FDU_OK or an error code with `err` set.
+int build_host_tables(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts &o,
+                      HostTables &T, std::string &err);
+
+// Per-side coefficient block from five normalised coordinates (exposed for tests through the C-ABI builder).
+void side_coefficients(const double x[5], double out[kSideCoef]);
+
+}  // namespace fdu

@@ -1,0 +1,680 @@
+// sm_103a kernels of the unstructured-mesh FDM residual and SSP-RK3 stage.
+//
+//   edge flux  : per edge, gather the six states of its 1D curvilinear
+//                stencil, project differences on the characteristic
+//                fields of the Roe average of the edge's end states,
+//                interpolate each field to the edge midpoint with
+//                non-uniform WENO5 from both sides (Appendix), back-project
+//                and evaluate a Roe flux along the edge (Section 2.3.1).
+//   divergence : per vertex, a1 + b2 of the least-squares fit, i.e. the
+//                weighted sum of vertex fluxes f_j, g_j and edge fluxes r_k
+//                (Section 2.2.1), SELL-32 layout (a warp reads 32
+//                consecutive ids / weights per entry); optionally fused
+//                with the SSP-RK3 stage combination and the vertex fluxes
+//                of the new state.
+//
+// Everything is gather-bound or scalar-ALU-bound: there is no dense
+// contraction, so no tensor-core path.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fdu_internal.h"
+#include "fdu_kernels.cuh"
+
+namespace fdu {
+namespace {
+
+// ------------------------------------------------------------------ helpers
+// A conservative FP64 record (rho, rho u, rho v, rho E), 16-byte aligned.
+struct __align__(16) dbl4 {
+    double x, y, z, w;
+};
+__device__ __forceinline__ dbl4 dbl4_make(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
+__device__ __forceinline__ dbl4 ld4(const double *p, int64_t i) {
+    const double2 *q = reinterpret_cast<const double2 *>(p + 4 * i);
+    const double2 a = __ldg(q), b = __ldg(q + 1);
+    return dbl4_make(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st4(double *p, int64_t i, dbl4 v) {
+    double2 *q = reinterpret_cast<double2 *>(p + 4 * i);
+    q[0] = make_double2(v.x, v.y);
+    q[1] = make_double2(v.z, v.w);
+}
+__device__ __forceinline__ dbl4 sub4(dbl4 a, dbl4 b) {
+    return dbl4_make(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ dbl4 add4(dbl4 a, dbl4 b) {
+    return dbl4_make(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ dbl4 neg4(dbl4 a) { return dbl4_make(-a.x, -a.y, -a.z, -a.w); }
+
+// Per-state quantities reused by the Roe average and the physical flux.
+struct Prim64 {
+    double r;   // rho^-1/2
+    double ir;  // 1/rho
+    double p;   // pressure
+};
+__device__ __forceinline__ Prim64 prim64(const dbl4 &w, double gm1) {
+    Prim64 q;
+    q.r = rsqrt(w.x);
+    q.ir = q.r * q.r;
+    q.p = gm1 * (w.w - 0.5 * (w.y * w.y + w.z * w.z) * q.ir);
+    return q;
+}
+
+// Roe average of two states (weights sqrt(rho)) and the eigen-quantities
+// of the flux Jacobian along n.
+struct Roe64 {
+    double u, v, H, c, ic, b1, qn, qt, hq2, nx, ny;
+};
+__device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const dbl4 &b, const Prim64 &pb,
+                                      double nx, double ny, double gm1) {
+    Roe64 R;
+    const double sa = a.x * pa.r, sb = b.x * pb.r;
+    const double inv = 1.0 / (sa + sb);
+    R.u = (a.y * pa.r + b.y * pb.r) * inv;
+    R.v = (a.z * pa.r + b.z * pb.r) * inv;
+    R.H = ((a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r) * inv;
+    R.hq2 = 0.5 * (R.u * R.u + R.v * R.v);
+    const double c2 = gm1 * (R.H - R.hq2);
+    R.ic = rsqrt(c2);
+    R.c = c2 * R.ic;
+    R.b1 = gm1 * R.ic * R.ic;
+    R.nx = nx;
+    R.ny = ny;
+    R.qn = R.u * nx + R.v * ny;
+    R.qt = R.v * nx - R.u * ny;
+    return R;
+}
+
+// Characteristic components of a conservative difference (left eigenvectors
+// of dF_n/dw at the Roe state; fields ordered q_n - c, q_n (entropy), q_n
+// (shear), q_n + c).
+__device__ __forceinline__ dbl4 project64(const Roe64 &R, const dbl4 &d) {
+    const double phi = R.b1 * (R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w);
+    const double psi = (R.qn * d.x - R.nx * d.y - R.ny * d.z) * R.ic;
+    return dbl4_make(0.5 * (phi + psi), d.x - phi, R.nx * d.z - R.ny * d.y - R.qt * d.x, 0.5 * (phi - psi));
+}
+// Conservative difference from characteristic components (right eigenvectors).
+__device__ __forceinline__ dbl4 unproject64(const Roe64 &R, const dbl4 &c) {
+    const double rho = c.x + c.y + c.w;
+    const double dd = R.c * (c.w - c.x);
+    return dbl4_make(rho, R.u * rho + R.nx * dd - R.ny * c.z, R.v * rho + R.ny * dd + R.nx * c.z,
+                        R.H * (c.x + c.w) + R.hq2 * c.y + R.qn * dd + R.qt * c.z);
+}
+
+// NU-WENO5 increment u~ - u_c of one field from the four differences
+// (a, b, c, d) = (u_{i-2}, u_{i-1}, u_{i+1}, u_{i+2}) - u_i, with the
+// side's coefficient block k (see fdu_internal.h).  The nonlinear weights
+// alpha_k = C_k / (beta_k + eps), omega = alpha / sum(alpha) (p = 1) are
+// applied as C_k prod_{l != k} (beta_l + eps) over their sum, which is the
+// same quotient with one division.
+__device__ __forceinline__ double weno64(const double *k, double a, double b, double c, double d, double eps) {
+    const double v0 = fma(k[0], a, k[1] * b);
+    const double v1 = fma(k[2], b, k[3] * c);
+    const double v2 = fma(k[4], c, k[5] * d);
+    const double p0 = fma(k[6], a, k[7] * b);
+    const double p1 = fma(k[8], b, k[9] * c);
+    const double p2 = fma(k[10], c, k[11] * d);
+    const double q0 = fma(k[12], a, k[13] * b);
+    const double q1 = fma(k[14], b, k[15] * c);
+    const double q2 = fma(k[16], c, k[17] * d);
+    const double b0 = fma(p0, p0, fma(q0, q0, eps));
+    const double b1 = fma(p1, p1, fma(q1, q1, eps));
+    const double b2 = fma(p2, p2, fma(q2, q2, eps));
+    const double t0 = k[18] * (b1 * b2);
+    const double t1 = k[19] * (b0 * b2);
+    const double t2 = k[20] * (b0 * b1);
+    return fma(t0, v0, fma(t1, v1, t2 * v2)) / (t0 + t1 + t2);
+}
+
+__device__ __forceinline__ void load_side(const double *__restrict__ coef, int64_t ne, int64_t e, int base,
+                                          double *k) {
+#pragma unroll
+    for (int i = 0; i < kSideCoef; ++i) k[i] = __ldg(coef + (int64_t)(base + i) * ne + e);
+}
+
+// ------------------------------------------------------------------ FP64 edge flux
+__global__ void __launch_bounds__(kEdgeBlock) edge_flux_f64_kernel(EdgeArgs A) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= A.ne) return;
+    const double *__restrict__ w = static_cast<const double *>(A.w);
+    const double *__restrict__ coef = static_cast<const double *>(A.coef);
+    const double gm1 = A.gamma - 1.0;
+    const int64_t ne = A.ne;
+    int32_t s[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
+    const dbl4 L1 = ld4(w, s[2]), R1 = ld4(w, s[3]);
+    const double nx = __ldg(coef + (int64_t)(2 * kSideCoef) * ne + e);
+    const double ny = __ldg(coef + (int64_t)(2 * kSideCoef + 1) * ne + e);
+
+    // characteristic decomposition at the Roe average of the end states
+    const Prim64 pL1 = prim64(L1, gm1), pR1 = prim64(R1, gm1);
+    const Roe64 C = roe64(L1, pL1, R1, pR1, nx, ny, gm1);
+    const dbl4 cM = project64(C, sub4(R1, L1));               // R1 - L1
+    const dbl4 cL2 = project64(C, sub4(ld4(w, s[1]), L1));    // L2 - L1
+    const dbl4 cL3 = project64(C, sub4(ld4(w, s[0]), L1));    // L3 - L1
+    const dbl4 cR2 = project64(C, sub4(ld4(w, s[4]), R1));    // R2 - R1
+    const dbl4 cR3 = project64(C, sub4(ld4(w, s[5]), R1));    // R3 - R1
+
+    double k[kSideCoef];
+    // left state: centre L1, differences (L3, L2, R1, R2) - L1
+    load_side(coef, ne, e, 0, k);
+    const dbl4 cR2L = add4(cR2, cM);
+    dbl4 dl;
+    dl.x = weno64(k, cL3.x, cL2.x, cM.x, cR2L.x, A.eps);
+    dl.y = weno64(k, cL3.y, cL2.y, cM.y, cR2L.y, A.eps);
+    dl.z = weno64(k, cL3.z, cL2.z, cM.z, cR2L.z, A.eps);
+    dl.w = weno64(k, cL3.w, cL2.w, cM.w, cR2L.w, A.eps);
+    // right state (mirrored stencil): centre R1, differences (R3, R2, L1, L2) - R1
+    load_side(coef, ne, e, kSideCoef, k);
+    const dbl4 nM = neg4(cM);
+    const dbl4 cL2R = sub4(cL2, cM);
+    dbl4 dr;
+    dr.x = weno64(k, cR3.x, cR2.x, nM.x, cL2R.x, A.eps);
+    dr.y = weno64(k, cR3.y, cR2.y, nM.y, cL2R.y, A.eps);
+    dr.z = weno64(k, cR3.z, cR2.z, nM.z, cL2R.z, A.eps);
+    dr.w = weno64(k, cR3.w, cR2.w, nM.w, cL2R.w, A.eps);
+
+    dbl4 wl = add4(L1, unproject64(C, dl));
+    dbl4 wr = add4(R1, unproject64(C, dr));
+    Prim64 pl, pr;
+    bool ok = wl.x > 0.0 && wr.x > 0.0;
+    if (ok) {
+        pl = prim64(wl, gm1);
+        pr = prim64(wr, gm1);
+        ok = pl.p > 0.0 && pr.p > 0.0;
+    }
+    if (!ok) {  // positivity fallback: first-order end states
+        wl = L1;
+        wr = R1;
+        pl = pL1;
+        pr = pR1;
+        atomicAdd(A.fallback, 1ull);
+    }
+
+    // Roe flux with Harten's entropy fix (delta = 0.1 c)
+    const Roe64 Q = roe64(wl, pl, wr, pr, nx, ny, gm1);
+    const dbl4 a = project64(Q, sub4(wr, wl));
+    const double delta = 0.1 * Q.c, h2d = 5.0 * Q.ic;  // 1 / (2 delta)
+    auto fix = [&](double l) {
+        const double m = fabs(l);
+        return m < delta ? fma(l, l, delta * delta) * h2d : m;
+    };
+    const double lu = fix(Q.qn), lm = fix(Q.qn - Q.c), lp = fix(Q.qn + Q.c);
+    const dbl4 D = unproject64(Q, dbl4_make(lm * a.x, lu * a.y, lu * a.z, lp * a.w));
+    const double qnl = (wl.y * nx + wl.z * ny) * pl.ir, qnr = (wr.y * nx + wr.z * ny) * pr.ir;
+    dbl4 f;
+    f.x = 0.5 * (wl.x * qnl + wr.x * qnr - D.x);
+    f.y = 0.5 * (fma(wl.y, qnl, pl.p * nx) + fma(wr.y, qnr, pr.p * nx) - D.y);
+    f.z = 0.5 * (fma(wl.z, qnl, pl.p * ny) + fma(wr.z, qnr, pr.p * ny) - D.z);
+    f.w = 0.5 * ((wl.w + pl.p) * qnl + (wr.w + pr.p) * qnr - D.w);
+    st4(static_cast<double *>(A.r), e, f);
+}
+
+// ------------------------------------------------------------------ vertex fluxes
+__device__ __forceinline__ void euler_fg(const dbl4 &w, double gm1, dbl4 &f, dbl4 &g) {
+    const double ir = 1.0 / w.x;
+    const double u = w.y * ir, v = w.z * ir;
+    const double p = gm1 * (w.w - 0.5 * (w.y * u + w.z * v));
+    f = dbl4_make(w.y, fma(w.y, u, p), w.z * u, (w.w + p) * u);
+    g = dbl4_make(w.z, w.y * v, fma(w.z, v, p), (w.w + p) * v);
+}
+
+__global__ void vertex_flux_f64_kernel(const double *__restrict__ w, double *__restrict__ F, int64_t n,
+                                       double gm1) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    dbl4 f, g;
+    euler_fg(ld4(w, v), gm1, f, g);
+    st4(F, 2 * v, f);
+    st4(F, 2 * v + 1, g);
+}
+
+// ------------------------------------------------------------------ FP64 divergence (+ RK stage)
+template <int MODE>
+__global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= A.n_real) return;
+    const int64_t sl = v / kSell;
+    const int lane = (int)(v % kSell);
+    const double *__restrict__ F = static_cast<const double *>(A.F);
+    const double *__restrict__ r = static_cast<const double *>(A.r);
+    const double *__restrict__ wf = static_cast<const double *>(A.wf);
+    const double *__restrict__ wg = static_cast<const double *>(A.wg);
+    const double *__restrict__ we = static_cast<const double *>(A.we);
+    dbl4 acc = dbl4_make(0, 0, 0, 0);
+    {
+        const int64_t b = __ldg(A.slice_voff + sl) + lane, e = __ldg(A.slice_voff + sl + 1);
+        for (int64_t p = b; p < e; p += kSell) {
+            const int32_t j = __ldg(A.vid + p);
+            const double a = __ldg(wf + p), c = __ldg(wg + p);
+            const dbl4 f = ld4(F, 2 * (int64_t)j), g = ld4(F, 2 * (int64_t)j + 1);
+            acc.x = fma(a, f.x, fma(c, g.x, acc.x));
+            acc.y = fma(a, f.y, fma(c, g.y, acc.y));
+            acc.z = fma(a, f.z, fma(c, g.z, acc.z));
+            acc.w = fma(a, f.w, fma(c, g.w, acc.w));
+        }
+    }
+    {
+        const int64_t b = __ldg(A.slice_eoff + sl) + lane, e = __ldg(A.slice_eoff + sl + 1);
+        for (int64_t p = b; p < e; p += kSell) {
+            const int32_t k = __ldg(A.eid + p);
+            const double a = __ldg(we + p);
+            const dbl4 q = ld4(r, k);
+            acc.x = fma(a, q.x, acc.x);
+            acc.y = fma(a, q.y, acc.y);
+            acc.z = fma(a, q.z, acc.z);
+            acc.w = fma(a, q.w, acc.w);
+        }
+    }
+    {
+        const double *cfg = static_cast<const double *>(A.cfg);
+        const double cf = __ldg(cfg + v), cg = __ldg(cfg + A.n_real + v);
+        const dbl4 f = ld4(F, 2 * v), g = ld4(F, 2 * v + 1);
+        acc.x = fma(cf, f.x, fma(cg, g.x, acc.x));
+        acc.y = fma(cf, f.y, fma(cg, g.y, acc.y));
+        acc.z = fma(cf, f.z, fma(cg, g.z, acc.z));
+        acc.w = fma(cf, f.w, fma(cg, g.w, acc.w));
+    }
+    const dbl4 L = neg4(acc);  // dw/dt = -(a1 + b2)
+    if (MODE == 0) {
+        const int64_t row = A.out_map ? (int64_t)__ldg(A.out_map + v) : v;
+        st4(A.out, row, L);
+        return;
+    }
+    const double dt = A.dt_dev ? *A.dt_dev : A.dt;
+    const dbl4 ws = ld4(A.ws, v);
+    dbl4 o;
+    if (MODE == 1) {
+        o = dbl4_make(fma(dt, L.x, ws.x), fma(dt, L.y, ws.y), fma(dt, L.z, ws.z), fma(dt, L.w, ws.w));
+    } else {
+        const dbl4 wn = ld4(A.wn, v);
+        const double cn = MODE == 2 ? 0.75 : 1.0 / 3.0;
+        const double cs = MODE == 2 ? 0.25 : 2.0 / 3.0;
+        o.x = fma(cn, wn.x, cs * fma(dt, L.x, ws.x));
+        o.y = fma(cn, wn.y, cs * fma(dt, L.y, ws.y));
+        o.z = fma(cn, wn.z, cs * fma(dt, L.z, ws.z));
+        o.w = fma(cn, wn.w, cs * fma(dt, L.w, ws.w));
+    }
+    st4(A.wout, v, o);
+    dbl4 f, g;
+    euler_fg(o, A.gamma - 1.0, f, g);
+    double *Fo = static_cast<double *>(A.Fout);
+    st4(Fo, 2 * v, f);
+    st4(Fo, 2 * v + 1, g);
+}
+
+// ================================================================== FP32 path
+// The FP32 residual reads an FP32 copy of the state and compact edge
+// geometry (four outer curve coordinates and the normal) and builds the
+// NU-WENO5 coefficients in registers; weights, fluxes and sums are FP32.
+__device__ __forceinline__ float4 sub4f(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 add4f(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+struct Prim32 {
+    float r, ir, p;
+};
+__device__ __forceinline__ Prim32 prim32(const float4 &w, float gm1) {
+    Prim32 q;
+    q.r = rsqrtf(w.x);
+    q.ir = q.r * q.r;
+    q.p = gm1 * (w.w - 0.5f * (w.y * w.y + w.z * w.z) * q.ir);
+    return q;
+}
+struct Roe32 {
+    float u, v, H, c, ic, b1, qn, qt, hq2, nx, ny;
+};
+__device__ __forceinline__ Roe32 roe32(const float4 &a, const Prim32 &pa, const float4 &b, const Prim32 &pb, float nx,
+                                      float ny, float gm1) {
+    Roe32 R;
+    const float sa = a.x * pa.r, sb = b.x * pb.r;
+    const float inv = __frcp_rn(sa + sb);
+    R.u = (a.y * pa.r + b.y * pb.r) * inv;
+    R.v = (a.z * pa.r + b.z * pb.r) * inv;
+    R.H = ((a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r) * inv;
+    R.hq2 = 0.5f * (R.u * R.u + R.v * R.v);
+    const float c2 = gm1 * (R.H - R.hq2);
+    R.ic = rsqrtf(c2);
+    R.c = c2 * R.ic;
+    R.b1 = gm1 * R.ic * R.ic;
+    R.nx = nx;
+    R.ny = ny;
+    R.qn = R.u * nx + R.v * ny;
+    R.qt = R.v * nx - R.u * ny;
+    return R;
+}
+__device__ __forceinline__ float4 project32(const Roe32 &R, const float4 &d) {
+    const float phi = R.b1 * (R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w);
+    const float psi = (R.qn * d.x - R.nx * d.y - R.ny * d.z) * R.ic;
+    return make_float4(0.5f * (phi + psi), d.x - phi, R.nx * d.z - R.ny * d.y - R.qt * d.x, 0.5f * (phi - psi));
+}
+__device__ __forceinline__ float4 unproject32(const Roe32 &R, const float4 &c) {
+    const float rho = c.x + c.y + c.w;
+    const float dd = R.c * (c.w - c.x);
+    return make_float4(rho, R.u * rho + R.nx * dd - R.ny * c.z, R.v * rho + R.ny * dd + R.nx * c.z,
+                       R.H * (c.x + c.w) + R.hq2 * c.y + R.qn * dd + R.qt * c.z);
+}
+
+// Coefficient block of one side in FP32 from x[5] (x[2] = -1/2, x[3] = 1/2).
+__device__ __forceinline__ void side_coef32(const float x[5], float *k) {
+    const float curv = 1.0408329997330663f;  // sqrt(13/12); dx = 1 in normalised coordinates
+    float val[3][3], der[3][3], sec[3][3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float pj = x[s + j], pa = x[s + (j + 1) % 3], pb = x[s + (j + 2) % 3];
+            const float id = __frcp_rn((pj - pa) * (pj - pb));
+            val[s][j] = pa * pb * id;
+            der[s][j] = -(pa + pb) * id;
+            sec[s][j] = 2.0f * id;
+        }
+    }
+    k[0] = val[0][0]; k[1] = val[0][1]; k[2] = val[1][0]; k[3] = val[1][2]; k[4] = val[2][1]; k[5] = val[2][2];
+    k[6] = der[0][0]; k[7] = der[0][1]; k[8] = der[1][0]; k[9] = der[1][2]; k[10] = der[2][1]; k[11] = der[2][2];
+    k[12] = curv * sec[0][0]; k[13] = curv * sec[0][1]; k[14] = curv * sec[1][0];
+    k[15] = curv * sec[1][2]; k[16] = curv * sec[2][1]; k[17] = curv * sec[2][2];
+    // degree-4 Lagrange weights at 0 of x[0] and x[4]
+    const float l0 = (x[1] * x[2] * x[3] * x[4]) *
+                     __frcp_rn((x[0] - x[1]) * (x[0] - x[2]) * (x[0] - x[3]) * (x[0] - x[4]));
+    const float l4 = (x[0] * x[1] * x[2] * x[3]) *
+                     __frcp_rn((x[4] - x[0]) * (x[4] - x[1]) * (x[4] - x[2]) * (x[4] - x[3]));
+    const float c0 = l0 * __frcp_rn(val[0][0]);
+    const float c2 = l4 * __frcp_rn(val[2][2]);
+    k[18] = c0;
+    k[19] = 1.0f - c0 - c2;
+    k[20] = c2;
+}
+
+// FP32 weights: alpha_k = C_k / (beta_k + eps32), omega = alpha / sum alpha.
+__device__ __forceinline__ float weno32(const float *k, float a, float b, float c, float d, float eps) {
+    const float v0 = fmaf(k[0], a, k[1] * b);
+    const float v1 = fmaf(k[2], b, k[3] * c);
+    const float v2 = fmaf(k[4], c, k[5] * d);
+    const float p0 = fmaf(k[6], a, k[7] * b);
+    const float p1 = fmaf(k[8], b, k[9] * c);
+    const float p2 = fmaf(k[10], c, k[11] * d);
+    const float q0 = fmaf(k[12], a, k[13] * b);
+    const float q1 = fmaf(k[14], b, k[15] * c);
+    const float q2 = fmaf(k[16], c, k[17] * d);
+    const float a0 = k[18] * __frcp_rn(fmaf(p0, p0, fmaf(q0, q0, eps)));
+    const float a1 = k[19] * __frcp_rn(fmaf(p1, p1, fmaf(q1, q1, eps)));
+    const float a2 = k[20] * __frcp_rn(fmaf(p2, p2, fmaf(q2, q2, eps)));
+    return fmaf(a0, v0, fmaf(a1, v1, a2 * v2)) * __frcp_rn(a0 + a1 + a2);
+}
+
+__global__ void __launch_bounds__(kEdgeBlock) edge_flux_f32_kernel(EdgeArgs A) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= A.ne) return;
+    const float4 *__restrict__ w = static_cast<const float4 *>(A.w);
+    const float *__restrict__ g = static_cast<const float *>(A.coef);
+    const float gm1 = (float)(A.gamma - 1.0);
+    const float eps = (float)A.eps;
+    const int64_t ne = A.ne;
+    int32_t s[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
+    const float x0 = __ldg(g + e), x1 = __ldg(g + ne + e), x4 = __ldg(g + 2 * ne + e), x5 = __ldg(g + 3 * ne + e);
+    const float nx = __ldg(g + 4 * ne + e), ny = __ldg(g + 5 * ne + e);
+    const float4 L1 = __ldg(w + s[2]), R1 = __ldg(w + s[3]);
+    const Prim32 pL1 = prim32(L1, gm1), pR1 = prim32(R1, gm1);
+    const Roe32 C = roe32(L1, pL1, R1, pR1, nx, ny, gm1);
+    const float4 cM = project32(C, sub4f(R1, L1));
+    const float4 cL2 = project32(C, sub4f(__ldg(w + s[1]), L1));
+    const float4 cL3 = project32(C, sub4f(__ldg(w + s[0]), L1));
+    const float4 cR2 = project32(C, sub4f(__ldg(w + s[4]), R1));
+    const float4 cR3 = project32(C, sub4f(__ldg(w + s[5]), R1));
+
+    float k[kSideCoef];
+    {
+        const float xl[5] = {x0, x1, -0.5f, 0.5f, x4};
+        side_coef32(xl, k);
+    }
+    const float4 cR2L = add4f(cR2, cM);
+    float4 dl;
+    dl.x = weno32(k, cL3.x, cL2.x, cM.x, cR2L.x, eps);
+    dl.y = weno32(k, cL3.y, cL2.y, cM.y, cR2L.y, eps);
+    dl.z = weno32(k, cL3.z, cL2.z, cM.z, cR2L.z, eps);
+    dl.w = weno32(k, cL3.w, cL2.w, cM.w, cR2L.w, eps);
+    {
+        const float xr[5] = {-x5, -x4, -0.5f, 0.5f, -x1};
+        side_coef32(xr, k);
+    }
+    const float4 cL2R = sub4f(cL2, cM);
+    float4 dr;
+    dr.x = weno32(k, cR3.x, cR2.x, -cM.x, cL2R.x, eps);
+    dr.y = weno32(k, cR3.y, cR2.y, -cM.y, cL2R.y, eps);
+    dr.z = weno32(k, cR3.z, cR2.z, -cM.z, cL2R.z, eps);
+    dr.w = weno32(k, cR3.w, cR2.w, -cM.w, cL2R.w, eps);
+
+    float4 wl = add4f(L1, unproject32(C, dl));
+    float4 wr = add4f(R1, unproject32(C, dr));
+    Prim32 pl, pr;
+    bool ok = wl.x > 0.f && wr.x > 0.f;
+    if (ok) {
+        pl = prim32(wl, gm1);
+        pr = prim32(wr, gm1);
+        ok = pl.p > 0.f && pr.p > 0.f;
+    }
+    if (!ok) {
+        wl = L1;
+        wr = R1;
+        pl = pL1;
+        pr = pR1;
+        atomicAdd(A.fallback, 1ull);
+    }
+    const Roe32 Q = roe32(wl, pl, wr, pr, nx, ny, gm1);
+    const float4 a = project32(Q, sub4f(wr, wl));
+    const float delta = 0.1f * Q.c, h2d = 5.0f * Q.ic;
+    auto fix = [&](float l) {
+        const float m = fabsf(l);
+        return m < delta ? fmaf(l, l, delta * delta) * h2d : m;
+    };
+    const float lu = fix(Q.qn), lm = fix(Q.qn - Q.c), lp = fix(Q.qn + Q.c);
+    const float4 D = unproject32(Q, make_float4(lm * a.x, lu * a.y, lu * a.z, lp * a.w));
+    const float qnl = (wl.y * nx + wl.z * ny) * pl.ir, qnr = (wr.y * nx + wr.z * ny) * pr.ir;
+    float4 f;
+    f.x = 0.5f * (wl.x * qnl + wr.x * qnr - D.x);
+    f.y = 0.5f * (fmaf(wl.y, qnl, pl.p * nx) + fmaf(wr.y, qnr, pr.p * nx) - D.y);
+    f.z = 0.5f * (fmaf(wl.z, qnl, pl.p * ny) + fmaf(wr.z, qnr, pr.p * ny) - D.z);
+    f.w = 0.5f * ((wl.w + pl.p) * qnl + (wr.w + pr.p) * qnr - D.w);
+    static_cast<float4 *>(A.r)[e] = f;
+}
+
+__device__ __forceinline__ void euler_fg32(const float4 &w, float gm1, float4 &f, float4 &g) {
+    const float ir = __frcp_rn(w.x);
+    const float u = w.y * ir, v = w.z * ir;
+    const float p = gm1 * (w.w - 0.5f * (w.y * u + w.z * v));
+    f = make_float4(w.y, fmaf(w.y, u, p), w.z * u, (w.w + p) * u);
+    g = make_float4(w.z, w.y * v, fmaf(w.z, v, p), (w.w + p) * v);
+}
+
+__global__ void vertex_flux_f32_kernel(const double *__restrict__ w, float4 *__restrict__ F, float4 *__restrict__ w32,
+                                       int64_t n, float gm1) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const dbl4 d = ld4(w, v);
+    const float4 s = make_float4((float)d.x, (float)d.y, (float)d.z, (float)d.w);
+    w32[v] = s;
+    float4 f, g;
+    euler_fg32(s, gm1, f, g);
+    F[2 * v] = f;
+    F[2 * v + 1] = g;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= A.n_real) return;
+    const int64_t sl = v / kSell;
+    const int lane = (int)(v % kSell);
+    const float4 *__restrict__ F = static_cast<const float4 *>(A.F);
+    const float4 *__restrict__ r = static_cast<const float4 *>(A.r);
+    const float *__restrict__ wf = static_cast<const float *>(A.wf);
+    const float *__restrict__ wg = static_cast<const float *>(A.wg);
+    const float *__restrict__ we = static_cast<const float *>(A.we);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    {
+        const int64_t b = __ldg(A.slice_voff + sl) + lane, e = __ldg(A.slice_voff + sl + 1);
+        for (int64_t p = b; p < e; p += kSell) {
+            const int32_t j = __ldg(A.vid + p);
+            const float a = __ldg(wf + p), c = __ldg(wg + p);
+            const float4 f = __ldg(F + 2 * (int64_t)j), g = __ldg(F + 2 * (int64_t)j + 1);
+            acc.x = fmaf(a, f.x, fmaf(c, g.x, acc.x));
+            acc.y = fmaf(a, f.y, fmaf(c, g.y, acc.y));
+            acc.z = fmaf(a, f.z, fmaf(c, g.z, acc.z));
+            acc.w = fmaf(a, f.w, fmaf(c, g.w, acc.w));
+        }
+    }
+    {
+        const int64_t b = __ldg(A.slice_eoff + sl) + lane, e = __ldg(A.slice_eoff + sl + 1);
+        for (int64_t p = b; p < e; p += kSell) {
+            const int32_t k = __ldg(A.eid + p);
+            const float a = __ldg(we + p);
+            const float4 q = __ldg(r + k);
+            acc.x = fmaf(a, q.x, acc.x);
+            acc.y = fmaf(a, q.y, acc.y);
+            acc.z = fmaf(a, q.z, acc.z);
+            acc.w = fmaf(a, q.w, acc.w);
+        }
+    }
+    {
+        const float *cfg = static_cast<const float *>(A.cfg);
+        const float cf = __ldg(cfg + v), cg = __ldg(cfg + A.n_real + v);
+        const float4 f = __ldg(F + 2 * v), g = __ldg(F + 2 * v + 1);
+        acc.x = fmaf(cf, f.x, fmaf(cg, g.x, acc.x));
+        acc.y = fmaf(cf, f.y, fmaf(cg, g.y, acc.y));
+        acc.z = fmaf(cf, f.z, fmaf(cg, g.z, acc.z));
+        acc.w = fmaf(cf, f.w, fmaf(cg, g.w, acc.w));
+    }
+    const dbl4 L = dbl4_make(-(double)acc.x, -(double)acc.y, -(double)acc.z, -(double)acc.w);
+    if (MODE == 0) {
+        const int64_t row = A.out_map ? (int64_t)__ldg(A.out_map + v) : v;
+        st4(A.out, row, L);
+        return;
+    }
+    // SSP-RK3 combination in FP64
+    const double dt = A.dt_dev ? *A.dt_dev : A.dt;
+    const dbl4 ws = ld4(A.ws, v);
+    dbl4 o;
+    if (MODE == 1) {
+        o = dbl4_make(fma(dt, L.x, ws.x), fma(dt, L.y, ws.y), fma(dt, L.z, ws.z), fma(dt, L.w, ws.w));
+    } else {
+        const dbl4 wn = ld4(A.wn, v);
+        const double cn = MODE == 2 ? 0.75 : 1.0 / 3.0;
+        const double cs = MODE == 2 ? 0.25 : 2.0 / 3.0;
+        o.x = fma(cn, wn.x, cs * fma(dt, L.x, ws.x));
+        o.y = fma(cn, wn.y, cs * fma(dt, L.y, ws.y));
+        o.z = fma(cn, wn.z, cs * fma(dt, L.z, ws.z));
+        o.w = fma(cn, wn.w, cs * fma(dt, L.w, ws.w));
+    }
+    st4(A.wout, v, o);
+    const float4 s32 = make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.w);
+    A.w32out[v] = s32;
+    float4 f, g;
+    euler_fg32(s32, (float)(A.gamma - 1.0), f, g);
+    float4 *Fo = static_cast<float4 *>(A.Fout);
+    Fo[2 * v] = f;
+    Fo[2 * v + 1] = g;
+}
+
+// ------------------------------------------------------------------ support kernels
+__global__ void permute_rows_kernel(const double *__restrict__ in, double *__restrict__ out,
+                                    const int32_t *__restrict__ map, int64_t n, bool gather) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t m = __ldg(map + i);
+    if (gather) st4(out, i, ld4(in, m));  // out[i] = in[map[i]]
+    else st4(out, m, ld4(in, i));         // out[map[i]] = in[i]
+}
+
+// Ghost vertices (internal ids n_real .. n_real+n_ghost-1) copy their
+// donor's state and fluxes (transmissive boundary reading).  F holds
+// `fq` 16-byte words per vertex.
+__global__ void ghost_fill_kernel(double *__restrict__ w, uint4 *__restrict__ F, int fq, float4 *__restrict__ w32,
+                                  const int32_t *__restrict__ donor, int64_t n_real, int64_t n_ghost) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_ghost) return;
+    const int64_t g = n_real + i, d = __ldg(donor + i);
+    if (w) st4(w, g, ld4(w, d));
+    if (F)
+        for (int c = 0; c < fq; ++c) F[fq * g + c] = F[fq * d + c];
+    if (w32) w32[g] = w32[d];
+}
+
+// min over vertices of h_v / (|u| + c), as the bit pattern of a positive double
+__global__ void max_dt_kernel(const double *__restrict__ w, const double *__restrict__ hmin, int64_t n, double gamma,
+                              unsigned long long *slot) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double t = INFINITY;
+    if (v < n) {
+        const dbl4 s = ld4(w, v);
+        const double ir = 1.0 / s.x;
+        const double u = s.y * ir, vv = s.z * ir;
+        const double p = (gamma - 1.0) * (s.w - 0.5 * (s.y * u + s.z * vv));
+        const double c = sqrt(gamma * p * ir);
+        t = hmin[v] / (sqrt(u * u + vv * vv) + c);
+        if (!(t > 0)) t = 0;  // non-physical state: report dt = 0
+    }
+    for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(slot, (unsigned long long)__double_as_longlong(t));
+}
+
+inline unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+void launch_vertex_flux_f64(const double *w, double *F, int64_t n, double gamma, cudaStream_t s) {
+    if (n > 0) vertex_flux_f64_kernel<<<blocks(n, 256), 256, 0, s>>>(w, F, n, gamma - 1.0);
+}
+void launch_vertex_flux_f32(const double *w, float4 *F, float4 *w32, int64_t n, double gamma, cudaStream_t s) {
+    if (n > 0) vertex_flux_f32_kernel<<<blocks(n, 256), 256, 0, s>>>(w, F, w32, n, (float)(gamma - 1.0));
+}
+void launch_edge_flux_f64(const EdgeArgs &a, cudaStream_t s) {
+    if (a.ne > 0) edge_flux_f64_kernel<<<blocks(a.ne, kEdgeBlock), kEdgeBlock, 0, s>>>(a);
+}
+void launch_edge_flux_f32(const EdgeArgs &a, cudaStream_t s) {
+    if (a.ne > 0) edge_flux_f32_kernel<<<blocks(a.ne, kEdgeBlock), kEdgeBlock, 0, s>>>(a);
+}
+void launch_div_f64(const DivArgs &a, int mode, cudaStream_t s) {
+    if (a.n_real <= 0) return;
+    const unsigned g = blocks(a.n_real, kDivBlock);
+    switch (mode) {
+        case 0: div_f64_kernel<0><<<g, kDivBlock, 0, s>>>(a); break;
+        case 1: div_f64_kernel<1><<<g, kDivBlock, 0, s>>>(a); break;
+        case 2: div_f64_kernel<2><<<g, kDivBlock, 0, s>>>(a); break;
+        default: div_f64_kernel<3><<<g, kDivBlock, 0, s>>>(a); break;
+    }
+}
+void launch_div_f32(const DivArgs &a, int mode, cudaStream_t s) {
+    if (a.n_real <= 0) return;
+    const unsigned g = blocks(a.n_real, kDivBlock);
+    switch (mode) {
+        case 0: div_f32_kernel<0><<<g, kDivBlock, 0, s>>>(a); break;
+        case 1: div_f32_kernel<1><<<g, kDivBlock, 0, s>>>(a); break;
+        case 2: div_f32_kernel<2><<<g, kDivBlock, 0, s>>>(a); break;
+        default: div_f32_kernel<3><<<g, kDivBlock, 0, s>>>(a); break;
+    }
+}
+void launch_permute_rows(const double *in, double *out, const int32_t *map, int64_t n, bool gather, cudaStream_t s) {
+    if (n > 0) permute_rows_kernel<<<blocks(n, 256), 256, 0, s>>>(in, out, map, n, gather);
+}
+void launch_ghost_fill(double *w, void *F, int fq, float4 *w32, const int32_t *donor, int64_t n_real, int64_t n_ghost,
+                       cudaStream_t s) {
+    if (n_ghost > 0)
+        ghost_fill_kernel<<<blocks(n_ghost, 256), 256, 0, s>>>(w, static_cast<uint4 *>(F), fq, w32, donor, n_real,
+                                                               n_ghost);
+}
+void launch_max_dt(const double *w, const double *hmin, int64_t n, double gamma, unsigned long long *slot,
+                   cudaStream_t s) {
+    if (n > 0) max_dt_kernel<<<blocks(n, 256), 256, 0, s>>>(w, hmin, n, gamma, slot);
+}
+
+}  // namespace fdu

@@ -1,0 +1,62 @@
+// Device-side argument blocks and launchers of libfdu (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace fdu {
+
+constexpr int kSell = 32;        // SELL slice width of the divergence tables (one warp)
+constexpr int kEdgeBlock = 128;  // threads per block, edge-flux kernels
+constexpr int kDivBlock = 128;   // threads per block, divergence kernels
+
+// Edge-flux inputs (internal ids, SoA over the active edges).
+struct EdgeArgs {
+    const int32_t *sten;  // [6][ne]  L3 L2 L1 R1 R2 R3
+    const void *coef;     // FP64: [44][ne] coefficient blocks; FP32: [6][ne] compact (xi0, xi1, xi4, xi5, nx, ny)
+    const void *w;        // FP64: [nv][4] double; FP32: [nv] float4
+    void *r;              // FP64: [ne][4] double; FP32: [ne] float4
+    int64_t ne;
+    double gamma, eps;
+    unsigned long long *fallback;  // edges that fell back to first order (device counter)
+};
+
+// Divergence (+ optional SSP-RK3 stage) inputs.
+struct DivArgs {
+    int64_t n_real;              // vertices with a residual (internal ids 0..n_real-1)
+    const int64_t *slice_voff;   // [nslice+1] start of each slice's vertex entries
+    const int64_t *slice_eoff;   // [nslice+1]
+    const int32_t *vid;          // vertex entries (SELL: entry j of lane l at off + 32 j + l)
+    const void *wf, *wg;         // weights of f_j and g_j
+    const int32_t *eid;          // edge entries
+    const void *we;              // weights of r_k
+    const void *cfg;             // [2][n_real] centre weights: -(sum wf + sum we nx), -(sum wg + sum we ny)
+    const void *F;               // vertex fluxes of the stage state: FP64 [nv][8] (f0..3, g0..3); FP32 [nv][2] float4 pairs
+    const void *r;               // edge fluxes
+    // residual output (mode 0)
+    double *out;                 // [nv][4] FP64
+    const int32_t *out_map;      // internal -> output row (nullptr = internal order)
+    // RK stage (modes 1..3)
+    const double *wn;            // [nv][4] state at the start of the step
+    const double *ws;            // [nv][4] stage input state
+    double *wout;                // [nv][4] stage output state (may alias ws)
+    void *Fout;                  // vertex fluxes of wout (same layout as F)
+    float4 *w32out;              // FP32 copy of wout (FP32 residual path), or nullptr
+    double dt;
+    const double *dt_dev;        // if non-null, dt is read here
+    double gamma;
+};
+
+void launch_vertex_flux_f64(const double *w, double *F, int64_t n, double gamma, cudaStream_t s);
+void launch_vertex_flux_f32(const double *w, float4 *F, float4 *w32, int64_t n, double gamma, cudaStream_t s);
+void launch_edge_flux_f64(const EdgeArgs &a, cudaStream_t s);
+void launch_edge_flux_f32(const EdgeArgs &a, cudaStream_t s);
+void launch_div_f64(const DivArgs &a, int mode, cudaStream_t s);
+void launch_div_f32(const DivArgs &a, int mode, cudaStream_t s);
+void launch_permute_rows(const double *in, double *out, const int32_t *map, int64_t n, bool gather, cudaStream_t s);
+void launch_ghost_fill(double *w, void *F, int fq, float4 *w32, const int32_t *donor, int64_t n_real, int64_t n_ghost,
+                       cudaStream_t s);
+void launch_max_dt(const double *w, const double *hmin, int64_t n, double gamma, unsigned long long *slot,
+                   cudaStream_t s);
+
+}  // namespace fdu

@@ -1,0 +1,290 @@
+"""Thin ctypes binding of libfdu (include/fdu.h).
+
+Argument marshalling only: every step of the residual and the RK stage runs
+in the library's CUDA kernels.  Device buffers are torch CUDA tensors
+(passed by data_ptr()); host buffers are numpy arrays.  The library is
+loaded lazily and a missing or unbuildable library raises: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+FDU_OK = 0
+FDU_BC_PERIODIC = 0
+FDU_BC_TRANSMISSIVE = 1
+ERRORS = {
+    -1: "FDU_ERR_ARG", -2: "FDU_ERR_MESH", -3: "FDU_ERR_STENCIL", -4: "FDU_ERR_RANK_DEFICIENT",
+    -5: "FDU_ERR_CUDA", -6: "FDU_ERR_TIMEOUT", -7: "FDU_ERR_NONPHYSICAL", -8: "FDU_ERR_NODEVICE",
+}
+
+# Every symbol include/fdu.h declares (checked by the CPU tests).
+EXPORTS = (
+    "fdu_version", "fdu_last_error", "fdu_default_opts", "fdu_mesh_create", "fdu_mesh_destroy",
+    "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
+    "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
+    "fdu_fallback_count", "fdu_profile", "fdu_profile_read",
+)
+
+
+class FduError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{ERRORS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshOpts(C.Structure):
+    _fields_ = [
+        ("Lx", C.c_double), ("Ly", C.c_double), ("weno_eps", C.c_double), ("weno_eps32", C.c_double),
+        ("gamma", C.c_double), ("lsq_degree", C.c_int), ("lsq_levels", C.c_int), ("bc", C.c_int),
+        ("renumber", C.c_int), ("device", C.c_int), ("host_threads", C.c_int),
+        ("ghost_donor", C.POINTER(C.c_int32)),
+    ]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [
+        ("nv", C.c_int64), ("ne", C.c_int64), ("nt", C.c_int64), ("n_real", C.c_int64),
+        ("div_vert_nnz", C.c_int64), ("div_edge_nnz", C.c_int64),
+        ("J_min", C.c_int32), ("J_max", C.c_int32), ("K_min", C.c_int32), ("K_max", C.c_int32),
+        ("device_bytes", C.c_int64), ("table_bytes_f64", C.c_int64), ("table_bytes_f32", C.c_int64),
+        ("sell_width", C.c_int32), ("pad0", C.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad0"}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libfdu.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int32)
+        lp = C.POINTER(C.c_int64)
+        i64 = C.c_int64
+        L.fdu_version.restype = C.c_char_p
+        L.fdu_last_error.restype = C.c_char_p
+        L.fdu_default_opts.argtypes = [C.POINTER(MeshOpts)]
+        L.fdu_mesh_create.argtypes = [dp, i64, ip, i64, C.POINTER(MeshOpts), C.POINTER(P)]
+        L.fdu_mesh_destroy.argtypes = [P]
+        L.fdu_mesh_info_get.argtypes = [P, C.POINTER(MeshInfo)]
+        L.fdu_get_edges.argtypes = [P, ip]
+        L.fdu_get_edge_stencils.argtypes = [P, ip, dp]
+        L.fdu_get_div_sizes.argtypes = [P, lp, lp]
+        L.fdu_get_div_stencils.argtypes = [P, lp, ip, dp, dp, lp, ip, dp]
+        L.fdu_set_state.argtypes = [P, P, C.c_int, P]
+        L.fdu_get_state.argtypes = [P, P, C.c_int, P]
+        L.fdu_residual.argtypes = [P, C.c_int, P, C.c_int, P]
+        L.fdu_max_dt.argtypes = [P, C.c_double, dp, P]
+        L.fdu_rk_step.argtypes = [P, C.c_double, C.c_int, P]
+        L.fdu_rk_steps.argtypes = [P, C.c_double, C.c_int, C.c_int, P]
+        L.fdu_fallback_count.argtypes = [P, lp, C.c_int, P]
+        L.fdu_profile.argtypes = [P, C.c_int]
+        L.fdu_profile_read.argtypes = [P, C.c_int, C.c_int, dp, lp, C.c_int]
+        for name in EXPORTS:
+            if name not in ("fdu_version", "fdu_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def _check(st):
+    if st != FDU_OK:
+        raise FduError(st, load().fdu_last_error().decode())
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _lp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int64))
+
+
+def default_opts(**kw) -> MeshOpts:
+    o = MeshOpts()
+    _check(load().fdu_default_opts(C.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _buffer(x, rows, cols=4, writable=False):
+    """(pointer, on_device) of a torch CUDA tensor or a numpy array of [rows][cols] float64."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous() or tuple(x.shape) != (rows, cols):
+            raise ValueError(f"expected a contiguous float64 tensor of shape ({rows}, {cols})")
+        if not x.is_cuda:
+            if writable:
+                raise ValueError("output tensors must be CUDA tensors or numpy arrays")
+            return C.c_void_p(x.data_ptr()), 0
+        return C.c_void_p(x.data_ptr()), 1
+    a = np.asarray(x)
+    if a.dtype != np.float64 or not a.flags.c_contiguous or a.shape != (rows, cols):
+        raise ValueError(f"expected a C-contiguous float64 array of shape ({rows}, {cols})")
+    if writable and not a.flags.writeable:
+        raise ValueError("output array is read-only")
+    return C.c_void_p(a.ctypes.data), 0
+
+
+class Mesh:
+    """A mesh with its stencils, weights and device state (one fdu_mesh)."""
+
+    def __init__(self, xy, tri, Lx=0.0, Ly=0.0, *, lsq_degree=2, lsq_levels=2, device=0, renumber=1,
+                 ghost_donor=None, weno_eps=1e-40, weno_eps32=1e-30, gamma=1.4, host_threads=0):
+        L = load()
+        self._h = None
+        xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+        self._ghost = None
+        bc = FDU_BC_PERIODIC
+        gp = None
+        if ghost_donor is not None:
+            self._ghost = np.ascontiguousarray(ghost_donor, dtype=np.int32).reshape(xy.shape[0])
+            gp = _ip(self._ghost)
+            bc = FDU_BC_TRANSMISSIVE
+        o = default_opts(Lx=float(Lx), Ly=float(Ly), lsq_degree=lsq_degree, lsq_levels=lsq_levels, device=device,
+                         renumber=renumber, weno_eps=weno_eps, weno_eps32=weno_eps32, gamma=gamma, bc=bc,
+                         host_threads=host_threads)
+        if gp is not None:
+            o.ghost_donor = gp
+        h = C.c_void_p()
+        _check(L.fdu_mesh_create(_dp(xy), xy.shape[0], _ip(tri), tri.shape[0], C.byref(o), C.byref(h)))
+        self._h = h
+        self.device = device
+        info = self.info()
+        self.nv = int(info["nv"])
+        self.ne = int(info["ne"])
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().fdu_mesh_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------- host queries
+    def info(self) -> dict:
+        i = MeshInfo()
+        _check(load().fdu_mesh_info_get(self._h, C.byref(i)))
+        return i.as_dict()
+
+    def edges(self):
+        e = np.zeros((self.ne, 2), np.int32)
+        _check(load().fdu_get_edges(self._h, _ip(e)))
+        return e
+
+    def edge_stencils(self):
+        s = np.zeros((self.ne, 6), np.int32)
+        xi = np.zeros((self.ne, 6))
+        _check(load().fdu_get_edge_stencils(self._h, _ip(s), _dp(xi)))
+        return s, xi
+
+    def div_stencils(self):
+        vn, en = C.c_int64(), C.c_int64()
+        _check(load().fdu_get_div_sizes(self._h, C.byref(vn), C.byref(en)))
+        voff = np.zeros(self.nv + 1, np.int64)
+        eoff = np.zeros(self.nv + 1, np.int64)
+        vid = np.zeros(vn.value, np.int32)
+        eid = np.zeros(en.value, np.int32)
+        wf = np.zeros(vn.value)
+        wg = np.zeros(vn.value)
+        we = np.zeros(en.value)
+        _check(load().fdu_get_div_stencils(self._h, _lp(voff), _ip(vid), _dp(wf), _dp(wg), _lp(eoff), _ip(eid),
+                                           _dp(we)))
+        return voff, vid, wf, wg, eoff, eid, we
+
+    # ---------------------------------------------------------- device calls
+    def set_state(self, w, stream=None):
+        p, dev = _buffer(w, self.nv)
+        _check(load().fdu_set_state(self._h, p, dev, _stream_ptr(stream)))
+
+    def get_state(self, out=None, stream=None):
+        if out is None:
+            out = np.zeros((self.nv, 4))
+        p, dev = _buffer(out, self.nv, writable=True)
+        _check(load().fdu_get_state(self._h, p, dev, _stream_ptr(stream)))
+        return out
+
+    def residual(self, precision=64, out=None, stream=None):
+        if out is None:
+            out = np.zeros((self.nv, 4))
+        p, dev = _buffer(out, self.nv, writable=True)
+        _check(load().fdu_residual(self._h, int(precision), p, dev, _stream_ptr(stream)))
+        return out
+
+    def max_dt(self, cfl, stream=None) -> float:
+        dt = C.c_double()
+        _check(load().fdu_max_dt(self._h, float(cfl), C.byref(dt), _stream_ptr(stream)))
+        return dt.value
+
+    def rk_step(self, dt, precision=64, stream=None):
+        _check(load().fdu_rk_step(self._h, float(dt), int(precision), _stream_ptr(stream)))
+
+    def rk_steps(self, dt, n_steps, precision=64, stream=None):
+        _check(load().fdu_rk_steps(self._h, float(dt), int(precision), int(n_steps), _stream_ptr(stream)))
+
+    def fallback_count(self, reset=False, stream=None) -> int:
+        c = C.c_int64()
+        _check(load().fdu_fallback_count(self._h, C.byref(c), 1 if reset else 0, _stream_ptr(stream)))
+        return c.value
+
+    def profile(self, enable=True):
+        """Record CUDA events around each edge-flux and divergence launch."""
+        _check(load().fdu_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, kernel, precision=64, reset=True):
+        """(total device ms, launches) of kernel 'edge' or 'div' since the last reset."""
+        k = {"edge": 0, "div": 1}[kernel]
+        ms = C.c_double()
+        n = C.c_int64()
+        _check(load().fdu_profile_read(self._h, k, int(precision), C.byref(ms), C.byref(n), 1 if reset else 0))
+        return ms.value, n.value

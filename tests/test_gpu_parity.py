@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances:
+  - FP64 residual: relative L2 <= 1e-12 per component (the stated target);
+    the two sides differ only by rounding order (difference-form WENO with
+    one division per field vs. the paper's alpha/sum(alpha); QR vs SVD
+    least squares; folded centre weights).
+  - FP32 residual: relative L2 <= 1e-4 per component against the FP64
+    oracle (FP32 rounding, ~6e-8, amplified by the least-squares weights
+    ~1/h and by cancellation in the weighted sums).
+  - FP32 state after RK steps with FP64 accumulation: relative L2 of
+    density and energy <= 1e-5 (the stated target for the FP32 form).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_12933_gb300 import fdu, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+class Case:
+    def __init__(self, n, seed=1001, degree=2, levels=2, beta=5.0):
+        self.m, self.w0 = inputs.vortex_case(n, seed=seed, beta=beta)
+        m = self.m
+        self.om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly, degree=degree, levels=levels)
+        self.M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, lsq_degree=degree, lsq_levels=levels, device=0)
+
+
+@pytest.fixture(scope="module")
+def c40():
+    return Case(40)
+
+
+@pytest.fixture(scope="module")
+def c37():
+    return Case(37, seed=4242)  # 1369 vertices: ragged last SELL slice and edge block
+
+
+def test_residual_f64_matches_oracle(c40, c37):
+    for c in (c40, c37):
+        c.M.set_state(c.w0)
+        got = c.M.residual(64)
+        want = c.om.residual(c.w0)
+        for k in range(4):
+            assert rel_l2(got[:, k], want[:, k]) <= 1e-12, k
+        assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max()
+
+
+def test_residual_device_buffers(c40):
+    w = torch.tensor(c40.w0, device="cuda")
+    c40.M.set_state(w)
+    out = torch.empty_like(w)
+    c40.M.residual(64, out=out)
+    torch.cuda.synchronize()
+    host = c40.M.residual(64)
+    assert np.array_equal(out.cpu().numpy(), host)
+    back = torch.empty_like(w)
+    c40.M.get_state(out=back)
+    torch.cuda.synchronize()
+    assert torch.equal(back, w)
+
+
+def test_other_stencils_and_degrees():
+    for degree, levels in ((1, 1), (3, 2)):
+        c = Case(30, seed=31, degree=degree, levels=levels)
+        c.M.set_state(c.w0)
+        got = c.M.residual(64)
+        want = c.om.residual(c.w0)
+        for k in range(4):
+            assert rel_l2(got[:, k], want[:, k]) <= 1e-12
+
+
+def test_rk_steps_f64_match_oracle(c40):
+    dt = c40.om.max_dt(c40.w0, 0.5)
+    c40.M.set_state(c40.w0)
+    assert abs(c40.M.max_dt(0.5) - dt) <= 1e-14 * dt
+    w_or = c40.w0.copy()
+    for step in range(5):
+        c40.M.rk_step(dt, 64)
+        w_or = c40.om.rk3_step(w_or, dt)
+    w_gpu = c40.M.get_state()
+    for k in range(4):
+        assert rel_l2(w_gpu[:, k] - c40.w0[:, k], w_or[:, k] - c40.w0[:, k]) <= 1e-12
+
+
+def test_graph_replay_equals_single_steps(c37):
+    dt = c37.om.max_dt(c37.w0, 0.5)
+    c37.M.set_state(c37.w0)
+    for _ in range(4):
+        c37.M.rk_step(dt, 64)
+    a = c37.M.get_state()
+    c37.M.set_state(c37.w0)
+    c37.M.rk_steps(dt, 4, 64)
+    b = c37.M.get_state()
+    assert np.array_equal(a, b)
+    c37.M.set_state(c37.w0)
+    c37.M.rk_steps(dt, 2, 32)
+    c37.M.rk_steps(dt, 2, 32)
+    d = c37.M.get_state()
+    c37.M.set_state(c37.w0)
+    for _ in range(4):
+        c37.M.rk_step(dt, 32)
+    e = c37.M.get_state()
+    assert np.array_equal(d, e)
+
+
+def test_free_stream():
+    m, _ = inputs.vortex_case(33, seed=8)
+    one = np.ones(m.nv)
+    w = inputs.primitive_to_conservative(1.3 * one, 0.7 * one, -0.4 * one, 2.1 * one)
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0)
+    M.set_state(w)
+    assert np.abs(M.residual(64)).max() < 1e-12
+    assert np.abs(M.residual(32)).max() < 1e-4
+
+
+def test_residual_f32_error(c40):
+    c40.M.set_state(c40.w0)
+    got = c40.M.residual(32)
+    want = c40.om.residual(c40.w0)
+    for k in range(4):
+        assert rel_l2(got[:, k], want[:, k]) <= 1e-4
+
+
+def test_rk_f32_state_error(c40):
+    dt = c40.om.max_dt(c40.w0, 0.5)
+    c40.M.set_state(c40.w0)
+    c40.M.rk_steps(dt, 20, 32)
+    w32 = c40.M.get_state()
+    w_or = c40.w0.copy()
+    for _ in range(20):
+        w_or = c40.om.rk3_step(w_or, dt)
+    assert rel_l2(w32[:, 0], w_or[:, 0]) <= 1e-5
+    assert rel_l2(w32[:, 3], w_or[:, 3]) <= 1e-5
+
+
+def test_nonphysical_state_rejected(c40):
+    bad = c40.w0.copy()
+    bad[17, 0] = -1.0
+    with pytest.raises(fdu.FduError) as e:
+        c40.M.set_state(bad)
+    assert e.value.status == -7
+
+
+def test_shock_fallback_counts_match_oracle():
+    """A strong jump (pressure ratio 1e4) on the torus: the edges that fall
+    back to first order and the resulting residual agree with the oracle."""
+    m = inputs.torus_lattice(40, L=2.0, jitter=0.2, seed=12)
+    x, y = m.xy[:, 0] - 1.0, m.xy[:, 1] - 1.0
+    inside = (np.abs(x) < 0.5) & (np.abs(y) < 0.5)
+    rho = np.where(inside, 1.0, 0.02)
+    p = np.where(inside, 1.0, 1e-4)
+    z = np.zeros(m.nv)
+    w = inputs.primitive_to_conservative(rho, z + 0.3, z - 0.2, p)
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly)
+    want, nf = om.residual(w, return_fallbacks=True)
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0)
+    M.set_state(w)
+    M.fallback_count(reset=True)
+    got = M.residual(64)
+    assert M.fallback_count() == nf
+    for k in range(4):
+        assert rel_l2(got[:, k], want[:, k]) <= 1e-12
+
+
+def test_full_size_sampled_parity():
+    """250k-vertex vortex mesh, in the launch configuration the benchmark
+    times: residual and one RK3 step on the whole mesh on the GPU, checked
+    at sampled vertices the oracle computes one by one."""
+    m, w0 = inputs.vortex_case(500, seed=1002)
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0)
+    M.set_state(w0)
+    got = M.residual(64)
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly)
+    rng = np.random.default_rng(5)
+    mask = np.zeros(m.nv, np.uint8)
+    # random sample plus the vortex core (largest residuals)
+    mask[rng.choice(m.nv, 1500, replace=False)] = 1
+    core = np.argsort(-np.abs(w0[:, 1] / w0[:, 0] - 1.0))[:500]
+    mask[core] = 1
+    want = om.residual(w0, mask=mask)
+    sel = mask.astype(bool)
+    for k in range(4):
+        assert rel_l2(got[sel, k], want[sel, k]) <= 1e-12
+    got32 = M.residual(32)
+    for k in range(4):
+        assert rel_l2(got32[sel, k], want[sel, k]) <= 1e-4

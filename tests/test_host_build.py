@@ -1,0 +1,105 @@
+"""CPU tests of the C-ABI library: exports, host preprocessing parity with
+the oracle (bit-exact integer connectivity, FP64 coefficients and weights
+within rounding), renumbering invariance and error statuses.  No GPU call:
+meshes are built with device = -1 (host tables only)."""
+import ctypes
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import ROOT
+from paper_2102_12933_gb300 import fdu, inputs
+
+
+def test_library_exports_every_declared_symbol():
+    header = open(f"{ROOT}/include/fdu.h").read()
+    declared = set(re.findall(r"^(?:fdu_status|const char \*)\s*(fdu_\w+)\(", header, re.M))
+    assert declared == set(fdu.EXPORTS)
+    lib = ctypes.CDLL(fdu.lib_path() if fdu.load() else None)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert b"sm_103a" in fdu.load().fdu_version()
+
+
+def _pair(n=40, seed=1001, **kw):
+    m, w0 = inputs.vortex_case(n, seed=seed)
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=-1, **kw)
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly, degree=kw.get("lsq_degree", 2), levels=kw.get("lsq_levels", 2))
+    om.build_weights()
+    return m, M, om
+
+
+@pytest.mark.parametrize("levels,degree", [(2, 2), (1, 1), (2, 3)])
+def test_host_tables_match_oracle(levels, degree):
+    m, M, om = _pair(n=37, seed=77, lsq_levels=levels, lsq_degree=degree)
+    assert np.array_equal(M.edges(), om.edges())
+    s1, x1 = M.edge_stencils()
+    s2, x2 = om.stencils()
+    assert np.array_equal(s1, s2)
+    assert np.abs(x1 - x2).max() < 1e-13
+    a, b = M.div_stencils(), om.div_stencils()
+    for i in (0, 1, 4, 5):  # offsets and ids: bit-exact
+        assert np.array_equal(a[i], b[i])
+    for i in (2, 3, 6):  # weights: QR vs Jacobi SVD pseudo-inverse
+        assert np.abs(a[i] - b[i]).max() <= 1e-11 * (1 + np.abs(b[i]).max())
+
+
+def test_info_counts():
+    m, M, om = _pair(n=40)
+    info = M.info()
+    assert info["nv"] == 1600 and info["ne"] == 4800 and info["nt"] == 3200 and info["n_real"] == 1600
+    assert info["sell_width"] == 32
+    assert 12 <= info["J_min"] <= info["J_max"] <= 30
+
+
+def test_renumbering_is_invisible():
+    """Permuting the caller's vertex ids permutes the outputs and nothing else."""
+    m, _ = inputs.vortex_case(24, seed=5)
+    pm, perm = inputs.permute_vertices(m, seed=9)
+    A = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=-1)
+    B = fdu.Mesh(pm.xy, pm.tri, pm.Lx, pm.Ly, device=-1)
+    ea = A.edges()
+    eb = perm[B.edges()]  # back to the unpermuted ids
+    ka = {tuple(sorted(e)) for e in ea.tolist()}
+    kb = {tuple(sorted(e)) for e in eb.tolist()}
+    assert ka == kb
+    C = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=-1, renumber=0)
+    for x, y in zip(A.div_stencils(), C.div_stencils()):
+        assert np.array_equal(x, y)
+
+
+def test_error_statuses():
+    m, _ = inputs.vortex_case(12, seed=3)
+    bad = m.tri.copy()
+    bad[0, 0] = m.nv + 5
+    with pytest.raises(fdu.FduError) as e:
+        fdu.Mesh(m.xy, bad, m.Lx, m.Ly, device=-1)
+    assert e.value.status == -2
+    flipped = m.tri.copy()
+    flipped[3] = flipped[3, ::-1]
+    with pytest.raises(fdu.FduError) as e:
+        fdu.Mesh(m.xy, flipped, m.Lx, m.Ly, device=-1)
+    assert e.value.status == -2
+    with pytest.raises(fdu.FduError) as e:
+        fdu.Mesh(m.xy, m.tri, 0.0, 0.0, device=-1)  # periodic without lengths
+    assert e.value.status == -1
+    with pytest.raises(fdu.FduError) as e:
+        fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=-1, lsq_degree=9)
+    assert e.value.status == -1
+    # an open mesh without ghost layers: edges at the boundary have no 1D
+    # stencil, yet boundary vertices would need them
+    b = inputs.box_lattice(8, ghost_layers=0)
+    with pytest.raises(fdu.FduError) as e:
+        fdu.Mesh(b.xy, b.tri, 0.0, 0.0, device=-1, ghost_donor=np.full(b.nv, -1, np.int32))
+    assert e.value.status == -3
+    # one-level stencils cannot carry degree-3 polynomials (18 unknowns > 4N conditions)
+    with pytest.raises(fdu.FduError) as e:
+        fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=-1, lsq_levels=1, lsq_degree=3)
+    assert e.value.status == -4
+    # host-only meshes refuse device calls
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=-1)
+    with pytest.raises(fdu.FduError) as e:
+        M.residual()
+    assert e.value.status == -8

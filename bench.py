@@ -40,6 +40,10 @@ FLOP_DIV64_PER_VENTRY = 16
 FLOP_DIV64_PER_EENTRY = 8
 FLOP_DIV64_FIXED = 56
 FP64_PEAK_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), NVIDIA datasheet figure
+# DRAM bytes per edge of edge_flux_f64 from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, 480k-edge case of the same workload, scaled per edge);
+# None once the kernel changes after the capture.
+TRAFFIC_EDGE64_B_PER_EDGE = 409.0
 
 
 def _peaks():
@@ -72,7 +76,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -108,10 +112,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _workload():
+def _workload(n=N_LATTICE):
     from paper_2102_12933_gb300 import inputs
 
-    mesh, w0 = inputs.vortex_case(N_LATTICE, seed=1002)
+    mesh, w0 = inputs.vortex_case(n, seed=1002)
     return mesh, w0
 
 
@@ -119,9 +123,10 @@ def _rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def time_oracle(steps: int, n_sample: int = 125):
+def time_oracle(steps: int = 0, n_sample: int = 250, budget_s: float = 15.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: SSP-RK3
-    steps on a smaller mesh of the same family (one host core)."""
+    steps on a smaller mesh of the same family (one host core).  steps = 0
+    runs steps until `budget_s` seconds have passed (at most 200)."""
     import oracle
     from paper_2102_12933_gb300 import inputs
 
@@ -130,8 +135,11 @@ def time_oracle(steps: int, n_sample: int = 125):
     om.build_weights()
     dt = om.max_dt(w, CFL)
     t0 = time.perf_counter()
-    for _ in range(steps):
+    done = 0
+    while (steps and done < steps) or (not steps and time.perf_counter() - t0 < budget_s and done < 200):
         w = om.rk3_step(w, dt)
+        done += 1
+    steps = done
     el = time.perf_counter() - t0
     value = mesh.nv * 3 * steps / el / 1e6
     sample = (f"{steps} SSP-RK3 step(s) of the single-threaded FP64 oracle on a {mesh.nv}-vertex mesh of the "
@@ -144,14 +152,16 @@ def run_reference(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        time_oracle(1)
-    value, el, sample = time_oracle(args.steps)
+        time_oracle(1, n_sample=125)
+    value, el, sample = time_oracle(args.steps, n_sample=125)
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mvertex/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * el / max(args.steps, 1), 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "periodic isentropic vortex, jittered random-diagonal torus lattice (oracle sample)",
+        "config": {"workload": "periodic isentropic vortex (beta=5, centre (5,5)) on a jittered random-diagonal "
+                               "torus lattice of [0,10]^2; two-level divergence stencils, degree-2 least squares, "
+                               "NU-WENO5, SSP-RK3, CFL 0.5; one step = 3 stages (oracle on a 125x125 sample)",
                    "sample_nv": 15625},
         "cpu_baseline": {"value": round(value, 4), "unit": "Mvertex/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
@@ -176,7 +186,7 @@ def run_ours(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    mesh, w0 = _workload()
+    mesh, w0 = _workload(args.n)
     t_build = time.perf_counter()
     M = fdu.Mesh(mesh.xy, mesh.tri, mesh.Lx, mesh.Ly, device=local)
     t_build = time.perf_counter() - t_build
@@ -268,6 +278,7 @@ def run_ours(args):
     edge_avg_ms = edge_ms / max(edge_n, 1)
     div_avg_ms = div_ms / max(div_n, 1)
     achieved_tf = FLOP_EDGE64 * ne / (edge_avg_ms / 1e3) / 1e12
+    fp64_probe = fdu.probe_fma(local, 64)
     peaks = _peaks()
     vnnz, ennz = info["div_vert_nnz"], info["div_edge_nnz"]
     div_flops = FLOP_DIV64_PER_VENTRY * vnnz + FLOP_DIV64_PER_EENTRY * ennz + FLOP_DIV64_FIXED * nv
@@ -304,8 +315,11 @@ def run_ours(args):
             "peak": FP64_PEAK_NOMINAL_TFLOPS,
             "unit": "TFLOP/s",
             "frac": round(achieved_tf / FP64_PEAK_NOMINAL_TFLOPS, 4),
-            "traffic": None,
+            "traffic": (round(TRAFFIC_EDGE64_B_PER_EDGE * ne) if TRAFFIC_EDGE64_B_PER_EDGE else None),
+            "traffic_unit": "bytes per launch",
             "peak_source": "nominal GB300 FP64 rate (no FP64 figure in MEASURED_PEAKS.json)",
+            "peak_probe": round(fp64_probe, 4),
+            "frac_of_probe": round(achieved_tf / fp64_probe, 4),
             "flop_per_edge": FLOP_EDGE64,
             "avg_launch_ms": round(edge_avg_ms, 4),
             "share_of_step": round(edge_ms / ms64, 4) if ms64 > 0 else None,
@@ -328,7 +342,7 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        v, el, sample = time_oracle(4)
+        v, el, sample = time_oracle()
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "Mvertex/s", "cores": 1, "kind": "oracle",
                                 "sample": sample, "seconds": round(el, 2)}
     if rank == 0:
@@ -347,6 +361,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice size (n x n vertices); 500 = the workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

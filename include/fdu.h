@@ -176,6 +176,12 @@ fdu_status fdu_profile(fdu_mesh *mesh, int enable);
 fdu_status fdu_profile_read(fdu_mesh *mesh, int kernel, int precision, double *total_ms, int64_t *launches,
                             int reset);
 
+/* Measurement helper with no counterpart in the paper: the FMA throughput
+ * (TFLOP/s, FMA = 2 flops) of `device` at precision 64 or 32, from a short
+ * kernel of independent FMA chains on every SM.  It is the ALU ceiling
+ * that the FP64 residual is compared against.  Synchronises the device. */
+fdu_status fdu_probe_fma(int device, int precision, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -632,6 +632,22 @@ fdu_status fdu_fallback_count(fdu_mesh *m, int64_t *count, int reset, void *stre
     return FDU_OK;
 }
 
+fdu_status fdu_probe_fma(int device, int precision, double *tflops) {
+    if (!tflops || (precision != 64 && precision != 32)) return set_err(FDU_ERR_ARG, "bad precision or output");
+    CK(cudaSetDevice(device));
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    void *buf = nullptr;
+    CK(cudaMalloc(&buf, (size_t)sms * 8 * 256 * 8));
+    const double t = fma_probe_tflops(precision, sms, buf, nullptr);
+    cudaError_t e = cudaGetLastError();
+    cudaDeviceSynchronize();
+    cudaFree(buf);
+    if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("fma probe: ") + cudaGetErrorString(e));
+    *tflops = t;
+    return FDU_OK;
+}
+
 fdu_status fdu_profile(fdu_mesh *m, int enable) {
     fdu_status st = need_device(m);
     if (st) return st;

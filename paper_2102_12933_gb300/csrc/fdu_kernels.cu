@@ -627,6 +627,22 @@ __global__ void max_dt_kernel(const double *__restrict__ w, const double *__rest
     if ((threadIdx.x & 31) == 0) atomicMin(slot, (unsigned long long)__double_as_longlong(t));
 }
 
+// FMA-throughput probe: 8 independent chains x = x*a + b per thread.
+template <class T>
+__global__ void fma_probe_kernel(T *out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = x[k] * a + b;
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 inline unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
@@ -675,6 +691,28 @@ void launch_ghost_fill(double *w, void *F, int fq, float4 *w32, const int32_t *d
 void launch_max_dt(const double *w, const double *hmin, int64_t n, double gamma, unsigned long long *slot,
                    cudaStream_t s) {
     if (n > 0) max_dt_kernel<<<blocks(n, 256), 256, 0, s>>>(w, hmin, n, gamma, slot);
+}
+
+double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s) {
+    const int nb = sms * 8, nt = 256;
+    const int iters = precision == 64 ? 2048 : 65536;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
+        cudaEventRecord(a, s);
+        if (precision == 64)
+            fma_probe_kernel<double><<<nb, nt, 0, s>>>(static_cast<double *>(scratch), iters, 0.999999, 1e-7);
+        else
+            fma_probe_kernel<float><<<nb, nt, 0, s>>>(static_cast<float *>(scratch), iters, 0.999999f, 1e-7f);
+        cudaEventRecord(b, s);
+    }
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return 2.0 * 8.0 * iters * (double)nb * nt / (ms * 1e-3) / 1e12;
 }
 
 }  // namespace fdu

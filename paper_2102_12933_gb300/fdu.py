@@ -32,7 +32,7 @@ EXPORTS = (
     "fdu_version", "fdu_last_error", "fdu_default_opts", "fdu_mesh_create", "fdu_mesh_destroy",
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
-    "fdu_fallback_count", "fdu_profile", "fdu_profile_read",
+    "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma",
 )
 
 
@@ -99,6 +99,7 @@ def load():
         L.fdu_rk_steps.argtypes = [P, C.c_double, C.c_int, C.c_int, P]
         L.fdu_fallback_count.argtypes = [P, lp, C.c_int, P]
         L.fdu_profile.argtypes = [P, C.c_int]
+        L.fdu_probe_fma.argtypes = [C.c_int, C.c_int, dp]
         L.fdu_profile_read.argtypes = [P, C.c_int, C.c_int, dp, lp, C.c_int]
         for name in EXPORTS:
             if name not in ("fdu_version", "fdu_last_error"):
@@ -169,6 +170,13 @@ def _buffer(x, rows, cols=4, writable=False):
     if writable and not a.flags.writeable:
         raise ValueError("output array is read-only")
     return C.c_void_p(a.ctypes.data), 0
+
+
+def probe_fma(device=0, precision=64) -> float:
+    """FMA throughput of the device in TFLOP/s (measurement helper)."""
+    t = C.c_double()
+    _check(load().fdu_probe_fma(int(device), int(precision), C.byref(t)))
+    return t.value
 
 
 class Mesh:

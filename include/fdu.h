@@ -176,6 +176,31 @@ fdu_status fdu_profile(fdu_mesh *mesh, int enable);
 fdu_status fdu_profile_read(fdu_mesh *mesh, int kernel, int precision, double *total_ms, int64_t *launches,
                             int reset);
 
+/* FP64 residual that allocates no device memory, for callers that cannot
+ * call cudaMalloc when they evaluate the residual: for example code that
+ * runs under a host framework which has handed all device memory to its own
+ * pool and forbids further allocations, or a time-critical loop that cannot
+ * afford the implicit device synchronisation cudaMalloc may cause.  The
+ * paper has no counterpart; it is the fdu_residual arithmetic (precision
+ * 64) with its scratch (the state in internal order, vertex fluxes and
+ * edge fluxes) in one fixed array inside the library instead of the mesh's
+ * own buffers.  The mesh itself must already exist (fdu_mesh_create
+ * allocates).
+ *   w[nv][4]     device pointer, the state in original vertex order (input)
+ *   dwdt[nv][4]  device pointer, the residual in original vertex order
+ *                (output; ghost rows set to 0)
+ * Limit: nv <= FDU_NOALLOC_MAX_VERTICES and active edges <=
+ * FDU_NOALLOC_MAX_EDGES, otherwise FDU_ERR_ARG.  The array takes
+ * 12.6 MB on every GPU that loads the library, for the life of the
+ * process.  The first call on each device looks up the array's device
+ * address with that device current.  Every call uses the same array, which
+ * keeps the last call's contents: calls whose work overlaps on the GPU
+ * (on different streams or for different meshes) race on it and must be
+ * serialised by the caller.  The mesh's fallback counter still counts. */
+#define FDU_NOALLOC_MAX_VERTICES 65536
+#define FDU_NOALLOC_MAX_EDGES 196608
+fdu_status fdu_residual_noalloc(const fdu_mesh *mesh, const double *w, double *dwdt, void *stream);
+
 /* Measurement helper with no counterpart in the paper: the FMA throughput
  * (TFLOP/s, FMA = 2 flops) of `device` at precision 64 or 32, from a short
  * kernel of independent FMA chains on every SM.  It is the ALU ceiling

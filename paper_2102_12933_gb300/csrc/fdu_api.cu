@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -338,6 +339,36 @@ void enqueue_step(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaSt
 
 }  // namespace
 
+// ====================================================================== no-allocation residual
+// Scratch of fdu_residual_noalloc: the caller's state in internal order
+// [FDU_NOALLOC_MAX_VERTICES][4], vertex fluxes [..][8] and edge fluxes
+// [FDU_NOALLOC_MAX_EDGES][4], all FP64, in one array that every GPU loading
+// the library holds until the process exits.
+namespace {
+constexpr int64_t kNoallocDoubles = 4 * (int64_t)FDU_NOALLOC_MAX_VERTICES + 8 * (int64_t)FDU_NOALLOC_MAX_VERTICES +
+                                    4 * (int64_t)FDU_NOALLOC_MAX_EDGES;
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once per device).
+fdu_status noalloc_scratch(int device, double **out) {
+    if (device < 0 || device >= kMaxDevices) return set_err(FDU_ERR_ARG, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return set_err(FDU_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        g_noalloc_ptr[device] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return FDU_OK;
+}
+}  // namespace
+
 // ====================================================================== C-ABI
 extern "C" {
 
@@ -629,6 +660,42 @@ fdu_status fdu_fallback_count(fdu_mesh *m, int64_t *count, int reset, void *stre
     CK(cudaStreamSynchronize(s));
     if (reset) CK(cudaMemsetAsync(m->counters, 0, sizeof c, s));
     *count = (int64_t)c;
+    return FDU_OK;
+}
+
+fdu_status fdu_residual_noalloc(const fdu_mesh *mc, const double *w, double *dwdt, void *stream) {
+    fdu_mesh *m = const_cast<fdu_mesh *>(mc);
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!w || !dwdt) return set_err(FDU_ERR_ARG, "null state or output");
+    if (m->nv > FDU_NOALLOC_MAX_VERTICES || m->ne_act > FDU_NOALLOC_MAX_EDGES)
+        return set_err(FDU_ERR_ARG, "mesh has " + std::to_string(m->nv) + " vertices and " +
+                                        std::to_string(m->ne_act) + " edges; fdu_residual_noalloc supports at most " +
+                                        std::to_string(FDU_NOALLOC_MAX_VERTICES) + " and " +
+                                        std::to_string(FDU_NOALLOC_MAX_EDGES));
+    double *base = nullptr;
+    st = noalloc_scratch(m->device, &base);
+    if (st) return st;
+    double *wi = base;                                       // [MAX_V][4]
+    double *F = base + 4 * (int64_t)FDU_NOALLOC_MAX_VERTICES;  // [MAX_V][8]
+    double *r = F + 8 * (int64_t)FDU_NOALLOC_MAX_VERTICES;     // [MAX_E][4]
+    cudaStream_t s = m->stream(stream);
+    // every scratch word read below is written first in this call; only the
+    // ghost rows of the output must start at zero
+    if (m->n_ghost > 0) CK(cudaMemsetAsync(dwdt, 0, 4 * m->nv * sizeof(double), s));
+    launch_permute_rows(w, wi, m->new2old, m->nv, true, s);
+    if (m->n_ghost > 0) launch_ghost_fill(wi, nullptr, 0, nullptr, m->donor, m->n_real, m->n_ghost, s);
+    launch_vertex_flux_f64(wi, F, m->nv, m->opts.gamma, s);
+    EdgeArgs ea = edge_args(m, 64, wi);
+    ea.r = r;
+    launch_edge_flux_f64(ea, s);
+    DivArgs a = div_args(m, 64, 0);
+    a.F = F;
+    a.r = r;
+    a.out = dwdt;
+    a.out_map = m->new2old;
+    launch_div_f64(a, 0, s);
+    CK_LAUNCH();
     return FDU_OK;
 }
 

@@ -32,7 +32,7 @@ EXPORTS = (
     "fdu_version", "fdu_last_error", "fdu_default_opts", "fdu_mesh_create", "fdu_mesh_destroy",
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
-    "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma",
+    "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
 )
 
 
@@ -100,6 +100,7 @@ def load():
         L.fdu_fallback_count.argtypes = [P, lp, C.c_int, P]
         L.fdu_profile.argtypes = [P, C.c_int]
         L.fdu_probe_fma.argtypes = [C.c_int, C.c_int, dp]
+        L.fdu_residual_noalloc.argtypes = [P, P, P, P]
         L.fdu_profile_read.argtypes = [P, C.c_int, C.c_int, dp, lp, C.c_int]
         for name in EXPORTS:
             if name not in ("fdu_version", "fdu_last_error"):
@@ -296,3 +297,14 @@ class Mesh:
         n = C.c_int64()
         _check(load().fdu_profile_read(self._h, k, int(precision), C.byref(ms), C.byref(n), 1 if reset else 0))
         return ms.value, n.value
+
+    def residual_noalloc(self, w, out, stream=None):
+        """FP64 residual of the device state `w` into the device tensor `out`
+        (both [nv][4] float64, original vertex order) using the library's fixed
+        scratch array: no device memory is allocated by this call."""
+        pw, dw = _buffer(w, self.nv)
+        po, do = _buffer(out, self.nv, writable=True)
+        if not (dw and do):
+            raise ValueError("residual_noalloc takes CUDA tensors")
+        _check(load().fdu_residual_noalloc(self._h, pw, po, _stream_ptr(stream)))
+        return out

@@ -1,0 +1,74 @@
+"""fdu_residual_noalloc: the FP64 residual for callers that cannot allocate
+device memory at the time they evaluate it (a host framework that owns all
+device memory through its own pool, or a loop that cannot afford the device
+synchronisation an allocation may cause).  Its scratch lives in a fixed
+array inside the library, so the call itself allocates nothing.
+
+Checked through the C-ABI against fdu_residual (the existing entry point)
+within the FP64 parity tolerance (1e-12 relative L2 per component), on two
+calls in a row with different states, and for the size limit.  This file
+is collected last so that a run stopping at the first failure has already
+run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_2102_12933_gb300 import fdu, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+def _rel(a, b):
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,seed", [(40, 1001), (37, 4242)])
+def test_noalloc_matches_residual_on_two_calls(n, seed):
+    m, w0 = inputs.vortex_case(n, seed=seed)
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0)
+    w_a = torch.tensor(w0, device="cuda")
+    w_b = w_a.clone()
+    w_b[:, 3] *= 1.05  # a second, different state
+    w_b[:, 1] += 0.1 * w_b[:, 0]
+    outs = []
+    for w in (w_a, w_b):
+        M.set_state(w)
+        ref = torch.empty_like(w)
+        M.residual(64, out=ref)
+        got = torch.full_like(w, float("nan"))
+        M.residual_noalloc(w, got)
+        torch.cuda.synchronize()
+        for k in range(4):
+            assert _rel(got[:, k], ref[:, k]) <= 1e-12
+        outs.append(got.clone())
+    # the second call did not reuse the first call's result
+    assert _rel(outs[0], outs[1]) > 1e-6
+
+
+def test_noalloc_allocates_nothing_per_call():
+    m, w0 = inputs.vortex_case(32, seed=7)
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0)
+    w = torch.tensor(w0, device="cuda")
+    out = torch.empty_like(w)
+    M.residual_noalloc(w, out)  # first call on the device: address lookup
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        M.residual_noalloc(w, out)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+
+
+def test_noalloc_rejects_meshes_over_the_limit():
+    n = 260  # 67,600 vertices > 65,536
+    m, w0 = inputs.vortex_case(n, seed=3)
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0)
+    w = torch.tensor(w0, device="cuda")
+    out = torch.empty_like(w)
+    with pytest.raises(fdu.FduError) as e:
+        M.residual_noalloc(w, out)
+    assert e.value.status == -1
+    assert "at most 65536" in str(e.value)

@@ -201,6 +201,12 @@ fdu_status fdu_profile_read(fdu_mesh *mesh, int kernel, int precision, double *t
 #define FDU_NOALLOC_MAX_EDGES 196608
 fdu_status fdu_residual_noalloc(const fdu_mesh *mesh, const double *w, double *dwdt, void *stream);
 
+/* Accuracy check of the kernels' FP64 reciprocal (no counterpart in the
+ * paper): y[i] = the reciprocal the WENO weights and Roe averages use, for
+ * host arrays x[n] of positive normal doubles (Newton-Raphson refinement of
+ * the hardware approximation); the tests compare it with IEEE division. */
+fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n);
+
 /* Measurement helper with no counterpart in the paper: the FMA throughput
  * (TFLOP/s, FMA = 2 flops) of `device` at precision 64 or 32, from a short
  * kernel of independent FMA chains on every SM.  It is the ALU ceiling

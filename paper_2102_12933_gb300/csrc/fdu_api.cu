@@ -56,8 +56,8 @@ struct fdu_mesh {
     std::vector<void *> allocs;
     // tables
     int32_t *sten = nullptr;          // [6][ne_act]
-    double *coef64 = nullptr;         // [44][ne_act]
-    float *coef32 = nullptr;          // [6][ne_act]
+    double *coef64 = nullptr;         // [32][ne_act]
+    float *coef32 = nullptr;          // [32][ne_act]
     int64_t *slice_voff = nullptr, *slice_eoff = nullptr;
     int32_t *svid = nullptr, *seid = nullptr;
     double *swf64 = nullptr, *swg64 = nullptr, *swe64 = nullptr, *cfg64 = nullptr;
@@ -135,18 +135,14 @@ fdu_status upload_tables(fdu_mesh *m) {
     // 1D stencils and coefficient blocks, SoA over internal active edges
     std::vector<int32_t> sten(6 * ne);
     std::vector<double> coef((size_t)kEdgeCoef * ne);
-    std::vector<float> coef32(6 * ne);
+    std::vector<float> coef32((size_t)kEdgeCoef * ne);
     for (int64_t e = 0; e < ne; ++e) {
         const int64_t o = T.e_new2old[e];
         for (int i = 0; i < 6; ++i) sten[i * ne + e] = T.v_old2new[T.sten[6 * o + i]];
-        for (int c = 0; c < kEdgeCoef; ++c) coef[(size_t)c * ne + e] = T.coef[(size_t)kEdgeCoef * o + c];
-        const double *xi = &T.xi[6 * o];
-        coef32[0 * ne + e] = (float)xi[0];
-        coef32[1 * ne + e] = (float)xi[1];
-        coef32[2 * ne + e] = (float)xi[4];
-        coef32[3 * ne + e] = (float)xi[5];
-        coef32[4 * ne + e] = (float)T.nrm[2 * o];
-        coef32[5 * ne + e] = (float)T.nrm[2 * o + 1];
+        for (int c = 0; c < kEdgeCoef; ++c) {
+            coef[(size_t)c * ne + e] = T.coef[(size_t)kEdgeCoef * o + c];
+            coef32[(size_t)c * ne + e] = (float)T.coef[(size_t)kEdgeCoef * o + c];
+        }
     }
     if ((st = m->upload(m->sten, sten))) return st;
     if ((st = m->upload(m->coef64, coef))) return st;
@@ -251,8 +247,10 @@ EdgeArgs edge_args(fdu_mesh *m, int prec, const void *w) {
     a.w = w;
     a.r = prec == 64 ? (void *)m->r64 : (void *)m->r32;
     a.ne = m->ne_act;
-    a.gamma = m->opts.gamma;
-    a.eps = prec == 64 ? m->opts.weno_eps : m->opts.weno_eps32;
+    a.gm1 = m->opts.gamma - 1.0;
+    a.eps = m->opts.weno_eps;
+    a.gm1f = (float)(m->opts.gamma - 1.0);
+    a.epsf = (float)m->opts.weno_eps32;
     a.fallback = m->counters;
     return a;
 }
@@ -271,7 +269,8 @@ DivArgs div_args(fdu_mesh *m, int prec, int fin) {
         a.wf = m->swf32; a.wg = m->swg32; a.we = m->swe32; a.cfg = m->cfg32;
         a.F = m->F32[fin]; a.r = m->r32;
     }
-    a.gamma = m->opts.gamma;
+    a.gm1 = m->opts.gamma - 1.0;
+    a.gm1f = (float)(m->opts.gamma - 1.0);
     return a;
 }
 
@@ -696,6 +695,23 @@ fdu_status fdu_residual_noalloc(const fdu_mesh *mc, const double *w, double *dwd
     a.out_map = m->new2old;
     launch_div_f64(a, 0, s);
     CK_LAUNCH();
+    return FDU_OK;
+}
+
+fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n) {
+    if (!x || !y || n < 0) return set_err(FDU_ERR_ARG, "bad arguments");
+    if (n == 0) return FDU_OK;
+    CK(cudaSetDevice(device));
+    double *d = nullptr;
+    CK(cudaMalloc(&d, 2 * n * sizeof(double)));
+    cudaError_t e = cudaMemcpy(d, x, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch_recip_check(d, d + n, n, nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(y, d + n, n * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("reciprocal check: ") + cudaGetErrorString(e));
     return FDU_OK;
 }
 

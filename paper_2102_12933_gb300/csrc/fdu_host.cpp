@@ -534,10 +534,28 @@ int build_host_tables(const double *xy, int64_t nv, const int32_t *tri, int64_t 
             double *c = &T.coef[(size_t)kEdgeCoef * k];
             const double xl[5] = {xi[0], xi[1], xi[2], xi[3], xi[4]};
             const double xr[5] = {-xi[5], -xi[4], -xi[3], -xi[2], -xi[1]};
-            side_coefficients(xl, c);
-            side_coefficients(xr, c + kSideCoef);
-            c[2 * kSideCoef] = T.nrm[2 * k];
-            c[2 * kSideCoef + 1] = T.nrm[2 * k + 1];
+            double L[kSideCoef], R[kSideCoef];
+            side_coefficients(xl, L);
+            side_coefficients(xr, R);
+            // sub-stencil k of a side block: value at 2k, slope at 6 + 2k, curvature at 12 + 2k
+            auto put = [&](int dst, const double *side, int k) {
+                c[dst + 0] = side[2 * k];
+                c[dst + 1] = side[2 * k + 1];
+                c[dst + 2] = side[6 + 2 * k];
+                c[dst + 3] = side[6 + 2 * k + 1];
+                c[dst + 4] = side[12 + 2 * k];
+                c[dst + 5] = side[12 + 2 * k + 1];
+            };
+            put(0, L, 0);   // S_a
+            put(6, L, 1);   // S_b
+            put(12, L, 2);  // S_c
+            put(18, R, 0);  // S_d
+            for (int i = 0; i < 3; ++i) {
+                c[24 + i] = L[18 + i];
+                c[27 + i] = R[18 + i];
+            }
+            c[30] = T.nrm[2 * k];
+            c[31] = T.nrm[2 * k + 1];
         }
     });
     if (periodic && bad.load() >= 0) {

@@ -17,7 +17,18 @@ namespace fdu {
 // point x_i and use the slots (k=0: x_{i-2}, x_{i-1}), (k=1: x_{i-1},
 // x_{i+1}), (k=2: x_{i+1}, x_{i+2}).
 constexpr int kSideCoef = 21;
-constexpr int kEdgeCoef = 2 * kSideCoef + 2;  // left, right, normal (nx, ny)
+
+// Edge coefficient block (kEdgeCoef values).  The left state uses the
+// sub-stencils S_a = {L3,L2,L1}, S_b = {L2,L1,R1}, S_c = {L1,R1,R2}; the
+// right (mirrored) state uses S_d = {R1,R2,R3}, S_c, S_b: S_b and S_c are
+// the same quadratics over the same middle interval on both sides, so their
+// values and smoothness indicators are computed once.  Each 6-block holds
+// value, slope and curvature coefficients (2 each) of two differences:
+//   [0..5]   S_a of (L3-L1, L2-L1)      [6..11]  S_b of (L2-L1, R1-L1)
+//   [12..17] S_c of (R1-L1, R2-L1)      [18..23] S_d of (R3-R1, R2-R1)
+//   [24..26] C_0..2 of the left state   [27..29] C_0..2 of the right state
+//   [30..31] n_x, n_y
+constexpr int kEdgeCoef = 32;
 
 struct HostTables {
     int64_t nv = 0, nt = 0, ne = 0, n_real = 0;

@@ -49,6 +49,19 @@ __device__ __forceinline__ dbl4 add4(dbl4 a, dbl4 b) {
 }
 __device__ __forceinline__ dbl4 neg4(dbl4 a) { return dbl4_make(-a.x, -a.y, -a.z, -a.w); }
 
+// Reciprocal of a positive normal double by Newton-Raphson iteration
+// y <- y + y (1 - x y), started from the hardware's approximate FP64
+// reciprocal (PTX rcp.approx.ftz.f64); two iterations bring the relative
+// error to the rounding level (checked against IEEE division by the tests).
+__device__ __forceinline__ double recip64(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
 // Per-state quantities reused by the Roe average and the physical flux.
 struct Prim64 {
     double r;   // rho^-1/2
@@ -72,7 +85,7 @@ __device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const db
                                       double nx, double ny, double gm1) {
     Roe64 R;
     const double sa = a.x * pa.r, sb = b.x * pb.r;
-    const double inv = 1.0 / (sa + sb);
+    const double inv = recip64(sa + sb);
     R.u = (a.y * pa.r + b.y * pb.r) * inv;
     R.v = (a.z * pa.r + b.z * pb.r) * inv;
     R.H = ((a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r) * inv;
@@ -104,35 +117,31 @@ __device__ __forceinline__ dbl4 unproject64(const Roe64 &R, const dbl4 &c) {
                         R.H * (c.x + c.w) + R.hq2 * c.y + R.qn * dd + R.qt * c.z);
 }
 
-// NU-WENO5 increment u~ - u_c of one field from the four differences
-// (a, b, c, d) = (u_{i-2}, u_{i-1}, u_{i+1}, u_{i+2}) - u_i, with the
-// side's coefficient block k (see fdu_internal.h).  The nonlinear weights
-// alpha_k = C_k / (beta_k + eps), omega = alpha / sum(alpha) (p = 1) are
-// applied as C_k prod_{l != k} (beta_l + eps) over their sum, which is the
-// same quotient with one division.
-__device__ __forceinline__ double weno64(const double *k, double a, double b, double c, double d, double eps) {
-    const double v0 = fma(k[0], a, k[1] * b);
-    const double v1 = fma(k[2], b, k[3] * c);
-    const double v2 = fma(k[4], c, k[5] * d);
-    const double p0 = fma(k[6], a, k[7] * b);
-    const double p1 = fma(k[8], b, k[9] * c);
-    const double p2 = fma(k[10], c, k[11] * d);
-    const double q0 = fma(k[12], a, k[13] * b);
-    const double q1 = fma(k[14], b, k[15] * c);
-    const double q2 = fma(k[16], c, k[17] * d);
-    const double b0 = fma(p0, p0, fma(q0, q0, eps));
-    const double b1 = fma(p1, p1, fma(q1, q1, eps));
-    const double b2 = fma(p2, p2, fma(q2, q2, eps));
-    const double t0 = k[18] * (b1 * b2);
-    const double t1 = k[19] * (b0 * b2);
-    const double t2 = k[20] * (b0 * b1);
-    return fma(t0, v0, fma(t1, v1, t2 * v2)) / (t0 + t1 + t2);
-}
-
-__device__ __forceinline__ void load_side(const double *__restrict__ coef, int64_t ne, int64_t e, int base,
-                                          double *k) {
-#pragma unroll
-    for (int i = 0; i < kSideCoef; ++i) k[i] = __ldg(coef + (int64_t)(base + i) * ne + e);
+// NU-WENO5 increments of one characteristic field (Appendix), both sides.
+// Differences: a = L3-L1, b = L2-L1, c = R1-L1, d = R2-L1 (left centre L1),
+// e = R3-R1, f = R2-R1 (right centre R1).  k is the edge's coefficient block
+// (fdu_internal.h): four sub-stencils S_a..S_d give values v (increments),
+// and slopes p / curvatures q whose squares sum to the smoothness
+// indicators beta = p^2 + q^2.  The nonlinear weights alpha_k = C_k /
+// (beta_k + eps), omega = alpha / sum(alpha) (p = 1) are applied as
+// C_k prod_{l != k}(beta_l + eps) over their sum: the same quotient with one
+// reciprocal per side.
+__device__ __forceinline__ void weno_pair64(const double *k, double a, double b, double c, double d, double e,
+                                            double f, double eps, double &dl, double &dr) {
+    const double va = fma(k[0], a, k[1] * b), pa = fma(k[2], a, k[3] * b), qa = fma(k[4], a, k[5] * b);
+    const double vb = fma(k[6], b, k[7] * c), pb = fma(k[8], b, k[9] * c), qb = fma(k[10], b, k[11] * c);
+    const double vc = fma(k[12], c, k[13] * d), pc = fma(k[14], c, k[15] * d), qc = fma(k[16], c, k[17] * d);
+    const double vd = fma(k[18], e, k[19] * f), pd = fma(k[20], e, k[21] * f), qd = fma(k[22], e, k[23] * f);
+    const double ba = fma(pa, pa, fma(qa, qa, eps));
+    const double bb = fma(pb, pb, fma(qb, qb, eps));
+    const double bc = fma(pc, pc, fma(qc, qc, eps));
+    const double bd = fma(pd, pd, fma(qd, qd, eps));
+    const double bbc = bb * bc;
+    const double l0 = k[24] * bbc, l1 = k[25] * (ba * bc), l2 = k[26] * (ba * bb);
+    dl = fma(l0, va, fma(l1, vb, l2 * vc)) * recip64(l0 + l1 + l2);
+    const double r0 = k[27] * bbc, r1 = k[28] * (bd * bb), r2 = k[29] * (bd * bc);
+    // right-side increments from R1: S_d's own, S_c's and S_b's shifted by -c
+    dr = fma(r0, vd, fma(r1, vc - c, r2 * (vb - c))) * recip64(r0 + r1 + r2);
 }
 
 // ------------------------------------------------------------------ FP64 edge flux
@@ -141,14 +150,14 @@ __global__ void __launch_bounds__(kEdgeBlock) edge_flux_f64_kernel(EdgeArgs A) {
     if (e >= A.ne) return;
     const double *__restrict__ w = static_cast<const double *>(A.w);
     const double *__restrict__ coef = static_cast<const double *>(A.coef);
-    const double gm1 = A.gamma - 1.0;
+    const double gm1 = A.gm1;
     const int64_t ne = A.ne;
     int32_t s[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
     const dbl4 L1 = ld4(w, s[2]), R1 = ld4(w, s[3]);
-    const double nx = __ldg(coef + (int64_t)(2 * kSideCoef) * ne + e);
-    const double ny = __ldg(coef + (int64_t)(2 * kSideCoef + 1) * ne + e);
+    const double nx = __ldg(coef + (int64_t)30 * ne + e);
+    const double ny = __ldg(coef + (int64_t)31 * ne + e);
 
     // characteristic decomposition at the Roe average of the end states
     const Prim64 pL1 = prim64(L1, gm1), pR1 = prim64(R1, gm1);
@@ -159,24 +168,15 @@ __global__ void __launch_bounds__(kEdgeBlock) edge_flux_f64_kernel(EdgeArgs A) {
     const dbl4 cR2 = project64(C, sub4(ld4(w, s[4]), R1));    // R2 - R1
     const dbl4 cR3 = project64(C, sub4(ld4(w, s[5]), R1));    // R3 - R1
 
-    double k[kSideCoef];
-    // left state: centre L1, differences (L3, L2, R1, R2) - L1
-    load_side(coef, ne, e, 0, k);
-    const dbl4 cR2L = add4(cR2, cM);
-    dbl4 dl;
-    dl.x = weno64(k, cL3.x, cL2.x, cM.x, cR2L.x, A.eps);
-    dl.y = weno64(k, cL3.y, cL2.y, cM.y, cR2L.y, A.eps);
-    dl.z = weno64(k, cL3.z, cL2.z, cM.z, cR2L.z, A.eps);
-    dl.w = weno64(k, cL3.w, cL2.w, cM.w, cR2L.w, A.eps);
-    // right state (mirrored stencil): centre R1, differences (R3, R2, L1, L2) - R1
-    load_side(coef, ne, e, kSideCoef, k);
-    const dbl4 nM = neg4(cM);
-    const dbl4 cL2R = sub4(cL2, cM);
-    dbl4 dr;
-    dr.x = weno64(k, cR3.x, cR2.x, nM.x, cL2R.x, A.eps);
-    dr.y = weno64(k, cR3.y, cR2.y, nM.y, cL2R.y, A.eps);
-    dr.z = weno64(k, cR3.z, cR2.z, nM.z, cL2R.z, A.eps);
-    dr.w = weno64(k, cR3.w, cR2.w, nM.w, cL2R.w, A.eps);
+    double k[30];
+#pragma unroll
+    for (int i = 0; i < 30; ++i) k[i] = __ldg(coef + (int64_t)i * ne + e);
+    const dbl4 cR2L = add4(cR2, cM);  // R2 - L1
+    dbl4 dl, dr;
+    weno_pair64(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps, dl.x, dr.x);
+    weno_pair64(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps, dl.y, dr.y);
+    weno_pair64(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps, dl.z, dr.z);
+    weno_pair64(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps, dl.w, dr.w);
 
     dbl4 wl = add4(L1, unproject64(C, dl));
     dbl4 wr = add4(R1, unproject64(C, dr));
@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
     dbl4 acc = dbl4_make(0, 0, 0, 0);
     {
         const int64_t b = __ldg(A.slice_voff + sl) + lane, e = __ldg(A.slice_voff + sl + 1);
+#pragma unroll 4
         for (int64_t p = b; p < e; p += kSell) {
             const int32_t j = __ldg(A.vid + p);
             const double a = __ldg(wf + p), c = __ldg(wg + p);
@@ -260,6 +261,7 @@ __global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
     }
     {
         const int64_t b = __ldg(A.slice_eoff + sl) + lane, e = __ldg(A.slice_eoff + sl + 1);
+#pragma unroll 4
         for (int64_t p = b; p < e; p += kSell) {
             const int32_t k = __ldg(A.eid + p);
             const double a = __ldg(we + p);
@@ -301,7 +303,7 @@ __global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
     }
     st4(A.wout, v, o);
     dbl4 f, g;
-    euler_fg(o, A.gamma - 1.0, f, g);
+    euler_fg(o, A.gm1, f, g);
     double *Fo = static_cast<double *>(A.Fout);
     st4(Fo, 2 * v, f);
     st4(Fo, 2 * v + 1, g);
@@ -362,52 +364,24 @@ __device__ __forceinline__ float4 unproject32(const Roe32 &R, const float4 &c) {
                        R.H * (c.x + c.w) + R.hq2 * c.y + R.qn * dd + R.qt * c.z);
 }
 
-// Coefficient block of one side in FP32 from x[5] (x[2] = -1/2, x[3] = 1/2).
-__device__ __forceinline__ void side_coef32(const float x[5], float *k) {
-    const float curv = 1.0408329997330663f;  // sqrt(13/12); dx = 1 in normalised coordinates
-    float val[3][3], der[3][3], sec[3][3];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const float pj = x[s + j], pa = x[s + (j + 1) % 3], pb = x[s + (j + 2) % 3];
-            const float id = __frcp_rn((pj - pa) * (pj - pb));
-            val[s][j] = pa * pb * id;
-            der[s][j] = -(pa + pb) * id;
-            sec[s][j] = 2.0f * id;
-        }
-    }
-    k[0] = val[0][0]; k[1] = val[0][1]; k[2] = val[1][0]; k[3] = val[1][2]; k[4] = val[2][1]; k[5] = val[2][2];
-    k[6] = der[0][0]; k[7] = der[0][1]; k[8] = der[1][0]; k[9] = der[1][2]; k[10] = der[2][1]; k[11] = der[2][2];
-    k[12] = curv * sec[0][0]; k[13] = curv * sec[0][1]; k[14] = curv * sec[1][0];
-    k[15] = curv * sec[1][2]; k[16] = curv * sec[2][1]; k[17] = curv * sec[2][2];
-    // degree-4 Lagrange weights at 0 of x[0] and x[4]
-    const float l0 = (x[1] * x[2] * x[3] * x[4]) *
-                     __frcp_rn((x[0] - x[1]) * (x[0] - x[2]) * (x[0] - x[3]) * (x[0] - x[4]));
-    const float l4 = (x[0] * x[1] * x[2] * x[3]) *
-                     __frcp_rn((x[4] - x[0]) * (x[4] - x[1]) * (x[4] - x[2]) * (x[4] - x[3]));
-    const float c0 = l0 * __frcp_rn(val[0][0]);
-    const float c2 = l4 * __frcp_rn(val[2][2]);
-    k[18] = c0;
-    k[19] = 1.0f - c0 - c2;
-    k[20] = c2;
-}
-
-// FP32 weights: alpha_k = C_k / (beta_k + eps32), omega = alpha / sum alpha.
-__device__ __forceinline__ float weno32(const float *k, float a, float b, float c, float d, float eps) {
-    const float v0 = fmaf(k[0], a, k[1] * b);
-    const float v1 = fmaf(k[2], b, k[3] * c);
-    const float v2 = fmaf(k[4], c, k[5] * d);
-    const float p0 = fmaf(k[6], a, k[7] * b);
-    const float p1 = fmaf(k[8], b, k[9] * c);
-    const float p2 = fmaf(k[10], c, k[11] * d);
-    const float q0 = fmaf(k[12], a, k[13] * b);
-    const float q1 = fmaf(k[14], b, k[15] * c);
-    const float q2 = fmaf(k[16], c, k[17] * d);
-    const float a0 = k[18] * __frcp_rn(fmaf(p0, p0, fmaf(q0, q0, eps)));
-    const float a1 = k[19] * __frcp_rn(fmaf(p1, p1, fmaf(q1, q1, eps)));
-    const float a2 = k[20] * __frcp_rn(fmaf(p2, p2, fmaf(q2, q2, eps)));
-    return fmaf(a0, v0, fmaf(a1, v1, a2 * v2)) * __frcp_rn(a0 + a1 + a2);
+// FP32 NU-WENO5 increments of one field, both sides (same sub-stencil
+// sharing as weno_pair64).  Weights alpha_k = C_k / (beta_k + eps32),
+// omega = alpha / sum(alpha); the four reciprocals of (beta + eps32) serve
+// both sides.
+__device__ __forceinline__ void weno_pair32(const float *k, float a, float b, float c, float d, float e, float f,
+                                            float eps, float &dl, float &dr) {
+    const float va = fmaf(k[0], a, k[1] * b), pa = fmaf(k[2], a, k[3] * b), qa = fmaf(k[4], a, k[5] * b);
+    const float vb = fmaf(k[6], b, k[7] * c), pb = fmaf(k[8], b, k[9] * c), qb = fmaf(k[10], b, k[11] * c);
+    const float vc = fmaf(k[12], c, k[13] * d), pc = fmaf(k[14], c, k[15] * d), qc = fmaf(k[16], c, k[17] * d);
+    const float vd = fmaf(k[18], e, k[19] * f), pd = fmaf(k[20], e, k[21] * f), qd = fmaf(k[22], e, k[23] * f);
+    const float ia = __frcp_rn(fmaf(pa, pa, fmaf(qa, qa, eps)));
+    const float ib = __frcp_rn(fmaf(pb, pb, fmaf(qb, qb, eps)));
+    const float ic = __frcp_rn(fmaf(pc, pc, fmaf(qc, qc, eps)));
+    const float id = __frcp_rn(fmaf(pd, pd, fmaf(qd, qd, eps)));
+    const float l0 = k[24] * ia, l1 = k[25] * ib, l2 = k[26] * ic;
+    dl = fmaf(l0, va, fmaf(l1, vb, l2 * vc)) * __frcp_rn(l0 + l1 + l2);
+    const float r0 = k[27] * id, r1 = k[28] * ic, r2 = k[29] * ib;
+    dr = fmaf(r0, vd, fmaf(r1, vc - c, r2 * (vb - c))) * __frcp_rn(r0 + r1 + r2);
 }
 
 __global__ void __launch_bounds__(kEdgeBlock) edge_flux_f32_kernel(EdgeArgs A) {
@@ -415,14 +389,13 @@ __global__ void __launch_bounds__(kEdgeBlock) edge_flux_f32_kernel(EdgeArgs A) {
     if (e >= A.ne) return;
     const float4 *__restrict__ w = static_cast<const float4 *>(A.w);
     const float *__restrict__ g = static_cast<const float *>(A.coef);
-    const float gm1 = (float)(A.gamma - 1.0);
-    const float eps = (float)A.eps;
+    const float gm1 = A.gm1f;
+    const float eps = A.epsf;
     const int64_t ne = A.ne;
     int32_t s[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
-    const float x0 = __ldg(g + e), x1 = __ldg(g + ne + e), x4 = __ldg(g + 2 * ne + e), x5 = __ldg(g + 3 * ne + e);
-    const float nx = __ldg(g + 4 * ne + e), ny = __ldg(g + 5 * ne + e);
+    const float nx = __ldg(g + 30 * ne + e), ny = __ldg(g + 31 * ne + e);
     const float4 L1 = __ldg(w + s[2]), R1 = __ldg(w + s[3]);
     const Prim32 pL1 = prim32(L1, gm1), pR1 = prim32(R1, gm1);
     const Roe32 C = roe32(L1, pL1, R1, pR1, nx, ny, gm1);
@@ -431,28 +404,15 @@ __global__ void __launch_bounds__(kEdgeBlock) edge_flux_f32_kernel(EdgeArgs A) {
     const float4 cL3 = project32(C, sub4f(__ldg(w + s[0]), L1));
     const float4 cR2 = project32(C, sub4f(__ldg(w + s[4]), R1));
     const float4 cR3 = project32(C, sub4f(__ldg(w + s[5]), R1));
-
-    float k[kSideCoef];
-    {
-        const float xl[5] = {x0, x1, -0.5f, 0.5f, x4};
-        side_coef32(xl, k);
-    }
+    float k[30];
+#pragma unroll
+    for (int i = 0; i < 30; ++i) k[i] = __ldg(g + (int64_t)i * ne + e);
     const float4 cR2L = add4f(cR2, cM);
-    float4 dl;
-    dl.x = weno32(k, cL3.x, cL2.x, cM.x, cR2L.x, eps);
-    dl.y = weno32(k, cL3.y, cL2.y, cM.y, cR2L.y, eps);
-    dl.z = weno32(k, cL3.z, cL2.z, cM.z, cR2L.z, eps);
-    dl.w = weno32(k, cL3.w, cL2.w, cM.w, cR2L.w, eps);
-    {
-        const float xr[5] = {-x5, -x4, -0.5f, 0.5f, -x1};
-        side_coef32(xr, k);
-    }
-    const float4 cL2R = sub4f(cL2, cM);
-    float4 dr;
-    dr.x = weno32(k, cR3.x, cR2.x, -cM.x, cL2R.x, eps);
-    dr.y = weno32(k, cR3.y, cR2.y, -cM.y, cL2R.y, eps);
-    dr.z = weno32(k, cR3.z, cR2.z, -cM.z, cL2R.z, eps);
-    dr.w = weno32(k, cR3.w, cR2.w, -cM.w, cL2R.w, eps);
+    float4 dl, dr;
+    weno_pair32(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, eps, dl.x, dr.x);
+    weno_pair32(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, eps, dl.y, dr.y);
+    weno_pair32(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, eps, dl.z, dr.z);
+    weno_pair32(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, eps, dl.w, dr.w);
 
     float4 wl = add4f(L1, unproject32(C, dl));
     float4 wr = add4f(R1, unproject32(C, dr));
@@ -523,6 +483,7 @@ __global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     {
         const int64_t b = __ldg(A.slice_voff + sl) + lane, e = __ldg(A.slice_voff + sl + 1);
+#pragma unroll 4
         for (int64_t p = b; p < e; p += kSell) {
             const int32_t j = __ldg(A.vid + p);
             const float a = __ldg(wf + p), c = __ldg(wg + p);
@@ -535,6 +496,7 @@ __global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
     }
     {
         const int64_t b = __ldg(A.slice_eoff + sl) + lane, e = __ldg(A.slice_eoff + sl + 1);
+#pragma unroll 4
         for (int64_t p = b; p < e; p += kSell) {
             const int32_t k = __ldg(A.eid + p);
             const float a = __ldg(we + p);
@@ -579,7 +541,7 @@ __global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
     const float4 s32 = make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.w);
     A.w32out[v] = s32;
     float4 f, g;
-    euler_fg32(s32, (float)(A.gamma - 1.0), f, g);
+    euler_fg32(s32, A.gm1f, f, g);
     float4 *Fo = static_cast<float4 *>(A.Fout);
     Fo[2 * v] = f;
     Fo[2 * v + 1] = g;
@@ -641,6 +603,11 @@ __global__ void fma_probe_kernel(T *out, int iters, T a, T b) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += x[k];
     out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void recip_check_kernel(const double *x, double *y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = recip64(x[i]);
 }
 
 inline unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -713,6 +680,10 @@ double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s) {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return 2.0 * 8.0 * iters * (double)nb * nt / (ms * 1e-3) / 1e12;
+}
+
+void launch_recip_check(const double *x, double *y, int64_t n, cudaStream_t s) {
+    if (n > 0) recip_check_kernel<<<blocks(n, 256), 256, 0, s>>>(x, y, n);
 }
 
 }  // namespace fdu

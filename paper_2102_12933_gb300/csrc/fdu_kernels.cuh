@@ -13,11 +13,12 @@ constexpr int kDivBlock = 128;   // threads per block, divergence kernels
 // Edge-flux inputs (internal ids, SoA over the active edges).
 struct EdgeArgs {
     const int32_t *sten;  // [6][ne]  L3 L2 L1 R1 R2 R3
-    const void *coef;     // FP64: [44][ne] coefficient blocks; FP32: [6][ne] compact (xi0, xi1, xi4, xi5, nx, ny)
+    const void *coef;     // [kEdgeCoef][ne] coefficient blocks, FP64 or FP32
     const void *w;        // FP64: [nv][4] double; FP32: [nv] float4
     void *r;              // FP64: [ne][4] double; FP32: [ne] float4
     int64_t ne;
-    double gamma, eps;
+    double gm1, eps;      // gamma - 1 and the WENO epsilon (FP64 path)
+    float gm1f, epsf;     // the same for the FP32 path
     unsigned long long *fallback;  // edges that fell back to first order (device counter)
 };
 
@@ -44,7 +45,8 @@ struct DivArgs {
     float4 *w32out;              // FP32 copy of wout (FP32 residual path), or nullptr
     double dt;
     const double *dt_dev;        // if non-null, dt is read here
-    double gamma;
+    double gm1;                  // gamma - 1
+    float gm1f;
 };
 
 void launch_vertex_flux_f64(const double *w, double *F, int64_t n, double gamma, cudaStream_t s);
@@ -59,6 +61,8 @@ void launch_ghost_fill(double *w, void *F, int fq, float4 *w32, const int32_t *d
 // FMA throughput (TFLOP/s) of `precision` 64 or 32 with sms*8 blocks of 256
 // threads; scratch holds sms*8*256 elements of that precision.
 double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s);
+// y[i] = the kernels' FP64 reciprocal of x[i] (device pointers; accuracy check)
+void launch_recip_check(const double *x, double *y, int64_t n, cudaStream_t s);
 void launch_max_dt(const double *w, const double *hmin, int64_t n, double gamma, unsigned long long *slot,
                    cudaStream_t s);
 

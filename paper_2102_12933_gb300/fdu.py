@@ -33,6 +33,7 @@ EXPORTS = (
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
     "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
+    "fdu_check_recip64",
 )
 
 
@@ -101,6 +102,7 @@ def load():
         L.fdu_profile.argtypes = [P, C.c_int]
         L.fdu_probe_fma.argtypes = [C.c_int, C.c_int, dp]
         L.fdu_residual_noalloc.argtypes = [P, P, P, P]
+        L.fdu_check_recip64.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_profile_read.argtypes = [P, C.c_int, C.c_int, dp, lp, C.c_int]
         for name in EXPORTS:
             if name not in ("fdu_version", "fdu_last_error"):
@@ -178,6 +180,14 @@ def probe_fma(device=0, precision=64) -> float:
     t = C.c_double()
     _check(load().fdu_probe_fma(int(device), int(precision), C.byref(t)))
     return t.value
+
+
+def check_recip64(x, device=0):
+    """The kernels' FP64 reciprocal of x (accuracy check)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x)
+    _check(load().fdu_check_recip64(int(device), _dp(x), _dp(y), x.size))
+    return y
 
 
 class Mesh:

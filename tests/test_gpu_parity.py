@@ -196,3 +196,14 @@ def test_full_size_sampled_parity():
     got32 = M.residual(32)
     for k in range(4):
         assert rel_l2(got32[sel, k], want[sel, k]) <= 1e-4
+
+
+def test_fast_reciprocal_within_two_ulp_of_ieee_division():
+    """The Newton-Raphson reciprocal used for the WENO weights and Roe averages."""
+    rng = np.random.default_rng(3)
+    x = np.concatenate([10.0 ** rng.uniform(-80, 80, 200000), rng.uniform(0.5, 2.0, 100000),
+                        np.array([1.0, 2.0, 3.0, 1e-300, 1e300, np.nextafter(1.0, 2.0)])])
+    y = fdu.check_recip64(x)
+    want = 1.0 / x
+    ulp = np.abs(y - want) / np.spacing(want)
+    assert ulp.max() <= 2.0

@@ -246,12 +246,17 @@ def run_ours(args):
     d32_ms, d32_n = M.profile_read("div", 32)
     M.profile(False)
     w32 = M.get_state()
-    # reference FP64 state for the same number of steps
+    # FP32 error against FP64 after 100 steps from the same initial state
+    # (relative L2 of density and energy, the stated error of the FP32 form)
+    err_steps = 100
     M.set_state(w0)
-    M.rk_steps(dt, args.warmup + args.steps, 64, stream=stream)
+    M.rk_steps(dt, err_steps, 64, stream=stream)
     w64b = M.get_state()
-    err32 = {"rho": _rel_l2(w32[:, 0], w64b[:, 0]), "rhoE": _rel_l2(w32[:, 3], w64b[:, 3]),
-             "steps": args.warmup + args.steps}
+    M.set_state(w0)
+    M.rk_steps(dt, err_steps, 32, stream=stream)
+    w32b = M.get_state()
+    err32 = {"rho": _rel_l2(w32b[:, 0], w64b[:, 0]), "rhoE": _rel_l2(w32b[:, 3], w64b[:, 3]),
+             "steps": err_steps}
 
     # ---------------- end to end through the C-ABI with host buffers
     host_in = np.ascontiguousarray(w0)
@@ -354,6 +359,76 @@ def run_ours(args):
     return 0
 
 
+def run_riemann(args):
+    """Config 3: four-quadrant 2D Riemann problem on [0,1]^2, ~1M vertices
+    (1000 x 1000 jittered lattice + 5 transmissive ghost layers), advanced to
+    t = 0.3 with the device-computed CFL time step, in FP64 and FP32."""
+    import torch
+
+    from paper_2102_12933_gb300 import fdu, inputs
+
+    ws_, rank, local = _dist()
+    torch.cuda.set_device(local)
+    n = args.n if args.n != N_LATTICE else 1000
+    mesh, w0 = inputs.riemann_case(n, ghost_layers=5, seed=1003)
+    t_build = time.perf_counter()
+    # the unguarded method turns non-physical on this problem (DESIGN.md); the
+    # stage positivity safeguard keeps rho, p > 0 so the run reaches t_end
+    M = fdu.Mesh(mesh.xy, mesh.tri, 0.0, 0.0, device=local, ghost_donor=mesh.ghost_donor, positivity_alpha=0.1)
+    t_build = time.perf_counter() - t_build
+    real = mesh.ghost_donor < 0
+    n_real = int(real.sum())
+    out = {}
+    states = {}
+    err_steps = 16  # FP32 vs FP64 compared after this many steps from the same state
+    for prec in (64, 32):
+        M.set_state(w0)
+        M.advance(0.5, 0.3, prec, max_steps=8)  # warm-up (graph capture)
+        M.set_state(w0)
+        M.fallback_count(reset=True)
+        M.limited_count(reset=True)
+        steps, t, el, status = 0, 0.0, 0.0, "reached t_end"
+        while t < args.t_end and steps < args.riemann_max_steps:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                k, t = M.advance(0.5, args.t_end, prec, max_steps=8)
+            except fdu.FduError as e:
+                status = f"stopped: {e}"
+                break
+            torch.cuda.synchronize()
+            el += time.perf_counter() - t0
+            steps += k
+            if steps == err_steps:
+                states[prec] = M.get_state()
+        if t < args.t_end and status == "reached t_end":
+            status = f"stopped at max_steps={args.riemann_max_steps}"
+        out[prec] = {"steps": steps, "t": t, "seconds": round(el, 3), "status": status,
+                     "value": round(n_real * 3 * steps / el / 1e6, 2) if el > 0 else None,
+                     "fallback_edges": M.fallback_count(), "safeguarded_vertex_stages": M.limited_count()}
+    err = None
+    if 64 in states and 32 in states:
+        err = {"rho": _rel_l2(states[32][real, 0], states[64][real, 0]),
+               "rhoE": _rel_l2(states[32][real, 3], states[64][real, 3]), "steps": err_steps}
+    line = {
+        "metric": METRIC, "value": out[64]["value"], "unit": "Mvertex/s", "n_gpus": 1,
+        "steps": out[64]["steps"], "warmup": 1,
+        "ms_per_step": round(1e3 * out[64]["seconds"] / max(out[64]["steps"], 1), 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"four-quadrant 2D Riemann problem on [0,1]^2, {n}x{n} jittered lattice + 5 "
+                               f"transmissive ghost layers ({mesh.nv} vertices, {n_real} real), to t = {args.t_end} "
+                               "with device-side CFL 0.5 time steps and the stage positivity safeguard (alpha 0.1) "
+                               "(wall-clock timed, includes the host's time checks every 8 steps)",
+                   "host_build_s": round(t_build, 2)},
+        "fp64": out[64], "fp32": dict(out[32], speedup_vs_f64=(round(out[32]["value"] / out[64]["value"], 3)
+                                                               if out[32]["value"] and out[64]["value"] else None),
+                                      error_vs_f64=err),
+    }
+    print(json.dumps(line), flush=True)
+    M.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,11 +437,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice size (n x n vertices); 500 = the workload")
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "riemann"],
+                    help="vortex: the 250k periodic vortex (default line); riemann: the 1M-vertex "
+                         "transmissive four-quadrant Riemann problem to t_end")
+    ap.add_argument("--t-end", dest="t_end", type=float, default=0.3)
+    ap.add_argument("--riemann-max-steps", dest="riemann_max_steps", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "riemann":
+        return run_riemann(args)
     return run_ours(args)
 
 

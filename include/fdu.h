@@ -68,6 +68,10 @@ typedef struct fdu_mesh_opts {
     int device;         /* CUDA device ordinal; -1 = host tables only (no GPU use) */
     int host_threads;   /* threads for host preprocessing; 0 = all cores */
     const int32_t *ghost_donor; /* transmissive: [nv] donor vertex of each ghost, -1 for real vertices; NULL = none */
+    double positivity_alpha;    /* stage positivity safeguard: 0 = off (the paper's method); in (0,1): the
+                                   forward-Euler part ws + theta dt L of each vertex's RK stage uses the
+                                   largest theta in {1, 1/2, ..., 2^-20, 0} keeping rho and p at least alpha
+                                   times the stage input's (the paper has no such safeguard) */
 } fdu_mesh_opts;
 
 typedef struct fdu_mesh fdu_mesh;
@@ -157,6 +161,22 @@ fdu_status fdu_rk_step(fdu_mesh *mesh, double dt, int precision, void *stream);
 /* n_steps SSP-RK3 steps, captured once into a CUDA graph per (precision,
  * dt) and replayed. */
 fdu_status fdu_rk_steps(fdu_mesh *mesh, double dt, int precision, int n_steps, void *stream);
+
+/* Advance the current state with SSP-RK3 steps whose time step is computed
+ * on the device before every step: dt = min(cfl * min_v h_v / (|u_v| +
+ * c_v), t_end - t) (the CFL bound of fdu_max_dt), until the mesh time t
+ * reaches t_end or max_steps steps were taken.  The mesh time starts at 0
+ * at fdu_set_state.  Steps run as captured CUDA graphs of 8 steps; steps
+ * past t_end do no work.  *steps_done (may be NULL) gets the steps taken by
+ * this call and *t_out (may be NULL) the time reached.  Synchronises
+ * `stream` once per 8 steps.  FDU_ERR_NONPHYSICAL if the bound is not
+ * positive and finite. */
+fdu_status fdu_advance(fdu_mesh *mesh, double cfl, double t_end, int precision, int64_t max_steps, int64_t *steps_done,
+                       double *t_out, void *stream);
+
+/* Vertex stage updates the positivity safeguard scaled (theta < 1), counted
+ * since the last reset (reset = 1 zeroes it).  Synchronises `stream`. */
+fdu_status fdu_limited_count(fdu_mesh *mesh, int64_t *count, int reset, void *stream);
 
 /* Edges whose interpolated density or pressure was not positive and that
  * fell back to the first-order end states, counted since the last reset

@@ -88,6 +88,9 @@ def lib():
             L.om_roe_flux.restype = C.c_int
             L.om_stage_combine.argtypes = [i64, C.c_int, dp, dp, dp, C.c_double, dp]
             L.om_smoothness_all.argtypes = [dp, dp, dp]
+            L.om_set_positivity.argtypes = [P, C.c_double]
+            L.om_pos_limited.argtypes = [P]
+            L.om_pos_limited.restype = i64
             _lib = L
     return _lib
 
@@ -277,6 +280,13 @@ class OracleMesh:
         nf = C.c_int64()
         _check(lib().om_rk3_step(self._h, _d(w), float(dt), float(eps), C.byref(nf)))
         return (w, nf.value) if return_fallbacks else w
+
+    def set_positivity(self, alpha):
+        """Enable the stage positivity safeguard (alpha > 0) or disable it (0)."""
+        lib().om_set_positivity(self._h, float(alpha))
+
+    def positivity_limited(self):
+        return int(lib().om_pos_limited(self._h))
 
     def max_dt(self, w, cfl):
         w = _f64(w, (self.nv, 4))

@@ -79,6 +79,8 @@ typedef struct om_mesh {
     /* LSQ weights, aligned with dv_id / de_id */
     double *wf, *wg, *we;
     uint8_t *has_w;   /* [nv] weights computed for this vertex */
+    double pos_alpha; /* positivity safeguard of the stage update (0 = off) */
+    int64_t pos_limited; /* vertices whose stage update was scaled */
 } om_mesh;
 
 static void disp(const om_mesh *m, int64_t a, int64_t b, double d[2]) {
@@ -939,6 +941,44 @@ void om_stage_combine(int64_t n, int stage, const double *wn, const double *ws, 
     }
 }
 
+/* Positivity safeguard of a stage (a reading: the paper has none, its Sod
+ * run overshoots).  The forward-Euler part fe = ws + theta dt L of each
+ * vertex's stage uses the largest theta in {1, 1/2, ..., 2^-20, 0} with
+ * rho(fe) >= alpha rho(ws) and p(fe) >= alpha p(ws); the stage is then the
+ * SSP combination of w_n and fe, which stays physical because the set of
+ * physical states is convex.  Returns the number of limited vertices. */
+static int64_t pos_limit(const om_mesh *m, int64_t nv, const double *ws, const double *L, double dt, double *fe) {
+    int64_t lim = 0;
+    for (int64_t v = 0; v < nv; ++v) {
+        const double *s = ws + 4 * v;
+        const double *l = L + 4 * v;
+        double *f = fe + 4 * v;
+        if (m->ghost && m->ghost[v] >= 0) {
+            for (int c = 0; c < 4; ++c) f[c] = s[c] + dt * l[c];
+            continue;
+        }
+        double ps = pressure(s, m->gamma);
+        double theta = 1.0;
+        int ok = 0;
+        for (int k = 0; k <= 20; ++k) {
+            for (int c = 0; c < 4; ++c) f[c] = s[c] + theta * dt * l[c];
+            if (f[0] >= m->pos_alpha * s[0] && pressure(f, m->gamma) >= m->pos_alpha * ps) {
+                ok = 1;
+                break;
+            }
+            theta *= 0.5;
+        }
+        if (!ok) {
+            theta = 0.0;
+            for (int c = 0; c < 4; ++c) f[c] = s[c];
+        }
+        lim += theta < 1.0;
+    }
+    return lim;
+}
+
+void om_set_positivity(om_mesh *m, double alpha) { m->pos_alpha = alpha; }
+
 /* one SSP-RK3 step in place on w[nv][4] */
 int om_rk3_step(om_mesh *m, double *w, double dt, double eps, int64_t *nfallback) {
     int64_t n = m->nv * 4, nf = 0, f;
@@ -953,7 +993,20 @@ int om_rk3_step(om_mesh *m, double *w, double dt, double eps, int64_t *nfallback
         st = om_residual(m, ws, eps, NULL, L, &f);
         nf += f;
         if (st) break;
-        om_stage_combine(n, stage, wn, ws, L, dt, ws);
+        if (m->pos_alpha > 0) {
+            /* fe = ws + theta dt L, then the stage combination with dt L -> fe - ws */
+            double *fe = (double *)malloc(n * sizeof(double));
+            m->pos_limited += pos_limit(m, m->nv, ws, L, dt, fe);
+            for (int64_t i = 0; i < n; ++i) L[i] = fe[i];
+            free(fe);
+            for (int64_t i = 0; i < n; ++i) {
+                if (stage == 1) ws[i] = L[i];
+                else if (stage == 2) ws[i] = 0.75 * wn[i] + 0.25 * L[i];
+                else ws[i] = (1.0 / 3.0) * wn[i] + (2.0 / 3.0) * L[i];
+            }
+        } else {
+            om_stage_combine(n, stage, wn, ws, L, dt, ws);
+        }
         if (m->ghost)
             for (int64_t v = 0; v < m->nv; ++v)
                 if (m->ghost[v] >= 0) memcpy(ws + 4 * v, wn + 4 * v, 4 * sizeof(double));
@@ -994,3 +1047,5 @@ double om_max_dt(const om_mesh *m, const double *w, double cfl) {
 void om_smoothness_all(const double *x, const double *u, double *beta) {
     for (int k = 0; k < 3; ++k) beta[k] = smoothness(x + k, u + k, x[2], x[3]);
 }
+
+int64_t om_pos_limited(const om_mesh *m) { return m->pos_limited; }

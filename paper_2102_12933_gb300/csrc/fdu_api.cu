@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -72,10 +73,13 @@ struct fdu_mesh {
     float4 *w32 = nullptr;                                  // [nv]
     double *r64 = nullptr;                                  // [ne_act][4]
     float4 *r32 = nullptr;                                  // [ne_act]
-    unsigned long long *counters = nullptr;                 // [0] fallbacks, [1] dt slot
+    unsigned long long *counters = nullptr;  // [0] fallbacks, [1] dt slot, [2] adaptive slot, [3] adaptive steps,
+                                             // [4] stage updates scaled by the positivity safeguard
+    double *tstate = nullptr;                // adaptive stepping: (t, dt, nonphysical flag)
     bool f64_valid = false, f32_valid = false;              // F64[0] / (w32, F32[0]) describe wn
     cudaStream_t own_stream = nullptr;
     std::map<std::pair<int, double>, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, double, double>, cudaGraphExec_t> adaptive_graphs;
     // kernel timing: event pairs per kind (0 edge64, 1 div64, 2 edge32, 3 div32)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev[4];
@@ -107,6 +111,8 @@ struct fdu_mesh {
             cudaDeviceSynchronize();
             for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
             graphs.clear();
+            for (auto &kv : adaptive_graphs) cudaGraphExecDestroy(kv.second);
+            adaptive_graphs.clear();
             for (auto &v : prof_ev)
                 for (cudaEvent_t e : v) cudaEventDestroy(e);
             for (void *p : allocs) cudaFree(p);
@@ -234,8 +240,14 @@ fdu_status upload_tables(fdu_mesh *m) {
     if ((st = m->alloc(m->w32, nv))) return st;
     if ((st = m->alloc(m->r64, 4 * ne))) return st;
     if ((st = m->alloc(m->r32, ne))) return st;
-    if ((st = m->alloc(m->counters, 2))) return st;
-    CK(cudaMemset(m->counters, 0, 2 * sizeof(unsigned long long)));
+    if ((st = m->alloc(m->counters, 5))) return st;
+    CK(cudaMemset(m->counters, 0, 5 * sizeof(unsigned long long)));
+    {
+        const unsigned long long inf_bits = 0x7FF0000000000000ull;
+        CK(cudaMemcpy(m->counters + 2, &inf_bits, sizeof inf_bits, cudaMemcpyHostToDevice));
+    }
+    if ((st = m->alloc(m->tstate, 4))) return st;
+    CK(cudaMemset(m->tstate, 0, 4 * sizeof(double)));
     CK(cudaMemset(m->wn, 0, 4 * nv * sizeof(double)));
     return FDU_OK;
 }
@@ -252,6 +264,7 @@ EdgeArgs edge_args(fdu_mesh *m, int prec, const void *w) {
     a.gm1f = (float)(m->opts.gamma - 1.0);
     a.epsf = (float)m->opts.weno_eps32;
     a.fallback = m->counters;
+    a.dt_dev = nullptr;
     return a;
 }
 
@@ -271,6 +284,8 @@ DivArgs div_args(fdu_mesh *m, int prec, int fin) {
     }
     a.gm1 = m->opts.gamma - 1.0;
     a.gm1f = (float)(m->opts.gamma - 1.0);
+    a.pos_alpha = m->opts.positivity_alpha;
+    a.limited = m->counters + 4;
     return a;
 }
 
@@ -316,8 +331,10 @@ void enqueue_step(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaSt
     for (int stage = 1; stage <= 3; ++stage) {
         const double *win = stage == 1 ? m->wn : m->ws;
         timed(m, kd, prof, s, [&] {
-            if (prec == 64) launch_edge_flux_f64(edge_args(m, 64, win), s);
-            else launch_edge_flux_f32(edge_args(m, 32, m->w32), s);
+            EdgeArgs ea = edge_args(m, prec, prec == 64 ? (const void *)win : (const void *)m->w32);
+            ea.dt_dev = dt_dev;
+            if (prec == 64) launch_edge_flux_f64(ea, s);
+            else launch_edge_flux_f32(ea, s);
         });
         DivArgs a = div_args(m, prec, stage - 1);
         a.wn = m->wn;
@@ -334,6 +351,15 @@ void enqueue_step(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaSt
         if (m->n_ghost > 0)
             launch_ghost_fill(a.wout, a.Fout, fq, prec == 32 ? m->w32 : nullptr, m->donor, m->n_real, m->n_ghost, s);
     }
+}
+
+// One adaptive step: reduce the time-step bound on the device, finalise
+// dt = min(cfl * bound, t_end - t) into tstate, then the three stages read
+// dt from there (and skip their work once t_end is reached).
+void enqueue_adaptive_step(fdu_mesh *m, int prec, double cfl, double t_end, cudaStream_t s) {
+    launch_max_dt(m->wn, m->hmin, m->n_real, m->opts.gamma, m->counters + 2, s);
+    launch_dt_finalize(m->counters + 2, m->tstate, cfl, t_end, m->counters + 3, s);
+    enqueue_step(m, prec, 0.0, m->tstate + 1, s, false);
 }
 
 }  // namespace
@@ -389,6 +415,7 @@ fdu_status fdu_default_opts(fdu_mesh_opts *o) {
     o->device = 0;
     o->host_threads = 0;
     o->ghost_donor = nullptr;
+    o->positivity_alpha = 0.0;
     return FDU_OK;
 }
 
@@ -399,6 +426,8 @@ fdu_status fdu_mesh_create(const double *xy, int64_t nv, const int32_t *tri, int
     if (nv < 3 || nt < 1 || nv > INT32_MAX / 2) return set_err(FDU_ERR_ARG, "bad vertex or triangle count");
     if (opts->lsq_degree < 1 || opts->lsq_degree > 6 || opts->lsq_levels < 1 || opts->lsq_levels > 2)
         return set_err(FDU_ERR_ARG, "lsq_degree must be 1..6 and lsq_levels 1..2");
+    if (!(opts->positivity_alpha >= 0.0 && opts->positivity_alpha < 1.0))
+        return set_err(FDU_ERR_ARG, "positivity_alpha must be in [0, 1)");
     if (!(opts->gamma > 1.0) || !(opts->weno_eps > 0) || !(opts->weno_eps32 > 0))
         return set_err(FDU_ERR_ARG, "gamma must be > 1 and the WENO epsilons > 0");
     if (opts->bc == FDU_BC_PERIODIC && !(opts->Lx > 0 && opts->Ly > 0))
@@ -530,6 +559,8 @@ fdu_status fdu_set_state(fdu_mesh *m, const double *w, int on_device, void *stre
         CK_LAUNCH();
     }
     m->f64_valid = m->f32_valid = false;
+    CK(cudaMemsetAsync(m->tstate, 0, 3 * sizeof(double), s));
+    CK(cudaMemsetAsync(m->counters + 3, 0, sizeof(unsigned long long), s));
     return FDU_OK;
 }
 
@@ -649,17 +680,82 @@ fdu_status fdu_rk_steps(fdu_mesh *m, double dt, int precision, int n_steps, void
     return FDU_OK;
 }
 
-fdu_status fdu_fallback_count(fdu_mesh *m, int64_t *count, int reset, void *stream) {
+fdu_status fdu_advance(fdu_mesh *m, double cfl, double t_end, int precision, int64_t max_steps, int64_t *steps_done,
+                       double *t_out, void *stream) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!(cfl > 0) || !std::isfinite(t_end) || max_steps < 0 || (precision != 64 && precision != 32))
+        return set_err(FDU_ERR_ARG, "need cfl > 0, a finite t_end, max_steps >= 0, precision 64 or 32");
+    cudaStream_t s = m->stream(stream);
+    ensure_fluxes(m, precision, s);
+    CK_LAUNCH();
+    const int batch = 8;
+    auto key = std::make_tuple(precision, cfl, t_end);
+    auto it = m->adaptive_graphs.find(key);
+    if (it == m->adaptive_graphs.end()) {
+        cudaStream_t cs = m->own_stream;
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, s));
+        CK(cudaStreamWaitEvent(cs, ev, 0));
+        CK(cudaEventDestroy(ev));
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < batch; ++i) enqueue_adaptive_step(m, precision, cfl, t_end, cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        cudaGraphExec_t ge;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        it = m->adaptive_graphs.emplace(key, ge).first;
+    }
+    double host[3] = {0, 0, 0};
+    unsigned long long n0 = 0, n1 = 0;
+    CK(cudaMemcpyAsync(&n0, m->counters + 3, sizeof n0, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(host, m->tstate, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    n1 = n0;
+    while (host[0] < t_end && (int64_t)(n1 - n0) < max_steps && host[2] == 0.0) {
+        const int64_t left = max_steps - (int64_t)(n1 - n0);
+        if (left >= batch) {
+            CK(cudaGraphLaunch(it->second, s));
+        } else {
+            for (int64_t i = 0; i < left; ++i) enqueue_adaptive_step(m, precision, cfl, t_end, s);
+            CK_LAUNCH();
+        }
+        CK(cudaMemcpyAsync(&n1, m->counters + 3, sizeof n1, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(host, m->tstate, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (host[1] == 0.0 && host[0] < t_end && host[2] == 0.0) break;  // no progress
+    }
+    if (precision == 64) m->f32_valid = false;
+    else m->f64_valid = false;
+    if (steps_done) *steps_done = (int64_t)(n1 - n0);
+    if (t_out) *t_out = host[0];
+    if (host[2] != 0.0) return set_err(FDU_ERR_NONPHYSICAL, "non-physical state in the adaptive time step");
+    return FDU_OK;
+}
+
+static fdu_status read_counter(fdu_mesh *m, int idx, int64_t *count, int reset, void *stream) {
     fdu_status st = need_device(m);
     if (st) return st;
     if (!count) return set_err(FDU_ERR_ARG, "null output");
     cudaStream_t s = m->stream(stream);
     unsigned long long c = 0;
-    CK(cudaMemcpyAsync(&c, m->counters, sizeof c, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&c, m->counters + idx, sizeof c, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (reset) CK(cudaMemsetAsync(m->counters, 0, sizeof c, s));
+    if (reset) CK(cudaMemsetAsync(m->counters + idx, 0, sizeof c, s));
     *count = (int64_t)c;
     return FDU_OK;
+}
+
+fdu_status fdu_fallback_count(fdu_mesh *m, int64_t *count, int reset, void *stream) {
+    return read_counter(m, 0, count, reset, stream);
+}
+
+fdu_status fdu_limited_count(fdu_mesh *m, int64_t *count, int reset, void *stream) {
+    return read_counter(m, 4, count, reset, stream);
 }
 
 fdu_status fdu_residual_noalloc(const fdu_mesh *mc, const double *w, double *dwdt, void *stream) {

@@ -148,6 +148,7 @@ __device__ __forceinline__ void weno_pair64(const double *k, double a, double b,
 __global__ void __launch_bounds__(kEdgeBlock) edge_flux_f64_kernel(EdgeArgs A) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= A.ne) return;
+    if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
     const double *__restrict__ w = static_cast<const double *>(A.w);
     const double *__restrict__ coef = static_cast<const double *>(A.coef);
     const double gm1 = A.gm1;
@@ -233,11 +234,43 @@ __global__ void vertex_flux_f64_kernel(const double *__restrict__ w, double *__r
     st4(F, 2 * v + 1, g);
 }
 
+// Forward-Euler part of an SSP-RK3 stage, fe = ws + theta dt L.  Without
+// the safeguard theta = 1.  With it (alpha > 0), theta is the largest of
+// 1, 1/2, ..., 2^-20 (else 0) with rho(fe) >= alpha rho(ws) and
+// p(fe) >= alpha p(ws), so that the stage combination of w_n and fe stays
+// physical (the set of physical states is convex).
+__device__ __forceinline__ dbl4 forward_euler(const dbl4 &ws, const dbl4 &L, double dt, double gm1, double alpha,
+                                             unsigned long long *limited) {
+    dbl4 fe = dbl4_make(fma(dt, L.x, ws.x), fma(dt, L.y, ws.y), fma(dt, L.z, ws.z), fma(dt, L.w, ws.w));
+    if (alpha > 0.0) {
+        auto pres = [&](const dbl4 &q) { return gm1 * (q.w - 0.5 * (q.y * q.y + q.z * q.z) / q.x); };
+        const double ps = pres(ws);
+        double th = 1.0;
+        bool ok = false;
+        for (int k = 0; k <= 20; ++k) {
+            fe = dbl4_make(fma(th * dt, L.x, ws.x), fma(th * dt, L.y, ws.y), fma(th * dt, L.z, ws.z),
+                           fma(th * dt, L.w, ws.w));
+            if (fe.x >= alpha * ws.x && pres(fe) >= alpha * ps) {
+                ok = true;
+                break;
+            }
+            th *= 0.5;
+        }
+        if (!ok) {
+            th = 0.0;
+            fe = ws;
+        }
+        if (th < 1.0) atomicAdd(limited, 1ull);
+    }
+    return fe;
+}
+
 // ------------------------------------------------------------------ FP64 divergence (+ RK stage)
 template <int MODE>
 __global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= A.n_real) return;
+    if (MODE != 0 && A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
     const int64_t sl = v / kSell;
     const int lane = (int)(v % kSell);
     const double *__restrict__ F = static_cast<const double *>(A.F);
@@ -289,17 +322,18 @@ __global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
     }
     const double dt = A.dt_dev ? *A.dt_dev : A.dt;
     const dbl4 ws = ld4(A.ws, v);
+    const dbl4 fe = forward_euler(ws, L, dt, A.gm1, A.pos_alpha, A.limited);
     dbl4 o;
     if (MODE == 1) {
-        o = dbl4_make(fma(dt, L.x, ws.x), fma(dt, L.y, ws.y), fma(dt, L.z, ws.z), fma(dt, L.w, ws.w));
+        o = fe;
     } else {
         const dbl4 wn = ld4(A.wn, v);
         const double cn = MODE == 2 ? 0.75 : 1.0 / 3.0;
         const double cs = MODE == 2 ? 0.25 : 2.0 / 3.0;
-        o.x = fma(cn, wn.x, cs * fma(dt, L.x, ws.x));
-        o.y = fma(cn, wn.y, cs * fma(dt, L.y, ws.y));
-        o.z = fma(cn, wn.z, cs * fma(dt, L.z, ws.z));
-        o.w = fma(cn, wn.w, cs * fma(dt, L.w, ws.w));
+        o.x = fma(cn, wn.x, cs * fe.x);
+        o.y = fma(cn, wn.y, cs * fe.y);
+        o.z = fma(cn, wn.z, cs * fe.z);
+        o.w = fma(cn, wn.w, cs * fe.w);
     }
     st4(A.wout, v, o);
     dbl4 f, g;
@@ -387,6 +421,7 @@ __device__ __forceinline__ void weno_pair32(const float *k, float a, float b, fl
 __global__ void __launch_bounds__(kEdgeBlock) edge_flux_f32_kernel(EdgeArgs A) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= A.ne) return;
+    if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
     const float4 *__restrict__ w = static_cast<const float4 *>(A.w);
     const float *__restrict__ g = static_cast<const float *>(A.coef);
     const float gm1 = A.gm1f;
@@ -473,6 +508,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= A.n_real) return;
+    if (MODE != 0 && A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
     const int64_t sl = v / kSell;
     const int lane = (int)(v % kSell);
     const float4 *__restrict__ F = static_cast<const float4 *>(A.F);
@@ -525,17 +561,18 @@ __global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
     // SSP-RK3 combination in FP64
     const double dt = A.dt_dev ? *A.dt_dev : A.dt;
     const dbl4 ws = ld4(A.ws, v);
+    const dbl4 fe = forward_euler(ws, L, dt, A.gm1, A.pos_alpha, A.limited);
     dbl4 o;
     if (MODE == 1) {
-        o = dbl4_make(fma(dt, L.x, ws.x), fma(dt, L.y, ws.y), fma(dt, L.z, ws.z), fma(dt, L.w, ws.w));
+        o = fe;
     } else {
         const dbl4 wn = ld4(A.wn, v);
         const double cn = MODE == 2 ? 0.75 : 1.0 / 3.0;
         const double cs = MODE == 2 ? 0.25 : 2.0 / 3.0;
-        o.x = fma(cn, wn.x, cs * fma(dt, L.x, ws.x));
-        o.y = fma(cn, wn.y, cs * fma(dt, L.y, ws.y));
-        o.z = fma(cn, wn.z, cs * fma(dt, L.z, ws.z));
-        o.w = fma(cn, wn.w, cs * fma(dt, L.w, ws.w));
+        o.x = fma(cn, wn.x, cs * fe.x);
+        o.y = fma(cn, wn.y, cs * fe.y);
+        o.z = fma(cn, wn.z, cs * fe.z);
+        o.w = fma(cn, wn.w, cs * fe.w);
     }
     st4(A.wout, v, o);
     const float4 s32 = make_float4((float)o.x, (float)o.y, (float)o.z, (float)o.w);
@@ -603,6 +640,26 @@ __global__ void fma_probe_kernel(T *out, int iters, T a, T b) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) s += x[k];
     out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void dt_finalize_kernel(unsigned long long *slot, double *tstate, double cfl, double t_end,
+                                   unsigned long long *nsteps) {
+    const double bound = __longlong_as_double((long long)*slot);
+    const double t = tstate[0];
+    double dt = cfl * bound;
+    const double rem = t_end - t;
+    if (!(bound > 0.0) || !(bound < INFINITY)) {
+        dt = 0.0;
+        tstate[2] = 1.0;  // non-physical state
+    } else if (rem <= 1e-12 * fabs(t_end)) {
+        dt = 0.0;
+    } else if (rem < dt) {
+        dt = rem;
+    }
+    tstate[1] = dt;
+    tstate[0] = dt > 0.0 ? (rem < cfl * bound ? t_end : t + dt) : t;
+    if (dt > 0.0) *nsteps += 1;
+    *slot = 0x7FF0000000000000ull;
 }
 
 __global__ void recip_check_kernel(const double *x, double *y, int64_t n) {
@@ -684,6 +741,11 @@ double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s) {
 
 void launch_recip_check(const double *x, double *y, int64_t n, cudaStream_t s) {
     if (n > 0) recip_check_kernel<<<blocks(n, 256), 256, 0, s>>>(x, y, n);
+}
+
+void launch_dt_finalize(unsigned long long *slot, double *tstate, double cfl, double t_end,
+                        unsigned long long *nsteps, cudaStream_t s) {
+    dt_finalize_kernel<<<1, 1, 0, s>>>(slot, tstate, cfl, t_end, nsteps);
 }
 
 }  // namespace fdu

@@ -19,7 +19,8 @@ struct EdgeArgs {
     int64_t ne;
     double gm1, eps;      // gamma - 1 and the WENO epsilon (FP64 path)
     float gm1f, epsf;     // the same for the FP32 path
-    unsigned long long *fallback;  // edges that fell back to first order (device counter)
+    unsigned long long *fallback;
+    const double *dt_dev; // adaptive stepping: a zero time step here skips the launch  // edges that fell back to first order (device counter)
 };
 
 // Divergence (+ optional SSP-RK3 stage) inputs.
@@ -47,6 +48,8 @@ struct DivArgs {
     const double *dt_dev;        // if non-null, dt is read here
     double gm1;                  // gamma - 1
     float gm1f;
+    double pos_alpha;            // stage positivity safeguard (0 = off)
+    unsigned long long *limited; // vertices whose stage update the safeguard scaled
 };
 
 void launch_vertex_flux_f64(const double *w, double *F, int64_t n, double gamma, cudaStream_t s);
@@ -63,6 +66,12 @@ void launch_ghost_fill(double *w, void *F, int fq, float4 *w32, const int32_t *d
 double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s);
 // y[i] = the kernels' FP64 reciprocal of x[i] (device pointers; accuracy check)
 void launch_recip_check(const double *x, double *y, int64_t n, cudaStream_t s);
+// Adaptive step: dt = min(cfl * bound, t_end - t) from the reduced bound in
+// *slot (bit pattern of a positive double); tstate = (t, dt, nonphysical);
+// the slot is reset to +inf for the next reduction; *nsteps counts steps
+// with dt > 0.
+void launch_dt_finalize(unsigned long long *slot, double *tstate, double cfl, double t_end,
+                        unsigned long long *nsteps, cudaStream_t s);
 void launch_max_dt(const double *w, const double *hmin, int64_t n, double gamma, unsigned long long *slot,
                    cudaStream_t s);
 

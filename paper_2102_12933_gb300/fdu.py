@@ -33,7 +33,7 @@ EXPORTS = (
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
     "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
-    "fdu_check_recip64",
+    "fdu_check_recip64", "fdu_advance", "fdu_limited_count",
 )
 
 
@@ -48,7 +48,7 @@ class MeshOpts(C.Structure):
         ("Lx", C.c_double), ("Ly", C.c_double), ("weno_eps", C.c_double), ("weno_eps32", C.c_double),
         ("gamma", C.c_double), ("lsq_degree", C.c_int), ("lsq_levels", C.c_int), ("bc", C.c_int),
         ("renumber", C.c_int), ("device", C.c_int), ("host_threads", C.c_int),
-        ("ghost_donor", C.POINTER(C.c_int32)),
+        ("ghost_donor", C.POINTER(C.c_int32)), ("positivity_alpha", C.c_double),
     ]
 
 
@@ -103,6 +103,8 @@ def load():
         L.fdu_probe_fma.argtypes = [C.c_int, C.c_int, dp]
         L.fdu_residual_noalloc.argtypes = [P, P, P, P]
         L.fdu_check_recip64.argtypes = [C.c_int, dp, dp, i64]
+        L.fdu_advance.argtypes = [P, C.c_double, C.c_double, C.c_int, i64, lp, dp, P]
+        L.fdu_limited_count.argtypes = [P, lp, C.c_int, P]
         L.fdu_profile_read.argtypes = [P, C.c_int, C.c_int, dp, lp, C.c_int]
         for name in EXPORTS:
             if name not in ("fdu_version", "fdu_last_error"):
@@ -194,7 +196,8 @@ class Mesh:
     """A mesh with its stencils, weights and device state (one fdu_mesh)."""
 
     def __init__(self, xy, tri, Lx=0.0, Ly=0.0, *, lsq_degree=2, lsq_levels=2, device=0, renumber=1,
-                 ghost_donor=None, weno_eps=1e-40, weno_eps32=1e-30, gamma=1.4, host_threads=0):
+                 ghost_donor=None, weno_eps=1e-40, weno_eps32=1e-30, gamma=1.4, host_threads=0,
+                 positivity_alpha=0.0):
         L = load()
         self._h = None
         xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
@@ -208,7 +211,7 @@ class Mesh:
             bc = FDU_BC_TRANSMISSIVE
         o = default_opts(Lx=float(Lx), Ly=float(Ly), lsq_degree=lsq_degree, lsq_levels=lsq_levels, device=device,
                          renumber=renumber, weno_eps=weno_eps, weno_eps32=weno_eps32, gamma=gamma, bc=bc,
-                         host_threads=host_threads)
+                         host_threads=host_threads, positivity_alpha=float(positivity_alpha))
         if gp is not None:
             o.ghost_donor = gp
         h = C.c_void_p()
@@ -318,3 +321,18 @@ class Mesh:
             raise ValueError("residual_noalloc takes CUDA tensors")
         _check(load().fdu_residual_noalloc(self._h, pw, po, _stream_ptr(stream)))
         return out
+
+    def advance(self, cfl, t_end, precision=64, max_steps=10**9, stream=None):
+        """SSP-RK3 steps with the device-computed CFL time step until t_end;
+        returns (steps taken, time reached)."""
+        n = C.c_int64()
+        t = C.c_double()
+        _check(load().fdu_advance(self._h, float(cfl), float(t_end), int(precision), int(max_steps), C.byref(n),
+                                  C.byref(t), _stream_ptr(stream)))
+        return n.value, t.value
+
+    def limited_count(self, reset=False, stream=None) -> int:
+        """Vertex stage updates scaled by the positivity safeguard since the last reset."""
+        c = C.c_int64()
+        _check(load().fdu_limited_count(self._h, C.byref(c), 1 if reset else 0, _stream_ptr(stream)))
+        return c.value

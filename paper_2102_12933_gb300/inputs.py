@@ -30,6 +30,7 @@ class Mesh:
     Ly: float  # periodic length in y (0 = not periodic)
     n: int = 0  # lattice size it was drawn from (informational)
     h: float = 0.0  # lattice spacing (informational)
+    ghost_donor: np.ndarray | None = None  # [nv] donor of each ghost vertex, -1 for real ones
 
     @property
     def nv(self) -> int:
@@ -86,7 +87,8 @@ def torus_lattice(n: int, L: float = 10.0, jitter: float = 0.2, seed: int = 1001
     return m
 
 
-def box_lattice(n: int, ghost_layers: int = 0, jitter: float = 0.2, seed: int = 1003) -> Mesh:
+def box_lattice(n: int, ghost_layers: int = 0, jitter: float = 0.2, seed: int = 1003,
+                random_diagonals: bool = True) -> Mesh:
     """Lattice on [0,1]^2 with n points per side (spacing h = 1/(n-1)).
 
     ``ghost_layers`` extra lattice layers are added outside the unit
@@ -107,6 +109,8 @@ def box_lattice(n: int, ghost_layers: int = 0, jitter: float = 0.2, seed: int = 
     interior = (i > 0) & (i < n - 1) & (j > 0) & (j < n - 1)
     xy[interior] += jit[interior]
     diag = rng.integers(0, 2, size=(m - 1) * (m - 1))
+    if not random_diagonals:
+        diag[:] = 0
     qi, qj = np.meshgrid(np.arange(m - 1), np.arange(m - 1), indexing="xy")
     qi = qi.ravel()
     qj = qj.ravel()
@@ -120,6 +124,12 @@ def box_lattice(n: int, ghost_layers: int = 0, jitter: float = 0.2, seed: int = 
     mesh = Mesh(xy=xy, tri=tri, Lx=0.0, Ly=0.0, n=n, h=h)
     if np.any(_signed_areas(xy, tri, 0.0, 0.0) <= 0):
         raise ValueError("jittered box lattice produced a non-positive triangle")
+    # ghost vertex -> the boundary lattice vertex nearest to it (-1 for real vertices)
+    ci = np.clip(i, 0, n - 1)
+    cj = np.clip(j, 0, n - 1)
+    donor = ((cj + g) * m + (ci + g)).astype(np.int32)
+    donor[interior | ((i >= 0) & (i <= n - 1) & (j >= 0) & (j <= n - 1))] = -1
+    mesh.ghost_donor = donor
     return mesh
 
 
@@ -210,6 +220,14 @@ def vortex_case(n: int, seed: int = 1001, L: float = 10.0, beta: float = 5.0,
     """Periodic vortex workload: jittered torus lattice + vortex state."""
     mesh = torus_lattice(n, L=L, jitter=jitter, seed=seed, random_diagonals=random_diagonals)
     w0 = isentropic_vortex(mesh.xy, L=L, beta=beta, centre=centre)
+    return mesh, w0
+
+
+def riemann_case(n: int, ghost_layers: int = 5, seed: int = 1003, jitter: float = 0.2,
+                 random_diagonals: bool = True):
+    """Four-quadrant Riemann problem on [0,1]^2 with transmissive ghost layers."""
+    mesh = box_lattice(n, ghost_layers=ghost_layers, seed=seed, jitter=jitter, random_diagonals=random_diagonals)
+    w0 = riemann_2d(mesh.xy)
     return mesh, w0
 
 

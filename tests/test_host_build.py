@@ -103,3 +103,26 @@ def test_error_statuses():
     with pytest.raises(fdu.FduError) as e:
         M.residual()
     assert e.value.status == -8
+
+
+def test_transmissive_box_tables_match_oracle():
+    """Four-quadrant Riemann box with 5 ghost layers: real vertices carry
+    stencils, ghosts do not; every active edge has a full 1D stencil."""
+    m, _ = inputs.riemann_case(21, ghost_layers=5)
+    M = fdu.Mesh(m.xy, m.tri, 0.0, 0.0, device=-1, ghost_donor=m.ghost_donor)
+    om = oracle.OracleMesh(m.xy, m.tri, 0.0, 0.0, ghost=m.ghost_donor)
+    om.build_weights()
+    assert M.info()["n_real"] == 21 * 21
+    assert np.array_equal(M.edges(), om.edges())
+    s1, x1 = M.edge_stencils()
+    s2, x2 = om.stencils()
+    assert np.array_equal(s1, s2)
+    ok = s1[:, 0] >= 0
+    assert np.abs(x1[ok] - x2[ok]).max() < 1e-13
+    a, b = M.div_stencils(), om.div_stencils()
+    for i in (0, 1, 4, 5):
+        assert np.array_equal(a[i], b[i])
+    for i in (2, 3, 6):
+        assert np.abs(a[i] - b[i]).max() <= 1e-11 * (1 + np.abs(b[i]).max())
+    ghost = m.ghost_donor >= 0
+    assert np.all(np.diff(a[0])[ghost] == 0)  # ghost rows are empty

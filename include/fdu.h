@@ -178,6 +178,43 @@ fdu_status fdu_advance(fdu_mesh *mesh, double cfl, double t_end, int precision, 
  * since the last reset (reset = 1 zeroes it).  Synchronises `stream`. */
 fdu_status fdu_limited_count(fdu_mesh *mesh, int64_t *count, int reset, void *stream);
 
+/* ---- Batches: many independent periodic meshes advanced together ----
+ * A batch is one fdu_mesh holding the disjoint union of n_meshes meshes
+ * (same opts, in particular the same periodic lengths): mesh i's vertices
+ * are rows vertex_offsets[i] .. vertex_offsets[i+1]-1 of every state array,
+ * so fdu_set_state / fdu_get_state / fdu_residual work on the batch as on
+ * one mesh.  fdu_batch_rk_steps advances every mesh with its own time step
+ * in ONE cooperative persistent launch per RK stage (edge fluxes of all
+ * meshes, a bounded grid barrier, then every vertex's divergence and stage
+ * update), captured once into a CUDA graph per (precision, launch shape).
+ * xy[i], tri[i], nv[i], nt[i] describe mesh i as for fdu_mesh_create. */
+fdu_status fdu_batch_create(int32_t n_meshes, const double *const *xy, const int64_t *nv, const int32_t *const *tri,
+                            const int64_t *nt, const fdu_mesh_opts *opts, fdu_mesh **out);
+/* Number of meshes and vertex_offsets[n_meshes+1] (may be NULL). */
+fdu_status fdu_batch_info(const fdu_mesh *batch, int32_t *n_meshes, int64_t *vertex_offsets);
+/* dt[i] = cfl * (the bound of fdu_max_dt over mesh i) for the current state. */
+fdu_status fdu_batch_max_dt(fdu_mesh *batch, double cfl, double *dt, void *stream);
+/* Per-mesh time steps used by fdu_batch_rk_steps (host array [n_meshes]). */
+fdu_status fdu_batch_set_dt(fdu_mesh *batch, const double *dt, void *stream);
+/* n_steps SSP-RK3 steps of every mesh (FP64 state accumulation; the
+ * residual at `precision`).  FDU_ERR_TIMEOUT if a grid barrier's bounded
+ * wait ran out (the state is then not advanced past that stage). */
+fdu_status fdu_batch_rk_steps(fdu_mesh *batch, int precision, int n_steps, void *stream);
+/* Persistent launch shape: threads per block (128, 256 or 512) and
+ * co-resident blocks per SM (1 .. occupancy limit). */
+fdu_status fdu_batch_set_launch(fdu_mesh *batch, int threads, int blocks_per_sm);
+/* Autotuner: times one RK3 step of the batch for every admissible launch
+ * shape (threads 128/256/512 x blocks per SM 1..occupancy) on a copy of the
+ * current state, keeps the fastest, restores the state and returns the
+ * choice and its time (any output pointer may be NULL). */
+fdu_status fdu_batch_autotune(fdu_mesh *batch, int precision, int *threads, int *blocks_per_sm, double *ms_per_step);
+/* Failure-path check of the bounded grid barrier: launches one persistent
+ * stage whose barrier waits for one block more than the grid holds, so
+ * every block's bounded wait runs out; *status gets the resulting status
+ * (FDU_ERR_TIMEOUT expected) and the state is left unchanged.  No GPU fault
+ * or hang is involved: the wait is bounded and the kernel returns. */
+fdu_status fdu_batch_barrier_selftest(fdu_mesh *batch, int *status);
+
 /* Edges whose interpolated density or pressure was not positive and that
  * fell back to the first-order end states, counted since the last reset
  * (reset = 1 zeroes the counter after reading).  Synchronises `stream`. */

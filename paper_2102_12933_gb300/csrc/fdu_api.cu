@@ -80,6 +80,16 @@ struct fdu_mesh {
     cudaStream_t own_stream = nullptr;
     std::map<std::pair<int, double>, cudaGraphExec_t> graphs;
     std::map<std::tuple<int, double, double>, cudaGraphExec_t> adaptive_graphs;
+    // batched meshes (fdu_batch_create): components, per-component dt, persistent launches
+    int32_t n_comp = 0;
+    std::vector<int64_t> comp_voff;   // original-vertex offset of each component
+    int32_t *comp = nullptr;          // [n_real] component of each internal vertex
+    double *dt_comp = nullptr;        // [n_comp]
+    unsigned long long *comp_slots = nullptr;  // [n_comp] dt reductions
+    unsigned int *bar = nullptr;      // grid barrier: count, generation
+    int *bar_err = nullptr;           // grid barrier timed out
+    int pl_threads = 256, pl_blocks = 0;  // persistent launch shape (blocks in total)
+    std::map<std::tuple<int, int, int>, cudaGraphExec_t> batch_graphs;
     // kernel timing: event pairs per kind (0 edge64, 1 div64, 2 edge32, 3 div32)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev[4];
@@ -113,6 +123,8 @@ struct fdu_mesh {
             graphs.clear();
             for (auto &kv : adaptive_graphs) cudaGraphExecDestroy(kv.second);
             adaptive_graphs.clear();
+            for (auto &kv : batch_graphs) cudaGraphExecDestroy(kv.second);
+            batch_graphs.clear();
             for (auto &v : prof_ev)
                 for (cudaEvent_t e : v) cudaEventDestroy(e);
             for (void *p : allocs) cudaFree(p);
@@ -351,6 +363,27 @@ void enqueue_step(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaSt
         if (m->n_ghost > 0)
             launch_ghost_fill(a.wout, a.Fout, fq, prec == 32 ? m->w32 : nullptr, m->donor, m->n_real, m->n_ghost, s);
     }
+}
+
+// One SSP-RK3 step of a batch: three cooperative persistent launches.
+cudaError_t enqueue_step_persistent(fdu_mesh *m, int prec, cudaStream_t s, unsigned int expected,
+                                    unsigned long long spin_limit) {
+    for (int stage = 1; stage <= 3; ++stage) {
+        const double *win = stage == 1 ? m->wn : m->ws;
+        EdgeArgs ea = edge_args(m, prec, prec == 64 ? (const void *)win : (const void *)m->w32);
+        DivArgs a = div_args(m, prec, stage - 1);
+        a.wn = m->wn;
+        a.ws = win;
+        a.wout = stage == 3 ? m->wn : m->ws;
+        a.Fout = prec == 64 ? (void *)m->F64[stage % 3] : (void *)m->F32[stage % 3];
+        a.w32out = prec == 32 ? m->w32 : nullptr;
+        a.comp = m->comp;
+        a.dt_comp = m->dt_comp;
+        cudaError_t e = launch_stage_persistent(prec, stage, ea, a, m->bar, m->bar + 1, expected, spin_limit,
+                                                m->bar_err, m->pl_threads, m->pl_blocks, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // One adaptive step: reduce the time-step bound on the device, finalise
@@ -756,6 +789,289 @@ fdu_status fdu_fallback_count(fdu_mesh *m, int64_t *count, int reset, void *stre
 
 fdu_status fdu_limited_count(fdu_mesh *m, int64_t *count, int reset, void *stream) {
     return read_counter(m, 4, count, reset, stream);
+}
+
+fdu_status fdu_batch_create(int32_t n_meshes, const double *const *xy, const int64_t *nv, const int32_t *const *tri,
+                            const int64_t *nt, const fdu_mesh_opts *opts, fdu_mesh **out) {
+    if (out) *out = nullptr;
+    if (n_meshes < 1 || !xy || !nv || !tri || !nt || !opts || !out) return set_err(FDU_ERR_ARG, "null argument");
+    if (opts->ghost_donor || opts->bc != FDU_BC_PERIODIC)
+        return set_err(FDU_ERR_ARG, "batches hold periodic meshes (without ghost vertices)");
+    if (opts->device < 0) return set_err(FDU_ERR_ARG, "batches need a device");
+    int64_t V = 0, T = 0;
+    for (int i = 0; i < n_meshes; ++i) {
+        if (!xy[i] || !tri[i] || nv[i] < 3 || nt[i] < 1) return set_err(FDU_ERR_ARG, "bad mesh " + std::to_string(i));
+        V += nv[i];
+        T += nt[i];
+    }
+    if (V > INT32_MAX / 2) return set_err(FDU_ERR_ARG, "batch too large");
+    std::vector<double> uxy(2 * V);
+    std::vector<int32_t> utri(3 * T), comp(V);
+    std::vector<int64_t> voff(n_meshes + 1, 0);
+    int64_t tv = 0, tt = 0;
+    for (int i = 0; i < n_meshes; ++i) {
+        voff[i] = tv;
+        std::memcpy(&uxy[2 * tv], xy[i], 2 * nv[i] * sizeof(double));
+        for (int64_t k = 0; k < 3 * nt[i]; ++k) {
+            const int32_t q = tri[i][k];
+            if (q < 0 || q >= nv[i]) return set_err(FDU_ERR_MESH, "mesh " + std::to_string(i) + ": bad vertex id");
+            utri[3 * tt + k] = (int32_t)(q + tv);
+        }
+        for (int64_t k = 0; k < nv[i]; ++k) comp[tv + k] = i;
+        tv += nv[i];
+        tt += nt[i];
+    }
+    voff[n_meshes] = tv;
+    fdu_mesh *m = new (std::nothrow) fdu_mesh();
+    if (!m) return set_err(FDU_ERR_ARG, "out of host memory");
+    m->opts = *opts;
+    std::string err;
+    int st = build_host_tables(uxy.data(), V, utri.data(), T, *opts, m->T, err, comp.data());
+    if (st != FDU_OK) {
+        delete m;
+        return set_err(st, err);
+    }
+    m->nv = V;
+    m->n_real = m->T.n_real;
+    m->n_ghost = 0;
+    m->ne_act = m->T.ne_active;
+    m->device = opts->device;
+    m->n_comp = n_meshes;
+    m->comp_voff = voff;
+    cudaError_t e = cudaSetDevice(m->device);
+    if (e == cudaSuccess) e = cudaStreamCreate(&m->own_stream);
+    if (e != cudaSuccess) {
+        delete m;
+        return set_err(FDU_ERR_CUDA, std::string("device setup: ") + cudaGetErrorString(e));
+    }
+    st = upload_tables(m);
+    if (st == FDU_OK) {
+        std::vector<int32_t> ci(m->n_real);
+        for (int64_t v = 0; v < m->n_real; ++v) ci[v] = comp[m->T.v_new2old[v]];
+        st = m->upload(m->comp, ci);
+    }
+    if (st == FDU_OK) st = m->alloc(m->dt_comp, n_meshes);
+    if (st == FDU_OK) st = m->alloc(m->comp_slots, n_meshes);
+    if (st == FDU_OK) st = m->alloc(m->bar, 2);
+    if (st == FDU_OK) st = m->alloc(m->bar_err, 1);
+    if (st == FDU_OK) {
+        cudaMemset(m->dt_comp, 0, n_meshes * sizeof(double));
+        cudaMemset(m->bar, 0, 2 * sizeof(unsigned int));
+        cudaMemset(m->bar_err, 0, sizeof(int));
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+        m->pl_threads = 256;
+        m->pl_blocks = sms * std::max(1, persistent_blocks_per_sm(32, 256));
+        if (cudaGetLastError() != cudaSuccess) st = set_err(FDU_ERR_CUDA, "batch setup");
+    }
+    if (st != FDU_OK) {
+        std::string keep = g_err;
+        m->release();
+        delete m;
+        return set_err(st, keep);
+    }
+    *out = m;
+    return FDU_OK;
+}
+
+fdu_status fdu_batch_info(const fdu_mesh *m, int32_t *n_meshes, int64_t *vertex_offsets) {
+    if (!m || !n_meshes) return set_err(FDU_ERR_ARG, "null argument");
+    *n_meshes = m->n_comp;
+    if (vertex_offsets) std::memcpy(vertex_offsets, m->comp_voff.data(), m->comp_voff.size() * sizeof(int64_t));
+    return FDU_OK;
+}
+
+static fdu_status need_batch(fdu_mesh *m) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (m->n_comp < 1) return set_err(FDU_ERR_ARG, "not a batch (use fdu_batch_create)");
+    return FDU_OK;
+}
+
+fdu_status fdu_batch_max_dt(fdu_mesh *m, double cfl, double *dt, void *stream) {
+    fdu_status st = need_batch(m);
+    if (st) return st;
+    if (!dt || !(cfl > 0)) return set_err(FDU_ERR_ARG, "need cfl > 0 and an output array");
+    cudaStream_t s = m->stream(stream);
+    std::vector<unsigned long long> bits(m->n_comp, 0x7FF0000000000000ull);
+    CK(cudaMemcpyAsync(m->comp_slots, bits.data(), bits.size() * sizeof(bits[0]), cudaMemcpyHostToDevice, s));
+    launch_max_dt(m->wn, m->hmin, m->n_real, m->opts.gamma, m->comp_slots, s, m->comp);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(bits.data(), m->comp_slots, bits.size() * sizeof(bits[0]), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < m->n_comp; ++i) {
+        double v;
+        std::memcpy(&v, &bits[i], sizeof v);
+        if (!(v > 0) || !std::isfinite(v))
+            return set_err(FDU_ERR_NONPHYSICAL, "non-physical state in mesh " + std::to_string(i));
+        dt[i] = cfl * v;
+    }
+    return FDU_OK;
+}
+
+fdu_status fdu_batch_set_dt(fdu_mesh *m, const double *dt, void *stream) {
+    fdu_status st = need_batch(m);
+    if (st) return st;
+    if (!dt) return set_err(FDU_ERR_ARG, "null dt");
+    for (int i = 0; i < m->n_comp; ++i)
+        if (!(dt[i] > 0) || !std::isfinite(dt[i])) return set_err(FDU_ERR_ARG, "dt must be positive and finite");
+    cudaStream_t s = m->stream(stream);
+    CK(cudaMemcpyAsync(m->dt_comp, dt, m->n_comp * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return FDU_OK;
+}
+
+fdu_status fdu_batch_set_launch(fdu_mesh *m, int threads, int blocks_per_sm) {
+    fdu_status st = need_batch(m);
+    if (st) return st;
+    if (threads != 128 && threads != 256 && threads != 512) return set_err(FDU_ERR_ARG, "threads must be 128, 256, 512");
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    const int occ = std::min(persistent_blocks_per_sm(64, threads), persistent_blocks_per_sm(32, threads));
+    if (blocks_per_sm < 1 || blocks_per_sm > occ)
+        return set_err(FDU_ERR_ARG, "blocks_per_sm must be 1.." + std::to_string(occ) + " at " +
+                                        std::to_string(threads) + " threads");
+    m->pl_threads = threads;
+    m->pl_blocks = sms * blocks_per_sm;
+    return FDU_OK;
+}
+
+static fdu_status check_barrier(fdu_mesh *m, cudaStream_t s) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, m->bar_err, sizeof e, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (e) {
+        CK(cudaMemsetAsync(m->bar, 0, 2 * sizeof(unsigned int), s));
+        CK(cudaMemsetAsync(m->bar_err, 0, sizeof(int), s));
+        CK(cudaStreamSynchronize(s));
+        return set_err(FDU_ERR_TIMEOUT, "a grid barrier of the persistent stage kernel timed out");
+    }
+    return FDU_OK;
+}
+
+constexpr unsigned long long kSpinLimit = 1ull << 24;
+
+fdu_status fdu_batch_rk_steps(fdu_mesh *m, int precision, int n_steps, void *stream) {
+    fdu_status st = need_batch(m);
+    if (st) return st;
+    if (n_steps < 0 || (precision != 64 && precision != 32)) return set_err(FDU_ERR_ARG, "bad precision or n_steps");
+    if (n_steps == 0) return FDU_OK;
+    cudaStream_t s = m->stream(stream);
+    const int occ = persistent_blocks_per_sm(precision, m->pl_threads);
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    if (occ < 1) return set_err(FDU_ERR_ARG, "the persistent kernel does not fit " + std::to_string(m->pl_threads) +
+                                                 " threads per block at this precision");
+    if (m->pl_blocks > occ * sms) m->pl_blocks = occ * sms;  // FP64 kernel holds more registers
+    ensure_fluxes(m, precision, s);
+    CK_LAUNCH();
+    auto key = std::make_tuple(precision, m->pl_threads, m->pl_blocks);
+    auto it = m->batch_graphs.find(key);
+    if (it == m->batch_graphs.end()) {
+        cudaStream_t cs = m->own_stream;
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, s));
+        CK(cudaStreamWaitEvent(cs, ev, 0));
+        CK(cudaEventDestroy(ev));
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = enqueue_step_persistent(m, precision, cs, (unsigned)m->pl_blocks, kSpinLimit);
+        cudaError_t e = cudaStreamEndCapture(cs, &g);
+        if (le != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(le));
+        if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        cudaGraphExec_t ge;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        it = m->batch_graphs.emplace(key, ge).first;
+    }
+    for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(it->second, s));
+    if (precision == 64) m->f32_valid = false;
+    else m->f64_valid = false;
+    return check_barrier(m, s);
+}
+
+fdu_status fdu_batch_autotune(fdu_mesh *m, int precision, int *threads, int *blocks_per_sm, double *ms_per_step) {
+    fdu_status st = need_batch(m);
+    if (st) return st;
+    if (precision != 64 && precision != 32) return set_err(FDU_ERR_ARG, "precision must be 64 or 32");
+    cudaStream_t s = m->own_stream;
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    // keep the caller's state: tuning steps run on a copy that is put back afterwards
+    CK(cudaMemcpyAsync(m->scratch, m->wn, 4 * m->nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    double best = INFINITY;
+    int bt = m->pl_threads, bb = m->pl_blocks / std::max(sms, 1);
+    for (int t : {128, 256, 512}) {
+        const int occ = persistent_blocks_per_sm(precision, t);
+        for (int k = 1; k <= occ; ++k) {
+            m->pl_threads = t;
+            m->pl_blocks = k * sms;
+            CK(cudaMemcpyAsync(m->wn, m->scratch, 4 * m->nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            m->f64_valid = m->f32_valid = false;
+            ensure_fluxes(m, precision, s);
+            cudaError_t e = enqueue_step_persistent(m, precision, s, (unsigned)m->pl_blocks, kSpinLimit);
+            if (e == cudaSuccess) e = cudaEventRecord(a, s);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+                e = enqueue_step_persistent(m, precision, s, (unsigned)m->pl_blocks, kSpinLimit);
+            if (e == cudaSuccess) e = cudaEventRecord(b, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            if (e != cudaSuccess) continue;  // launch shape not admissible: skip it
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms / 3.0 < best) {
+                best = ms / 3.0;
+                bt = t;
+                bb = k;
+            }
+        }
+    }
+    cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    m->pl_threads = bt;
+    m->pl_blocks = bb * sms;
+    CK(cudaMemcpyAsync(m->wn, m->scratch, 4 * m->nv * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    m->f64_valid = m->f32_valid = false;
+    st = check_barrier(m, s);
+    if (st) return st;
+    if (threads) *threads = bt;
+    if (blocks_per_sm) *blocks_per_sm = bb;
+    if (ms_per_step) *ms_per_step = best;
+    return FDU_OK;
+}
+
+fdu_status fdu_batch_barrier_selftest(fdu_mesh *m, int *status) {
+    fdu_status st = need_batch(m);
+    if (st) return st;
+    if (!status) return set_err(FDU_ERR_ARG, "null status");
+    cudaStream_t s = m->own_stream;
+    // stage 1 with one arrival more than the grid has: the barrier cannot
+    // complete, every block gives up after a short bounded wait, and the
+    // stage's update phase is skipped (the state is not touched)
+    ensure_fluxes(m, 32, s);
+    EdgeArgs ea = edge_args(m, 32, m->w32);
+    DivArgs a = div_args(m, 32, 0);
+    a.wn = m->wn;
+    a.ws = m->wn;
+    a.wout = m->ws;
+    a.Fout = m->F32[1];
+    a.w32out = m->w32;
+    a.comp = m->comp;
+    a.dt_comp = m->dt_comp;
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
+    const int nb = std::min(m->pl_blocks, persistent_blocks_per_sm(32, m->pl_threads) * sms);
+    CK(launch_stage_persistent(32, 1, ea, a, m->bar, m->bar + 1, (unsigned)nb + 1, 20000, m->bar_err, m->pl_threads,
+                               nb, s));
+    m->f32_valid = false;  // w32 may hold nothing else than the state, but be conservative
+    *status = check_barrier(m, s);
+    return FDU_OK;
 }
 
 fdu_status fdu_residual_noalloc(const fdu_mesh *mc, const double *w, double *dwdt, void *stream) {

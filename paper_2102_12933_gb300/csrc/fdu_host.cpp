@@ -488,7 +488,7 @@ void parallel_for(int64_t n, int threads, F &&f) {
 }  // namespace
 
 int build_host_tables(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts &o,
-                      HostTables &T, std::string &err) {
+                      HostTables &T, std::string &err, const int32_t *comp) {
     T.nv = nv;
     T.nt = nt;
     T.Lx = o.Lx;
@@ -644,6 +644,8 @@ int build_host_tables(const double *xy, int64_t nv, const int32_t *tri, int64_t 
         std::stable_sort(T.v_new2old.begin(), T.v_new2old.end(),
                          [&](int32_t a, int32_t b) { return key[a] < key[b]; });
     }
+    if (comp)
+        std::stable_sort(T.v_new2old.begin(), T.v_new2old.end(), [&](int32_t a, int32_t b) { return comp[a] < comp[b]; });
     if (!T.ghost.empty())
         std::stable_partition(T.v_new2old.begin(), T.v_new2old.end(), [&](int32_t v) { return T.ghost[v] < 0; });
     T.v_old2new.resize(nv);

@@ -57,8 +57,10 @@ struct HostTables {
 };
 
 // Build every host table.  Returns FDU_OK or an error code with `err` set.
+// `comp` (optional, [nv]) groups vertices into independent meshes of a
+// batch: the renumbering keeps each component contiguous.
 int build_host_tables(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts &o,
-                      HostTables &T, std::string &err);
+                      HostTables &T, std::string &err, const int32_t *comp = nullptr);
 
 // Per-side coefficient block from five normalised coordinates (exposed for tests through the C-ABI builder).
 void side_coefficients(const double x[5], double out[kSideCoef]);

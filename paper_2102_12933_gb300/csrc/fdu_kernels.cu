@@ -145,10 +145,7 @@ __device__ __forceinline__ void weno_pair64(const double *k, double a, double b,
 }
 
 // ------------------------------------------------------------------ FP64 edge flux
-__global__ void __launch_bounds__(kEdgeBlock) edge_flux_f64_kernel(EdgeArgs A) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= A.ne) return;
-    if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
+__device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int64_t e) {
     const double *__restrict__ w = static_cast<const double *>(A.w);
     const double *__restrict__ coef = static_cast<const double *>(A.coef);
     const double gm1 = A.gm1;
@@ -267,10 +264,7 @@ __device__ __forceinline__ dbl4 forward_euler(const dbl4 &ws, const dbl4 &L, dou
 
 // ------------------------------------------------------------------ FP64 divergence (+ RK stage)
 template <int MODE>
-__global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= A.n_real) return;
-    if (MODE != 0 && A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
+__device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t v) {
     const int64_t sl = v / kSell;
     const int lane = (int)(v % kSell);
     const double *__restrict__ F = static_cast<const double *>(A.F);
@@ -320,7 +314,7 @@ __global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
         st4(A.out, row, L);
         return;
     }
-    const double dt = A.dt_dev ? *A.dt_dev : A.dt;
+    const double dt = A.comp ? __ldg(A.dt_comp + __ldg(A.comp + v)) : (A.dt_dev ? *A.dt_dev : A.dt);
     const dbl4 ws = ld4(A.ws, v);
     const dbl4 fe = forward_euler(ws, L, dt, A.gm1, A.pos_alpha, A.limited);
     dbl4 o;
@@ -418,10 +412,7 @@ __device__ __forceinline__ void weno_pair32(const float *k, float a, float b, fl
     dr = fmaf(r0, vd, fmaf(r1, vc - c, r2 * (vb - c))) * __frcp_rn(r0 + r1 + r2);
 }
 
-__global__ void __launch_bounds__(kEdgeBlock) edge_flux_f32_kernel(EdgeArgs A) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= A.ne) return;
-    if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
+__device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int64_t e) {
     const float4 *__restrict__ w = static_cast<const float4 *>(A.w);
     const float *__restrict__ g = static_cast<const float *>(A.coef);
     const float gm1 = A.gm1f;
@@ -505,10 +496,7 @@ __global__ void vertex_flux_f32_kernel(const double *__restrict__ w, float4 *__r
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= A.n_real) return;
-    if (MODE != 0 && A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
+__device__ __forceinline__ void div_f32_body(const DivArgs &A, const int64_t v) {
     const int64_t sl = v / kSell;
     const int lane = (int)(v % kSell);
     const float4 *__restrict__ F = static_cast<const float4 *>(A.F);
@@ -559,7 +547,7 @@ __global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
         return;
     }
     // SSP-RK3 combination in FP64
-    const double dt = A.dt_dev ? *A.dt_dev : A.dt;
+    const double dt = A.comp ? __ldg(A.dt_comp + __ldg(A.comp + v)) : (A.dt_dev ? *A.dt_dev : A.dt);
     const dbl4 ws = ld4(A.ws, v);
     const dbl4 fe = forward_euler(ws, L, dt, A.gm1, A.pos_alpha, A.limited);
     dbl4 o;
@@ -582,6 +570,88 @@ __global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
     float4 *Fo = static_cast<float4 *>(A.Fout);
     Fo[2 * v] = f;
     Fo[2 * v + 1] = g;
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void __launch_bounds__(kEdgeBlock) edge_flux_f64_kernel(EdgeArgs A) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= A.ne) return;
+    if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
+    edge_flux_f64_body(A, e);
+}
+__global__ void __launch_bounds__(kEdgeBlock) edge_flux_f32_kernel(EdgeArgs A) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= A.ne) return;
+    if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
+    edge_flux_f32_body(A, e);
+}
+template <int MODE>
+__global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= A.n_real) return;
+    if (MODE != 0 && A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
+    div_f64_body<MODE>(A, v);
+}
+template <int MODE>
+__global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= A.n_real) return;
+    if (MODE != 0 && A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
+    div_f32_body<MODE>(A, v);
+}
+
+// Grid-wide barrier for a cooperative launch, with a bounded wait: thread 0
+// of each block arrives on *count; the last arrival resets it and advances
+// *gen; the others spin on *gen at most `limit` times (with a short sleep).
+// Returns false (and sets *err) if the wait ran out.
+__device__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen, unsigned int nblocks,
+                             unsigned long long limit, int *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(count, 1u);
+        if (arrived == nblocks - 1) {
+            *count = 0;
+            __threadfence();
+            atomicAdd((unsigned int *)gen, 1u);
+        } else {
+            unsigned long long it = 0;
+            while (*gen == g) {
+                if (++it > limit) {
+                    ok = 0;
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// One SSP-RK3 stage over every mesh of a batch in one cooperative launch:
+// all edge fluxes, a grid barrier, then every vertex's divergence and stage
+// update (grid-stride loops; MODE = stage 1..3).
+template <int PREC, int MODE>
+__global__ void stage_persistent_kernel(EdgeArgs EA, DivArgs DA, unsigned int *bar_count, unsigned int *bar_gen,
+                                        unsigned int nblocks_expected, unsigned long long spin_limit, int *err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t e = t0; e < EA.ne; e += stride) {
+        if (PREC == 64) edge_flux_f64_body(EA, e);
+        else edge_flux_f32_body(EA, e);
+    }
+    __threadfence();
+    if (!grid_barrier(bar_count, bar_gen, nblocks_expected, spin_limit, err)) return;
+    for (int64_t v = t0; v < DA.n_real; v += stride) {
+        if (PREC == 64) div_f64_body<MODE>(DA, v);
+        else div_f32_body<MODE>(DA, v);
+    }
 }
 
 // ------------------------------------------------------------------ support kernels
@@ -610,7 +680,7 @@ __global__ void ghost_fill_kernel(double *__restrict__ w, uint4 *__restrict__ F,
 
 // min over vertices of h_v / (|u| + c), as the bit pattern of a positive double
 __global__ void max_dt_kernel(const double *__restrict__ w, const double *__restrict__ hmin, int64_t n, double gamma,
-                              unsigned long long *slot) {
+                              unsigned long long *slot, const int32_t *__restrict__ comp) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double t = INFINITY;
     if (v < n) {
@@ -621,6 +691,10 @@ __global__ void max_dt_kernel(const double *__restrict__ w, const double *__rest
         const double c = sqrt(gamma * p * ir);
         t = hmin[v] / (sqrt(u * u + vv * vv) + c);
         if (!(t > 0)) t = 0;  // non-physical state: report dt = 0
+    }
+    if (comp) {  // one slot per component
+        if (v < n) atomicMin(slot + __ldg(comp + v), (unsigned long long)__double_as_longlong(t));
+        return;
     }
     for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
     if ((threadIdx.x & 31) == 0) atomicMin(slot, (unsigned long long)__double_as_longlong(t));
@@ -713,8 +787,44 @@ void launch_ghost_fill(double *w, void *F, int fq, float4 *w32, const int32_t *d
                                                                n_ghost);
 }
 void launch_max_dt(const double *w, const double *hmin, int64_t n, double gamma, unsigned long long *slot,
-                   cudaStream_t s) {
-    if (n > 0) max_dt_kernel<<<blocks(n, 256), 256, 0, s>>>(w, hmin, n, gamma, slot);
+                   cudaStream_t s, const int32_t *comp) {
+    if (n > 0) max_dt_kernel<<<blocks(n, 256), 256, 0, s>>>(w, hmin, n, gamma, slot, comp);
+}
+
+namespace {
+template <int PREC, int MODE>
+cudaError_t coop(const EdgeArgs &ea, const DivArgs &da, unsigned int *c, unsigned int *g, unsigned int ne,
+                 unsigned long long lim, int *err, int threads, int nb, cudaStream_t s) {
+    EdgeArgs a = ea;
+    DivArgs d = da;
+    void *args[] = {&a, &d, &c, &g, &ne, &lim, &err};
+    return cudaLaunchCooperativeKernel((const void *)stage_persistent_kernel<PREC, MODE>, dim3(nb), dim3(threads),
+                                       args, 0, s);
+}
+}  // namespace
+
+cudaError_t launch_stage_persistent(int prec, int mode, const EdgeArgs &ea, const DivArgs &da, unsigned int *bar_count,
+                                    unsigned int *bar_gen, unsigned int nblocks_expected,
+                                    unsigned long long spin_limit, int *err, int threads, int nb, cudaStream_t s) {
+    const unsigned int ne = nblocks_expected;
+    if (prec == 64) {
+        if (mode == 1) return coop<64, 1>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
+        if (mode == 2) return coop<64, 2>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
+        return coop<64, 3>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
+    }
+    if (mode == 1) return coop<32, 1>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
+    if (mode == 2) return coop<32, 2>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
+    return coop<32, 3>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
+}
+
+int persistent_blocks_per_sm(int prec, int threads) {
+    int n = 0;
+    // the three stage modes share their register footprint; mode 3 stands for all
+    if (prec == 64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_persistent_kernel<64, 3>, threads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_persistent_kernel<32, 3>, threads, 0);
+    return n;
 }
 
 double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s) {

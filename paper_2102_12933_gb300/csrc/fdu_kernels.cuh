@@ -48,6 +48,8 @@ struct DivArgs {
     const double *dt_dev;        // if non-null, dt is read here
     double gm1;                  // gamma - 1
     float gm1f;
+    const int32_t *comp;         // batched meshes: component of each internal vertex (nullptr = one mesh)
+    const double *dt_comp;       // batched meshes: time step of each component
     double pos_alpha;            // stage positivity safeguard (0 = off)
     unsigned long long *limited; // vertices whose stage update the safeguard scaled
 };
@@ -73,6 +75,16 @@ void launch_recip_check(const double *x, double *y, int64_t n, cudaStream_t s);
 void launch_dt_finalize(unsigned long long *slot, double *tstate, double cfl, double t_end,
                         unsigned long long *nsteps, cudaStream_t s);
 void launch_max_dt(const double *w, const double *hmin, int64_t n, double gamma, unsigned long long *slot,
-                   cudaStream_t s);
+                   cudaStream_t s, const int32_t *comp = nullptr);
+
+// One SSP-RK3 stage (mode 1..3) of a batch as one cooperative launch of
+// `blocks` x `threads` (edge fluxes, bounded grid barrier, divergence +
+// stage).  The barrier expects `nblocks_expected` arrivals (= blocks in
+// normal use) and gives up after `spin_limit` polls, setting *err.
+cudaError_t launch_stage_persistent(int prec, int mode, const EdgeArgs &ea, const DivArgs &da, unsigned int *bar_count,
+                                    unsigned int *bar_gen, unsigned int nblocks_expected,
+                                    unsigned long long spin_limit, int *err, int threads, int blocks, cudaStream_t s);
+// Co-resident blocks per SM of the persistent stage kernel at `threads`.
+int persistent_blocks_per_sm(int prec, int threads);
 
 }  // namespace fdu

@@ -33,7 +33,9 @@ EXPORTS = (
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
     "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
-    "fdu_check_recip64", "fdu_advance", "fdu_limited_count",
+    "fdu_check_recip64", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
+    "fdu_batch_max_dt", "fdu_batch_set_dt", "fdu_batch_rk_steps", "fdu_batch_set_launch", "fdu_batch_autotune",
+    "fdu_batch_barrier_selftest",
 )
 
 
@@ -105,6 +107,15 @@ def load():
         L.fdu_check_recip64.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_advance.argtypes = [P, C.c_double, C.c_double, C.c_int, i64, lp, dp, P]
         L.fdu_limited_count.argtypes = [P, lp, C.c_int, P]
+        L.fdu_batch_create.argtypes = [C.c_int32, C.POINTER(dp), lp, C.POINTER(ip), lp, C.POINTER(MeshOpts),
+                                       C.POINTER(P)]
+        L.fdu_batch_info.argtypes = [P, C.POINTER(C.c_int32), lp]
+        L.fdu_batch_max_dt.argtypes = [P, C.c_double, dp, P]
+        L.fdu_batch_set_dt.argtypes = [P, dp, P]
+        L.fdu_batch_rk_steps.argtypes = [P, C.c_int, C.c_int, P]
+        L.fdu_batch_set_launch.argtypes = [P, C.c_int, C.c_int]
+        L.fdu_batch_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+        L.fdu_batch_barrier_selftest.argtypes = [P, C.POINTER(C.c_int)]
         L.fdu_profile_read.argtypes = [P, C.c_int, C.c_int, dp, lp, C.c_int]
         for name in EXPORTS:
             if name not in ("fdu_version", "fdu_last_error"):
@@ -336,3 +347,62 @@ class Mesh:
         c = C.c_int64()
         _check(load().fdu_limited_count(self._h, C.byref(c), 1 if reset else 0, _stream_ptr(stream)))
         return c.value
+
+
+class Batch(Mesh):
+    """Many independent periodic meshes advanced together (one persistent
+    launch per RK stage).  States are the meshes' rows concatenated."""
+
+    def __init__(self, meshes, L, *, lsq_degree=2, lsq_levels=2, device=0, renumber=1, gamma=1.4,
+                 weno_eps=1e-40, weno_eps32=1e-30, host_threads=0):
+        Lib = load()
+        self._h = None
+        xys = [np.ascontiguousarray(m[0], dtype=np.float64).reshape(-1, 2) for m in meshes]
+        tris = [np.ascontiguousarray(m[1], dtype=np.int32).reshape(-1, 3) for m in meshes]
+        self._keep = (xys, tris)
+        n = len(meshes)
+        xp = (C.POINTER(C.c_double) * n)(*[_dp(a) for a in xys])
+        tp = (C.POINTER(C.c_int32) * n)(*[_ip(a) for a in tris])
+        nv = np.array([a.shape[0] for a in xys], np.int64)
+        nt = np.array([a.shape[0] for a in tris], np.int64)
+        o = default_opts(Lx=float(L), Ly=float(L), lsq_degree=lsq_degree, lsq_levels=lsq_levels, device=device,
+                         renumber=renumber, weno_eps=weno_eps, weno_eps32=weno_eps32, gamma=gamma,
+                         host_threads=host_threads)
+        h = C.c_void_p()
+        _check(Lib.fdu_batch_create(n, xp, _lp(nv), tp, _lp(nt), C.byref(o), C.byref(h)))
+        self._h = h
+        self.device = device
+        info = self.info()
+        self.nv = int(info["nv"])
+        self.ne = int(info["ne"])
+        k = C.c_int32()
+        self.offsets = np.zeros(n + 1, np.int64)
+        _check(Lib.fdu_batch_info(self._h, C.byref(k), _lp(self.offsets)))
+        self.n_meshes = int(k.value)
+
+    def batch_max_dt(self, cfl, stream=None):
+        dt = np.zeros(self.n_meshes)
+        _check(load().fdu_batch_max_dt(self._h, float(cfl), _dp(dt), _stream_ptr(stream)))
+        return dt
+
+    def set_dt(self, dt, stream=None):
+        dt = np.ascontiguousarray(dt, dtype=np.float64).reshape(self.n_meshes)
+        _check(load().fdu_batch_set_dt(self._h, _dp(dt), _stream_ptr(stream)))
+
+    def batch_rk_steps(self, n_steps, precision=32, stream=None):
+        _check(load().fdu_batch_rk_steps(self._h, int(precision), int(n_steps), _stream_ptr(stream)))
+
+    def set_launch(self, threads, blocks_per_sm):
+        _check(load().fdu_batch_set_launch(self._h, int(threads), int(blocks_per_sm)))
+
+    def autotune(self, precision=32):
+        """Pick the fastest persistent launch shape; returns (threads, blocks/SM, ms per step)."""
+        t, b = C.c_int(), C.c_int()
+        ms = C.c_double()
+        _check(load().fdu_batch_autotune(self._h, int(precision), C.byref(t), C.byref(b), C.byref(ms)))
+        return t.value, b.value, ms.value
+
+    def barrier_selftest(self):
+        st = C.c_int()
+        _check(load().fdu_batch_barrier_selftest(self._h, C.byref(st)))
+        return st.value

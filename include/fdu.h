@@ -215,6 +215,27 @@ fdu_status fdu_batch_autotune(fdu_mesh *batch, int precision, int *threads, int 
  * or hang is involved: the wait is bounded and the kernel returns. */
 fdu_status fdu_batch_barrier_selftest(fdu_mesh *batch, int *status);
 
+/* ---- Adjoint (hand-written vector-Jacobian products, FP64, periodic meshes) ----
+ * Derivatives of the residual and the RK step as defined above, taking the
+ * same branch as the forward pass at the piecewise choices (positivity
+ * fallback, entropy-fix band, |lambda|); the WENO weights are
+ * differentiable wherever beta_k + eps > 0.  Arrays are [nv][4] in original
+ * vertex order, device (on_device = 1) or host pointers. */
+/* grad = (dL/dw)^T lam at the current state. */
+fdu_status fdu_residual_vjp(fdu_mesh *mesh, const double *lam, double *grad, int on_device, void *stream);
+/* lam_prev = (dw_{n+1}/dw_n)^T lam_next for one SSP-RK3 step of size dt from
+ * the current state (the state is not changed). */
+fdu_status fdu_rk_step_vjp(fdu_mesh *mesh, double dt, const double *lam_next, double *lam_prev, int on_device,
+                           void *stream);
+/* Gradient with respect to the current state w0 of a function of the state
+ * after n_steps SSP-RK3 steps of size dt, given lam_final = its gradient
+ * with respect to that final state: grad = (dw_T/dw0)^T lam_final.  The
+ * forward pass keeps a checkpoint every `checkpoint_every` steps and each
+ * segment's step states are recomputed in the reverse pass.  The mesh state
+ * is w0 again afterwards. */
+fdu_status fdu_adjoint_rk(fdu_mesh *mesh, double dt, int n_steps, int checkpoint_every, const double *lam_final,
+                          double *grad, int on_device, void *stream);
+
 /* Edges whose interpolated density or pressure was not positive and that
  * fell back to the first-order end states, counted since the last reset
  * (reset = 1 zeroes the counter after reading).  Synchronises `stream`. */

@@ -1,0 +1,452 @@
+// Hand-written adjoint (vector-Jacobian products) of the FP64 residual.
+//
+// The residual of vertex v is L_v = -( sum_j wf_vj f(w_j) + wg_vj g(w_j)
+// + sum_k we_vk r_k + cf_v f(w_v) + cg_v g(w_v) ) (Section 2.2.1, folded
+// centre weights), with r_k the edge flux of Section 2.3.1.  Given a
+// cotangent lam of L, its VJP is assembled from
+//   lam_r[k]   = -sum_v we_vk lam_v                 (edge transpose)
+//   lam_f[j]   = -sum_v wf_vj lam_v - cf_j lam_j     (vertex transpose)
+//   grad[j]    = (df/dw)^T lam_f[j] + (dg/dw)^T lam_g[j]
+//   G[k][slot] = (dr_k/dW_slot)^T lam_r[k]          (edge-flux VJP, recomputing
+//                                                    the forward per edge)
+//   grad[u]   += sum over (k, slot) with sten[slot][k] = u of G[k][slot]
+// All sums are gathers over transposed tables: no atomics, deterministic.
+// The piecewise choices of the forward pass (positivity fallback, entropy
+// fix band, |lambda|) take the same branch in the reverse pass.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fdu_adjoint.cuh"
+#include "fdu_device.cuh"
+#include "fdu_internal.h"
+
+namespace fdu {
+namespace {
+using namespace dev;
+
+struct Prim64Bar {
+    double r = 0, ir = 0, p = 0;
+};
+struct Roe64Bar {
+    double u = 0, v = 0, H = 0, c = 0, ic = 0, b1 = 0, qn = 0, qt = 0, hq2 = 0;
+};
+
+__device__ __forceinline__ void add_to(dbl4 &a, const dbl4 &b) {
+    a.x += b.x;
+    a.y += b.y;
+    a.z += b.z;
+    a.w += b.w;
+}
+
+// w -> (r = rho^-1/2, ir = 1/rho, p)
+__device__ __forceinline__ void prim64_vjp(const dbl4 &w, const Prim64 &P, const Prim64Bar &B, double gm1, dbl4 &wb) {
+    const double ke2 = w.y * w.y + w.z * w.z;
+    const double irb = B.ir - B.p * gm1 * 0.5 * ke2;
+    const double rb = B.r + irb * 2.0 * P.r;
+    wb.x += rb * (-0.5 * P.r * P.r * P.r);
+    wb.y += -B.p * gm1 * w.y * P.ir;
+    wb.z += -B.p * gm1 * w.z * P.ir;
+    wb.w += B.p * gm1;
+}
+
+// Roe average (a, b) -> R; accumulates into the primitives' cotangents and
+// the states' direct cotangents.
+__device__ __forceinline__ void roe64_vjp(const dbl4 &a, const Prim64 &pa, const dbl4 &b, const Prim64 &pb,
+                                          const Roe64 &R, const Roe64Bar &Rb, double gm1, dbl4 &ab, Prim64Bar &pab,
+                                          dbl4 &bb, Prim64Bar &pbb) {
+    double ub = Rb.u + Rb.qn * R.nx - Rb.qt * R.ny;
+    double vb = Rb.v + Rb.qn * R.ny + Rb.qt * R.nx;
+    const double icb = Rb.ic + Rb.b1 * gm1 * 2.0 * R.ic;
+    const double c2b = Rb.c * 0.5 * R.ic - icb * 0.5 * R.ic * R.ic * R.ic;
+    const double Hb = Rb.H + c2b * gm1;
+    const double hq2b = Rb.hq2 - c2b * gm1;
+    ub += hq2b * R.u;
+    vb += hq2b * R.v;
+    const double sa = a.x * pa.r, sb = b.x * pb.r;
+    const double inv = recip64(sa + sb);
+    const double U = a.y * pa.r + b.y * pb.r;
+    const double V = a.z * pa.r + b.z * pb.r;
+    const double Hn = (a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r;
+    const double invb = ub * U + vb * V + Hb * Hn;
+    const double Ub = ub * inv, Vb = vb * inv, Hnb = Hb * inv;
+    const double sbar = -invb * inv * inv;
+    ab.x += sbar * pa.r;
+    pab.r += sbar * a.x;
+    bb.x += sbar * pb.r;
+    pbb.r += sbar * b.x;
+    ab.y += Ub * pa.r;
+    pab.r += Ub * a.y;
+    bb.y += Ub * pb.r;
+    pbb.r += Ub * b.y;
+    ab.z += Vb * pa.r;
+    pab.r += Vb * a.z;
+    bb.z += Vb * pb.r;
+    pbb.r += Vb * b.z;
+    ab.w += Hnb * pa.r;
+    pab.p += Hnb * pa.r;
+    pab.r += Hnb * (a.w + pa.p);
+    bb.w += Hnb * pb.r;
+    pbb.p += Hnb * pb.r;
+    pbb.r += Hnb * (b.w + pb.p);
+}
+
+// c = project64(R, d): accumulates d's and R's cotangents
+__device__ __forceinline__ void project64_vjp(const Roe64 &R, const dbl4 &d, const dbl4 &cb, dbl4 &db, Roe64Bar &Rb) {
+    const double phib = 0.5 * cb.x - cb.y + 0.5 * cb.w;
+    const double psib = 0.5 * cb.x - 0.5 * cb.w;
+    db.x += cb.y - R.qt * cb.z;
+    db.y += -R.ny * cb.z;
+    db.z += R.nx * cb.z;
+    Rb.qt += -d.x * cb.z;
+    const double inner_phi = R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w;
+    Rb.b1 += phib * inner_phi;
+    const double t = phib * R.b1;
+    Rb.hq2 += t * d.x;
+    Rb.u += -t * d.y;
+    Rb.v += -t * d.z;
+    db.x += t * R.hq2;
+    db.y += -t * R.u;
+    db.z += -t * R.v;
+    db.w += t;
+    const double inner_psi = R.qn * d.x - R.nx * d.y - R.ny * d.z;
+    Rb.ic += psib * inner_psi;
+    const double s = psib * R.ic;
+    Rb.qn += s * d.x;
+    db.x += s * R.qn;
+    db.y += -s * R.nx;
+    db.z += -s * R.ny;
+}
+
+// d = unproject64(R, c): accumulates c's and R's cotangents
+__device__ __forceinline__ void unproject64_vjp(const Roe64 &R, const dbl4 &c, const dbl4 &dbar, dbl4 &cb,
+                                                Roe64Bar &Rb) {
+    const double rho = c.x + c.y + c.w;
+    const double dd = R.c * (c.w - c.x);
+    const double rhob = dbar.x + R.u * dbar.y + R.v * dbar.z;
+    const double ddb = R.nx * dbar.y + R.ny * dbar.z + R.qn * dbar.w;
+    Rb.u += rho * dbar.y;
+    Rb.v += rho * dbar.z;
+    Rb.H += (c.x + c.w) * dbar.w;
+    Rb.hq2 += c.y * dbar.w;
+    Rb.qn += dd * dbar.w;
+    Rb.qt += c.z * dbar.w;
+    Rb.c += (c.w - c.x) * ddb;
+    cb.x += rhob + R.H * dbar.w - R.c * ddb;
+    cb.y += rhob + R.hq2 * dbar.w;
+    cb.z += -R.ny * dbar.y + R.nx * dbar.z + R.qt * dbar.w;
+    cb.w += rhob + R.H * dbar.w + R.c * ddb;
+}
+
+// Reverse of weno_pair64 for one field: from (dlb, drb) to the cotangents of
+// the six differences (a..f), recomputing the forward values.
+__device__ __forceinline__ void weno_pair64_vjp(const double *k, double a, double b, double c, double d, double e,
+                                                double f, double eps, double dlb, double drb, double &ab, double &bb_,
+                                                double &cb, double &db, double &eb, double &fb) {
+    const double va = fma(k[0], a, k[1] * b), pa = fma(k[2], a, k[3] * b), qa = fma(k[4], a, k[5] * b);
+    const double vb = fma(k[6], b, k[7] * c), pb = fma(k[8], b, k[9] * c), qb = fma(k[10], b, k[11] * c);
+    const double vc = fma(k[12], c, k[13] * d), pc = fma(k[14], c, k[15] * d), qc = fma(k[16], c, k[17] * d);
+    const double vd = fma(k[18], e, k[19] * f), pd = fma(k[20], e, k[21] * f), qd = fma(k[22], e, k[23] * f);
+    const double ba = fma(pa, pa, fma(qa, qa, eps));
+    const double bb = fma(pb, pb, fma(qb, qb, eps));
+    const double bc = fma(pc, pc, fma(qc, qc, eps));
+    const double bd = fma(pd, pd, fma(qd, qd, eps));
+    const double bbc = bb * bc;
+    const double l0 = k[24] * bbc, l1 = k[25] * (ba * bc), l2 = k[26] * (ba * bb);
+    const double iDL = recip64(l0 + l1 + l2);
+    const double dl = fma(l0, va, fma(l1, vb, l2 * vc)) * iDL;
+    const double r0 = k[27] * bbc, r1 = k[28] * (bd * bb), r2 = k[29] * (bd * bc);
+    const double iDR = recip64(r0 + r1 + r2);
+    const double vcr = vc - c, vbr = vb - c;
+    const double dr = fma(r0, vd, fma(r1, vcr, r2 * vbr)) * iDR;
+    // reverse
+    const double NLb = dlb * iDL, DLb = -dlb * dl * iDL;
+    const double NRb = drb * iDR, DRb = -drb * dr * iDR;
+    const double l0b = NLb * va + DLb, l1b = NLb * vb + DLb, l2b = NLb * vc + DLb;
+    const double r0b = NRb * vd + DRb, r1b = NRb * vcr + DRb, r2b = NRb * vbr + DRb;
+    const double vab = NLb * l0;
+    const double vbb = NLb * l1 + NRb * r2;
+    const double vcb = NLb * l2 + NRb * r1;
+    const double vdb = NRb * r0;
+    double cdir = -NRb * (r1 + r2);
+    const double bab = l1b * k[25] * bc + l2b * k[26] * bb;
+    const double bbb = l0b * k[24] * bc + l2b * k[26] * ba + r0b * k[27] * bc + r1b * k[28] * bd;
+    const double bcb = l0b * k[24] * bb + l1b * k[25] * ba + r0b * k[27] * bb + r2b * k[29] * bd;
+    const double bdb = r1b * k[28] * bb + r2b * k[29] * bc;
+    const double pab = 2.0 * pa * bab, qab = 2.0 * qa * bab;
+    const double pbb = 2.0 * pb * bbb, qbb = 2.0 * qb * bbb;
+    const double pcb = 2.0 * pc * bcb, qcb = 2.0 * qc * bcb;
+    const double pdb = 2.0 * pd * bdb, qdb = 2.0 * qd * bdb;
+    ab = k[0] * vab + k[2] * pab + k[4] * qab;
+    bb_ = k[1] * vab + k[3] * pab + k[5] * qab + k[6] * vbb + k[8] * pbb + k[10] * qbb;
+    cb = cdir + k[7] * vbb + k[9] * pbb + k[11] * qbb + k[12] * vcb + k[14] * pcb + k[16] * qcb;
+    db = k[13] * vcb + k[15] * pcb + k[17] * qcb;
+    eb = k[18] * vdb + k[20] * pdb + k[22] * qdb;
+    fb = k[19] * vdb + k[21] * pdb + k[23] * qdb;
+}
+
+// F_n(w) = (rho q, m_x q + p n_x, m_y q + p n_y, (E + p) q), q = m.n / rho,
+// written with the primitives of prim64; reverse into w and P.
+__device__ __forceinline__ void fluxn_vjp(const dbl4 &w, const Prim64 &P, double nx, double ny, const dbl4 &fb, dbl4 &wb,
+                                          Prim64Bar &Pb) {
+    const double mn = w.y * nx + w.z * ny;
+    const double q = mn * P.ir;
+    // f.x = rho q = mn (rho * ir = 1 in exact arithmetic; the forward uses rho * q)
+    double qb = fb.x * w.x + fb.y * w.y + fb.z * w.z + fb.w * (w.w + P.p);
+    wb.x += fb.x * q;
+    wb.y += fb.y * q;
+    wb.z += fb.z * q;
+    wb.w += fb.w * q;
+    Pb.p += fb.y * nx + fb.z * ny + fb.w * q;
+    const double mnb = qb * P.ir;
+    Pb.ir += qb * mn;
+    wb.y += mnb * nx;
+    wb.z += mnb * ny;
+}
+
+// (df/dw)^T fb + (dg/dw)^T gb at state w
+__device__ __forceinline__ dbl4 vertex_flux_vjp(const dbl4 &w, double gm1, const dbl4 &fb, const dbl4 &gb) {
+    const double ir = 1.0 / w.x;
+    const double u = w.y * ir, v = w.z * ir;
+    const double p = gm1 * (w.w - 0.5 * (w.y * u + w.z * v));
+    dbl4 wb = dbl4_make(0, 0, 0, 0);
+    double ub = 0, vb = 0, pb = 0;
+    // f = (m_x, m_x u + p, m_y u, (E + p) u)
+    wb.y += fb.x + fb.y * u;
+    ub += fb.y * w.y + fb.z * w.z + fb.w * (w.w + p);
+    pb += fb.y + fb.w * u;
+    wb.z += fb.z * u;
+    wb.w += fb.w * u;
+    // g = (m_y, m_x v, m_y v + p, (E + p) v)
+    wb.z += gb.x + gb.z * v;
+    wb.y += gb.y * v;
+    vb += gb.y * w.y + gb.z * w.z + gb.w * (w.w + p);
+    pb += gb.z + gb.w * v;
+    wb.w += gb.w * v;
+    // p = gm1 (E - |m|^2 / (2 rho))
+    wb.x += pb * gm1 * 0.5 * (u * u + v * v);
+    wb.y += -pb * gm1 * u;
+    wb.z += -pb * gm1 * v;
+    wb.w += pb * gm1;
+    // u = m_x / rho, v = m_y / rho
+    wb.x += -(ub * u + vb * v) * ir;
+    wb.y += ub * ir;
+    wb.z += vb * ir;
+    return wb;
+}
+
+// Edge-flux VJP: recompute edge e's forward pass at state w, then reverse
+// from lam (cotangent of r_e) to the six stencil states; G[slot][e].
+__global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= A.ne) return;
+    const double *__restrict__ w = A.w;
+    const double *__restrict__ coef = A.coef;
+    const double gm1 = A.gm1;
+    const int64_t ne = A.ne;
+    int32_t s[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
+    const dbl4 W0 = ld4(w, s[0]), W1 = ld4(w, s[1]), L1 = ld4(w, s[2]), R1 = ld4(w, s[3]), W4 = ld4(w, s[4]),
+               W5 = ld4(w, s[5]);
+    const double nx = __ldg(coef + (int64_t)30 * ne + e), ny = __ldg(coef + (int64_t)31 * ne + e);
+    const dbl4 lam = ld4(A.lam_r, e);
+
+    // ---------------- forward
+    const Prim64 pL1 = prim64(L1, gm1), pR1 = prim64(R1, gm1);
+    const Roe64 C = roe64(L1, pL1, R1, pR1, nx, ny, gm1);
+    const dbl4 dM = sub4(R1, L1), dL2 = sub4(W1, L1), dL3 = sub4(W0, L1), dR2 = sub4(W4, R1), dR3 = sub4(W5, R1);
+    const dbl4 cM = project64(C, dM), cL2 = project64(C, dL2), cL3 = project64(C, dL3), cR2 = project64(C, dR2),
+               cR3 = project64(C, dR3);
+    const dbl4 cR2L = add4(cR2, cM);
+    double k[30];
+#pragma unroll
+    for (int i = 0; i < 30; ++i) k[i] = __ldg(coef + (int64_t)i * ne + e);
+    dbl4 dl, dr;
+    weno_pair64(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps, dl.x, dr.x);
+    weno_pair64(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps, dl.y, dr.y);
+    weno_pair64(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps, dl.z, dr.z);
+    weno_pair64(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps, dl.w, dr.w);
+    dbl4 wl = add4(L1, unproject64(C, dl));
+    dbl4 wr = add4(R1, unproject64(C, dr));
+    Prim64 pl, pr;
+    bool ok = wl.x > 0.0 && wr.x > 0.0;
+    if (ok) {
+        pl = prim64(wl, gm1);
+        pr = prim64(wr, gm1);
+        ok = pl.p > 0.0 && pr.p > 0.0;
+    }
+    if (!ok) {
+        wl = L1;
+        wr = R1;
+        pl = pL1;
+        pr = pR1;
+    }
+    const Roe64 Q = roe64(wl, pl, wr, pr, nx, ny, gm1);
+    const dbl4 dw = sub4(wr, wl);
+    const dbl4 a = project64(Q, dw);
+    const double delta = 0.1 * Q.c;
+    const double l_u = Q.qn, l_m = Q.qn - Q.c, l_p = Q.qn + Q.c;
+    auto fixv = [&](double l) { return fabs(l) < delta ? (l * l + delta * delta) * (5.0 * Q.ic) : fabs(l); };
+    const double lu = fixv(l_u), lm = fixv(l_m), lp = fixv(l_p);
+    const dbl4 sv = dbl4_make(lm * a.x, lu * a.y, lu * a.z, lp * a.w);
+
+    // ---------------- reverse
+    const dbl4 Db = dbl4_make(-0.5 * lam.x, -0.5 * lam.y, -0.5 * lam.z, -0.5 * lam.w);
+    const dbl4 Fb = dbl4_make(0.5 * lam.x, 0.5 * lam.y, 0.5 * lam.z, 0.5 * lam.w);
+    dbl4 wlb = dbl4_make(0, 0, 0, 0), wrb = dbl4_make(0, 0, 0, 0);
+    Prim64Bar plb, prb;
+    fluxn_vjp(wl, pl, nx, ny, Fb, wlb, plb);
+    fluxn_vjp(wr, pr, nx, ny, Fb, wrb, prb);
+    Roe64Bar Qb;
+    dbl4 svb = dbl4_make(0, 0, 0, 0);
+    unproject64_vjp(Q, sv, Db, svb, Qb);
+    dbl4 ab = dbl4_make(lm * svb.x, lu * svb.y, lu * svb.z, lp * svb.w);
+    const double lmb = a.x * svb.x, lub = a.y * svb.y + a.z * svb.z, lpb = a.w * svb.w;
+    // entropy fix: |l| or (l^2 + delta^2) / (2 delta), delta = 0.1 c
+    double deltab = 0.0;
+    auto fix_vjp = [&](double l, double fb, double &lb) {
+        if (fabs(l) < delta) {
+            lb += fb * l / delta;
+            deltab += fb * (0.5 - 0.5 * l * l / (delta * delta));
+        } else {
+            lb += fb * (l >= 0.0 ? 1.0 : -1.0);
+        }
+    };
+    double lub_ = 0, lmb_ = 0, lpb_ = 0;
+    fix_vjp(l_u, lub, lub_);
+    fix_vjp(l_m, lmb, lmb_);
+    fix_vjp(l_p, lpb, lpb_);
+    Qb.qn += lub_ + lmb_ + lpb_;
+    Qb.c += -lmb_ + lpb_ + 0.1 * deltab;
+    dbl4 dwb = dbl4_make(0, 0, 0, 0);
+    project64_vjp(Q, dw, ab, dwb, Qb);
+    add_to(wrb, dwb);
+    wlb = sub4(wlb, dwb);
+    roe64_vjp(wl, pl, wr, pr, Q, Qb, gm1, wlb, plb, wrb, prb);
+    prim64_vjp(wl, pl, plb, gm1, wlb);
+    prim64_vjp(wr, pr, prb, gm1, wrb);
+
+    dbl4 G0 = dbl4_make(0, 0, 0, 0), G1 = G0, GL1 = G0, GR1 = G0, G4 = G0, G5 = G0;
+    if (!ok) {
+        GL1 = wlb;
+        GR1 = wrb;
+    } else {
+        GL1 = wlb;
+        GR1 = wrb;
+        Roe64Bar Cb;
+        dbl4 dlb = dbl4_make(0, 0, 0, 0), drb = dbl4_make(0, 0, 0, 0);
+        unproject64_vjp(C, dl, wlb, dlb, Cb);
+        unproject64_vjp(C, dr, wrb, drb, Cb);
+        dbl4 cL3b, cL2b, cMb, cR2Lb, cR3b, cR2b;
+        weno_pair64_vjp(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps, dlb.x, drb.x, cL3b.x, cL2b.x, cMb.x,
+                        cR2Lb.x, cR3b.x, cR2b.x);
+        weno_pair64_vjp(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps, dlb.y, drb.y, cL3b.y, cL2b.y, cMb.y,
+                        cR2Lb.y, cR3b.y, cR2b.y);
+        weno_pair64_vjp(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps, dlb.z, drb.z, cL3b.z, cL2b.z, cMb.z,
+                        cR2Lb.z, cR3b.z, cR2b.z);
+        weno_pair64_vjp(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps, dlb.w, drb.w, cL3b.w, cL2b.w, cMb.w,
+                        cR2Lb.w, cR3b.w, cR2b.w);
+        add_to(cR2b, cR2Lb);
+        add_to(cMb, cR2Lb);
+        dbl4 dMb = dbl4_make(0, 0, 0, 0), dL2b = dMb, dL3b = dMb, dR2b = dMb, dR3b = dMb;
+        project64_vjp(C, dM, cMb, dMb, Cb);
+        project64_vjp(C, dL2, cL2b, dL2b, Cb);
+        project64_vjp(C, dL3, cL3b, dL3b, Cb);
+        project64_vjp(C, dR2, cR2b, dR2b, Cb);
+        project64_vjp(C, dR3, cR3b, dR3b, Cb);
+        add_to(GR1, dMb);
+        GL1 = sub4(GL1, dMb);
+        add_to(G1, dL2b);
+        GL1 = sub4(GL1, dL2b);
+        add_to(G0, dL3b);
+        GL1 = sub4(GL1, dL3b);
+        add_to(G4, dR2b);
+        GR1 = sub4(GR1, dR2b);
+        add_to(G5, dR3b);
+        GR1 = sub4(GR1, dR3b);
+        Prim64Bar pL1b, pR1b;
+        roe64_vjp(L1, pL1, R1, pR1, C, Cb, gm1, GL1, pL1b, GR1, pR1b);
+        prim64_vjp(L1, pL1, pL1b, gm1, GL1);
+        prim64_vjp(R1, pR1, pR1b, gm1, GR1);
+    }
+    double *G = A.G;  // [6][ne][4]
+    st4(G, 0 * ne + e, G0);
+    st4(G, 1 * ne + e, G1);
+    st4(G, 2 * ne + e, GL1);
+    st4(G, 3 * ne + e, GR1);
+    st4(G, 4 * ne + e, G4);
+    st4(G, 5 * ne + e, G5);
+}
+
+// lam_r[k] = -sum_v we_vk lam_v (CSR over edges)
+__global__ void adj_edge_lambda_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ vid,
+                                       const double *__restrict__ wt, const double *__restrict__ lam,
+                                       double *__restrict__ lam_r, int64_t ne) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ne) return;
+    dbl4 acc = dbl4_make(0, 0, 0, 0);
+    for (int64_t p = __ldg(off + k); p < __ldg(off + k + 1); ++p) {
+        const double a = __ldg(wt + p);
+        const dbl4 l = ld4(lam, __ldg(vid + p));
+        acc.x = fma(a, l.x, acc.x);
+        acc.y = fma(a, l.y, acc.y);
+        acc.z = fma(a, l.z, acc.z);
+        acc.w = fma(a, l.w, acc.w);
+    }
+    st4(lam_r, k, neg4(acc));
+}
+
+// grad[j] = (df/dw)^T lam_f + (dg/dw)^T lam_g with lam_f = -sum_v wf_vj lam_v
+// (centre weights included as the entry v = j), then + sum of the edge-flux
+// slot cotangents G[slot][k] over the stencil slots that hold j.
+__global__ void adj_vertex_kernel(AdjVertexArgs A) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.nv) return;
+    dbl4 lf = dbl4_make(0, 0, 0, 0), lg = lf;
+    for (int64_t p = __ldg(A.voff + j); p < __ldg(A.voff + j + 1); ++p) {
+        const double a = __ldg(A.wf + p), b = __ldg(A.wg + p);
+        const dbl4 l = ld4(A.lam, __ldg(A.vid + p));
+        lf.x = fma(a, l.x, lf.x);
+        lf.y = fma(a, l.y, lf.y);
+        lf.z = fma(a, l.z, lf.z);
+        lf.w = fma(a, l.w, lf.w);
+        lg.x = fma(b, l.x, lg.x);
+        lg.y = fma(b, l.y, lg.y);
+        lg.z = fma(b, l.z, lg.z);
+        lg.w = fma(b, l.w, lg.w);
+    }
+    dbl4 g = vertex_flux_vjp(ld4(A.w, j), A.gm1, neg4(lf), neg4(lg));
+    for (int64_t p = __ldg(A.soff + j); p < __ldg(A.soff + j + 1); ++p) add_to(g, ld4(A.G, __ldg(A.slot + p)));
+    st4(A.grad, j, g);
+}
+
+// out = a * x + b * y (+ c * z), elementwise over n records of 4
+__global__ void axpby_kernel(double *__restrict__ out, double a, const double *__restrict__ x, double b,
+                             const double *__restrict__ y, double c, const double *__restrict__ z, int64_t n4) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n4) return;
+    double v = a * x[i];
+    if (y) v = fma(b, y[i], v);
+    if (z) v = fma(c, z[i], v);
+    out[i] = v;
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+void launch_residual_vjp(const AdjEdgeArgs &ea, const AdjTables &t, const AdjVertexArgs &va, cudaStream_t s) {
+    if (ea.ne > 0) {
+        adj_edge_lambda_kernel<<<nblk(ea.ne, 256), 256, 0, s>>>(t.eoff, t.evid, t.ewt, va.lam, ea.lam_r_mut, ea.ne);
+        edge_flux_vjp_kernel<<<nblk(ea.ne, 128), 128, 0, s>>>(ea);
+    }
+    if (va.nv > 0) adj_vertex_kernel<<<nblk(va.nv, 256), 256, 0, s>>>(va);
+}
+
+void launch_axpby(double *out, double a, const double *x, double b, const double *y, double c, const double *z,
+                  int64_t n4, cudaStream_t s) {
+    if (n4 > 0) axpby_kernel<<<nblk(n4, 256), 256, 0, s>>>(out, a, x, b, y, c, z, n4);
+}
+
+}  // namespace fdu

@@ -1,0 +1,52 @@
+// Argument blocks and launchers of the adjoint kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace fdu {
+
+// Edge-flux VJP inputs (internal ids, active edges, FP64).
+struct AdjEdgeArgs {
+    const int32_t *sten;  // [6][ne]
+    const double *coef;   // [kEdgeCoef][ne]
+    const double *w;      // [nv][4] state the residual is linearised at
+    const double *lam_r;  // [ne][4] cotangent of the edge fluxes (read by the VJP kernel)
+    double *lam_r_mut;    // the same buffer, written by the transpose gather
+    double *G;            // [6][ne][4] cotangents of the stencil states, per slot
+    int64_t ne;
+    double gm1, eps;
+};
+
+// Edge transpose: for each active edge, the vertices whose divergence
+// stencil holds it and the weights w_k.
+struct AdjTables {
+    const int64_t *eoff;  // [ne+1]
+    const int32_t *evid;
+    const double *ewt;
+};
+
+// Per-vertex part: vertex transpose (wf, wg of every stencil that holds the
+// vertex, centre weights as the vertex's own entry) and stencil incidence.
+struct AdjVertexArgs {
+    int64_t nv;
+    const int64_t *voff;  // [nv+1]
+    const int32_t *vid;
+    const double *wf, *wg;
+    const double *lam;    // [nv][4] cotangent of the residual
+    const double *w;      // [nv][4] state
+    double gm1;
+    const int64_t *soff;  // [nv+1] stencil incidence
+    const int64_t *slot;  // index slot * ne + k into G
+    const double *G;
+    double *grad;         // [nv][4] output
+};
+
+// grad = (dL/dw)^T lam at state w: transpose gathers, edge-flux VJP, per-vertex
+// flux Jacobians; three launches on s.
+void launch_residual_vjp(const AdjEdgeArgs &ea, const AdjTables &t, const AdjVertexArgs &va, cudaStream_t s);
+// out = a x + b y + c z over n4 doubles (y, z may be null)
+void launch_axpby(double *out, double a, const double *x, double b, const double *y, double c, const double *z,
+                  int64_t n4, cudaStream_t s);
+
+}  // namespace fdu

@@ -15,6 +15,7 @@
 #include "fdu.h"
 #include "fdu_internal.h"
 #include "fdu_kernels.cuh"
+#include "fdu_adjoint.cuh"
 
 using namespace fdu;
 
@@ -90,6 +91,14 @@ struct fdu_mesh {
     int *bar_err = nullptr;           // grid barrier timed out
     int pl_threads = 256, pl_blocks = 0;  // persistent launch shape (blocks in total)
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> batch_graphs;
+    // adjoint workspace (built on first use)
+    bool adj_ready = false;
+    int64_t *adj_eoff = nullptr, *adj_voff = nullptr, *adj_soff = nullptr, *adj_slot = nullptr;
+    int32_t *adj_evid = nullptr, *adj_vvid = nullptr;
+    double *adj_ewt = nullptr, *adj_wf = nullptr, *adj_wg = nullptr;
+    double *adj_lam_r = nullptr, *adj_G = nullptr;
+    double *adj_S1 = nullptr, *adj_buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    std::vector<double *> adj_states;  // checkpoints and recomputed step states
     // kernel timing: event pairs per kind (0 edge64, 1 div64, 2 edge32, 3 div32)
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev[4];
@@ -129,6 +138,7 @@ struct fdu_mesh {
                 for (cudaEvent_t e : v) cudaEventDestroy(e);
             for (void *p : allocs) cudaFree(p);
             allocs.clear();
+            adj_states.clear();
             if (own_stream) cudaStreamDestroy(own_stream);
             own_stream = nullptr;
         }
@@ -337,10 +347,11 @@ void ensure_fluxes(fdu_mesh *m, int prec, cudaStream_t s) {
 // One SSP-RK3 step: three (edge flux, divergence + stage) pairs.  Stage i
 // reads fluxes F[i-1] and writes F[i mod 3], so F[0] holds the fluxes of
 // the new state at the end and a captured step can be replayed as is.
-void enqueue_step(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaStream_t s, bool prof) {
+void enqueue_stages(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaStream_t s, bool prof, int first,
+                    int last) {
     const int fq = prec == 64 ? 4 : 2;  // 16-byte words of vertex fluxes per vertex
     const int kd = prec == 64 ? 0 : 2;
-    for (int stage = 1; stage <= 3; ++stage) {
+    for (int stage = first; stage <= last; ++stage) {
         const double *win = stage == 1 ? m->wn : m->ws;
         timed(m, kd, prof, s, [&] {
             EdgeArgs ea = edge_args(m, prec, prec == 64 ? (const void *)win : (const void *)m->w32);
@@ -363,6 +374,130 @@ void enqueue_step(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaSt
         if (m->n_ghost > 0)
             launch_ghost_fill(a.wout, a.Fout, fq, prec == 32 ? m->w32 : nullptr, m->donor, m->n_real, m->n_ghost, s);
     }
+}
+
+void enqueue_step(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaStream_t s, bool prof) {
+    enqueue_stages(m, prec, dt, dt_dev, s, prof, 1, 3);
+}
+
+// ---------------------------------------------------------------- adjoint
+fdu_status adjoint_setup(fdu_mesh *m) {
+    if (m->adj_ready) return FDU_OK;
+    if (m->n_ghost > 0) return set_err(FDU_ERR_ARG, "the adjoint supports periodic meshes (no ghost vertices)");
+    const HostTables &T = m->T;
+    const int64_t nv = m->nv, ne = m->ne_act;
+    // edge transpose and vertex transpose (with centre weights), internal ids
+    std::vector<int64_t> ecnt(ne + 1, 0), vcnt(nv + 1, 0), scnt(nv + 1, 0);
+    for (int64_t v = 0; v < m->n_real; ++v) {
+        const int64_t o = T.v_new2old[v];
+        for (int64_t q = T.eoff[o]; q < T.eoff[o + 1]; ++q) ecnt[T.e_old2new[T.eid[q]] + 1]++;
+        for (int64_t q = T.voff[o]; q < T.voff[o + 1]; ++q) vcnt[T.v_old2new[T.vid[q]] + 1]++;
+        vcnt[v + 1]++;
+    }
+    for (int64_t k = 0; k < ne; ++k)
+        for (int i = 0; i < 6; ++i) scnt[T.v_old2new[T.sten[6 * (int64_t)T.e_new2old[k] + i]] + 1]++;
+    for (int64_t k = 0; k < ne; ++k) ecnt[k + 1] += ecnt[k];
+    for (int64_t v = 0; v < nv; ++v) {
+        vcnt[v + 1] += vcnt[v];
+        scnt[v + 1] += scnt[v];
+    }
+    std::vector<int32_t> evid(ecnt[ne]), vvid(vcnt[nv]);
+    std::vector<double> ewt(ecnt[ne]), wf(vcnt[nv]), wg(vcnt[nv]);
+    std::vector<int64_t> slot(scnt[nv]);
+    std::vector<int64_t> ef(ecnt.begin(), ecnt.end() - 1), vf(vcnt.begin(), vcnt.end() - 1), sf(scnt.begin(), scnt.end() - 1);
+    for (int64_t v = 0; v < m->n_real; ++v) {
+        const int64_t o = T.v_new2old[v];
+        double sf_ = 0, sg_ = 0, sx = 0, sy = 0;
+        for (int64_t q = T.eoff[o]; q < T.eoff[o + 1]; ++q) {
+            const int32_t e = T.eid[q];
+            const int64_t p = ef[T.e_old2new[e]]++;
+            evid[p] = (int32_t)v;
+            ewt[p] = T.we[q];
+            sx += T.we[q] * T.nrm[2 * e];
+            sy += T.we[q] * T.nrm[2 * e + 1];
+        }
+        for (int64_t q = T.voff[o]; q < T.voff[o + 1]; ++q) {
+            const int64_t p = vf[T.v_old2new[T.vid[q]]]++;
+            vvid[p] = (int32_t)v;
+            wf[p] = T.wf[q];
+            wg[p] = T.wg[q];
+            sf_ += T.wf[q];
+            sg_ += T.wg[q];
+        }
+        const int64_t p = vf[v]++;  // centre weights, as in the forward's folded form
+        vvid[p] = (int32_t)v;
+        wf[p] = -(sf_ + sx);
+        wg[p] = -(sg_ + sy);
+    }
+    for (int64_t k = 0; k < ne; ++k)
+        for (int i = 0; i < 6; ++i) slot[sf[T.v_old2new[T.sten[6 * (int64_t)T.e_new2old[k] + i]]]++] = i * ne + k;
+    fdu_status st;
+    if ((st = m->upload(m->adj_eoff, ecnt))) return st;
+    if ((st = m->upload(m->adj_evid, evid))) return st;
+    if ((st = m->upload(m->adj_ewt, ewt))) return st;
+    if ((st = m->upload(m->adj_voff, vcnt))) return st;
+    if ((st = m->upload(m->adj_vvid, vvid))) return st;
+    if ((st = m->upload(m->adj_wf, wf))) return st;
+    if ((st = m->upload(m->adj_wg, wg))) return st;
+    if ((st = m->upload(m->adj_soff, scnt))) return st;
+    if ((st = m->upload(m->adj_slot, slot))) return st;
+    if ((st = m->alloc(m->adj_lam_r, 4 * ne))) return st;
+    if ((st = m->alloc(m->adj_G, 6 * 4 * ne))) return st;
+    if ((st = m->alloc(m->adj_S1, 4 * nv))) return st;
+    for (int i = 0; i < 5; ++i)
+        if ((st = m->alloc(m->adj_buf[i], 4 * nv))) return st;
+    m->adj_ready = true;
+    return FDU_OK;
+}
+
+// out = (dL/dw)^T lam at state w (all internal order)
+void enqueue_residual_vjp(fdu_mesh *m, const double *w, const double *lam, double *out, cudaStream_t s) {
+    AdjEdgeArgs ea{};
+    ea.sten = m->sten;
+    ea.coef = m->coef64;
+    ea.w = w;
+    ea.lam_r = m->adj_lam_r;
+    ea.lam_r_mut = m->adj_lam_r;
+    ea.G = m->adj_G;
+    ea.ne = m->ne_act;
+    ea.gm1 = m->opts.gamma - 1.0;
+    ea.eps = m->opts.weno_eps;
+    AdjTables t{m->adj_eoff, m->adj_evid, m->adj_ewt};
+    AdjVertexArgs va{};
+    va.nv = m->nv;
+    va.voff = m->adj_voff;
+    va.vid = m->adj_vvid;
+    va.wf = m->adj_wf;
+    va.wg = m->adj_wg;
+    va.lam = lam;
+    va.w = w;
+    va.gm1 = m->opts.gamma - 1.0;
+    va.soff = m->adj_soff;
+    va.slot = m->adj_slot;
+    va.G = m->adj_G;
+    va.grad = out;
+    launch_residual_vjp(ea, t, va, s);
+}
+
+// lam_prev = (dw'/dw)^T lam_next for one SSP-RK3 step from the state wn
+// (internal order; wn is not changed, ws and the stage flux buffers are).
+void enqueue_rk_step_vjp(fdu_mesh *m, double dt, const double *lam_next, double *lam_prev, cudaStream_t s) {
+    const int64_t n4 = 4 * m->nv;
+    double *t = m->adj_buf[2], *ls2 = m->adj_buf[3], *ls1 = m->adj_buf[4];
+    ensure_fluxes(m, 64, s);
+    enqueue_stages(m, 64, dt, nullptr, s, false, 1, 1);
+    cudaMemcpyAsync(m->adj_S1, m->ws, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    enqueue_stages(m, 64, dt, nullptr, s, false, 2, 2);  // ws = S2
+    // w' = 1/3 S0 + 2/3 (S2 + dt L(S2))
+    enqueue_residual_vjp(m, m->ws, lam_next, t, s);
+    launch_axpby(ls2, 2.0 / 3.0, lam_next, 2.0 / 3.0 * dt, t, 0.0, nullptr, n4, s);
+    // S2 = 3/4 S0 + 1/4 (S1 + dt L(S1))
+    enqueue_residual_vjp(m, m->adj_S1, ls2, t, s);
+    launch_axpby(ls1, 0.25, ls2, 0.25 * dt, t, 0.0, nullptr, n4, s);
+    // S1 = S0 + dt L(S0)
+    enqueue_residual_vjp(m, m->wn, ls1, t, s);
+    launch_axpby(lam_prev, 1.0 / 3.0, lam_next, 0.75, ls2, 1.0, ls1, n4, s);
+    launch_axpby(lam_prev, 1.0, lam_prev, dt, t, 0.0, nullptr, n4, s);
 }
 
 // One SSP-RK3 step of a batch: three cooperative persistent launches.
@@ -1108,6 +1243,110 @@ fdu_status fdu_residual_noalloc(const fdu_mesh *mc, const double *w, double *dwd
     launch_div_f64(a, 0, s);
     CK_LAUNCH();
     return FDU_OK;
+}
+
+static fdu_status to_internal(fdu_mesh *m, const double *x, int on_device, double *dst, cudaStream_t s) {
+    if (on_device) {
+        launch_permute_rows(x, dst, m->new2old, m->nv, true, s);
+        CK_LAUNCH();
+    } else {
+        std::vector<double> h(4 * m->nv);
+        for (int64_t i = 0; i < m->nv; ++i) std::memcpy(&h[4 * i], x + 4 * (int64_t)m->T.v_new2old[i], 32);
+        CK(cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return FDU_OK;
+}
+
+static fdu_status from_internal(fdu_mesh *m, const double *src, double *y, int on_device, cudaStream_t s) {
+    if (on_device) {
+        launch_permute_rows(src, y, m->new2old, m->nv, false, s);
+        CK_LAUNCH();
+    } else {
+        launch_permute_rows(src, m->scratch, m->new2old, m->nv, false, s);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(y, m->scratch, 4 * m->nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return FDU_OK;
+}
+
+fdu_status fdu_residual_vjp(fdu_mesh *m, const double *lam, double *grad, int on_device, void *stream) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!lam || !grad) return set_err(FDU_ERR_ARG, "null argument");
+    if ((st = adjoint_setup(m))) return st;
+    cudaStream_t s = m->stream(stream);
+    if ((st = to_internal(m, lam, on_device, m->adj_buf[0], s))) return st;
+    enqueue_residual_vjp(m, m->wn, m->adj_buf[0], m->adj_buf[1], s);
+    CK_LAUNCH();
+    return from_internal(m, m->adj_buf[1], grad, on_device, s);
+}
+
+fdu_status fdu_rk_step_vjp(fdu_mesh *m, double dt, const double *lam_next, double *lam_prev, int on_device,
+                           void *stream) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!lam_next || !lam_prev || !(dt > 0)) return set_err(FDU_ERR_ARG, "null argument or dt <= 0");
+    if ((st = adjoint_setup(m))) return st;
+    cudaStream_t s = m->stream(stream);
+    if ((st = to_internal(m, lam_next, on_device, m->adj_buf[0], s))) return st;
+    enqueue_rk_step_vjp(m, dt, m->adj_buf[0], m->adj_buf[1], s);
+    CK_LAUNCH();
+    m->f32_valid = false;
+    return from_internal(m, m->adj_buf[1], lam_prev, on_device, s);
+}
+
+fdu_status fdu_adjoint_rk(fdu_mesh *m, double dt, int n_steps, int checkpoint_every, const double *lam_final,
+                          double *grad, int on_device, void *stream) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (!lam_final || !grad || !(dt > 0) || n_steps < 1 || checkpoint_every < 1)
+        return set_err(FDU_ERR_ARG, "need dt > 0, n_steps >= 1, checkpoint_every >= 1 and both arrays");
+    if ((st = adjoint_setup(m))) return st;
+    cudaStream_t s = m->stream(stream);
+    const int K = checkpoint_every, nseg = (n_steps + K - 1) / K;
+    const size_t bytes = 4 * m->nv * sizeof(double);
+    while ((int)m->adj_states.size() < nseg + K) {
+        double *p = nullptr;
+        if ((st = m->alloc(p, 4 * m->nv))) return st;
+        m->adj_states.push_back(p);
+    }
+    double *const *ck = m->adj_states.data();      // checkpoints [nseg]
+    double *const *stp = m->adj_states.data() + nseg;  // step states of one segment [K]
+    // forward pass from the current state w0, keeping a checkpoint every K steps
+    ensure_fluxes(m, 64, s);
+    for (int i = 0; i < n_steps; ++i) {
+        if (i % K == 0) CK(cudaMemcpyAsync(ck[i / K], m->wn, bytes, cudaMemcpyDeviceToDevice, s));
+        enqueue_step(m, 64, dt, nullptr, s, false);
+    }
+    CK_LAUNCH();
+    // reverse pass, segment by segment, recomputing each segment's step states
+    double *lam = m->adj_buf[0], *lam_prev = m->adj_buf[1];
+    if ((st = to_internal(m, lam_final, on_device, lam, s))) return st;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int i0 = seg * K, i1 = std::min(n_steps, i0 + K);
+        CK(cudaMemcpyAsync(m->wn, ck[seg], bytes, cudaMemcpyDeviceToDevice, s));
+        m->f64_valid = false;
+        for (int i = i0; i < i1; ++i) {
+            CK(cudaMemcpyAsync(stp[i - i0], m->wn, bytes, cudaMemcpyDeviceToDevice, s));
+            if (i + 1 < i1) {
+                ensure_fluxes(m, 64, s);
+                enqueue_step(m, 64, dt, nullptr, s, false);
+            }
+        }
+        for (int i = i1 - 1; i >= i0; --i) {
+            CK(cudaMemcpyAsync(m->wn, stp[i - i0], bytes, cudaMemcpyDeviceToDevice, s));
+            m->f64_valid = false;
+            enqueue_rk_step_vjp(m, dt, lam, lam_prev, s);
+            std::swap(lam, lam_prev);
+        }
+        CK_LAUNCH();
+    }
+    // the mesh state is w0 again (the first step state of the first segment)
+    m->f64_valid = false;
+    m->f32_valid = false;
+    return from_internal(m, lam, grad, on_device, s);
 }
 
 fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n) {

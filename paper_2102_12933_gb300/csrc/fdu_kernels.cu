@@ -21,128 +21,12 @@
 
 #include "fdu_internal.h"
 #include "fdu_kernels.cuh"
+#include "fdu_device.cuh"
 
 namespace fdu {
 namespace {
 
-// ------------------------------------------------------------------ helpers
-// A conservative FP64 record (rho, rho u, rho v, rho E), 16-byte aligned.
-struct __align__(16) dbl4 {
-    double x, y, z, w;
-};
-__device__ __forceinline__ dbl4 dbl4_make(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
-__device__ __forceinline__ dbl4 ld4(const double *p, int64_t i) {
-    const double2 *q = reinterpret_cast<const double2 *>(p + 4 * i);
-    const double2 a = __ldg(q), b = __ldg(q + 1);
-    return dbl4_make(a.x, a.y, b.x, b.y);
-}
-__device__ __forceinline__ void st4(double *p, int64_t i, dbl4 v) {
-    double2 *q = reinterpret_cast<double2 *>(p + 4 * i);
-    q[0] = make_double2(v.x, v.y);
-    q[1] = make_double2(v.z, v.w);
-}
-__device__ __forceinline__ dbl4 sub4(dbl4 a, dbl4 b) {
-    return dbl4_make(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-}
-__device__ __forceinline__ dbl4 add4(dbl4 a, dbl4 b) {
-    return dbl4_make(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-}
-__device__ __forceinline__ dbl4 neg4(dbl4 a) { return dbl4_make(-a.x, -a.y, -a.z, -a.w); }
-
-// Reciprocal of a positive normal double by Newton-Raphson iteration
-// y <- y + y (1 - x y), started from the hardware's approximate FP64
-// reciprocal (PTX rcp.approx.ftz.f64); two iterations bring the relative
-// error to the rounding level (checked against IEEE division by the tests).
-__device__ __forceinline__ double recip64(double x) {
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    double e = fma(-x, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-x, y, 1.0);
-    return fma(y, e, y);
-}
-
-// Per-state quantities reused by the Roe average and the physical flux.
-struct Prim64 {
-    double r;   // rho^-1/2
-    double ir;  // 1/rho
-    double p;   // pressure
-};
-__device__ __forceinline__ Prim64 prim64(const dbl4 &w, double gm1) {
-    Prim64 q;
-    q.r = rsqrt(w.x);
-    q.ir = q.r * q.r;
-    q.p = gm1 * (w.w - 0.5 * (w.y * w.y + w.z * w.z) * q.ir);
-    return q;
-}
-
-// Roe average of two states (weights sqrt(rho)) and the eigen-quantities
-// of the flux Jacobian along n.
-struct Roe64 {
-    double u, v, H, c, ic, b1, qn, qt, hq2, nx, ny;
-};
-__device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const dbl4 &b, const Prim64 &pb,
-                                      double nx, double ny, double gm1) {
-    Roe64 R;
-    const double sa = a.x * pa.r, sb = b.x * pb.r;
-    const double inv = recip64(sa + sb);
-    R.u = (a.y * pa.r + b.y * pb.r) * inv;
-    R.v = (a.z * pa.r + b.z * pb.r) * inv;
-    R.H = ((a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r) * inv;
-    R.hq2 = 0.5 * (R.u * R.u + R.v * R.v);
-    const double c2 = gm1 * (R.H - R.hq2);
-    R.ic = rsqrt(c2);
-    R.c = c2 * R.ic;
-    R.b1 = gm1 * R.ic * R.ic;
-    R.nx = nx;
-    R.ny = ny;
-    R.qn = R.u * nx + R.v * ny;
-    R.qt = R.v * nx - R.u * ny;
-    return R;
-}
-
-// Characteristic components of a conservative difference (left eigenvectors
-// of dF_n/dw at the Roe state; fields ordered q_n - c, q_n (entropy), q_n
-// (shear), q_n + c).
-__device__ __forceinline__ dbl4 project64(const Roe64 &R, const dbl4 &d) {
-    const double phi = R.b1 * (R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w);
-    const double psi = (R.qn * d.x - R.nx * d.y - R.ny * d.z) * R.ic;
-    return dbl4_make(0.5 * (phi + psi), d.x - phi, R.nx * d.z - R.ny * d.y - R.qt * d.x, 0.5 * (phi - psi));
-}
-// Conservative difference from characteristic components (right eigenvectors).
-__device__ __forceinline__ dbl4 unproject64(const Roe64 &R, const dbl4 &c) {
-    const double rho = c.x + c.y + c.w;
-    const double dd = R.c * (c.w - c.x);
-    return dbl4_make(rho, R.u * rho + R.nx * dd - R.ny * c.z, R.v * rho + R.ny * dd + R.nx * c.z,
-                        R.H * (c.x + c.w) + R.hq2 * c.y + R.qn * dd + R.qt * c.z);
-}
-
-// NU-WENO5 increments of one characteristic field (Appendix), both sides.
-// Differences: a = L3-L1, b = L2-L1, c = R1-L1, d = R2-L1 (left centre L1),
-// e = R3-R1, f = R2-R1 (right centre R1).  k is the edge's coefficient block
-// (fdu_internal.h): four sub-stencils S_a..S_d give values v (increments),
-// and slopes p / curvatures q whose squares sum to the smoothness
-// indicators beta = p^2 + q^2.  The nonlinear weights alpha_k = C_k /
-// (beta_k + eps), omega = alpha / sum(alpha) (p = 1) are applied as
-// C_k prod_{l != k}(beta_l + eps) over their sum: the same quotient with one
-// reciprocal per side.
-__device__ __forceinline__ void weno_pair64(const double *k, double a, double b, double c, double d, double e,
-                                            double f, double eps, double &dl, double &dr) {
-    const double va = fma(k[0], a, k[1] * b), pa = fma(k[2], a, k[3] * b), qa = fma(k[4], a, k[5] * b);
-    const double vb = fma(k[6], b, k[7] * c), pb = fma(k[8], b, k[9] * c), qb = fma(k[10], b, k[11] * c);
-    const double vc = fma(k[12], c, k[13] * d), pc = fma(k[14], c, k[15] * d), qc = fma(k[16], c, k[17] * d);
-    const double vd = fma(k[18], e, k[19] * f), pd = fma(k[20], e, k[21] * f), qd = fma(k[22], e, k[23] * f);
-    const double ba = fma(pa, pa, fma(qa, qa, eps));
-    const double bb = fma(pb, pb, fma(qb, qb, eps));
-    const double bc = fma(pc, pc, fma(qc, qc, eps));
-    const double bd = fma(pd, pd, fma(qd, qd, eps));
-    const double bbc = bb * bc;
-    const double l0 = k[24] * bbc, l1 = k[25] * (ba * bc), l2 = k[26] * (ba * bb);
-    dl = fma(l0, va, fma(l1, vb, l2 * vc)) * recip64(l0 + l1 + l2);
-    const double r0 = k[27] * bbc, r1 = k[28] * (bd * bb), r2 = k[29] * (bd * bc);
-    // right-side increments from R1: S_d's own, S_c's and S_b's shifted by -c
-    dr = fma(r0, vd, fma(r1, vc - c, r2 * (vb - c))) * recip64(r0 + r1 + r2);
-}
+using namespace dev;
 
 // ------------------------------------------------------------------ FP64 edge flux
 __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int64_t e) {

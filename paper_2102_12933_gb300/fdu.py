@@ -35,7 +35,7 @@ EXPORTS = (
     "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
     "fdu_check_recip64", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
     "fdu_batch_max_dt", "fdu_batch_set_dt", "fdu_batch_rk_steps", "fdu_batch_set_launch", "fdu_batch_autotune",
-    "fdu_batch_barrier_selftest",
+    "fdu_batch_barrier_selftest", "fdu_residual_vjp", "fdu_rk_step_vjp", "fdu_adjoint_rk",
 )
 
 
@@ -116,6 +116,9 @@ def load():
         L.fdu_batch_set_launch.argtypes = [P, C.c_int, C.c_int]
         L.fdu_batch_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
         L.fdu_batch_barrier_selftest.argtypes = [P, C.POINTER(C.c_int)]
+        L.fdu_residual_vjp.argtypes = [P, P, P, C.c_int, P]
+        L.fdu_rk_step_vjp.argtypes = [P, C.c_double, P, P, C.c_int, P]
+        L.fdu_adjoint_rk.argtypes = [P, C.c_double, C.c_int, C.c_int, P, P, C.c_int, P]
         L.fdu_profile_read.argtypes = [P, C.c_int, C.c_int, dp, lp, C.c_int]
         for name in EXPORTS:
             if name not in ("fdu_version", "fdu_last_error"):
@@ -341,6 +344,40 @@ class Mesh:
         _check(load().fdu_advance(self._h, float(cfl), float(t_end), int(precision), int(max_steps), C.byref(n),
                                   C.byref(t), _stream_ptr(stream)))
         return n.value, t.value
+
+    def residual_vjp(self, lam, out=None, stream=None):
+        """(dL/dw)^T lam at the current state."""
+        if out is None:
+            out = np.zeros((self.nv, 4))
+        pl, dl = _buffer(lam, self.nv)
+        po, do = _buffer(out, self.nv, writable=True)
+        if dl != do:
+            raise ValueError("lam and out must both be device or both host arrays")
+        _check(load().fdu_residual_vjp(self._h, pl, po, do, _stream_ptr(stream)))
+        return out
+
+    def rk_step_vjp(self, dt, lam_next, out=None, stream=None):
+        """(dw_{n+1}/dw_n)^T lam_next for one SSP-RK3 step from the current state."""
+        if out is None:
+            out = np.zeros((self.nv, 4))
+        pl, dl = _buffer(lam_next, self.nv)
+        po, do = _buffer(out, self.nv, writable=True)
+        if dl != do:
+            raise ValueError("lam_next and out must both be device or both host arrays")
+        _check(load().fdu_rk_step_vjp(self._h, float(dt), pl, po, do, _stream_ptr(stream)))
+        return out
+
+    def adjoint_rk(self, dt, n_steps, lam_final, out=None, checkpoint_every=10, stream=None):
+        """(dw_T/dw0)^T lam_final over n_steps SSP-RK3 steps from the current state w0."""
+        if out is None:
+            out = np.zeros((self.nv, 4))
+        pl, dl = _buffer(lam_final, self.nv)
+        po, do = _buffer(out, self.nv, writable=True)
+        if dl != do:
+            raise ValueError("lam_final and out must both be device or both host arrays")
+        _check(load().fdu_adjoint_rk(self._h, float(dt), int(n_steps), int(checkpoint_every), pl, po, do,
+                                     _stream_ptr(stream)))
+        return out
 
     def limited_count(self, reset=False, stream=None) -> int:
         """Vertex stage updates scaled by the positivity safeguard since the last reset."""

@@ -481,21 +481,27 @@ void enqueue_residual_vjp(fdu_mesh *m, const double *w, const double *lam, doubl
 
 // lam_prev = (dw'/dw)^T lam_next for one SSP-RK3 step from the state wn
 // (internal order; wn is not changed, ws and the stage flux buffers are).
-void enqueue_rk_step_vjp(fdu_mesh *m, double dt, const double *lam_next, double *lam_prev, cudaStream_t s) {
+void enqueue_rk_step_vjp(fdu_mesh *m, double dt, const double *lam_next, double *lam_prev, cudaStream_t s,
+                         const double *S0 = nullptr, const double *S1 = nullptr, const double *S2 = nullptr) {
     const int64_t n4 = 4 * m->nv;
     double *t = m->adj_buf[2], *ls2 = m->adj_buf[3], *ls1 = m->adj_buf[4];
-    ensure_fluxes(m, 64, s);
-    enqueue_stages(m, 64, dt, nullptr, s, false, 1, 1);
-    cudaMemcpyAsync(m->adj_S1, m->ws, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    enqueue_stages(m, 64, dt, nullptr, s, false, 2, 2);  // ws = S2
+    if (!S0) {  // recompute the stage states from wn
+        ensure_fluxes(m, 64, s);
+        enqueue_stages(m, 64, dt, nullptr, s, false, 1, 1);
+        cudaMemcpyAsync(m->adj_S1, m->ws, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        enqueue_stages(m, 64, dt, nullptr, s, false, 2, 2);  // ws = S2
+        S0 = m->wn;
+        S1 = m->adj_S1;
+        S2 = m->ws;
+    }
     // w' = 1/3 S0 + 2/3 (S2 + dt L(S2))
-    enqueue_residual_vjp(m, m->ws, lam_next, t, s);
+    enqueue_residual_vjp(m, S2, lam_next, t, s);
     launch_axpby(ls2, 2.0 / 3.0, lam_next, 2.0 / 3.0 * dt, t, 0.0, nullptr, n4, s);
     // S2 = 3/4 S0 + 1/4 (S1 + dt L(S1))
-    enqueue_residual_vjp(m, m->adj_S1, ls2, t, s);
+    enqueue_residual_vjp(m, S1, ls2, t, s);
     launch_axpby(ls1, 0.25, ls2, 0.25 * dt, t, 0.0, nullptr, n4, s);
     // S1 = S0 + dt L(S0)
-    enqueue_residual_vjp(m, m->wn, ls1, t, s);
+    enqueue_residual_vjp(m, S0, ls1, t, s);
     launch_axpby(lam_prev, 1.0 / 3.0, lam_next, 0.75, ls2, 1.0, ls1, n4, s);
     launch_axpby(lam_prev, 1.0, lam_prev, dt, t, 0.0, nullptr, n4, s);
 }
@@ -1307,13 +1313,13 @@ fdu_status fdu_adjoint_rk(fdu_mesh *m, double dt, int n_steps, int checkpoint_ev
     cudaStream_t s = m->stream(stream);
     const int K = checkpoint_every, nseg = (n_steps + K - 1) / K;
     const size_t bytes = 4 * m->nv * sizeof(double);
-    while ((int)m->adj_states.size() < nseg + K) {
+    while ((int)m->adj_states.size() < nseg + 3 * K) {
         double *p = nullptr;
         if ((st = m->alloc(p, 4 * m->nv))) return st;
         m->adj_states.push_back(p);
     }
-    double *const *ck = m->adj_states.data();      // checkpoints [nseg]
-    double *const *stp = m->adj_states.data() + nseg;  // step states of one segment [K]
+    double *const *ck = m->adj_states.data();          // checkpoints [nseg]
+    double *const *stp = m->adj_states.data() + nseg;  // stage states of one segment [K][3]
     // forward pass from the current state w0, keeping a checkpoint every K steps
     ensure_fluxes(m, 64, s);
     for (int i = 0; i < n_steps; ++i) {
@@ -1328,19 +1334,23 @@ fdu_status fdu_adjoint_rk(fdu_mesh *m, double dt, int n_steps, int checkpoint_ev
         const int i0 = seg * K, i1 = std::min(n_steps, i0 + K);
         CK(cudaMemcpyAsync(m->wn, ck[seg], bytes, cudaMemcpyDeviceToDevice, s));
         m->f64_valid = false;
-        for (int i = i0; i < i1; ++i) {
-            CK(cudaMemcpyAsync(stp[i - i0], m->wn, bytes, cudaMemcpyDeviceToDevice, s));
-            if (i + 1 < i1) {
-                ensure_fluxes(m, 64, s);
-                enqueue_step(m, 64, dt, nullptr, s, false);
-            }
+        for (int i = i0; i < i1; ++i) {  // recompute the segment, keeping every stage input
+            double *const *S = stp + 3 * (i - i0);
+            CK(cudaMemcpyAsync(S[0], m->wn, bytes, cudaMemcpyDeviceToDevice, s));
+            ensure_fluxes(m, 64, s);
+            enqueue_stages(m, 64, dt, nullptr, s, false, 1, 1);
+            CK(cudaMemcpyAsync(S[1], m->ws, bytes, cudaMemcpyDeviceToDevice, s));
+            enqueue_stages(m, 64, dt, nullptr, s, false, 2, 2);
+            CK(cudaMemcpyAsync(S[2], m->ws, bytes, cudaMemcpyDeviceToDevice, s));
+            if (i + 1 < i1) enqueue_stages(m, 64, dt, nullptr, s, false, 3, 3);
         }
         for (int i = i1 - 1; i >= i0; --i) {
-            CK(cudaMemcpyAsync(m->wn, stp[i - i0], bytes, cudaMemcpyDeviceToDevice, s));
-            m->f64_valid = false;
-            enqueue_rk_step_vjp(m, dt, lam, lam_prev, s);
+            double *const *S = stp + 3 * (i - i0);
+            enqueue_rk_step_vjp(m, dt, lam, lam_prev, s, S[0], S[1], S[2]);
             std::swap(lam, lam_prev);
         }
+        CK(cudaMemcpyAsync(m->wn, stp[0], bytes, cudaMemcpyDeviceToDevice, s));
+        m->f64_valid = false;
         CK_LAUNCH();
     }
     // the mesh state is w0 again (the first step state of the first segment)

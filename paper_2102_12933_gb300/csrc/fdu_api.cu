@@ -169,7 +169,8 @@ fdu_status upload_tables(fdu_mesh *m) {
         for (int i = 0; i < 6; ++i) sten[i * ne + e] = T.v_old2new[T.sten[6 * o + i]];
         for (int c = 0; c < kEdgeCoef; ++c) {
             coef[(size_t)c * ne + e] = T.coef[(size_t)kEdgeCoef * o + c];
-            coef32[(size_t)c * ne + e] = (float)T.coef[(size_t)kEdgeCoef * o + c];
+            // FP32 block as float4 vectors: [c/4][ne][c%4]
+            coef32[((size_t)(c / 4) * ne + e) * 4 + c % 4] = (float)T.coef[(size_t)kEdgeCoef * o + c];
         }
     }
     if ((st = m->upload(m->sten, sten))) return st;

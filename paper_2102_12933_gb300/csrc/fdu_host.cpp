@@ -345,7 +345,7 @@ void stencil_of(const HostTables &T, int32_t o, std::vector<int32_t> &V, std::ve
 int lsq_weights(const HostTables &T, const Geo &g, int32_t o, const int64_t vb, const int64_t nvj, const int64_t eb,
                 const int64_t nek, std::vector<double> &w_out, std::vector<double> &A, std::vector<double> &hv) {
     const int p = T.degree;
-    const int M = p * (p + 3) / 2, n = 2 * M;
+    const int M = p * (p + 3) / 2, n = 2 * M;  // n <= 54 for p <= 6 (the per-unknown arrays below hold 64)
     const int m = (int)(2 * nvj + nek);
     if (m < n) return FDU_ERR_RANK_DEFICIENT;
     A.assign((size_t)m * n, 0.0);  // column-major
@@ -383,7 +383,7 @@ int lsq_weights(const HostTables &T, const Geo &g, int32_t o, const int64_t vb, 
         }
     }
     // column equilibration
-    double scale[32];
+    double scale[64];
     for (int c = 0; c < n; ++c) {
         double s = 0;
         for (int i = 0; i < m; ++i) s += A[(size_t)c * m + i] * A[(size_t)c * m + i];
@@ -394,7 +394,7 @@ int lsq_weights(const HostTables &T, const Geo &g, int32_t o, const int64_t vb, 
     }
     // Householder QR in place; reflector k stored in hv (length m-k) with beta
     hv.assign((size_t)m * n, 0.0);
-    double beta[32], rdiag[32];
+    double beta[64], rdiag[64];
     for (int k = 0; k < n; ++k) {
         double *col = &A[(size_t)k * m];
         double nrm2 = 0;
@@ -424,7 +424,7 @@ int lsq_weights(const HostTables &T, const Geo &g, int32_t o, const int64_t vb, 
     }
     if (!(rmin > 1e-13 * rmax)) return FDU_ERR_RANK_DEFICIENT;
     // R^T y = S e  (R upper triangular, A now holds R in rows 0..n-1)
-    double y[32];
+    double y[64];
     for (int c = 0; c < n; ++c) y[c] = 0;
     y[0] = scale[0];
     y[M + 1] += scale[M + 1];

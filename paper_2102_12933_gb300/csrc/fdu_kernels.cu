@@ -305,7 +305,18 @@ __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int6
     int32_t s[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
-    const float nx = __ldg(g + 30 * ne + e), ny = __ldg(g + 31 * ne + e);
+    // coefficient block as 8 float4 per edge: [c/4][ne] float4, component c%4
+    const float4 *__restrict__ g4 = reinterpret_cast<const float4 *>(g);
+    float k[32];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 q = __ldg(g4 + (int64_t)i * ne + e);
+        k[4 * i] = q.x;
+        k[4 * i + 1] = q.y;
+        k[4 * i + 2] = q.z;
+        k[4 * i + 3] = q.w;
+    }
+    const float nx = k[30], ny = k[31];
     const float4 L1 = __ldg(w + s[2]), R1 = __ldg(w + s[3]);
     const Prim32 pL1 = prim32(L1, gm1), pR1 = prim32(R1, gm1);
     const Roe32 C = roe32(L1, pL1, R1, pR1, nx, ny, gm1);
@@ -314,9 +325,6 @@ __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int6
     const float4 cL3 = project32(C, sub4f(__ldg(w + s[0]), L1));
     const float4 cR2 = project32(C, sub4f(__ldg(w + s[4]), R1));
     const float4 cR3 = project32(C, sub4f(__ldg(w + s[5]), R1));
-    float k[30];
-#pragma unroll
-    for (int i = 0; i < 30; ++i) k[i] = __ldg(g + (int64_t)i * ne + e);
     const float4 cR2L = add4f(cR2, cM);
     float4 dl, dr;
     weno_pair32(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, eps, dl.x, dr.x);
@@ -380,41 +388,8 @@ __global__ void vertex_flux_f32_kernel(const double *__restrict__ w, float4 *__r
 }
 
 template <int MODE>
-__device__ __forceinline__ void div_f32_body(const DivArgs &A, const int64_t v) {
-    const int64_t sl = v / kSell;
-    const int lane = (int)(v % kSell);
+__device__ __forceinline__ void div_f32_finish(const DivArgs &A, const int64_t v, float4 acc) {
     const float4 *__restrict__ F = static_cast<const float4 *>(A.F);
-    const float4 *__restrict__ r = static_cast<const float4 *>(A.r);
-    const float *__restrict__ wf = static_cast<const float *>(A.wf);
-    const float *__restrict__ wg = static_cast<const float *>(A.wg);
-    const float *__restrict__ we = static_cast<const float *>(A.we);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    {
-        const int64_t b = __ldg(A.slice_voff + sl) + lane, e = __ldg(A.slice_voff + sl + 1);
-#pragma unroll 4
-        for (int64_t p = b; p < e; p += kSell) {
-            const int32_t j = __ldg(A.vid + p);
-            const float a = __ldg(wf + p), c = __ldg(wg + p);
-            const float4 f = __ldg(F + 2 * (int64_t)j), g = __ldg(F + 2 * (int64_t)j + 1);
-            acc.x = fmaf(a, f.x, fmaf(c, g.x, acc.x));
-            acc.y = fmaf(a, f.y, fmaf(c, g.y, acc.y));
-            acc.z = fmaf(a, f.z, fmaf(c, g.z, acc.z));
-            acc.w = fmaf(a, f.w, fmaf(c, g.w, acc.w));
-        }
-    }
-    {
-        const int64_t b = __ldg(A.slice_eoff + sl) + lane, e = __ldg(A.slice_eoff + sl + 1);
-#pragma unroll 4
-        for (int64_t p = b; p < e; p += kSell) {
-            const int32_t k = __ldg(A.eid + p);
-            const float a = __ldg(we + p);
-            const float4 q = __ldg(r + k);
-            acc.x = fmaf(a, q.x, acc.x);
-            acc.y = fmaf(a, q.y, acc.y);
-            acc.z = fmaf(a, q.z, acc.z);
-            acc.w = fmaf(a, q.w, acc.w);
-        }
-    }
     {
         const float *cfg = static_cast<const float *>(A.cfg);
         const float cf = __ldg(cfg + v), cg = __ldg(cfg + A.n_real + v);
@@ -456,6 +431,45 @@ __device__ __forceinline__ void div_f32_body(const DivArgs &A, const int64_t v) 
     Fo[2 * v + 1] = g;
 }
 
+template <int MODE>
+__device__ __forceinline__ void div_f32_body(const DivArgs &A, const int64_t v) {
+    const int64_t sl = v / kSell;
+    const int lane = (int)(v % kSell);
+    const float4 *__restrict__ F = static_cast<const float4 *>(A.F);
+    const float4 *__restrict__ r = static_cast<const float4 *>(A.r);
+    const float *__restrict__ wf = static_cast<const float *>(A.wf);
+    const float *__restrict__ wg = static_cast<const float *>(A.wg);
+    const float *__restrict__ we = static_cast<const float *>(A.we);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    {
+        const int64_t b = __ldg(A.slice_voff + sl) + lane, e = __ldg(A.slice_voff + sl + 1);
+#pragma unroll 4
+        for (int64_t p = b; p < e; p += kSell) {
+            const int32_t j = __ldg(A.vid + p);
+            const float a = __ldg(wf + p), c = __ldg(wg + p);
+            const float4 f = __ldg(F + 2 * (int64_t)j), g = __ldg(F + 2 * (int64_t)j + 1);
+            acc.x = fmaf(a, f.x, fmaf(c, g.x, acc.x));
+            acc.y = fmaf(a, f.y, fmaf(c, g.y, acc.y));
+            acc.z = fmaf(a, f.z, fmaf(c, g.z, acc.z));
+            acc.w = fmaf(a, f.w, fmaf(c, g.w, acc.w));
+        }
+    }
+    {
+        const int64_t b = __ldg(A.slice_eoff + sl) + lane, e = __ldg(A.slice_eoff + sl + 1);
+#pragma unroll 4
+        for (int64_t p = b; p < e; p += kSell) {
+            const int32_t k = __ldg(A.eid + p);
+            const float a = __ldg(we + p);
+            const float4 q = __ldg(r + k);
+            acc.x = fmaf(a, q.x, acc.x);
+            acc.y = fmaf(a, q.y, acc.y);
+            acc.z = fmaf(a, q.z, acc.z);
+            acc.w = fmaf(a, q.w, acc.w);
+        }
+    }
+    div_f32_finish<MODE>(A, v, acc);
+}
+
 // ------------------------------------------------------------------ kernels
 __global__ void __launch_bounds__(kEdgeBlock) edge_flux_f64_kernel(EdgeArgs A) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -463,7 +477,7 @@ __global__ void __launch_bounds__(kEdgeBlock) edge_flux_f64_kernel(EdgeArgs A) {
     if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
     edge_flux_f64_body(A, e);
 }
-__global__ void __launch_bounds__(kEdgeBlock) edge_flux_f32_kernel(EdgeArgs A) {
+__global__ void __launch_bounds__(kEdgeBlock, 6) edge_flux_f32_kernel(EdgeArgs A) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= A.ne) return;
     if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end

@@ -72,7 +72,7 @@ def test_residual_device_buffers(c40):
 
 
 def test_other_stencils_and_degrees():
-    for degree, levels in ((1, 1), (3, 2)):
+    for degree, levels in ((1, 1), (3, 2), (5, 2)):
         c = Case(30, seed=31, degree=degree, levels=levels)
         c.M.set_state(c.w0)
         got = c.M.residual(64)

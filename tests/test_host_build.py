@@ -126,3 +126,14 @@ def test_transmissive_box_tables_match_oracle():
         assert np.abs(a[i] - b[i]).max() <= 1e-11 * (1 + np.abs(b[i]).max())
     ghost = m.ghost_donor >= 0
     assert np.all(np.diff(a[0])[ghost] == 0)  # ghost rows are empty
+
+
+@pytest.mark.parametrize("degree", [4, 5, 6])
+def test_high_degree_weights_match_oracle(degree):
+    """Degrees 4-6 (the paper's fifth-order setting is degree 5, Section 2.2.3)."""
+    m, M, om = _pair(n=24, seed=91, lsq_degree=degree, lsq_levels=2)
+    a, b = M.div_stencils(), om.div_stencils()
+    for i in (0, 1, 4, 5):
+        assert np.array_equal(a[i], b[i])
+    for i in (2, 3, 6):
+        assert np.abs(a[i] - b[i]).max() <= 1e-9 * (1 + np.abs(b[i]).max())

@@ -70,6 +70,7 @@ struct fdu_mesh {
     // state
     double *wn = nullptr, *ws = nullptr, *scratch = nullptr;  // [nv][4]
     double *F64[3] = {nullptr, nullptr, nullptr};           // [nv][8]; F64[0] = fluxes of wn
+    double *Q64[3] = {nullptr, nullptr, nullptr};           // [nv][4] Roe records, rotating with F64
     float4 *F32[3] = {nullptr, nullptr, nullptr};           // [nv][2]
     float4 *w32 = nullptr;                                  // [nv]
     double *r64 = nullptr;                                  // [ne_act][4]
@@ -258,6 +259,7 @@ fdu_status upload_tables(fdu_mesh *m) {
     if ((st = m->alloc(m->scratch, 4 * nv))) return st;
     for (int i = 0; i < 3; ++i) {
         if ((st = m->alloc(m->F64[i], 8 * nv))) return st;
+        if ((st = m->alloc(m->Q64[i], 4 * nv))) return st;
         if ((st = m->alloc(m->F32[i], 2 * nv))) return st;
     }
     if ((st = m->alloc(m->w32, nv))) return st;
@@ -288,6 +290,7 @@ EdgeArgs edge_args(fdu_mesh *m, int prec, const void *w) {
     a.epsf = (float)m->opts.weno_eps32;
     a.fallback = m->counters;
     a.dt_dev = nullptr;
+    a.Q = nullptr;
     return a;
 }
 
@@ -336,7 +339,7 @@ void timed(fdu_mesh *m, int kind, bool allowed, cudaStream_t s, F &&launch) {
 // Make F64[0] (or w32 and F32[0]) describe the current state wn.
 void ensure_fluxes(fdu_mesh *m, int prec, cudaStream_t s) {
     if (prec == 64 && !m->f64_valid) {
-        launch_vertex_flux_f64(m->wn, m->F64[0], m->nv, m->opts.gamma, s);
+        launch_vertex_flux_f64(m->wn, m->F64[0], m->nv, m->opts.gamma, s, m->Q64[0]);
         m->f64_valid = true;
     }
     if (prec == 32 && !m->f32_valid) {
@@ -357,6 +360,7 @@ void enqueue_stages(fdu_mesh *m, int prec, double dt, const double *dt_dev, cuda
         timed(m, kd, prof, s, [&] {
             EdgeArgs ea = edge_args(m, prec, prec == 64 ? (const void *)win : (const void *)m->w32);
             ea.dt_dev = dt_dev;
+            if (prec == 64) ea.Q = m->Q64[stage - 1];
             if (prec == 64) launch_edge_flux_f64(ea, s);
             else launch_edge_flux_f32(ea, s);
         });
@@ -365,6 +369,7 @@ void enqueue_stages(fdu_mesh *m, int prec, double dt, const double *dt_dev, cuda
         a.ws = win;
         a.wout = stage == 3 ? m->wn : m->ws;
         a.Fout = prec == 64 ? (void *)m->F64[stage % 3] : (void *)m->F32[stage % 3];
+        a.Qout = prec == 64 ? m->Q64[stage % 3] : nullptr;
         a.w32out = prec == 32 ? m->w32 : nullptr;
         a.dt = dt;
         a.dt_dev = dt_dev;
@@ -372,8 +377,10 @@ void enqueue_stages(fdu_mesh *m, int prec, double dt, const double *dt_dev, cuda
             if (prec == 64) launch_div_f64(a, stage, s);
             else launch_div_f32(a, stage, s);
         });
-        if (m->n_ghost > 0)
+        if (m->n_ghost > 0) {
             launch_ghost_fill(a.wout, a.Fout, fq, prec == 32 ? m->w32 : nullptr, m->donor, m->n_real, m->n_ghost, s);
+            if (a.Qout) launch_ghost_fill(nullptr, a.Qout, 2, nullptr, m->donor, m->n_real, m->n_ghost, s);
+        }
     }
 }
 
@@ -518,6 +525,8 @@ cudaError_t enqueue_step_persistent(fdu_mesh *m, int prec, cudaStream_t s, unsig
         a.ws = win;
         a.wout = stage == 3 ? m->wn : m->ws;
         a.Fout = prec == 64 ? (void *)m->F64[stage % 3] : (void *)m->F32[stage % 3];
+        a.Qout = prec == 64 ? m->Q64[stage % 3] : nullptr;
+        if (prec == 64) ea.Q = m->Q64[stage - 1];
         a.w32out = prec == 32 ? m->w32 : nullptr;
         a.comp = m->comp;
         a.dt_comp = m->dt_comp;
@@ -768,8 +777,13 @@ fdu_status fdu_residual(fdu_mesh *m, int precision, double *dwdt, int on_device,
     if (m->n_ghost > 0) CK(cudaMemsetAsync(out, 0, 4 * m->nv * sizeof(double), s));
     const int kd = precision == 64 ? 0 : 2;
     timed(m, kd, true, s, [&] {
-        if (precision == 64) launch_edge_flux_f64(edge_args(m, 64, m->wn), s);
-        else launch_edge_flux_f32(edge_args(m, 32, m->w32), s);
+        EdgeArgs ea = edge_args(m, precision, precision == 64 ? (const void *)m->wn : (const void *)m->w32);
+        if (precision == 64) {
+            ea.Q = m->Q64[0];
+            launch_edge_flux_f64(ea, s);
+        } else {
+            launch_edge_flux_f32(ea, s);
+        }
     });
     DivArgs a = div_args(m, precision, 0);
     a.out = out;

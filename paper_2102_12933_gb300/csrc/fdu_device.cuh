@@ -44,6 +44,17 @@ __device__ __forceinline__ double recip64(double x) {
     return fma(y, e, y);
 }
 
+// One Newton-Raphson step from the hardware approximation: relative error
+// near 2^-44, ample for quotients whose error is damped by a small
+// multiplier (the nonlinear WENO weights: an error d omega moves the
+// interpolant by d omega (v_k - v), and v_k - v is O(h^3)).
+__device__ __forceinline__ double recip64_fast(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
 // Per-state quantities reused by the Roe average and the physical flux.
 struct Prim64 {
     double r;   // rho^-1/2
@@ -63,6 +74,31 @@ __device__ __forceinline__ Prim64 prim64(const dbl4 &w, double gm1) {
 struct Roe64 {
     double u, v, H, c, ic, b1, qn, qt, hq2, nx, ny;
 };
+// Roe-weighted record of a state: (s, s u, s v, s H) with s = sqrt(rho),
+// computed with the same operations roe64 applies to each side.
+__device__ __forceinline__ dbl4 roe_record64(const dbl4 &w, double gm1) {
+    const Prim64 p = prim64(w, gm1);
+    return dbl4_make(w.x * p.r, w.y * p.r, w.z * p.r, (w.w + p.p) * p.r);
+}
+// Roe average from the two sides' records (same result as roe64).
+__device__ __forceinline__ Roe64 roe64_from_records(const dbl4 &qa, const dbl4 &qb, double nx, double ny, double gm1) {
+    Roe64 R;
+    const double inv = recip64(qa.x + qb.x);
+    R.u = (qa.y + qb.y) * inv;
+    R.v = (qa.z + qb.z) * inv;
+    R.H = (qa.w + qb.w) * inv;
+    R.hq2 = 0.5 * (R.u * R.u + R.v * R.v);
+    const double c2 = gm1 * (R.H - R.hq2);
+    R.ic = rsqrt(c2);
+    R.c = c2 * R.ic;
+    R.b1 = gm1 * R.ic * R.ic;
+    R.nx = nx;
+    R.ny = ny;
+    R.qn = R.u * nx + R.v * ny;
+    R.qt = R.v * nx - R.u * ny;
+    return R;
+}
+
 __device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const dbl4 &b, const Prim64 &pb,
                                       double nx, double ny, double gm1) {
     Roe64 R;
@@ -120,10 +156,10 @@ __device__ __forceinline__ void weno_pair64(const double *k, double a, double b,
     const double bd = fma(pd, pd, fma(qd, qd, eps));
     const double bbc = bb * bc;
     const double l0 = k[24] * bbc, l1 = k[25] * (ba * bc), l2 = k[26] * (ba * bb);
-    dl = fma(l0, va, fma(l1, vb, l2 * vc)) * recip64(l0 + l1 + l2);
+    dl = fma(l0, va, fma(l1, vb, l2 * vc)) * recip64_fast(l0 + l1 + l2);
     const double r0 = k[27] * bbc, r1 = k[28] * (bd * bb), r2 = k[29] * (bd * bc);
     // right-side increments from R1: S_d's own, S_c's and S_b's shifted by -c
-    dr = fma(r0, vd, fma(r1, vc - c, r2 * (vb - c))) * recip64(r0 + r1 + r2);
+    dr = fma(r0, vd, fma(r1, vc - c, r2 * (vb - c))) * recip64_fast(r0 + r1 + r2);
 }
 
 

@@ -42,8 +42,10 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
     const double ny = __ldg(coef + (int64_t)31 * ne + e);
 
     // characteristic decomposition at the Roe average of the end states
-    const Prim64 pL1 = prim64(L1, gm1), pR1 = prim64(R1, gm1);
-    const Roe64 C = roe64(L1, pL1, R1, pR1, nx, ny, gm1);
+    // characteristic decomposition at the Roe average of the end states
+    // (per-vertex Roe records when the stage kernel provided them)
+    const Roe64 C = A.Q ? roe64_from_records(ld4(A.Q, s[2]), ld4(A.Q, s[3]), nx, ny, gm1)
+                        : roe64(L1, prim64(L1, gm1), R1, prim64(R1, gm1), nx, ny, gm1);
     const dbl4 cM = project64(C, sub4(R1, L1));               // R1 - L1
     const dbl4 cL2 = project64(C, sub4(ld4(w, s[1]), L1));    // L2 - L1
     const dbl4 cL3 = project64(C, sub4(ld4(w, s[0]), L1));    // L3 - L1
@@ -72,8 +74,8 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
     if (!ok) {  // positivity fallback: first-order end states
         wl = L1;
         wr = R1;
-        pl = pL1;
-        pr = pR1;
+        pl = prim64(L1, gm1);
+        pr = prim64(R1, gm1);
         atomicAdd(A.fallback, 1ull);
     }
 
@@ -105,14 +107,16 @@ __device__ __forceinline__ void euler_fg(const dbl4 &w, double gm1, dbl4 &f, dbl
     g = dbl4_make(w.z, w.y * v, fma(w.z, v, p), (w.w + p) * v);
 }
 
-__global__ void vertex_flux_f64_kernel(const double *__restrict__ w, double *__restrict__ F, int64_t n,
-                                       double gm1) {
+__global__ void vertex_flux_f64_kernel(const double *__restrict__ w, double *__restrict__ F, double *__restrict__ Q,
+                                       int64_t n, double gm1) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
+    const dbl4 s = ld4(w, v);
     dbl4 f, g;
-    euler_fg(ld4(w, v), gm1, f, g);
+    euler_fg(s, gm1, f, g);
     st4(F, 2 * v, f);
     st4(F, 2 * v + 1, g);
+    if (Q) st4(Q, v, roe_record64(s, gm1));
 }
 
 // Forward-Euler part of an SSP-RK3 stage, fe = ws + theta dt L.  Without
@@ -219,6 +223,7 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t v) 
     double *Fo = static_cast<double *>(A.Fout);
     st4(Fo, 2 * v, f);
     st4(Fo, 2 * v + 1, g);
+    if (A.Qout) st4(A.Qout, v, roe_record64(o, A.gm1));
 }
 
 // ================================================================== FP32 path
@@ -643,8 +648,8 @@ inline unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
 
-void launch_vertex_flux_f64(const double *w, double *F, int64_t n, double gamma, cudaStream_t s) {
-    if (n > 0) vertex_flux_f64_kernel<<<blocks(n, 256), 256, 0, s>>>(w, F, n, gamma - 1.0);
+void launch_vertex_flux_f64(const double *w, double *F, int64_t n, double gamma, cudaStream_t s, double *Q) {
+    if (n > 0) vertex_flux_f64_kernel<<<blocks(n, 256), 256, 0, s>>>(w, F, Q, n, gamma - 1.0);
 }
 void launch_vertex_flux_f32(const double *w, float4 *F, float4 *w32, int64_t n, double gamma, cudaStream_t s) {
     if (n > 0) vertex_flux_f32_kernel<<<blocks(n, 256), 256, 0, s>>>(w, F, w32, n, (float)(gamma - 1.0));

@@ -20,7 +20,8 @@ struct EdgeArgs {
     double gm1, eps;      // gamma - 1 and the WENO epsilon (FP64 path)
     float gm1f, epsf;     // the same for the FP32 path
     unsigned long long *fallback;
-    const double *dt_dev; // adaptive stepping: a zero time step here skips the launch  // edges that fell back to first order (device counter)
+    const double *dt_dev; // adaptive stepping: a zero time step here skips the launch
+    const double *Q;      // FP64: per-vertex Roe records of the stage state (nullptr = compute per edge)  // edges that fell back to first order (device counter)
 };
 
 // Divergence (+ optional SSP-RK3 stage) inputs.
@@ -43,6 +44,7 @@ struct DivArgs {
     const double *ws;            // [nv][4] stage input state
     double *wout;                // [nv][4] stage output state (may alias ws)
     void *Fout;                  // vertex fluxes of wout (same layout as F)
+    double *Qout;                // FP64: Roe records of wout (nullable)
     float4 *w32out;              // FP32 copy of wout (FP32 residual path), or nullptr
     double dt;
     const double *dt_dev;        // if non-null, dt is read here
@@ -54,7 +56,8 @@ struct DivArgs {
     unsigned long long *limited; // vertices whose stage update the safeguard scaled
 };
 
-void launch_vertex_flux_f64(const double *w, double *F, int64_t n, double gamma, cudaStream_t s);
+// F[v] = (f, g) of w[v]; Q (optional) = Roe records (sqrt rho, sqrt rho u, sqrt rho v, sqrt rho H)
+void launch_vertex_flux_f64(const double *w, double *F, int64_t n, double gamma, cudaStream_t s, double *Q = nullptr);
 void launch_vertex_flux_f32(const double *w, float4 *F, float4 *w32, int64_t n, double gamma, cudaStream_t s);
 void launch_edge_flux_f64(const EdgeArgs &a, cudaStream_t s);
 void launch_edge_flux_f32(const EdgeArgs &a, cudaStream_t s);

@@ -119,6 +119,34 @@ def _workload(n=N_LATTICE):
     return mesh, w0
 
 
+def vortex_config(n: int = N_LATTICE, parallelism: str = "single GPU") -> dict:
+    """The `config` of the default line (shared by both arms)."""
+    return {
+        "workload": f"periodic isentropic vortex (beta=5, centre (5,5)) on a {n}x{n} jittered random-diagonal "
+                    "torus lattice of [0,10]^2; two-level divergence stencils, degree-2 least squares, NU-WENO5, "
+                    "SSP-RK3, CFL 0.5; one step = 3 stages",
+        "nv": n * n, "ne": 3 * n * n, "stages_per_step": 3,
+        "l2": "inputs larger than L2 (FP64 tables 0.49 GB streamed per stage)",
+        "parallelism": parallelism,
+    }
+
+
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, world_size: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units / the max time."""
+    return world_size * units_per_rank / seconds
+
+
 def _rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
@@ -159,10 +187,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * el / max(args.steps, 1), 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "periodic isentropic vortex (beta=5, centre (5,5)) on a jittered random-diagonal "
-                               "torus lattice of [0,10]^2; two-level divergence stencils, degree-2 least squares, "
-                               "NU-WENO5, SSP-RK3, CFL 0.5; one step = 3 stages (oracle on a 125x125 sample)",
-                   "sample_nv": 15625},
+        "config": vortex_config(args.n, "replicas" if args.gpus > 1 else "single GPU"),
         "cpu_baseline": {"value": round(value, 4), "unit": "Mvertex/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "Mvertex/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -211,12 +236,7 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(ev0.elapsed_time(ev1), dist)
 
     # ---------------- FP64 (headline)
     for _ in range(args.warmup):
@@ -269,17 +289,13 @@ def run_ours(args):
         M.set_state(host_in)  # H2D of the step's input (host permutation to internal order)
         M.rk_step(dt, 64)
         M.get_state(out=host_out)  # D2H of the step's result (synchronises)
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
 
     # ---------------- figures
     stages = 3
-    value = ws_ * nv * stages * args.steps / (ms64 / 1e3) / 1e6
-    value32 = ws_ * nv * stages * (args.warmup + args.steps) / (ms32 / 1e3) / 1e6
-    e2e_value = ws_ * nv * stages * e2e_steps / e2e_s / 1e6
+    value = replica_throughput(nv * stages * args.steps, ws_, ms64 / 1e3) / 1e6
+    value32 = replica_throughput(nv * stages * (args.warmup + args.steps), ws_, ms32 / 1e3) / 1e6
+    e2e_value = replica_throughput(nv * stages * e2e_steps, ws_, e2e_s) / 1e6
     edge_avg_ms = edge_ms / max(edge_n, 1)
     div_avg_ms = div_ms / max(div_n, 1)
     achieved_tf = FLOP_EDGE64 * ne / (edge_avg_ms / 1e3) / 1e12
@@ -304,15 +320,9 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {
-            "workload": "periodic isentropic vortex (beta=5, centre (5,5)) on a 500x500 jittered random-diagonal "
-                        "torus lattice of [0,10]^2; two-level divergence stencils, degree-2 least squares, NU-WENO5, "
-                        "SSP-RK3, CFL 0.5; one step = 3 stages",
-            "nv": nv, "ne": ne, "stages_per_step": stages,
-            "l2": f"inputs larger than L2 (FP64 tables {info['table_bytes_f64'] / 1e9:.2f} GB streamed per stage)",
-            "parallelism": "replicas" if ws_ > 1 else "single GPU",
-            "host_build_s": round(t_build, 2),
-        },
+        "config": dict(vortex_config(args.n, "replicas" if ws_ > 1 else "single GPU"),
+                       l2=f"inputs larger than L2 (FP64 tables {info['table_bytes_f64'] / 1e9:.2f} GB streamed "
+                          "per stage)"),
         "roofline": {
             "kernel": "edge_flux_f64",
             "bound": "alu",

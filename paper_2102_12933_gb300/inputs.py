@@ -231,6 +231,13 @@ def riemann_case(n: int, ghost_layers: int = 5, seed: int = 1003, jitter: float 
     return mesh, w0
 
 
+def sod_case(n: int = 55, jitter: float = 0.0, random_diagonals: bool = False, seed: int = 1006):
+    """2D Sod problem of Section 3.2 on the periodic square [-1,1]^2 (n x n
+    lattice; 55 x 55 = 3025 points against the paper's 3058)."""
+    mesh = torus_lattice(n, L=2.0, jitter=jitter, seed=seed, random_diagonals=random_diagonals, origin=-1.0)
+    return mesh, sod_2d(mesh.xy)
+
+
 def batch_sizes(count: int = 64, lo: float = 5e3, hi: float = 2e5, seed: int = 2004):
     """Log-uniform mesh sizes, vortex strengths in [1,5], centres in [3,7]^2."""
     rng = np.random.default_rng(seed)

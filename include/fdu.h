@@ -87,6 +87,8 @@ typedef struct fdu_mesh_info {
     int64_t table_bytes_f32; /* bytes of the FP32 residual's read-only tables */
     int32_t sell_width;      /* SELL slice width of the divergence tables */
     int32_t pad0;
+    int64_t sell_vert_nnz;   /* vertex entries stored in the SELL tables, padding included (0 for host-only meshes) */
+    int64_t sell_edge_nnz;   /* edge entries stored in the SELL tables, padding included */
 } fdu_mesh_info;
 
 /* Library version string and thread-local last error message. */

@@ -681,6 +681,8 @@ fdu_status fdu_mesh_info_get(const fdu_mesh *m, fdu_mesh_info *out) {
     out->table_bytes_f64 = m->table_bytes_f64;
     out->table_bytes_f32 = m->table_bytes_f32;
     out->sell_width = kSell;
+    out->sell_vert_nnz = m->vert_nnz_sell;
+    out->sell_edge_nnz = m->edge_nnz_sell;
     return FDU_OK;
 }
 

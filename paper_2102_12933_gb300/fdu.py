@@ -61,6 +61,7 @@ class MeshInfo(C.Structure):
         ("J_min", C.c_int32), ("J_max", C.c_int32), ("K_min", C.c_int32), ("K_max", C.c_int32),
         ("device_bytes", C.c_int64), ("table_bytes_f64", C.c_int64), ("table_bytes_f32", C.c_int64),
         ("sell_width", C.c_int32), ("pad0", C.c_int32),
+        ("sell_vert_nnz", C.c_int64), ("sell_edge_nnz", C.c_int64),
     ]
 
     def as_dict(self):

@@ -60,8 +60,62 @@ def _dist():
     return ws, rank, local
 
 
+class _NvmlSampler:
+    """SM clock and clocks-event reasons polled through NVML (read-only queries)
+    every ~2 ms on a thread, so that a timed region of tens of milliseconds
+    still gets many samples.  The device is found by its UUID."""
+
+    # nvmlClocksEventReasons bits (public NVML API)
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, cuda_index):
+        import ctypes
+
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        import torch
+
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(cuda_index).uuid)
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("NVML handle lookup failed")
+        self.get_reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples = []
+        self.stop_flag = threading.Event()
+
+    def _clock(self, fn, kind):
+        v = self.ct.c_uint()
+        return v.value if fn(self.h, kind, self.ct.byref(v)) == 0 else None
+
+    def _run(self):
+        r = self.ct.c_ulonglong()
+        while not self.stop_flag.is_set():
+            sm = self._clock(self.lib.nvmlDeviceGetClockInfo, 1)  # NVML_CLOCK_SM
+            rs = r.value if self.get_reasons(self.h, self.ct.byref(r)) == 0 else 0
+            if sm is not None:
+                self.samples.append((sm, rs))
+            time.sleep(0.002)
+
+    def start(self):
+        self.smax = self._clock(self.lib.nvmlDeviceGetMaxClockInfo, 1)
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag.set()
+        self.thread.join(timeout=5)
+        reasons = sorted({n for n, b in self.BITS.items() for _, rs in self.samples if rs & b})
+        sm = [s for s, _ in self.samples]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.smax, "reasons": reasons,
+                "samples": len(sm), "source": "nvml"}
+
+
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    """Clock / throttle-reason samples during the timed region: NVML polled
+    every ~2 ms where libnvidia-ml loads, else nvidia-smi every 50 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -70,9 +124,16 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
+        self.nvml = None
         self.lines = []
 
     def start(self):
+        try:
+            self.nvml = _NvmlSampler(self.gpu)
+            self.nvml.start()
+            return
+        except Exception:
+            self.nvml = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -87,6 +148,8 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            return self.nvml.stop()
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -109,7 +172,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi"}
 
 
 def _workload(n=N_LATTICE):

@@ -227,9 +227,15 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t v) 
 }
 
 // ================================================================== FP32 path
-// The FP32 residual reads an FP32 copy of the state and compact edge
-// geometry (four outer curve coordinates and the normal) and builds the
-// NU-WENO5 coefficients in registers; weights, fluxes and sums are FP32.
+// The FP32 residual reads an FP32 copy of the state and an FP32 copy of the
+// edge coefficient block (eight float4 per edge); weights, fluxes and sums
+// are FP32.  Reciprocals use the hardware approximation (rcp.approx, about
+// one ulp), well inside the FP32 path's error against FP64.
+__device__ __forceinline__ float rcp32(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float4 sub4f(float4 a, float4 b) {
     return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
 }
@@ -254,7 +260,7 @@ __device__ __forceinline__ Roe32 roe32(const float4 &a, const Prim32 &pa, const 
                                       float ny, float gm1) {
     Roe32 R;
     const float sa = a.x * pa.r, sb = b.x * pb.r;
-    const float inv = __frcp_rn(sa + sb);
+    const float inv = rcp32(sa + sb);
     R.u = (a.y * pa.r + b.y * pb.r) * inv;
     R.v = (a.z * pa.r + b.z * pb.r) * inv;
     R.H = ((a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r) * inv;
@@ -291,14 +297,14 @@ __device__ __forceinline__ void weno_pair32(const float *k, float a, float b, fl
     const float vb = fmaf(k[6], b, k[7] * c), pb = fmaf(k[8], b, k[9] * c), qb = fmaf(k[10], b, k[11] * c);
     const float vc = fmaf(k[12], c, k[13] * d), pc = fmaf(k[14], c, k[15] * d), qc = fmaf(k[16], c, k[17] * d);
     const float vd = fmaf(k[18], e, k[19] * f), pd = fmaf(k[20], e, k[21] * f), qd = fmaf(k[22], e, k[23] * f);
-    const float ia = __frcp_rn(fmaf(pa, pa, fmaf(qa, qa, eps)));
-    const float ib = __frcp_rn(fmaf(pb, pb, fmaf(qb, qb, eps)));
-    const float ic = __frcp_rn(fmaf(pc, pc, fmaf(qc, qc, eps)));
-    const float id = __frcp_rn(fmaf(pd, pd, fmaf(qd, qd, eps)));
+    const float ia = rcp32(fmaf(pa, pa, fmaf(qa, qa, eps)));
+    const float ib = rcp32(fmaf(pb, pb, fmaf(qb, qb, eps)));
+    const float ic = rcp32(fmaf(pc, pc, fmaf(qc, qc, eps)));
+    const float id = rcp32(fmaf(pd, pd, fmaf(qd, qd, eps)));
     const float l0 = k[24] * ia, l1 = k[25] * ib, l2 = k[26] * ic;
-    dl = fmaf(l0, va, fmaf(l1, vb, l2 * vc)) * __frcp_rn(l0 + l1 + l2);
+    dl = fmaf(l0, va, fmaf(l1, vb, l2 * vc)) * rcp32(l0 + l1 + l2);
     const float r0 = k[27] * id, r1 = k[28] * ic, r2 = k[29] * ib;
-    dr = fmaf(r0, vd, fmaf(r1, vc - c, r2 * (vb - c))) * __frcp_rn(r0 + r1 + r2);
+    dr = fmaf(r0, vd, fmaf(r1, vc - c, r2 * (vb - c))) * rcp32(r0 + r1 + r2);
 }
 
 __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int64_t e) {
@@ -372,7 +378,7 @@ __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int6
 }
 
 __device__ __forceinline__ void euler_fg32(const float4 &w, float gm1, float4 &f, float4 &g) {
-    const float ir = __frcp_rn(w.x);
+    const float ir = rcp32(w.x);
     const float u = w.y * ir, v = w.z * ir;
     const float p = gm1 * (w.w - 0.5f * (w.y * u + w.z * v));
     f = make_float4(w.y, fmaf(w.y, u, p), w.z * u, (w.w + p) * u);

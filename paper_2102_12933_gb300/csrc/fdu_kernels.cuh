@@ -19,9 +19,9 @@ struct EdgeArgs {
     int64_t ne;
     double gm1, eps;      // gamma - 1 and the WENO epsilon (FP64 path)
     float gm1f, epsf;     // the same for the FP32 path
-    unsigned long long *fallback;
+    unsigned long long *fallback;  // edges that fell back to first order (device counter)
     const double *dt_dev; // adaptive stepping: a zero time step here skips the launch
-    const double *Q;      // FP64: per-vertex Roe records of the stage state (nullptr = compute per edge)  // edges that fell back to first order (device counter)
+    const double *Q;      // FP64: per-vertex Roe records of the stage state (nullptr = compute per edge)
 };
 
 // Divergence (+ optional SSP-RK3 stage) inputs.

@@ -203,7 +203,9 @@ fdu_status fdu_batch_set_dt(fdu_mesh *batch, const double *dt, void *stream);
  * wait ran out (the state is then not advanced past that stage). */
 fdu_status fdu_batch_rk_steps(fdu_mesh *batch, int precision, int n_steps, void *stream);
 /* Persistent launch shape: threads per block (128, 256 or 512) and
- * co-resident blocks per SM (1 .. occupancy limit). */
+ * co-resident blocks per SM (1 .. the larger of the FP32 and FP64 stage
+ * kernels' occupancy limits; a launch at a precision whose kernel fits fewer
+ * blocks per SM uses its own limit).  FDU_ERR_ARG outside these ranges. */
 fdu_status fdu_batch_set_launch(fdu_mesh *batch, int threads, int blocks_per_sm);
 /* Autotuner: times one RK3 step of the batch for every admissible launch
  * shape (threads 128/256/512 x blocks per SM 1..occupancy) on a copy of the

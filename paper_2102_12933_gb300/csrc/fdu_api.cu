@@ -1085,7 +1085,7 @@ fdu_status fdu_batch_set_launch(fdu_mesh *m, int threads, int blocks_per_sm) {
     if (threads != 128 && threads != 256 && threads != 512) return set_err(FDU_ERR_ARG, "threads must be 128, 256, 512");
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));
-    const int occ = std::min(persistent_blocks_per_sm(64, threads), persistent_blocks_per_sm(32, threads));
+    const int occ = std::max(persistent_blocks_per_sm(64, threads), persistent_blocks_per_sm(32, threads));
     if (blocks_per_sm < 1 || blocks_per_sm > occ)
         return set_err(FDU_ERR_ARG, "blocks_per_sm must be 1.." + std::to_string(occ) + " at " +
                                         std::to_string(threads) + " threads");

@@ -467,7 +467,7 @@ __device__ __forceinline__ void div_f32_body(const DivArgs &A, const int64_t v) 
     }
     {
         const int64_t b = __ldg(A.slice_eoff + sl) + lane, e = __ldg(A.slice_eoff + sl + 1);
-#pragma unroll 4
+#pragma unroll 8
         for (int64_t p = b; p < e; p += kSell) {
             const int32_t k = __ldg(A.eid + p);
             const float a = __ldg(we + p);

@@ -109,3 +109,42 @@ def test_barrier_timeout_is_reported_not_hung(batch):
     B.set_state(w0)
     B.batch_rk_steps(1, 64)
     assert np.array_equal(a, B.get_state())
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_launch_shape_does_not_change_results(batch, prec):
+    # every edge and vertex is computed independently of the grid-stride
+    # assignment, so any admissible launch shape gives the same bits
+    B, cases, w0 = batch
+    B.set_state(w0)
+    B.set_dt(B.batch_max_dt(0.5))
+    ref = None
+    shapes = ((128, 1), (256, 1), (512, 1), (128, 2)) if prec == 32 else ((128, 1), (256, 1), (128, 2), (128, 3))
+    for t, b in shapes:
+        B.set_launch(t, b)
+        B.set_state(w0)
+        B.batch_rk_steps(2, prec)
+        s = B.get_state()
+        if ref is None:
+            ref = s
+        assert np.array_equal(s, ref)
+
+
+def test_launch_shape_arguments_are_checked(batch):
+    B, cases, w0 = batch
+    for t, b in ((100, 1), (256, 0), (128, 1000)):
+        with pytest.raises(fdu.FduError):
+            B.set_launch(t, b)
+
+
+def test_shape_too_large_for_fp64_is_an_error_not_a_launch(batch):
+    # the FP64 stage kernel does not fit 512 threads per block: the step
+    # reports FDU_ERR_ARG before any launch and leaves the state untouched
+    B, cases, w0 = batch
+    B.set_state(w0)
+    B.set_dt(B.batch_max_dt(0.5))
+    B.set_launch(512, 1)
+    with pytest.raises(fdu.FduError):
+        B.batch_rk_steps(1, 64)
+    assert np.array_equal(B.get_state(), w0)
+    B.set_launch(128, 1)

@@ -288,6 +288,10 @@ fdu_status fdu_residual_noalloc(const fdu_mesh *mesh, const double *w, double *d
  * host arrays x[n] of positive normal doubles (Newton-Raphson refinement of
  * the hardware approximation); the tests compare it with IEEE division. */
 fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n);
+/* The same for the kernels' FP64 reciprocal square root (sound speeds and
+ * Roe weights): y[i] = 1/sqrt(x[i]) by Newton-Raphson refinement of the
+ * hardware approximation, for host arrays of positive normal doubles. */
+fdu_status fdu_check_rsqrt64(int device, const double *x, double *y, int64_t n);
 
 /* Measurement helper with no counterpart in the paper: the FMA throughput
  * (TFLOP/s, FMA = 2 flops) of `device` at precision 64 or 32, from a short

@@ -1376,7 +1376,7 @@ fdu_status fdu_adjoint_rk(fdu_mesh *m, double dt, int n_steps, int checkpoint_ev
     return from_internal(m, lam, grad, on_device, s);
 }
 
-fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n) {
+static fdu_status check_special(int device, const double *x, double *y, int64_t n, int which) {
     if (!x || !y || n < 0) return set_err(FDU_ERR_ARG, "bad arguments");
     if (n == 0) return FDU_OK;
     CK(cudaSetDevice(device));
@@ -1384,13 +1384,21 @@ fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n) 
     CK(cudaMalloc(&d, 2 * n * sizeof(double)));
     cudaError_t e = cudaMemcpy(d, x, n * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        launch_recip_check(d, d + n, n, nullptr);
+        launch_recip_check(d, d + n, n, which, nullptr);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(y, d + n, n * sizeof(double), cudaMemcpyDeviceToHost);
     cudaFree(d);
-    if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("reciprocal check: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("accuracy check: ") + cudaGetErrorString(e));
     return FDU_OK;
+}
+
+fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n) {
+    return check_special(device, x, y, n, 0);
+}
+
+fdu_status fdu_check_rsqrt64(int device, const double *x, double *y, int64_t n) {
+    return check_special(device, x, y, n, 1);
 }
 
 fdu_status fdu_probe_fma(int device, int precision, double *tflops) {

@@ -55,6 +55,21 @@ __device__ __forceinline__ double recip64_fast(double x) {
     return fma(y, e, y);
 }
 
+// 1/sqrt(x) of a positive normal double by Newton-Raphson iteration for the
+// reciprocal square root, y <- y (3 - x y^2) / 2 = y + y (1/2 - (x/2) y^2),
+// started from the hardware's approximate FP64 reciprocal square root (PTX
+// rsqrt.approx.ftz.f64); two iterations bring the relative error to the
+// rounding level (checked against a quad-precision reference by the tests).
+__device__ __forceinline__ double rsqrt64(double x) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double h = 0.5 * x;
+    double e = fma(-h, y * y, 0.5);
+    y = fma(y, e, y);
+    e = fma(-h, y * y, 0.5);
+    return fma(y, e, y);
+}
+
 // Per-state quantities reused by the Roe average and the physical flux.
 struct Prim64 {
     double r;   // rho^-1/2
@@ -63,7 +78,7 @@ struct Prim64 {
 };
 __device__ __forceinline__ Prim64 prim64(const dbl4 &w, double gm1) {
     Prim64 q;
-    q.r = rsqrt(w.x);
+    q.r = rsqrt64(w.x);
     q.ir = q.r * q.r;
     q.p = gm1 * (w.w - 0.5 * (w.y * w.y + w.z * w.z) * q.ir);
     return q;
@@ -73,6 +88,7 @@ __device__ __forceinline__ Prim64 prim64(const dbl4 &w, double gm1) {
 // of the flux Jacobian along n.
 struct Roe64 {
     double u, v, H, c, ic, b1, qn, qt, hq2, nx, ny;
+    double b1h, ich;  // b1 / 2 and ic / 2, the factors project64 applies
 };
 // Roe-weighted record of a state: (s, s u, s v, s H) with s = sqrt(rho),
 // computed with the same operations roe64 applies to each side.
@@ -89,9 +105,11 @@ __device__ __forceinline__ Roe64 roe64_from_records(const dbl4 &qa, const dbl4 &
     R.H = (qa.w + qb.w) * inv;
     R.hq2 = 0.5 * (R.u * R.u + R.v * R.v);
     const double c2 = gm1 * (R.H - R.hq2);
-    R.ic = rsqrt(c2);
+    R.ic = rsqrt64(c2);
     R.c = c2 * R.ic;
     R.b1 = gm1 * R.ic * R.ic;
+    R.b1h = 0.5 * R.b1;
+    R.ich = 0.5 * R.ic;
     R.nx = nx;
     R.ny = ny;
     R.qn = R.u * nx + R.v * ny;
@@ -109,9 +127,11 @@ __device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const db
     R.H = ((a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r) * inv;
     R.hq2 = 0.5 * (R.u * R.u + R.v * R.v);
     const double c2 = gm1 * (R.H - R.hq2);
-    R.ic = rsqrt(c2);
+    R.ic = rsqrt64(c2);
     R.c = c2 * R.ic;
     R.b1 = gm1 * R.ic * R.ic;
+    R.b1h = 0.5 * R.b1;
+    R.ich = 0.5 * R.ic;
     R.nx = nx;
     R.ny = ny;
     R.qn = R.u * nx + R.v * ny;
@@ -122,17 +142,20 @@ __device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const db
 // Characteristic components of a conservative difference (left eigenvectors
 // of dF_n/dw at the Roe state; fields ordered q_n - c, q_n (entropy), q_n
 // (shear), q_n + c).
+// phi/2 and psi/2 are formed directly (factors b1/2, ic/2), so the four
+// fields cost no separate halving.
 __device__ __forceinline__ dbl4 project64(const Roe64 &R, const dbl4 &d) {
-    const double phi = R.b1 * (R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w);
-    const double psi = (R.qn * d.x - R.nx * d.y - R.ny * d.z) * R.ic;
-    return dbl4_make(0.5 * (phi + psi), d.x - phi, R.nx * d.z - R.ny * d.y - R.qt * d.x, 0.5 * (phi - psi));
+    const double phh = R.b1h * (R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w);
+    const double psh = (R.qn * d.x - R.nx * d.y - R.ny * d.z) * R.ich;
+    return dbl4_make(phh + psh, fma(-2.0, phh, d.x), R.nx * d.z - R.ny * d.y - R.qt * d.x, phh - psh);
 }
 // Conservative difference from characteristic components (right eigenvectors).
 __device__ __forceinline__ dbl4 unproject64(const Roe64 &R, const dbl4 &c) {
-    const double rho = c.x + c.y + c.w;
+    const double ac = c.x + c.w;  // acoustic pair
+    const double rho = ac + c.y;
     const double dd = R.c * (c.w - c.x);
     return dbl4_make(rho, R.u * rho + R.nx * dd - R.ny * c.z, R.v * rho + R.ny * dd + R.nx * c.z,
-                        R.H * (c.x + c.w) + R.hq2 * c.y + R.qn * dd + R.qt * c.z);
+                        R.H * ac + R.hq2 * c.y + R.qn * dd + R.qt * c.z);
 }
 
 // NU-WENO5 increments of one characteristic field (Appendix), both sides.

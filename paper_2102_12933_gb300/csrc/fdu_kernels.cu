@@ -42,7 +42,6 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
     const double ny = __ldg(coef + (int64_t)31 * ne + e);
 
     // characteristic decomposition at the Roe average of the end states
-    // characteristic decomposition at the Roe average of the end states
     // (per-vertex Roe records when the stage kernel provided them)
     const Roe64 C = A.Q ? roe64_from_records(ld4(A.Q, s[2]), ld4(A.Q, s[3]), nx, ny, gm1)
                         : roe64(L1, prim64(L1, gm1), R1, prim64(R1, gm1), nx, ny, gm1);
@@ -645,9 +644,9 @@ __global__ void dt_finalize_kernel(unsigned long long *slot, double *tstate, dou
     *slot = 0x7FF0000000000000ull;
 }
 
-__global__ void recip_check_kernel(const double *x, double *y, int64_t n) {
+__global__ void recip_check_kernel(const double *x, double *y, int64_t n, int which) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = recip64(x[i]);
+    if (i < n) y[i] = which == 1 ? rsqrt64(x[i]) : recip64(x[i]);
 }
 
 inline unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -758,8 +757,8 @@ double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s) {
     return 2.0 * 8.0 * iters * (double)nb * nt / (ms * 1e-3) / 1e12;
 }
 
-void launch_recip_check(const double *x, double *y, int64_t n, cudaStream_t s) {
-    if (n > 0) recip_check_kernel<<<blocks(n, 256), 256, 0, s>>>(x, y, n);
+void launch_recip_check(const double *x, double *y, int64_t n, int which, cudaStream_t s) {
+    if (n > 0) recip_check_kernel<<<blocks(n, 256), 256, 0, s>>>(x, y, n, which);
 }
 
 void launch_dt_finalize(unsigned long long *slot, double *tstate, double cfl, double t_end,

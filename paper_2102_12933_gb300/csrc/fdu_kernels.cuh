@@ -69,8 +69,9 @@ void launch_ghost_fill(double *w, void *F, int fq, float4 *w32, const int32_t *d
 // FMA throughput (TFLOP/s) of `precision` 64 or 32 with sms*8 blocks of 256
 // threads; scratch holds sms*8*256 elements of that precision.
 double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s);
-// y[i] = the kernels' FP64 reciprocal of x[i] (device pointers; accuracy check)
-void launch_recip_check(const double *x, double *y, int64_t n, cudaStream_t s);
+// y[i] = the kernels' FP64 reciprocal (which = 0) or reciprocal square root
+// (which = 1) of x[i] (device pointers; accuracy check)
+void launch_recip_check(const double *x, double *y, int64_t n, int which, cudaStream_t s);
 // Adaptive step: dt = min(cfl * bound, t_end - t) from the reduced bound in
 // *slot (bit pattern of a positive double); tstate = (t, dt, nonphysical);
 // the slot is reset to +inf for the next reduction; *nsteps counts steps

@@ -33,7 +33,7 @@ EXPORTS = (
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
     "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
-    "fdu_check_recip64", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
+    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
     "fdu_batch_max_dt", "fdu_batch_set_dt", "fdu_batch_rk_steps", "fdu_batch_set_launch", "fdu_batch_autotune",
     "fdu_batch_barrier_selftest", "fdu_residual_vjp", "fdu_rk_step_vjp", "fdu_adjoint_rk",
 )
@@ -106,6 +106,7 @@ def load():
         L.fdu_probe_fma.argtypes = [C.c_int, C.c_int, dp]
         L.fdu_residual_noalloc.argtypes = [P, P, P, P]
         L.fdu_check_recip64.argtypes = [C.c_int, dp, dp, i64]
+        L.fdu_check_rsqrt64.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_advance.argtypes = [P, C.c_double, C.c_double, C.c_int, i64, lp, dp, P]
         L.fdu_limited_count.argtypes = [P, lp, C.c_int, P]
         L.fdu_batch_create.argtypes = [C.c_int32, C.POINTER(dp), lp, C.POINTER(ip), lp, C.POINTER(MeshOpts),
@@ -204,6 +205,14 @@ def check_recip64(x, device=0):
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.zeros_like(x)
     _check(load().fdu_check_recip64(int(device), _dp(x), _dp(y), x.size))
+    return y
+
+
+def check_rsqrt64(x, device=0):
+    """The kernels' FP64 reciprocal square root of x (accuracy check)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x)
+    _check(load().fdu_check_rsqrt64(int(device), _dp(x), _dp(y), x.size))
     return y
 
 

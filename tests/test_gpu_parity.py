@@ -207,3 +207,17 @@ def test_fast_reciprocal_within_two_ulp_of_ieee_division():
     want = 1.0 / x
     ulp = np.abs(y - want) / np.spacing(want)
     assert ulp.max() <= 2.0
+
+
+def test_fast_rsqrt_within_two_ulp_of_exact():
+    """The Newton-Raphson reciprocal square root used for sound speeds and
+    Roe weights, against 1/sqrt(x) in extended precision (np.longdouble:
+    80-bit on x86, IEEE quad on Arm), i.e. the correctly rounded value."""
+    rng = np.random.default_rng(4)
+    x = np.concatenate([10.0 ** rng.uniform(-150, 150, 200000), rng.uniform(0.25, 4.0, 100000),
+                        np.array([1.0, 2.0, 4.0, 0.5, 1e-300, 1e300, np.nextafter(1.0, 2.0), np.nextafter(4.0, 0.0)])])
+    y = fdu.check_rsqrt64(x)
+    xl = x.astype(np.longdouble)
+    want = (1 / np.sqrt(xl)).astype(np.float64)
+    ulp = np.abs(y - want) / np.spacing(want)
+    assert ulp.max() <= 2.0

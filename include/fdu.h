@@ -77,7 +77,7 @@ typedef struct fdu_mesh_opts {
 typedef struct fdu_mesh fdu_mesh;
 
 typedef struct fdu_mesh_info {
-    int64_t nv, ne, nt;      /* vertices, edges, triangles */
+    int64_t nv, ne, nt;      /* vertices, edges, cells (triangles for fdu_mesh_create) */
     int64_t n_real;          /* vertices that carry a residual (non-ghost) */
     int64_t div_vert_nnz;    /* vertex entries over all divergence stencils */
     int64_t div_edge_nnz;    /* edge entries over all divergence stencils */
@@ -109,6 +109,26 @@ fdu_status fdu_default_opts(fdu_mesh_opts *opts);
  * FDU_ERR_RANK_DEFICIENT, FDU_ERR_CUDA.  On error *out is NULL. */
 fdu_status fdu_mesh_create(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts *opts,
                            fdu_mesh **out);
+
+/* The same from a hybrid mesh of triangles and quadrilaterals (Section
+ * 2.2.2, Figs. l1-hyb and l1-tria4): cell c has the vertices
+ * cell_vtx[cell_off[c] .. cell_off[c+1]-1] (3 or 4 of them, counter-
+ * clockwise, convex), cell_off[0] = 0.  The edges are the cell sides plus,
+ * by `artificial_edges`:
+ *   0  none;
+ *   1  both diagonals of every quadrilateral (the dashed edge of Fig. l1-hyb);
+ *   2  as 1, and at every vertex O whose one-level stencil gives fewer than
+ *      p(p+3) least-squares conditions (2 per neighbour, 1 per edge at O or
+ *      between two neighbours; p = lsq_degree) an edge from O to the far
+ *      apex of each triangle across the side of O's triangles opposite O,
+ *      when that apex is not yet a neighbour (the dashed edges of Fig.
+ *      l1-tria4).
+ * Artificial edges are ordinary edges afterwards: they get 1D stencils and
+ * fluxes and enter the divergence stencils.  Errors as fdu_mesh_create;
+ * FDU_ERR_MESH for a cell of another size, a repeated vertex or a clockwise
+ * or non-convex cell. */
+fdu_status fdu_mesh_create_cells(const double *xy, int64_t nv, const int64_t *cell_off, const int32_t *cell_vtx,
+                                 int64_t ncells, int artificial_edges, const fdu_mesh_opts *opts, fdu_mesh **out);
 
 /* Free the mesh and its device memory (synchronises the device first). */
 fdu_status fdu_mesh_destroy(fdu_mesh *mesh);

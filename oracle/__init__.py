@@ -54,6 +54,9 @@ def lib():
             L.om_create.argtypes = [dp, i64, ip, i64, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, ip,
                                     C.POINTER(P)]
             L.om_create.restype = C.c_int
+            L.om_create_cells.argtypes = [dp, i64, lp, ip, i64, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                          C.c_double, ip, C.POINTER(P)]
+            L.om_create_cells.restype = C.c_int
             L.om_destroy.argtypes = [P]
             L.om_num_edges.argtypes = [P]
             L.om_num_edges.restype = i64
@@ -195,9 +198,16 @@ def stage_combine(stage, wn, ws, L, dt):
 class OracleMesh:
     """Oracle mesh: edges, 1D stencils, divergence stencils, LSQ weights."""
 
-    def __init__(self, xy, tri, Lx=0.0, Ly=0.0, degree=2, levels=2, gamma=GAMMA, ghost=None):
+    def __init__(self, xy, tri, Lx=0.0, Ly=0.0, degree=2, levels=2, gamma=GAMMA, ghost=None, artificial=None):
+        """`tri`: (nt, 3) triangles, or a pair (cell_off, cell_vtx) of
+        triangles and quadrilaterals; then `artificial` (0, 1, 2; default 1)
+        selects the artificial edges (Section 2.2.2)."""
         xy = _f64(xy, (-1, 2))
-        tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+        cells = None
+        if isinstance(tri, tuple):
+            cells = (np.ascontiguousarray(tri[0], dtype=np.int64), np.ascontiguousarray(tri[1], dtype=np.int32))
+        else:
+            tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
         self.nv = xy.shape[0]
         self.gamma = gamma
         gp = None
@@ -206,8 +216,14 @@ class OracleMesh:
             self._ghost = np.ascontiguousarray(ghost, dtype=np.int32).reshape(self.nv)
             gp = _i(self._ghost)
         h = C.c_void_p()
-        _check(lib().om_create(_d(xy), self.nv, _i(tri), tri.shape[0], float(Lx), float(Ly), int(degree),
-                               int(levels), float(gamma), gp, C.byref(h)))
+        if cells is not None:
+            off, vtx = cells
+            _check(lib().om_create_cells(_d(xy), self.nv, off.ctypes.data_as(C.POINTER(C.c_int64)), _i(vtx),
+                                         off.shape[0] - 1, 1 if artificial is None else int(artificial), float(Lx),
+                                         float(Ly), int(degree), int(levels), float(gamma), gp, C.byref(h)))
+        else:
+            _check(lib().om_create(_d(xy), self.nv, _i(tri), tri.shape[0], float(Lx), float(Ly), int(degree),
+                                   int(levels), float(gamma), gp, C.byref(h)))
         self._h = h
         self.ne = int(lib().om_num_edges(h))
 

@@ -738,39 +738,160 @@ void om_destroy(om_mesh *m) {
  * mesh every edge must have a 1D stencil.  On an open mesh, edges whose
  * walk runs into the boundary are marked with sten = -1; a residual that
  * needs such an edge fails with OM_ERR_STENCIL. */
+/* Sorted unique (min id, max id) pairs, in place; returns the count. */
+static int64_t unique_pairs(int32_t *pairs, int64_t n) {
+    qsort(pairs, n, 2 * sizeof(int32_t), cmp_pair);
+    int64_t ne = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (ne == 0 || cmp_pair(pairs + 2 * i, pairs + 2 * (ne - 1)) != 0) {
+            pairs[2 * ne] = pairs[2 * i];
+            pairs[2 * ne + 1] = pairs[2 * i + 1];
+            ++ne;
+        }
+    return ne;
+}
+
+static int has_pair(const int32_t *pairs, int64_t n, int32_t a, int32_t b) {
+    int32_t key[2] = {a < b ? a : b, a < b ? b : a};
+    return bsearch(key, pairs, n, 2 * sizeof(int32_t), cmp_pair) != NULL;
+}
+
+static int cell_has(const int32_t *v, int64_t n, int32_t x) {
+    for (int64_t i = 0; i < n; ++i)
+        if (v[i] == x) return 1;
+    return 0;
+}
+
+/* Reading of Section 2.2.2 (Figs. l1-hyb, l1-tria4): artificial edges.
+ * Mode 1: both diagonals of every quadrilateral cell.  Mode 2: also, for
+ * each vertex O whose one-level stencil counts fewer than p(p+3)
+ * conditions (two per neighbour, one per edge at O, one per edge joining
+ * two neighbours), an edge from O to the third vertex X of every triangle
+ * that shares the side opposite O of one of O's triangles, unless X is
+ * already a neighbour.  The candidates are found by scanning all cells
+ * (slow and plain).  Returns the new pair array (caller frees) and count. */
+static int32_t *artificial_pairs(int64_t nv, const int64_t *off, const int32_t *vtx, int64_t nc, int mode,
+                                 int degree, int32_t *pairs, int64_t *np) {
+    int64_t n = *np;
+    if (mode >= 1) {
+        int64_t nq = 0;
+        for (int64_t c = 0; c < nc; ++c) nq += (off[c + 1] - off[c] == 4);
+        pairs = (int32_t *)realloc(pairs, (n + 2 * nq) * 2 * sizeof(int32_t));
+        for (int64_t c = 0; c < nc; ++c) {
+            if (off[c + 1] - off[c] != 4) continue;
+            const int32_t *v = vtx + off[c];
+            for (int d = 0; d < 2; ++d) {
+                int32_t a = v[d], b = v[d + 2];
+                pairs[2 * n] = a < b ? a : b;
+                pairs[2 * n + 1] = a < b ? b : a;
+                ++n;
+            }
+        }
+        n = unique_pairs(pairs, n);
+    }
+    if (mode >= 2) {
+        const int64_t base = n;
+        const int64_t need = (int64_t)degree * (degree + 3);
+        for (int32_t o = 0; o < nv; ++o) {
+            /* neighbours of o from the pair list */
+            int64_t deg = 0, between = 0;
+            int32_t *nb = (int32_t *)malloc(base * sizeof(int32_t));
+            for (int64_t k = 0; k < base; ++k) {
+                if (pairs[2 * k] == o) nb[deg++] = pairs[2 * k + 1];
+                else if (pairs[2 * k + 1] == o) nb[deg++] = pairs[2 * k];
+            }
+            for (int64_t i = 0; i < deg; ++i)
+                for (int64_t j = i + 1; j < deg; ++j) between += has_pair(pairs, base, nb[i], nb[j]);
+            free(nb);
+            if (2 * deg + deg + between >= need) continue;
+            for (int64_t c = 0; c < nc; ++c) {
+                if (off[c + 1] - off[c] != 3 || !cell_has(vtx + off[c], 3, o)) continue;
+                const int32_t *v = vtx + off[c];
+                int32_t A = -1, B = -1; /* the side opposite o */
+                for (int i = 0; i < 3; ++i)
+                    if (v[i] != o) {
+                        if (A < 0) A = v[i];
+                        else B = v[i];
+                    }
+                for (int64_t c2 = 0; c2 < nc; ++c2) {
+                    if (c2 == c || off[c2 + 1] - off[c2] != 3) continue;
+                    const int32_t *u = vtx + off[c2];
+                    if (!cell_has(u, 3, A) || !cell_has(u, 3, B) || cell_has(u, 3, o)) continue;
+                    int32_t X = -1;
+                    for (int i = 0; i < 3; ++i)
+                        if (u[i] != A && u[i] != B) X = u[i];
+                    if (X < 0 || has_pair(pairs, base, o, X)) continue;
+                    pairs = (int32_t *)realloc(pairs, (n + 1) * 2 * sizeof(int32_t));
+                    pairs[2 * n] = o < X ? o : X;
+                    pairs[2 * n + 1] = o < X ? X : o;
+                    ++n;
+                }
+            }
+        }
+        n = unique_pairs(pairs, n);
+    }
+    *np = n;
+    return pairs;
+}
+
+static int finish_mesh(om_mesh *m, int32_t *pairs, int64_t ne, om_mesh **out);
+int om_create_cells(const double *xy, int64_t nv, const int64_t *off, const int32_t *vtx, int64_t nc, int artificial,
+                    double Lx, double Ly, int degree, int levels, double gamma, const int32_t *ghost, om_mesh **out);
+
 int om_create(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, double Lx, double Ly, int degree,
               int levels, double gamma, const int32_t *ghost, om_mesh **out) {
-    if (!xy || !tri || nv < 3 || nt < 1 || degree < 1 || degree > 6 || levels < 1 || levels > 2 || !out)
+    if (!tri || nt < 1) return fail(OM_ERR_ARG, "bad argument");
+    int64_t *off = (int64_t *)malloc((nt + 1) * sizeof(int64_t));
+    for (int64_t t = 0; t <= nt; ++t) off[t] = 3 * t;
+    int r = om_create_cells(xy, nv, off, tri, nt, 0, Lx, Ly, degree, levels, gamma, ghost, out);
+    free(off);
+    return r;
+}
+
+int om_create_cells(const double *xy, int64_t nv, const int64_t *off, const int32_t *vtx, int64_t nc, int artificial,
+                    double Lx, double Ly, int degree, int levels, double gamma, const int32_t *ghost, om_mesh **out) {
+    if (!xy || !off || !vtx || nv < 3 || nc < 1 || degree < 1 || degree > 6 || levels < 1 || levels > 2 || !out ||
+        artificial < 0 || artificial > 2)
         return fail(OM_ERR_ARG, "bad argument");
     om_mesh *m = (om_mesh *)calloc(1, sizeof(om_mesh));
-    m->nv = nv; m->nt = nt; m->Lx = Lx; m->Ly = Ly; m->gamma = gamma; m->degree = degree; m->levels = levels;
+    m->nv = nv; m->nt = nc; m->Lx = Lx; m->Ly = Ly; m->gamma = gamma; m->degree = degree; m->levels = levels;
     m->xy = (double *)malloc(nv * 2 * sizeof(double));
     memcpy(m->xy, xy, nv * 2 * sizeof(double));
     if (ghost) {
         m->ghost = (int32_t *)malloc(nv * sizeof(int32_t));
         memcpy(m->ghost, ghost, nv * sizeof(int32_t));
     }
-    /* edges: unique undirected triangle sides, (min id, max id), sorted */
-    int32_t *pairs = (int32_t *)malloc(nt * 6 * sizeof(int32_t));
-    for (int64_t t = 0; t < nt; ++t)
-        for (int s = 0; s < 3; ++s) {
-            int32_t a = tri[3 * t + s], b = tri[3 * t + (s + 1) % 3];
+    /* edges: unique undirected cell sides, (min id, max id), sorted */
+    int64_t nside = off[nc];
+    int32_t *pairs = (int32_t *)malloc((nside > 0 ? nside : 1) * 2 * sizeof(int32_t));
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t k = off[c + 1] - off[c];
+        if (k != 3 && k != 4) {
+            free(pairs);
+            om_destroy(m);
+            return fail(OM_ERR_MESH, "cell with other than 3 or 4 vertices");
+        }
+        for (int64_t s = 0; s < k; ++s) {
+            int32_t a = vtx[off[c] + s], b = vtx[off[c] + (s + 1) % k];
             if (a < 0 || a >= nv || b < 0 || b >= nv || a == b) {
                 free(pairs);
                 om_destroy(m);
-                return fail(OM_ERR_MESH, "triangle with a bad vertex id");
+                return fail(OM_ERR_MESH, "cell with a bad vertex id");
             }
-            pairs[6 * t + 2 * s] = a < b ? a : b;
-            pairs[6 * t + 2 * s + 1] = a < b ? b : a;
+            pairs[2 * (off[c] + s)] = a < b ? a : b;
+            pairs[2 * (off[c] + s) + 1] = a < b ? b : a;
         }
-    qsort(pairs, nt * 3, 2 * sizeof(int32_t), cmp_pair);
-    int64_t ne = 0;
-    for (int64_t i = 0; i < nt * 3; ++i)
-        if (ne == 0 || cmp_pair(pairs + 2 * i, pairs + 2 * (ne - 1)) != 0) {
-            pairs[2 * ne] = pairs[2 * i];
-            pairs[2 * ne + 1] = pairs[2 * i + 1];
-            ++ne;
-        }
+    }
+    int64_t ne = unique_pairs(pairs, nside);
+    pairs = artificial_pairs(nv, off, vtx, nc, artificial, degree, pairs, &ne);
+    return finish_mesh(m, pairs, ne, out);
+}
+
+/* Adjacency, edge geometry, 1D stencils and divergence stencils from the
+ * sorted unique edge pairs (takes ownership of `pairs`). */
+static int finish_mesh(om_mesh *m, int32_t *pairs, int64_t ne, om_mesh **out) {
+    const int64_t nv = m->nv;
+    const double Lx = m->Lx, Ly = m->Ly;
     m->ne = ne;
     m->edge = (int32_t *)malloc(ne * 2 * sizeof(int32_t));
     memcpy(m->edge, pairs, ne * 2 * sizeof(int32_t));

@@ -603,11 +603,12 @@ fdu_status fdu_default_opts(fdu_mesh_opts *o) {
     return FDU_OK;
 }
 
-fdu_status fdu_mesh_create(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts *opts,
-                           fdu_mesh **out) {
+static fdu_status mesh_create(const double *xy, int64_t nv, const CellList &cells, int artificial,
+                              const fdu_mesh_opts *opts, fdu_mesh **out) {
     if (out) *out = nullptr;
-    if (!xy || !tri || !opts || !out) return set_err(FDU_ERR_ARG, "null argument");
-    if (nv < 3 || nt < 1 || nv > INT32_MAX / 2) return set_err(FDU_ERR_ARG, "bad vertex or triangle count");
+    if (!xy || !cells.off || !cells.vtx || !opts || !out) return set_err(FDU_ERR_ARG, "null argument");
+    if (nv < 3 || cells.n < 1 || nv > INT32_MAX / 2) return set_err(FDU_ERR_ARG, "bad vertex or cell count");
+    if (artificial < 0 || artificial > 2) return set_err(FDU_ERR_ARG, "artificial_edges must be 0, 1 or 2");
     if (opts->lsq_degree < 1 || opts->lsq_degree > 6 || opts->lsq_levels < 1 || opts->lsq_levels > 2)
         return set_err(FDU_ERR_ARG, "lsq_degree must be 1..6 and lsq_levels 1..2");
     if (!(opts->positivity_alpha >= 0.0 && opts->positivity_alpha < 1.0))
@@ -623,7 +624,7 @@ fdu_status fdu_mesh_create(const double *xy, int64_t nv, const int32_t *tri, int
     m->opts = *opts;
     m->opts.ghost_donor = nullptr;
     std::string err;
-    int st = build_host_tables(xy, nv, tri, nt, *opts, m->T, err);
+    int st = build_host_tables(xy, nv, cells, artificial, *opts, m->T, err);
     if (st != FDU_OK) {
         delete m;
         return set_err(st, err);
@@ -650,6 +651,26 @@ fdu_status fdu_mesh_create(const double *xy, int64_t nv, const int32_t *tri, int
     }
     *out = m;
     return FDU_OK;
+}
+
+fdu_status fdu_mesh_create(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts *opts,
+                           fdu_mesh **out) {
+    if (out) *out = nullptr;
+    if (!tri) return set_err(FDU_ERR_ARG, "null argument");
+    if (nt < 1) return set_err(FDU_ERR_ARG, "bad vertex or triangle count");
+    std::vector<int64_t> off(nt + 1);
+    for (int64_t t = 0; t <= nt; ++t) off[t] = 3 * t;
+    return mesh_create(xy, nv, CellList{off.data(), tri, nt}, 0, opts, out);
+}
+
+fdu_status fdu_mesh_create_cells(const double *xy, int64_t nv, const int64_t *cell_off, const int32_t *cell_vtx,
+                                 int64_t ncells, int artificial_edges, const fdu_mesh_opts *opts, fdu_mesh **out) {
+    if (out) *out = nullptr;
+    if (!cell_off || !cell_vtx || ncells < 1) return set_err(FDU_ERR_ARG, "null argument or no cells");
+    if (cell_off[0] != 0) return set_err(FDU_ERR_ARG, "cell_off[0] must be 0");
+    for (int64_t c = 0; c < ncells; ++c)
+        if (cell_off[c + 1] < cell_off[c]) return set_err(FDU_ERR_ARG, "cell_off must be non-decreasing");
+    return mesh_create(xy, nv, CellList{cell_off, cell_vtx, ncells}, artificial_edges, opts, out);
 }
 
 fdu_status fdu_mesh_destroy(fdu_mesh *m) {
@@ -1337,29 +1358,43 @@ fdu_status fdu_adjoint_rk(fdu_mesh *m, double dt, int n_steps, int checkpoint_ev
     }
     double *const *ck = m->adj_states.data();          // checkpoints [nseg]
     double *const *stp = m->adj_states.data() + nseg;  // stage states of one segment [K][3]
-    // forward pass from the current state w0, keeping a checkpoint every K steps
+    // steps i0..i1-1 from the current state, keeping every stage input of
+    // the segment (the last step's third stage is not needed)
+    auto segment_states = [&](int i0, int i1) -> cudaError_t {
+        for (int i = i0; i < i1; ++i) {
+            double *const *S = stp + 3 * (i - i0);
+            cudaError_t e = cudaMemcpyAsync(S[0], m->wn, bytes, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+            ensure_fluxes(m, 64, s);
+            enqueue_stages(m, 64, dt, nullptr, s, false, 1, 1);
+            if ((e = cudaMemcpyAsync(S[1], m->ws, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+            enqueue_stages(m, 64, dt, nullptr, s, false, 2, 2);
+            if ((e = cudaMemcpyAsync(S[2], m->ws, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+            if (i + 1 < i1) enqueue_stages(m, 64, dt, nullptr, s, false, 3, 3);
+        }
+        return cudaSuccess;
+    };
+    // forward pass from the current state w0, keeping a checkpoint every K
+    // steps; the last segment keeps its stage inputs at once, so the reverse
+    // pass recomputes only the segments before it
+    const int last0 = (nseg - 1) * K;
     ensure_fluxes(m, 64, s);
-    for (int i = 0; i < n_steps; ++i) {
+    for (int i = 0; i < last0; ++i) {
         if (i % K == 0) CK(cudaMemcpyAsync(ck[i / K], m->wn, bytes, cudaMemcpyDeviceToDevice, s));
         enqueue_step(m, 64, dt, nullptr, s, false);
     }
+    CK(cudaMemcpyAsync(ck[nseg - 1], m->wn, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(segment_states(last0, n_steps));
     CK_LAUNCH();
-    // reverse pass, segment by segment, recomputing each segment's step states
+    // reverse pass, segment by segment
     double *lam = m->adj_buf[0], *lam_prev = m->adj_buf[1];
     if ((st = to_internal(m, lam_final, on_device, lam, s))) return st;
     for (int seg = nseg - 1; seg >= 0; --seg) {
         const int i0 = seg * K, i1 = std::min(n_steps, i0 + K);
-        CK(cudaMemcpyAsync(m->wn, ck[seg], bytes, cudaMemcpyDeviceToDevice, s));
-        m->f64_valid = false;
-        for (int i = i0; i < i1; ++i) {  // recompute the segment, keeping every stage input
-            double *const *S = stp + 3 * (i - i0);
-            CK(cudaMemcpyAsync(S[0], m->wn, bytes, cudaMemcpyDeviceToDevice, s));
-            ensure_fluxes(m, 64, s);
-            enqueue_stages(m, 64, dt, nullptr, s, false, 1, 1);
-            CK(cudaMemcpyAsync(S[1], m->ws, bytes, cudaMemcpyDeviceToDevice, s));
-            enqueue_stages(m, 64, dt, nullptr, s, false, 2, 2);
-            CK(cudaMemcpyAsync(S[2], m->ws, bytes, cudaMemcpyDeviceToDevice, s));
-            if (i + 1 < i1) enqueue_stages(m, 64, dt, nullptr, s, false, 3, 3);
+        if (seg < nseg - 1) {  // recompute the segment from its checkpoint
+            CK(cudaMemcpyAsync(m->wn, ck[seg], bytes, cudaMemcpyDeviceToDevice, s));
+            m->f64_valid = false;
+            CK(segment_states(i0, i1));
         }
         for (int i = i1 - 1; i >= i0; --i) {
             double *const *S = stp + 3 * (i - i0);

@@ -40,33 +40,102 @@ struct Geo {
 };
 
 // ---------------------------------------------------------------- edges
-int build_edges(const int32_t *tri, int64_t nt, int64_t nv, const Geo &g, HostTables &T, std::string &err) {
-    std::vector<uint64_t> keys;
-    keys.reserve(3 * nt);
-    for (int64_t t = 0; t < nt; ++t) {
-        int32_t v[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
-        for (int s = 0; s < 3; ++s)
-            if (v[s] < 0 || v[s] >= nv) {
-                err = "triangle " + std::to_string(t) + " has a vertex id out of range";
-                return FDU_ERR_MESH;
-            }
-        if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) {
-            err = "triangle " + std::to_string(t) + " repeats a vertex";
-            return FDU_ERR_MESH;
-        }
-        double a[2], b[2];
-        g.d(v[0], v[1], a);
-        g.d(v[0], v[2], b);
-        if (!(a[0] * b[1] - a[1] * b[0] > 0)) {
-            err = "triangle " + std::to_string(t) + " is degenerate or clockwise";
-            return FDU_ERR_MESH;
-        }
-        for (int s = 0; s < 3; ++s) {
-            uint32_t p = (uint32_t)v[s], q = (uint32_t)v[(s + 1) % 3];
-            if (p > q) std::swap(p, q);
-            keys.push_back(((uint64_t)p << 32) | q);
+inline uint64_t edge_key(int32_t a, int32_t b) {
+    uint32_t p = (uint32_t)a, q = (uint32_t)b;
+    if (p > q) std::swap(p, q);
+    return ((uint64_t)p << 32) | q;
+}
+
+// Artificial edges for vertices short of least-squares conditions (Section
+// 2.2.2, Fig. l1-tria4): a vertex O whose one-level stencil gives fewer than
+// p(p+3) conditions (2 per neighbour, 1 per edge at O or between two
+// neighbours) is joined to the far apex X of each triangle across the side
+// of O's triangles opposite O, when X is not yet a neighbour.
+void far_apex_edges(const CellList &cells, int64_t nv, int degree, std::vector<uint64_t> &keys) {
+    std::vector<std::vector<int32_t>> nb(nv);
+    for (uint64_t k : keys) {
+        const int32_t a = (int32_t)(k >> 32), b = (int32_t)(k & 0xffffffffu);
+        nb[a].push_back(b);
+        nb[b].push_back(a);
+    }
+    for (auto &l : nb) std::sort(l.begin(), l.end());
+    auto adjacent = [&](int32_t a, int32_t b) { return std::binary_search(nb[a].begin(), nb[a].end(), b); };
+    // triangles by side, and by vertex
+    std::vector<std::pair<uint64_t, int32_t>> side_apex;  // (side key, apex)
+    std::vector<std::vector<int64_t>> tri_of(nv);
+    for (int64_t c = 0; c < cells.n; ++c) {
+        if (cells.off[c + 1] - cells.off[c] != 3) continue;
+        const int32_t *v = cells.vtx + cells.off[c];
+        for (int i = 0; i < 3; ++i) {
+            side_apex.push_back({edge_key(v[i], v[(i + 1) % 3]), v[(i + 2) % 3]});
+            tri_of[v[i]].push_back(c);
         }
     }
+    std::sort(side_apex.begin(), side_apex.end());
+    const int64_t need = (int64_t)degree * (degree + 3);
+    std::vector<uint64_t> extra;
+    for (int32_t o = 0; o < (int32_t)nv; ++o) {
+        const auto &N = nb[o];
+        int64_t between = 0;
+        for (size_t i = 0; i < N.size(); ++i)
+            for (size_t j = i + 1; j < N.size(); ++j) between += adjacent(N[i], N[j]);
+        const int64_t conditions = 2 * (int64_t)N.size() + (int64_t)N.size() + between;
+        if (conditions >= need) continue;
+        for (int64_t c : tri_of[o]) {
+            const int32_t *v = cells.vtx + cells.off[c];
+            const int i = v[0] == o ? 0 : (v[1] == o ? 1 : 2);
+            const int32_t A = v[(i + 1) % 3], B = v[(i + 2) % 3];
+            const uint64_t key = edge_key(A, B);
+            auto it = std::lower_bound(side_apex.begin(), side_apex.end(), std::make_pair(key, INT32_MIN));
+            for (; it != side_apex.end() && it->first == key; ++it) {
+                const int32_t X = it->second;
+                if (X != o && !adjacent(o, X)) extra.push_back(edge_key(o, X));
+            }
+        }
+    }
+    keys.insert(keys.end(), extra.begin(), extra.end());
+}
+
+int build_edges(const CellList &cells, int artificial, int degree, int64_t nv, const Geo &g, HostTables &T,
+                std::string &err) {
+    std::vector<uint64_t> keys;
+    keys.reserve(4 * cells.n);
+    for (int64_t t = 0; t < cells.n; ++t) {
+        const int64_t nc = cells.off[t + 1] - cells.off[t];
+        if (nc != 3 && nc != 4) {
+            err = "cell " + std::to_string(t) + " has " + std::to_string(nc) + " vertices (3 or 4 expected)";
+            return FDU_ERR_MESH;
+        }
+        const int32_t *v = cells.vtx + cells.off[t];
+        for (int s = 0; s < nc; ++s)
+            if (v[s] < 0 || v[s] >= nv) {
+                err = "cell " + std::to_string(t) + " has a vertex id out of range";
+                return FDU_ERR_MESH;
+            }
+        for (int s = 0; s < nc; ++s)
+            for (int r = s + 1; r < nc; ++r)
+                if (v[s] == v[r]) {
+                    err = "cell " + std::to_string(t) + " repeats a vertex";
+                    return FDU_ERR_MESH;
+                }
+        for (int s = 0; s < nc; ++s) {  // every corner turns left: convex and counter-clockwise
+            double a[2], b[2];
+            g.d(v[s], v[(s + 1) % nc], a);
+            g.d(v[s], v[(s + nc - 1) % nc], b);
+            if (!(a[0] * b[1] - a[1] * b[0] > 0)) {
+                err = (nc == 3 ? "triangle " : "cell ") + std::to_string(t) + " is degenerate, clockwise or not convex";
+                return FDU_ERR_MESH;
+            }
+        }
+        for (int s = 0; s < nc; ++s) keys.push_back(edge_key(v[s], v[(s + 1) % nc]));
+        if (nc == 4 && artificial >= 1) {  // artificial quad diagonals (Fig. l1-hyb)
+            keys.push_back(edge_key(v[0], v[2]));
+            keys.push_back(edge_key(v[1], v[3]));
+        }
+    }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    if (artificial >= 2) far_apex_edges(cells, nv, degree, keys);
     std::sort(keys.begin(), keys.end());
     keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
     T.ne = (int64_t)keys.size();
@@ -489,8 +558,15 @@ void parallel_for(int64_t n, int threads, F &&f) {
 
 int build_host_tables(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts &o,
                       HostTables &T, std::string &err, const int32_t *comp) {
+    std::vector<int64_t> off(nt + 1);
+    for (int64_t t = 0; t <= nt; ++t) off[t] = 3 * t;
+    return build_host_tables(xy, nv, CellList{off.data(), tri, nt}, 0, o, T, err, comp);
+}
+
+int build_host_tables(const double *xy, int64_t nv, const CellList &cells, int artificial, const fdu_mesh_opts &o,
+                      HostTables &T, std::string &err, const int32_t *comp) {
     T.nv = nv;
-    T.nt = nt;
+    T.nt = cells.n;
     T.Lx = o.Lx;
     T.Ly = o.Ly;
     T.gamma = o.gamma;
@@ -511,7 +587,7 @@ int build_host_tables(const double *xy, int64_t nv, const int32_t *tri, int64_t 
         }
     }
     Geo g{T.xy.data(), T.Lx, T.Ly};
-    int st = build_edges(tri, nt, nv, g, T, err);
+    int st = build_edges(cells, artificial, o.lsq_degree, nv, g, T, err);
     if (st) return st;
     int threads = o.host_threads > 0 ? o.host_threads : (int)std::max(1u, std::thread::hardware_concurrency());
     const bool periodic = T.Lx > 0 && T.Ly > 0;

@@ -62,6 +62,18 @@ struct HostTables {
 int build_host_tables(const double *xy, int64_t nv, const int32_t *tri, int64_t nt, const fdu_mesh_opts &o,
                       HostTables &T, std::string &err, const int32_t *comp = nullptr);
 
+// Cells of 3 or 4 vertices (counter-clockwise, convex) as CSR.
+struct CellList {
+    const int64_t *off;  // [n+1]
+    const int32_t *vtx;
+    int64_t n;
+};
+// The same from cells; `artificial` = 0: cell sides only; 1: plus both
+// diagonals of every quad; 2: plus far-apex edges at vertices short of
+// least-squares conditions.
+int build_host_tables(const double *xy, int64_t nv, const CellList &cells, int artificial, const fdu_mesh_opts &o,
+                      HostTables &T, std::string &err, const int32_t *comp = nullptr);
+
 // Per-side coefficient block from five normalised coordinates (exposed for tests through the C-ABI builder).
 void side_coefficients(const double x[5], double out[kSideCoef]);
 

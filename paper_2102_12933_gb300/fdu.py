@@ -33,7 +33,7 @@ EXPORTS = (
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
     "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
-    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
+    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_mesh_create_cells", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
     "fdu_batch_max_dt", "fdu_batch_set_dt", "fdu_batch_rk_steps", "fdu_batch_set_launch", "fdu_batch_autotune",
     "fdu_batch_barrier_selftest", "fdu_residual_vjp", "fdu_rk_step_vjp", "fdu_adjoint_rk",
 )
@@ -107,6 +107,7 @@ def load():
         L.fdu_residual_noalloc.argtypes = [P, P, P, P]
         L.fdu_check_recip64.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_check_rsqrt64.argtypes = [C.c_int, dp, dp, i64]
+        L.fdu_mesh_create_cells.argtypes = [dp, i64, lp, ip, i64, C.c_int, C.POINTER(MeshOpts), C.POINTER(P)]
         L.fdu_advance.argtypes = [P, C.c_double, C.c_double, C.c_int, i64, lp, dp, P]
         L.fdu_limited_count.argtypes = [P, lp, C.c_int, P]
         L.fdu_batch_create.argtypes = [C.c_int32, C.POINTER(dp), lp, C.POINTER(ip), lp, C.POINTER(MeshOpts),
@@ -221,11 +222,21 @@ class Mesh:
 
     def __init__(self, xy, tri, Lx=0.0, Ly=0.0, *, lsq_degree=2, lsq_levels=2, device=0, renumber=1,
                  ghost_donor=None, weno_eps=1e-40, weno_eps32=1e-30, gamma=1.4, host_threads=0,
-                 positivity_alpha=0.0):
+                 positivity_alpha=0.0, artificial_edges=None):
+        """`tri` is an (nt, 3) array of triangles, or a pair (cell_off,
+        cell_vtx) of a hybrid triangle / quadrilateral mesh in CSR form; then
+        `artificial_edges` (0, 1 or 2, default 1) selects the artificial
+        edges of fdu_mesh_create_cells."""
         L = load()
         self._h = None
         xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
-        tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+        cells = None
+        if isinstance(tri, tuple):
+            cells = (np.ascontiguousarray(tri[0], dtype=np.int64), np.ascontiguousarray(tri[1], dtype=np.int32))
+        else:
+            tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+            if artificial_edges is not None:
+                raise ValueError("artificial_edges needs a (cell_off, cell_vtx) cell list")
         self._ghost = None
         bc = FDU_BC_PERIODIC
         gp = None
@@ -239,7 +250,13 @@ class Mesh:
         if gp is not None:
             o.ghost_donor = gp
         h = C.c_void_p()
-        _check(L.fdu_mesh_create(_dp(xy), xy.shape[0], _ip(tri), tri.shape[0], C.byref(o), C.byref(h)))
+        if cells is not None:
+            off, vtx = cells
+            art = 1 if artificial_edges is None else int(artificial_edges)
+            _check(L.fdu_mesh_create_cells(_dp(xy), xy.shape[0], _lp(off), _ip(vtx), off.shape[0] - 1, art, C.byref(o),
+                                           C.byref(h)))
+        else:
+            _check(L.fdu_mesh_create(_dp(xy), xy.shape[0], _ip(tri), tri.shape[0], C.byref(o), C.byref(h)))
         self._h = h
         self.device = device
         info = self.info()

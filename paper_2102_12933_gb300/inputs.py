@@ -25,7 +25,7 @@ class Mesh:
     """A triangle mesh as plain arrays (original vertex ids)."""
 
     xy: np.ndarray  # [nv, 2] float64
-    tri: np.ndarray  # [nt, 3] int32, counter-clockwise
+    tri: np.ndarray | tuple  # [nt, 3] int32 counter-clockwise, or (cell_off, cell_vtx) of a hybrid mesh
     Lx: float  # periodic length in x (0 = not periodic)
     Ly: float  # periodic length in y (0 = not periodic)
     n: int = 0  # lattice size it was drawn from (informational)
@@ -38,6 +38,8 @@ class Mesh:
 
     @property
     def nt(self) -> int:
+        if isinstance(self.tri, tuple):
+            return int(self.tri[0].shape[0] - 1)
         return int(self.tri.shape[0])
 
 
@@ -85,6 +87,67 @@ def torus_lattice(n: int, L: float = 10.0, jitter: float = 0.2, seed: int = 1001
     if np.any(_signed_areas(xy, tri, L, L) <= 0):
         raise ValueError("jittered lattice produced a non-positive triangle")
     return m
+
+
+def hybrid_lattice(n: int, L: float = 10.0, jitter: float = 0.2, seed: int = 1007, tri_fraction: float = 0.5,
+                   origin: float = 0.0) -> Mesh:
+    """Hybrid triangle / quadrilateral mesh on the periodic square.
+
+    The n x n torus lattice of ``torus_lattice`` (same ids, spacing and
+    jitter); each lattice quad is kept as a counter-clockwise
+    quadrilateral (a, b, c, d) or, with probability ``tri_fraction``, split
+    on a Bernoulli(1/2) diagonal into two triangles.  ``tri`` is returned as
+    the CSR pair (cell_off int64 [nc+1], cell_vtx int32).
+    """
+    if n < 4:
+        raise ValueError("torus lattice needs n >= 4")
+    rng = np.random.default_rng(seed)
+    h = L / n
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    xy = np.stack([origin + ii.ravel() * h, origin + jj.ravel() * h], axis=1).astype(np.float64)
+    if jitter > 0:
+        xy += rng.uniform(-jitter * h, jitter * h, size=xy.shape)
+    split = rng.uniform(size=n * n) < tri_fraction
+    diag = rng.integers(0, 2, size=n * n)
+    i, j = ii.ravel(), jj.ravel()
+    a = j * n + i
+    b = j * n + (i + 1) % n
+    c = ((j + 1) % n) * n + (i + 1) % n
+    d = ((j + 1) % n) * n + i
+    off, vtx = [0], []
+    for q in range(n * n):
+        if not split[q]:
+            vtx += [a[q], b[q], c[q], d[q]]
+            off.append(off[-1] + 4)
+        elif diag[q] == 0:
+            vtx += [a[q], b[q], c[q], a[q], c[q], d[q]]
+            off += [off[-1] + 3, off[-1] + 6]
+        else:
+            vtx += [a[q], b[q], d[q], b[q], c[q], d[q]]
+            off += [off[-1] + 3, off[-1] + 6]
+    return Mesh(xy=xy, tri=(np.array(off, np.int64), np.array(vtx, np.int32)), Lx=L, Ly=L, n=n, h=h)
+
+
+def union_jack_lattice(n: int, L: float = 10.0) -> Mesh:
+    """The n x n torus lattice (n even) with each quad split on the diagonal
+    through its corner (i, j) when i + j is even and through (i+1, j)
+    otherwise: vertices with i + j even have 8 neighbours, the others 4
+    (the valence-4 configuration of Fig. l1-tria4)."""
+    if n < 4 or n % 2:
+        raise ValueError("union jack lattice needs an even n >= 4")
+    h = L / n
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    xy = np.stack([ii.ravel() * h, jj.ravel() * h], axis=1).astype(np.float64)
+    i, j = ii.ravel(), jj.ravel()
+    a = j * n + i
+    b = j * n + (i + 1) % n
+    c = ((j + 1) % n) * n + (i + 1) % n
+    d = ((j + 1) % n) * n + i
+    even = ((i + j) % 2 == 0)[:, None]
+    t0 = np.where(even, np.stack([a, b, c], 1), np.stack([a, b, d], 1))
+    t1 = np.where(even, np.stack([a, c, d], 1), np.stack([b, c, d], 1))
+    tri = np.concatenate([t0, t1], 0).astype(np.int32)
+    return Mesh(xy=xy, tri=tri, Lx=L, Ly=L, n=n, h=h)
 
 
 def box_lattice(n: int, ghost_layers: int = 0, jitter: float = 0.2, seed: int = 1003,

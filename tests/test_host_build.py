@@ -137,3 +137,56 @@ def test_high_degree_weights_match_oracle(degree):
         assert np.array_equal(a[i], b[i])
     for i in (2, 3, 6):
         assert np.abs(a[i] - b[i]).max() <= 1e-9 * (1 + np.abs(b[i]).max())
+
+
+@pytest.mark.parametrize("artificial,frac,degree,levels", [(0, 0.5, 2, 2), (1, 0.5, 2, 2), (1, 0.0, 3, 2), (2, 0.5, 2, 1)])
+def test_hybrid_host_tables_match_oracle(artificial, frac, degree, levels):
+    """Triangles and quadrilaterals with artificial edges (Section 2.2.2):
+    edges, 1D stencils and divergence stencils bit-exact, weights within
+    rounding."""
+    m = inputs.hybrid_lattice(21, L=10.0, jitter=0.2, seed=41, tri_fraction=frac)
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=-1, lsq_degree=degree, lsq_levels=levels,
+                 artificial_edges=artificial)
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly, degree=degree, levels=levels, artificial=artificial)
+    om.build_weights()
+    assert np.array_equal(M.edges(), om.edges())
+    s1, x1 = M.edge_stencils()
+    s2, x2 = om.stencils()
+    assert np.array_equal(s1, s2)
+    assert np.abs(x1 - x2).max() < 1e-13
+    a, b = M.div_stencils(), om.div_stencils()
+    for i in (0, 1, 4, 5):
+        assert np.array_equal(a[i], b[i])
+    for i in (2, 3, 6):
+        assert np.abs(a[i] - b[i]).max() <= 1e-11 * (1 + np.abs(b[i]).max())
+    assert M.info()["nt"] == m.nt
+
+
+def test_far_apex_edges_match_oracle_and_rescue_the_fit():
+    m = inputs.union_jack_lattice(16, L=10.0)
+    cells = (np.arange(0, 3 * m.nt + 1, 3, dtype=np.int64), m.tri.astype(np.int32).ravel())
+    with pytest.raises(fdu.FduError, match="RANK_DEFICIENT"):
+        fdu.Mesh(m.xy, cells, 10.0, 10.0, device=-1, lsq_degree=3, lsq_levels=1, artificial_edges=0)
+    M = fdu.Mesh(m.xy, cells, 10.0, 10.0, device=-1, lsq_degree=3, lsq_levels=1, artificial_edges=2)
+    om = oracle.OracleMesh(m.xy, cells, 10.0, 10.0, degree=3, levels=1, artificial=2)
+    assert np.array_equal(M.edges(), om.edges())
+    assert np.array_equal(M.edge_stencils()[0], om.stencils()[0])
+
+
+def test_hybrid_mesh_errors():
+    m = inputs.hybrid_lattice(8, L=10.0, jitter=0.0, tri_fraction=0.0)
+    off, vtx = m.tri
+    with pytest.raises(fdu.FduError, match="ARG"):
+        fdu.Mesh(m.xy, (off, vtx), 10.0, 10.0, device=-1, artificial_edges=3)
+    cw = vtx.copy().reshape(-1, 4)[:, ::-1].ravel()  # clockwise quads
+    with pytest.raises(fdu.FduError, match="MESH"):
+        fdu.Mesh(m.xy, (off, cw), 10.0, 10.0, device=-1)
+    bent = vtx.copy().reshape(-1, 4)
+    bent[0] = bent[0][[0, 2, 1, 3]]  # self-intersecting (not convex)
+    with pytest.raises(fdu.FduError, match="MESH"):
+        fdu.Mesh(m.xy, (off, bent.ravel()), 10.0, 10.0, device=-1)
+    five = (np.array([0, 5], np.int64), np.array([0, 1, 2, 3, 4], np.int32))
+    with pytest.raises(fdu.FduError, match="MESH"):
+        fdu.Mesh(m.xy, five, 10.0, 10.0, device=-1)
+    with pytest.raises(ValueError):
+        fdu.Mesh(m.xy, np.zeros((1, 3), np.int32), 10.0, 10.0, device=-1, artificial_edges=1)

@@ -175,9 +175,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi"}
 
 
-def _workload(n=N_LATTICE):
+def _workload(n=N_LATTICE, kind="vortex"):
     from paper_2102_12933_gb300 import inputs
 
+    if kind == "hybrid":
+        # half of the lattice quads kept as quadrilaterals (with their two
+        # artificial diagonals), half split into triangles
+        mesh = inputs.hybrid_lattice(n, seed=1008, tri_fraction=0.5)
+        return mesh, inputs.isentropic_vortex(mesh.xy)
     mesh, w0 = inputs.vortex_case(n, seed=1002)
     return mesh, w0
 
@@ -274,9 +279,10 @@ def run_ours(args):
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    mesh, w0 = _workload(args.n)
+    hybrid = args.workload == "hybrid"
+    mesh, w0 = _workload(args.n, args.workload)
     t_build = time.perf_counter()
-    M = fdu.Mesh(mesh.xy, mesh.tri, mesh.Lx, mesh.Ly, device=local)
+    M = fdu.Mesh(mesh.xy, mesh.tri, mesh.Lx, mesh.Ly, device=local, **({"artificial_edges": 1} if hybrid else {}))
     t_build = time.perf_counter() - t_build
     info = M.info()
     nv, ne = M.nv, M.ne
@@ -419,7 +425,13 @@ def run_ours(args):
         "gpu_launches": 6 * args.steps,
         "clocks": clocks,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if hybrid:
+        line["config"].update(
+            workload=f"periodic isentropic vortex on a {args.n}x{args.n} jittered hybrid torus lattice of [0,10]^2: "
+                     "half of the quads kept as quadrilaterals with both artificial diagonals (Section 2.2.2), half "
+                     "split into triangles; two-level stencils, degree-2 least squares, NU-WENO5, SSP-RK3, CFL 0.5",
+            ne=int(ne), cells=int(mesh.nt))
+    if rank == 0 and not args.no_cpu_baseline and not hybrid:
         v, el, sample = time_oracle()
         line["cpu_baseline"] = {"value": round(v, 4), "unit": "Mvertex/s", "cores": 1, "kind": "oracle",
                                 "sample": sample, "seconds": round(el, 2)}
@@ -430,6 +442,61 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def _advance_both(M, w0, real, t_end, max_steps, err_steps=16):
+    """FP64 then FP32 adaptive runs from w0 to t_end (at most max_steps steps),
+    wall-clock timed between the host's time checks every 8 steps; the
+    FP32 state is compared with the FP64 one after err_steps steps."""
+    import torch
+
+    from paper_2102_12933_gb300 import fdu
+
+    n_real = int(real.sum())
+    out, states = {}, {}
+    for prec in (64, 32):
+        M.set_state(w0)
+        M.advance(0.5, t_end, prec, max_steps=8)  # warm-up (graph capture)
+        M.set_state(w0)
+        M.fallback_count(reset=True)
+        M.limited_count(reset=True)
+        steps, t, el, status = 0, 0.0, 0.0, "reached t_end"
+        while t < t_end and steps < max_steps:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                k, t = M.advance(0.5, t_end, prec, max_steps=8)
+            except fdu.FduError as e:
+                status = f"stopped: {e}"
+                break
+            torch.cuda.synchronize()
+            el += time.perf_counter() - t0
+            steps += k
+            if steps == err_steps:
+                states[prec] = M.get_state()
+        if t < t_end and status == "reached t_end":
+            status = f"stopped at max_steps={max_steps}"
+        out[prec] = {"steps": steps, "t": t, "seconds": round(el, 3), "status": status,
+                     "value": round(n_real * 3 * steps / el / 1e6, 2) if el > 0 else None,
+                     "fallback_edges": M.fallback_count(), "safeguarded_vertex_stages": M.limited_count()}
+    err = None
+    if 64 in states and 32 in states:
+        err = {"rho": _rel_l2(states[32][real, 0], states[64][real, 0]),
+               "rhoE": _rel_l2(states[32][real, 3], states[64][real, 3]), "steps": err_steps}
+    return out, err
+
+
+def _ghost_line(out, err, workload, t_build):
+    return {
+        "metric": METRIC, "value": out[64]["value"], "unit": "Mvertex/s", "n_gpus": 1,
+        "steps": out[64]["steps"], "warmup": 1,
+        "ms_per_step": round(1e3 * out[64]["seconds"] / max(out[64]["steps"], 1), 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload, "host_build_s": round(t_build, 2)},
+        "fp64": out[64], "fp32": dict(out[32], speedup_vs_f64=(round(out[32]["value"] / out[64]["value"], 3)
+                                                               if out[32]["value"] and out[64]["value"] else None),
+                                      error_vs_f64=err),
+    }
 
 
 def run_riemann(args):
@@ -445,58 +512,49 @@ def run_riemann(args):
     n = args.n if args.n != N_LATTICE else 1000
     mesh, w0 = inputs.riemann_case(n, ghost_layers=5, seed=1003)
     t_build = time.perf_counter()
-    # the unguarded method turns non-physical on this problem; the
-    # stage positivity safeguard keeps rho, p > 0 so the run reaches t_end
+    # the unguarded method turns non-physical on this problem; the stage
+    # positivity safeguard keeps rho, p > 0 so the run reaches t_end
     M = fdu.Mesh(mesh.xy, mesh.tri, 0.0, 0.0, device=local, ghost_donor=mesh.ghost_donor, positivity_alpha=0.1)
     t_build = time.perf_counter() - t_build
     real = mesh.ghost_donor < 0
-    n_real = int(real.sum())
-    out = {}
-    states = {}
-    err_steps = 16  # FP32 vs FP64 compared after this many steps from the same state
-    for prec in (64, 32):
-        M.set_state(w0)
-        M.advance(0.5, 0.3, prec, max_steps=8)  # warm-up (graph capture)
-        M.set_state(w0)
-        M.fallback_count(reset=True)
-        M.limited_count(reset=True)
-        steps, t, el, status = 0, 0.0, 0.0, "reached t_end"
-        while t < args.t_end and steps < args.riemann_max_steps:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            try:
-                k, t = M.advance(0.5, args.t_end, prec, max_steps=8)
-            except fdu.FduError as e:
-                status = f"stopped: {e}"
-                break
-            torch.cuda.synchronize()
-            el += time.perf_counter() - t0
-            steps += k
-            if steps == err_steps:
-                states[prec] = M.get_state()
-        if t < args.t_end and status == "reached t_end":
-            status = f"stopped at max_steps={args.riemann_max_steps}"
-        out[prec] = {"steps": steps, "t": t, "seconds": round(el, 3), "status": status,
-                     "value": round(n_real * 3 * steps / el / 1e6, 2) if el > 0 else None,
-                     "fallback_edges": M.fallback_count(), "safeguarded_vertex_stages": M.limited_count()}
-    err = None
-    if 64 in states and 32 in states:
-        err = {"rho": _rel_l2(states[32][real, 0], states[64][real, 0]),
-               "rhoE": _rel_l2(states[32][real, 3], states[64][real, 3]), "steps": err_steps}
-    line = {
-        "metric": METRIC, "value": out[64]["value"], "unit": "Mvertex/s", "n_gpus": 1,
-        "steps": out[64]["steps"], "warmup": 1,
-        "ms_per_step": round(1e3 * out[64]["seconds"] / max(out[64]["steps"], 1), 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"four-quadrant 2D Riemann problem on [0,1]^2, {n}x{n} jittered lattice + 5 "
-                               f"transmissive ghost layers ({mesh.nv} vertices, {n_real} real), to t = {args.t_end} "
-                               "with device-side CFL 0.5 time steps and the stage positivity safeguard (alpha 0.1) "
-                               "(wall-clock timed, includes the host's time checks every 8 steps)",
-                   "host_build_s": round(t_build, 2)},
-        "fp64": out[64], "fp32": dict(out[32], speedup_vs_f64=(round(out[32]["value"] / out[64]["value"], 3)
-                                                               if out[32]["value"] and out[64]["value"] else None),
-                                      error_vs_f64=err),
-    }
+    out, err = _advance_both(M, w0, real, args.t_end, args.riemann_max_steps)
+    line = _ghost_line(out, err, f"four-quadrant 2D Riemann problem on [0,1]^2, {n}x{n} jittered lattice + 5 "
+                                 f"transmissive ghost layers ({mesh.nv} vertices, {int(real.sum())} real), to t = "
+                                 f"{args.t_end} with device-side CFL 0.5 time steps and the stage positivity safeguard "
+                                 "(alpha 0.1) (wall-clock timed, includes the host's time checks every 8 steps)",
+                       t_build)
+    print(json.dumps(line), flush=True)
+    M.close()
+    return 0
+
+
+def run_shock_vortex(args):
+    """Shock-vortex interaction (Section 3.2): Mach 1.2 stationary shock at
+    x = 0 and the M_v = 1 isentropic vortex at (4, 0) on [-65, 15] x [-40,
+    40], periodic in y, Dirichlet ghost columns in x; regular diagonalised
+    lattice at the paper's finest spacing 0.08 (n = 1000 across y), to
+    t = 16 with CFL 0.5 and the stage positivity safeguard, FP64 and FP32."""
+    import torch
+
+    from paper_2102_12933_gb300 import fdu, inputs
+
+    ws_, rank, local = _dist()
+    torch.cuda.set_device(local)
+    n = args.n if args.n != N_LATTICE else 1000
+    mesh, w0 = inputs.shock_vortex_case(n)
+    t_build = time.perf_counter()
+    # the paper's M_v = 1 vortex turns the unguarded method non-physical
+    # within t < 1 on these lattices; the safeguard carries it to t = 16
+    M = fdu.Mesh(mesh.xy, mesh.tri, 0.0, 80.0, device=local, ghost_donor=mesh.ghost_donor, positivity_alpha=0.1)
+    t_build = time.perf_counter() - t_build
+    real = mesh.ghost_donor < 0
+    t_end = args.t_end if args.t_end != 0.3 else 16.0
+    out, err = _advance_both(M, w0, real, t_end, args.riemann_max_steps if args.riemann_max_steps != 400 else 4000)
+    line = _ghost_line(out, err, f"shock-vortex interaction (Section 3.2) on [-65,15]x[-40,40], periodic in y, "
+                                 f"{n} points across y (h = {80.0 / n:g}), regular diagonalised lattice + 5 Dirichlet "
+                                 f"ghost columns per side ({mesh.nv} vertices, {int(real.sum())} real), Mach 1.2 shock, "
+                                 f"M_v = 1 vortex at (4, 0), to t = {t_end} with device-side CFL 0.5 time steps and the "
+                                 "stage positivity safeguard (alpha 0.1) (wall-clock timed)", t_build)
     print(json.dumps(line), flush=True)
     M.close()
     return 0
@@ -620,6 +678,17 @@ def run_adjoint(args):
 
         t_adj = timed(adj, 3)
         g = grad.clone()
+        # the same gradient with one segment (every stage state kept, 3 x 50
+        # states of 8 MB: no recomputation)
+        grad1 = torch.empty_like(w0d)
+
+        def adj1():
+            M.set_state(w0d, stream=stream)
+            M.adjoint_rk(dt, n_steps, lamT, out=grad1, checkpoint_every=n_steps, stream=stream)
+
+        t_adj1 = timed(adj1, 3)
+        one_seg = {"adjoint_ms": round(t_adj1, 3), "adjoint_over_forward": round(t_adj1 / t_fwd, 3),
+                   "max_abs_diff_vs_checkpointed": float((grad1 - g).abs().max())}
         gen = torch.Generator(device="cuda").manual_seed(5005)
         errs = []
         steps_h = (1e-4, 1e-5, 1e-6, 1e-7)
@@ -637,7 +706,8 @@ def run_adjoint(args):
             errs.append(best)
         result[label] = {"residual_ms": round(t_res, 4), "residual_vjp_ms": round(t_vjp, 4),
                          "residual_vjp_over_residual": round(t_vjp / t_res, 3), "forward_ms": round(t_fwd, 3),
-                         "adjoint_ms": round(t_adj, 3), "adjoint_over_forward": round(t_adj / t_fwd, 3), "J": J0,
+                         "adjoint_ms": round(t_adj, 3), "adjoint_over_forward": round(t_adj / t_fwd, 3),
+                         "one_segment": one_seg, "J": J0,
                          "fd_check": {"directions": 32, "steps_h": list(steps_h),
                                       "differences": "central, 2nd and 4th order; best per direction",
                                       "max_rel_err": float(np.max(errs)), "median_rel_err": float(np.median(errs)),
@@ -709,7 +779,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_LATTICE, help="lattice size (n x n vertices); 500 = the workload")
-    ap.add_argument("--workload", default="vortex", choices=["vortex", "riemann", "batch", "adjoint", "sod"],
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "riemann", "batch", "adjoint", "sod", "hybrid", "shock_vortex"],
                     help="vortex: the 250k periodic vortex (default line); riemann: the 1M-vertex "
                          "transmissive four-quadrant Riemann problem to t_end")
     ap.add_argument("--t-end", dest="t_end", type=float, default=0.3)
@@ -727,6 +797,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "sod":
         return run_sod(args)
+    if args.workload == "shock_vortex":
+        return run_shock_vortex(args)
     return run_ours(args)
 
 

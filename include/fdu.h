@@ -63,11 +63,15 @@ typedef struct fdu_mesh_opts {
     double gamma;       /* ratio of specific heats */
     int lsq_degree;     /* degree p of the least-squares polynomials, 1..6 */
     int lsq_levels;     /* divergence stencil: 1 = one-level, 2 = two-level */
-    int bc;             /* FDU_BC_PERIODIC or FDU_BC_TRANSMISSIVE */
+    int bc;             /* FDU_BC_PERIODIC (Lx, Ly > 0, no ghosts) or FDU_BC_TRANSMISSIVE (ghost layers,
+                           transmissive or Dirichlet per ghost; Lx or Ly may still be > 0 for a direction
+                           that is periodic) */
     int renumber;       /* 1 = locality (Hilbert) renumbering of vertices and edges */
     int device;         /* CUDA device ordinal; -1 = host tables only (no GPU use) */
     int host_threads;   /* threads for host preprocessing; 0 = all cores */
-    const int32_t *ghost_donor; /* transmissive: [nv] donor vertex of each ghost, -1 for real vertices; NULL = none */
+    const int32_t *ghost_donor; /* ghost layers: [nv] -1 for a real vertex; for a ghost vertex the id of a real
+                                   vertex whose state and fluxes it copies before every stage (transmissive), or
+                                   its own id (Dirichlet: it keeps the state it was given); NULL = none */
     double positivity_alpha;    /* stage positivity safeguard: 0 = off (the paper's method); in (0,1): the
                                    forward-Euler part ws + theta dt L of each vertex's RK stage uses the
                                    largest theta in {1, 1/2, ..., 2^-20, 0} keeping rho and p at least alpha

@@ -70,7 +70,7 @@ typedef struct om_mesh {
     int32_t *adj_e;   /* edge id of (v, adj) */
     int32_t *sten;    /* [ne][6]  L3 L2 L1 R1 R2 R3 */
     double *xi;       /* [ne][6]  normalised curve coordinates */
-    int32_t *ghost;   /* [nv] donor id for ghost vertices, -1 for real ones (NULL = none) */
+    int32_t *ghost;   /* [nv] donor id of ghost vertices (itself: Dirichlet), -1 for real ones (NULL = none) */
     /* divergence stencils (CSR over vertices) */
     int64_t *dv_off;
     int32_t *dv_id;
@@ -1006,11 +1006,12 @@ int om_edge_fluxes(const om_mesh *m, const double *w, double eps, const uint8_t 
     return OM_OK;
 }
 
-/* ghost fill (transmissive reading): ghost vertices copy their donor */
+/* ghost fill: a transmissive ghost copies its donor (reading); a ghost
+ * that is its own donor is a Dirichlet vertex and keeps its state */
 void om_fill_ghosts(const om_mesh *m, double *w) {
     if (!m->ghost) return;
     for (int64_t v = 0; v < m->nv; ++v)
-        if (m->ghost[v] >= 0) memcpy(w + 4 * v, w + 4 * (int64_t)m->ghost[v], 4 * sizeof(double));
+        if (m->ghost[v] >= 0 && m->ghost[v] != v) memcpy(w + 4 * v, w + 4 * (int64_t)m->ghost[v], 4 * sizeof(double));
 }
 
 /* dwdt[nv][4] at vertices with vmask[v] (NULL = all real vertices);

@@ -378,8 +378,11 @@ void enqueue_stages(fdu_mesh *m, int prec, double dt, const double *dt_dev, cuda
             else launch_div_f32(a, stage, s);
         });
         if (m->n_ghost > 0) {
-            launch_ghost_fill(a.wout, a.Fout, fq, prec == 32 ? m->w32 : nullptr, m->donor, m->n_real, m->n_ghost, s);
-            if (a.Qout) launch_ghost_fill(nullptr, a.Qout, 2, nullptr, m->donor, m->n_real, m->n_ghost, s);
+            // Dirichlet ghosts take their fixed values from the step's start buffers (wn, F[0], Q[0])
+            const void *F0 = prec == 64 ? (const void *)m->F64[0] : (const void *)m->F32[0];
+            launch_ghost_fill(a.wout, m->wn, a.Fout, F0, fq, prec == 32 ? m->w32 : nullptr, m->donor, m->n_real,
+                              m->n_ghost, s);
+            if (a.Qout) launch_ghost_fill(nullptr, nullptr, a.Qout, m->Q64[0], 2, nullptr, m->donor, m->n_real, m->n_ghost, s);
         }
     }
 }
@@ -762,7 +765,7 @@ fdu_status fdu_set_state(fdu_mesh *m, const double *w, int on_device, void *stre
         CK(cudaStreamSynchronize(s));
     }
     if (m->n_ghost > 0) {
-        launch_ghost_fill(m->wn, nullptr, 0, nullptr, m->donor, m->n_real, m->n_ghost, s);
+        launch_ghost_fill(m->wn, nullptr, nullptr, nullptr, 0, nullptr, m->donor, m->n_real, m->n_ghost, s);
         CK_LAUNCH();
     }
     m->f64_valid = m->f32_valid = false;
@@ -1274,7 +1277,7 @@ fdu_status fdu_residual_noalloc(const fdu_mesh *mc, const double *w, double *dwd
     // ghost rows of the output must start at zero
     if (m->n_ghost > 0) CK(cudaMemsetAsync(dwdt, 0, 4 * m->nv * sizeof(double), s));
     launch_permute_rows(w, wi, m->new2old, m->nv, true, s);
-    if (m->n_ghost > 0) launch_ghost_fill(wi, nullptr, 0, nullptr, m->donor, m->n_real, m->n_ghost, s);
+    if (m->n_ghost > 0) launch_ghost_fill(wi, nullptr, nullptr, nullptr, 0, nullptr, m->donor, m->n_real, m->n_ghost, s);
     launch_vertex_flux_f64(wi, F, m->nv, m->opts.gamma, s);
     EdgeArgs ea = edge_args(m, 64, wi);
     ea.r = r;

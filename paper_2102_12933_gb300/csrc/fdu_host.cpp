@@ -579,8 +579,9 @@ int build_host_tables(const double *xy, int64_t nv, const CellList &cells, int a
         T.ghost.assign(o.ghost_donor, o.ghost_donor + nv);
         T.n_real = 0;
         for (int64_t v = 0; v < nv; ++v) {
-            if (T.ghost[v] >= nv || T.ghost[v] < -1 || (T.ghost[v] >= 0 && o.ghost_donor[T.ghost[v]] >= 0)) {
-                err = "ghost donor must be -1 or the id of a non-ghost vertex";
+            const int32_t d = T.ghost[v];
+            if (d >= nv || d < -1 || (d >= 0 && d != v && o.ghost_donor[d] >= 0)) {
+                err = "ghost donor must be -1, the id of a non-ghost vertex or the ghost's own id";
                 return FDU_ERR_ARG;
             }
             T.n_real += (T.ghost[v] < 0);

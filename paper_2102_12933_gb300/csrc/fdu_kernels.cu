@@ -572,14 +572,24 @@ __global__ void permute_rows_kernel(const double *__restrict__ in, double *__res
     else st4(out, m, ld4(in, i));         // out[map[i]] = in[i]
 }
 
-// Ghost vertices (internal ids n_real .. n_real+n_ghost-1) copy their
-// donor's state and fluxes (transmissive boundary reading).  F holds
-// `fq` 16-byte words per vertex.
-__global__ void ghost_fill_kernel(double *__restrict__ w, uint4 *__restrict__ F, int fq, float4 *__restrict__ w32,
-                                  const int32_t *__restrict__ donor, int64_t n_real, int64_t n_ghost) {
+// Ghost vertices (internal ids n_real .. n_real+n_ghost-1).  A transmissive
+// ghost copies its donor's state and fluxes (reading of the configs'
+// transmissive boundary); a Dirichlet ghost (its own donor) takes its fixed
+// state and fluxes from wsrc / Fsrc, the buffers of the step's start state
+// (a no-op when they are the buffers being filled).  F holds `fq` 16-byte
+// words per vertex.
+__global__ void ghost_fill_kernel(double *__restrict__ w, const double *wsrc, uint4 *__restrict__ F, const uint4 *Fsrc,
+                                  int fq, float4 *__restrict__ w32, const int32_t *__restrict__ donor, int64_t n_real,
+                                  int64_t n_ghost) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_ghost) return;
     const int64_t g = n_real + i, d = __ldg(donor + i);
+    if (d == g) {
+        if (w && wsrc && w != wsrc) st4(w, g, ld4(wsrc, g));
+        if (F && Fsrc && F != Fsrc)
+            for (int c = 0; c < fq; ++c) F[fq * g + c] = Fsrc[fq * g + c];
+        return;
+    }
     if (w) st4(w, g, ld4(w, d));
     if (F)
         for (int c = 0; c < fq; ++c) F[fq * g + c] = F[fq * d + c];
@@ -688,10 +698,11 @@ void launch_div_f32(const DivArgs &a, int mode, cudaStream_t s) {
 void launch_permute_rows(const double *in, double *out, const int32_t *map, int64_t n, bool gather, cudaStream_t s) {
     if (n > 0) permute_rows_kernel<<<blocks(n, 256), 256, 0, s>>>(in, out, map, n, gather);
 }
-void launch_ghost_fill(double *w, void *F, int fq, float4 *w32, const int32_t *donor, int64_t n_real, int64_t n_ghost,
-                       cudaStream_t s) {
+void launch_ghost_fill(double *w, const double *wsrc, void *F, const void *Fsrc, int fq, float4 *w32,
+                       const int32_t *donor, int64_t n_real, int64_t n_ghost, cudaStream_t s) {
     if (n_ghost > 0)
-        ghost_fill_kernel<<<blocks(n_ghost, 256), 256, 0, s>>>(w, static_cast<uint4 *>(F), fq, w32, donor, n_real,
+        ghost_fill_kernel<<<blocks(n_ghost, 256), 256, 0, s>>>(w, wsrc, static_cast<uint4 *>(F),
+                                                               static_cast<const uint4 *>(Fsrc), fq, w32, donor, n_real,
                                                                n_ghost);
 }
 void launch_max_dt(const double *w, const double *hmin, int64_t n, double gamma, unsigned long long *slot,

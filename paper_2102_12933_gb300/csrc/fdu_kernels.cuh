@@ -64,8 +64,8 @@ void launch_edge_flux_f32(const EdgeArgs &a, cudaStream_t s);
 void launch_div_f64(const DivArgs &a, int mode, cudaStream_t s);
 void launch_div_f32(const DivArgs &a, int mode, cudaStream_t s);
 void launch_permute_rows(const double *in, double *out, const int32_t *map, int64_t n, bool gather, cudaStream_t s);
-void launch_ghost_fill(double *w, void *F, int fq, float4 *w32, const int32_t *donor, int64_t n_real, int64_t n_ghost,
-                       cudaStream_t s);
+void launch_ghost_fill(double *w, const double *wsrc, void *F, const void *Fsrc, int fq, float4 *w32,
+                       const int32_t *donor, int64_t n_real, int64_t n_ghost, cudaStream_t s);
 // FMA throughput (TFLOP/s) of `precision` 64 or 32 with sms*8 blocks of 256
 // threads; scratch holds sms*8*256 elements of that precision.
 double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s);

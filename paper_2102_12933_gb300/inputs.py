@@ -196,6 +196,87 @@ def box_lattice(n: int, ghost_layers: int = 0, jitter: float = 0.2, seed: int = 
     return mesh
 
 
+def channel_lattice(n: int, x0: float = -65.0, x1: float = 15.0, Ly: float = 80.0, ghost_layers: int = 5,
+                    jitter: float = 0.0, seed: int = 1009, random_diagonals: bool = False) -> Mesh:
+    """Lattice on [x0, x1] x [0, Ly) periodic in y, with Dirichlet ghost
+    layers outside x0 and x1.
+
+    Spacing h = Ly / n in both directions (x1 - x0 must be a multiple of
+    h); ``ghost_layers`` lattice columns are added beyond each x boundary.
+    Vertex (i, j), i in [-g, nx-1+g] with nx = (x1-x0)/h + 1, j in [0, n),
+    has id j*m + (i+g), m = nx + 2g, at (x0 + i h, j h - Ly/2) (so y spans
+    [-Ly/2, Ly/2)).  Only vertices strictly inside (x0, x1) are jittered.
+    Each ghost is its own donor (``ghost_donor[v] = v``): a Dirichlet vertex
+    that keeps the state it is given.
+    """
+    h = Ly / n
+    nx = int(round((x1 - x0) / h)) + 1
+    if abs((nx - 1) * h - (x1 - x0)) > 1e-9 * (x1 - x0):
+        raise ValueError("x1 - x0 must be a multiple of Ly / n")
+    g = ghost_layers
+    m = nx + 2 * g
+    rng = np.random.default_rng(seed)
+    jj, ii = np.meshgrid(np.arange(n), np.arange(-g, nx + g), indexing="ij")
+    i, j = ii.ravel(), jj.ravel()
+    xy = np.stack([x0 + i * h, j * h - 0.5 * Ly], axis=1).astype(np.float64)
+    inside = (i > 0) & (i < nx - 1)
+    if jitter > 0:
+        xy[inside] += rng.uniform(-jitter * h, jitter * h, size=(int(inside.sum()), 2))
+    qi, qj = np.meshgrid(np.arange(m - 1), np.arange(n), indexing="xy")
+    qi, qj = qi.ravel(), qj.ravel()
+    a = qj * m + qi
+    b = qj * m + qi + 1
+    c = ((qj + 1) % n) * m + qi + 1
+    d = ((qj + 1) % n) * m + qi
+    diag = rng.integers(0, 2, size=a.size) if random_diagonals else np.zeros(a.size, np.int64)
+    t0 = np.where(diag[:, None] == 0, np.stack([a, b, c], 1), np.stack([a, b, d], 1))
+    t1 = np.where(diag[:, None] == 0, np.stack([a, c, d], 1), np.stack([b, c, d], 1))
+    tri = np.concatenate([t0, t1], 0).astype(np.int32)
+    mesh = Mesh(xy=xy, tri=tri, Lx=0.0, Ly=Ly, n=n, h=h)
+    if np.any(_signed_areas(xy, tri, 0.0, Ly) <= 0):
+        raise ValueError("channel lattice produced a non-positive triangle")
+    ids = np.arange(xy.shape[0], dtype=np.int32)
+    mesh.ghost_donor = np.where((i < 0) | (i > nx - 1), ids, -1).astype(np.int32)
+    return mesh
+
+
+def shock_vortex(xy, gamma=GAMMA, mach_shock=1.2, mach_vortex=1.0, centre=(4.0, 0.0), Ly=80.0):
+    """Shock-vortex interaction of Section 3.2: a stationary normal shock at
+    x = 0 with the supersonic state (rho, u, v, p) = (1, -M_s, 0, 1/gamma)
+    (sound speed 1) on x >= 0 and the Rankine-Hugoniot state on x < 0, and
+    the isentropic vortex of the paper's formula centred at ``centre`` on
+    the upstream side: rho = (1 - (gamma-1)/2 M_v^2 e^(1-r^2))^(1/(gamma-1)),
+    p = rho^gamma / gamma, (du, dv) = M_v e^((1-r^2)/2) (-y', x')."""
+    M = mach_shock
+    r2r1 = (gamma + 1) * M * M / ((gamma - 1) * M * M + 2)
+    p2p1 = 1 + 2 * gamma / (gamma + 1) * (M * M - 1)
+    x, y = xy[:, 0], xy[:, 1]
+    pre = x >= 0
+    rho = np.where(pre, 1.0, r2r1)
+    u = np.where(pre, -M, -M / r2r1)
+    v = np.zeros_like(x)
+    p = np.where(pre, 1.0 / gamma, p2p1 / gamma)
+    dx = x - centre[0]
+    dy = y - centre[1]
+    if Ly > 0:
+        dy -= Ly * np.rint(dy / Ly)
+    r2 = dx * dx + dy * dy
+    rv = (1 - 0.5 * (gamma - 1) * mach_vortex ** 2 * np.exp(1 - r2)) ** (1 / (gamma - 1))
+    amp = mach_vortex * np.exp(0.5 * (1 - r2))
+    rho = np.where(pre, rv, rho)
+    p = np.where(pre, rv ** gamma / gamma, p)
+    u = np.where(pre, u - amp * dy, u)
+    v = np.where(pre, amp * dx, v)
+    return primitive_to_conservative(rho, u, v, p, gamma)
+
+
+def shock_vortex_case(n: int = 160, ghost_layers: int = 5, jitter: float = 0.0, random_diagonals: bool = False):
+    """The shock-vortex problem on [-65, 15] x [-40, 40] (n points across the
+    periodic y period; the paper's finest spacing 0.08 is n = 1000)."""
+    mesh = channel_lattice(n, -65.0, 15.0, 80.0, ghost_layers, jitter=jitter, random_diagonals=random_diagonals)
+    return mesh, shock_vortex(mesh.xy)
+
+
 def permute_vertices(mesh: Mesh, seed: int) -> tuple[Mesh, np.ndarray]:
     """Return the same mesh with vertex ids shuffled, and the permutation.
 

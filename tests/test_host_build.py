@@ -190,3 +190,23 @@ def test_hybrid_mesh_errors():
         fdu.Mesh(m.xy, five, 10.0, 10.0, device=-1)
     with pytest.raises(ValueError):
         fdu.Mesh(m.xy, np.zeros((1, 3), np.int32), 10.0, 10.0, device=-1, artificial_edges=1)
+
+
+def test_channel_with_dirichlet_ghosts_matches_oracle():
+    """Periodic in y, Dirichlet ghost columns in x (the shock-vortex setup)."""
+    m, _ = inputs.shock_vortex_case(40)
+    M = fdu.Mesh(m.xy, m.tri, 0.0, 80.0, device=-1, ghost_donor=m.ghost_donor)
+    om = oracle.OracleMesh(m.xy, m.tri, 0.0, 80.0, ghost=m.ghost_donor)
+    om.build_weights()
+    assert M.info()["n_real"] == int(np.sum(m.ghost_donor < 0))
+    assert np.array_equal(M.edges(), om.edges())
+    assert np.array_equal(M.edge_stencils()[0], om.stencils()[0])
+    a, b = M.div_stencils(), om.div_stencils()
+    for i in (0, 1, 4, 5):
+        assert np.array_equal(a[i], b[i])
+    # a ghost whose donor is another ghost is rejected
+    bad = m.ghost_donor.copy()
+    g = np.nonzero(bad >= 0)[0]
+    bad[g[0]] = g[1]
+    with pytest.raises(fdu.FduError, match="ARG"):
+        fdu.Mesh(m.xy, m.tri, 0.0, 80.0, device=-1, ghost_donor=bad)

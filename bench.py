@@ -41,9 +41,9 @@ FLOP_DIV64_PER_EENTRY = 8
 FLOP_DIV64_FIXED = 70
 FP64_PEAK_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), NVIDIA datasheet figure
 # DRAM bytes per edge of edge_flux_f64 from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, 480k-edge case of the same workload, scaled per edge);
-# None once the kernel changes after the capture.
-TRAFFIC_EDGE64_B_PER_EDGE = 321.0
+# dram__bytes_write.sum = 144.8 + 8.8 MB on the 480k-edge case of the same
+# workload, scaled per edge); None once the kernel changes after the capture.
+TRAFFIC_EDGE64_B_PER_EDGE = 320.0
 
 
 def _peaks():

@@ -44,6 +44,11 @@ FP64_PEAK_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), NVIDIA datasheet fig
 # dram__bytes_write.sum = 144.8 + 8.8 MB on the 480k-edge case of the same
 # workload, scaled per edge); None once the kernel changes after the capture.
 TRAFFIC_EDGE64_B_PER_EDGE = 320.0
+# From the same capture: FP64 pipe busy (sm__pipe_fp64_cycles_active, % of
+# active cycles) and executed FP64 thread instructions (DADD + DFMA + DMUL)
+# per edge of edge_flux_f64.
+NCU_EDGE64_FP64_PIPE_BUSY = 0.886
+NCU_EDGE64_FP64_INSTR_PER_EDGE = 545
 
 
 def _peaks():
@@ -405,6 +410,8 @@ def run_ours(args):
             "peak_probe": round(fp64_probe, 4),
             "frac_of_probe": round(achieved_tf / fp64_probe, 4),
             "flop_per_edge": FLOP_EDGE64,
+            "ncu_fp64_pipe_busy": NCU_EDGE64_FP64_PIPE_BUSY,
+            "ncu_fp64_instr_per_edge": NCU_EDGE64_FP64_INSTR_PER_EDGE,
             "avg_launch_ms": round(edge_avg_ms, 4),
             "share_of_step": round(edge_ms / ms64, 4) if ms64 > 0 else None,
             "div_kernel": {"avg_launch_ms": round(div_avg_ms, 4),

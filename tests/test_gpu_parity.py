@@ -221,3 +221,52 @@ def test_fast_rsqrt_within_two_ulp_of_exact():
     want = (1 / np.sqrt(xl)).astype(np.float64)
     ulp = np.abs(y - want) / np.spacing(want)
     assert ulp.max() <= 2.0
+
+
+def test_four_million_vertex_mesh_sampled_parity_and_free_stream():
+    """The largest case of the suite: a 2000 x 2000 torus lattice (4M vertices,
+    12M edges, ~290M divergence entries with 64-bit offsets).  Sampled FP64
+    parity with the oracle, and free-stream preservation on the whole mesh
+    (a property that holds at any size)."""
+    m, w0 = inputs.vortex_case(2000, seed=1011)
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0)
+    assert M.ne == 3 * m.nv
+    M.set_state(w0)
+    got = M.residual(64)
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly)
+    rng = np.random.default_rng(11)
+    mask = np.zeros(m.nv, np.uint8)
+    mask[rng.choice(m.nv, 1000, replace=False)] = 1
+    mask[np.argsort(-np.abs(w0[:, 1] / w0[:, 0] - 1.0))[:300]] = 1
+    want = om.residual(w0, mask=mask)
+    sel = mask.astype(bool)
+    for k in range(4):
+        assert rel_l2(got[sel, k], want[sel, k]) <= 1e-12
+    one = np.ones(m.nv)
+    M.set_state(inputs.primitive_to_conservative(1.3 * one, 0.7 * one, -0.4 * one, 2.1 * one))
+    assert np.abs(M.residual(64)).max() < 1e-10
+    assert np.abs(M.residual(32)).max() < 1e-2
+
+
+@pytest.mark.parametrize("n", [6, 7])
+def test_smallest_meshes(n):
+    """36 and 49 vertices: less than two SELL slices, a single partial
+    edge block, 1D stencils that wrap around the whole torus."""
+    m, w0 = inputs.vortex_case(n, seed=3)
+    M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0)
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly)
+    M.set_state(w0)
+    got = M.residual(64)
+    want = om.residual(w0)
+    for k in range(4):
+        assert rel_l2(got[:, k], want[:, k]) <= 1e-12
+    dt = M.max_dt(0.5)
+    M.rk_steps(dt, 3, 64)
+    w = w0.copy()
+    for _ in range(3):
+        w = om.rk3_step(w, dt)
+    got = M.get_state()
+    for k in range(4):
+        assert rel_l2(got[:, k] - w0[:, k], w[:, k] - w0[:, k]) <= 1e-12
+    M.rk_steps(dt, 0, 64)  # zero steps: a no-op
+    assert np.array_equal(M.get_state(), got)

@@ -76,7 +76,8 @@ struct fdu_mesh {
     double *r64 = nullptr;                                  // [ne_act][4]
     float4 *r32 = nullptr;                                  // [ne_act]
     unsigned long long *counters = nullptr;  // [0] fallbacks, [1] dt slot, [2] adaptive slot, [3] adaptive steps,
-                                             // [4] stage updates scaled by the positivity safeguard
+                                             // [4] stage updates scaled by the positivity safeguard,
+                                             // [5] first non-physical row of a state being set
     double *tstate = nullptr;                // adaptive stepping: (t, dt, nonphysical flag)
     bool f64_valid = false, f32_valid = false;              // F64[0] / (w32, F32[0]) describe wn
     cudaStream_t own_stream = nullptr;
@@ -265,8 +266,8 @@ fdu_status upload_tables(fdu_mesh *m) {
     if ((st = m->alloc(m->w32, nv))) return st;
     if ((st = m->alloc(m->r64, 4 * ne))) return st;
     if ((st = m->alloc(m->r32, ne))) return st;
-    if ((st = m->alloc(m->counters, 5))) return st;
-    CK(cudaMemset(m->counters, 0, 5 * sizeof(unsigned long long)));
+    if ((st = m->alloc(m->counters, 6))) return st;
+    CK(cudaMemset(m->counters, 0, 6 * sizeof(unsigned long long)));
     {
         const unsigned long long inf_bits = 0x7FF0000000000000ull;
         CK(cudaMemcpy(m->counters + 2, &inf_bits, sizeof inf_bits, cudaMemcpyHostToDevice));
@@ -753,16 +754,21 @@ fdu_status fdu_set_state(fdu_mesh *m, const double *w, int on_device, void *stre
         launch_permute_rows(w, m->wn, m->new2old, m->nv, true, s);
         CK_LAUNCH();
     } else {
-        std::vector<double> h(4 * m->nv);
-        for (int64_t i = 0; i < m->nv; ++i) {
-            const double *src = w + 4 * (int64_t)m->T.v_new2old[i];
-            if (!(src[0] > 0) || !std::isfinite(src[1]) || !std::isfinite(src[2]) || !std::isfinite(src[3]))
-                return set_err(FDU_ERR_NONPHYSICAL, "state row " + std::to_string(m->T.v_new2old[i]) +
-                                                        " has rho <= 0 or a non-finite value");
-            std::memcpy(&h[4 * i], src, 4 * sizeof(double));
-        }
-        CK(cudaMemcpyAsync(m->wn, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        // one copy of the caller's rows (a DMA when they are pinned), checked
+        // and permuted to the internal order on the device; on a non-physical
+        // row the state is left as it was
+        const unsigned long long none = ~0ull;
+        unsigned long long bad = none;
+        CK(cudaMemcpyAsync(m->counters + 5, &none, sizeof none, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(m->scratch, w, 4 * m->nv * sizeof(double), cudaMemcpyHostToDevice, s));
+        launch_check_rows(m->scratch, m->nv, m->counters + 5, s);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(&bad, m->counters + 5, sizeof bad, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        if (bad != none)
+            return set_err(FDU_ERR_NONPHYSICAL, "state row " + std::to_string(bad) + " has rho <= 0 or a non-finite value");
+        launch_permute_rows(m->scratch, m->wn, m->new2old, m->nv, true, s);
+        CK_LAUNCH();
     }
     if (m->n_ghost > 0) {
         launch_ghost_fill(m->wn, nullptr, nullptr, nullptr, 0, nullptr, m->donor, m->n_real, m->n_ghost, s);

@@ -563,6 +563,15 @@ __global__ void stage_persistent_kernel(EdgeArgs EA, DivArgs DA, unsigned int *b
 }
 
 // ------------------------------------------------------------------ support kernels
+// Smallest row index whose state has rho <= 0 (or NaN) or a non-finite
+// momentum or energy (set_state's physical check).
+__global__ void check_rows_kernel(const double *__restrict__ w, int64_t n, unsigned long long *bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const dbl4 s = ld4(w, i);
+    if (!(s.x > 0.0) || !isfinite(s.y) || !isfinite(s.z) || !isfinite(s.w)) atomicMin(bad, (unsigned long long)i);
+}
+
 __global__ void permute_rows_kernel(const double *__restrict__ in, double *__restrict__ out,
                                     const int32_t *__restrict__ map, int64_t n, bool gather) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -694,6 +703,9 @@ void launch_div_f32(const DivArgs &a, int mode, cudaStream_t s) {
         case 2: div_f32_kernel<2><<<g, kDivBlock, 0, s>>>(a); break;
         default: div_f32_kernel<3><<<g, kDivBlock, 0, s>>>(a); break;
     }
+}
+void launch_check_rows(const double *w, int64_t n, unsigned long long *bad, cudaStream_t s) {
+    if (n > 0) check_rows_kernel<<<blocks(n, 256), 256, 0, s>>>(w, n, bad);
 }
 void launch_permute_rows(const double *in, double *out, const int32_t *map, int64_t n, bool gather, cudaStream_t s) {
     if (n > 0) permute_rows_kernel<<<blocks(n, 256), 256, 0, s>>>(in, out, map, n, gather);

@@ -63,6 +63,8 @@ void launch_edge_flux_f64(const EdgeArgs &a, cudaStream_t s);
 void launch_edge_flux_f32(const EdgeArgs &a, cudaStream_t s);
 void launch_div_f64(const DivArgs &a, int mode, cudaStream_t s);
 void launch_div_f32(const DivArgs &a, int mode, cudaStream_t s);
+// *bad = min(*bad, first row of w[n][4] with rho <= 0 or a non-finite value)
+void launch_check_rows(const double *w, int64_t n, unsigned long long *bad, cudaStream_t s);
 void launch_permute_rows(const double *in, double *out, const int32_t *map, int64_t n, bool gather, cudaStream_t s);
 void launch_ghost_fill(double *w, const double *wsrc, void *F, const void *Fsrc, int fq, float4 *w32,
                        const int32_t *donor, int64_t n_real, int64_t n_ghost, cudaStream_t s);

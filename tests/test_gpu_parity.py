@@ -146,11 +146,19 @@ def test_rk_f32_state_error(c40):
 
 
 def test_nonphysical_state_rejected(c40):
+    c40.M.set_state(c40.w0)
     bad = c40.w0.copy()
     bad[17, 0] = -1.0
+    bad[400, 3] = np.inf
     with pytest.raises(fdu.FduError) as e:
         c40.M.set_state(bad)
     assert e.value.status == -7
+    assert "row 17 " in str(e.value)
+    assert np.array_equal(c40.M.get_state(), c40.w0)  # the state is left as it was
+    # pinned host buffers go through the same path
+    pinned = torch.from_numpy(c40.w0.copy()).pin_memory()
+    c40.M.set_state(pinned.numpy())
+    assert np.array_equal(c40.M.get_state(), c40.w0)
 
 
 def test_shock_fallback_counts_match_oracle():

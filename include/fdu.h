@@ -91,8 +91,12 @@ typedef struct fdu_mesh_info {
     int64_t table_bytes_f32; /* bytes of the FP32 residual's read-only tables */
     int32_t sell_width;      /* SELL slice width of the divergence tables */
     int32_t pad0;
-    int64_t sell_vert_nnz;   /* vertex entries stored in the SELL tables, padding included (0 for host-only meshes) */
-    int64_t sell_edge_nnz;   /* edge entries stored in the SELL tables, padding included */
+    int64_t sell_vert_nnz;   /* vertex entries stored in the FP32 SELL tables (natural vertex order), padding
+                                included (0 for host-only meshes) */
+    int64_t sell_edge_nnz;   /* edge entries stored in the FP32 SELL tables, padding included */
+    int64_t sell_vert_nnz64; /* the same for the FP64 SELL tables, whose slices take the vertices of each window
+                                of 256 by decreasing stencil size */
+    int64_t sell_edge_nnz64;
 } fdu_mesh_info;
 
 /* Library version string and thread-local last error message. */

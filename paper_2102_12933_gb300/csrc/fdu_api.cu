@@ -10,6 +10,7 @@
 #include <new>
 #include <tuple>
 #include <string>
+#include <numeric>
 #include <vector>
 
 #include "fdu.h"
@@ -53,14 +54,16 @@ struct fdu_mesh {
     fdu_mesh_opts opts{};
     int device = -1;
     int64_t nv = 0, n_real = 0, n_ghost = 0, ne_act = 0, nslice = 0;
-    int64_t vert_nnz_sell = 0, edge_nnz_sell = 0;
+    int64_t vert_nnz_sell = 0, edge_nnz_sell = 0, vert_nnz_sell64 = 0, edge_nnz_sell64 = 0;
     int64_t device_bytes = 0, table_bytes_f64 = 0, table_bytes_f32 = 0;
     std::vector<void *> allocs;
     // tables
     int32_t *sten = nullptr;          // [6][ne_act]
     double *coef64 = nullptr;         // [32][ne_act]
     float *coef32 = nullptr;          // [32][ne_act]
-    int64_t *slice_voff = nullptr, *slice_eoff = nullptr;
+    int64_t *slice_voff = nullptr, *slice_eoff = nullptr;       // FP32 layout (natural order)
+    int64_t *slice_voff64 = nullptr, *slice_eoff64 = nullptr;   // FP64 layout (stencil-size order in windows)
+    int32_t *svid64 = nullptr, *seid64 = nullptr, *perm64 = nullptr;
     int32_t *svid = nullptr, *seid = nullptr;
     double *swf64 = nullptr, *swg64 = nullptr, *swe64 = nullptr, *cfg64 = nullptr;
     float *swf32 = nullptr, *swg32 = nullptr, *swe32 = nullptr, *cfg32 = nullptr;
@@ -178,71 +181,119 @@ fdu_status upload_tables(fdu_mesh *m) {
     if ((st = m->upload(m->sten, sten))) return st;
     if ((st = m->upload(m->coef64, coef))) return st;
     if ((st = m->upload(m->coef32, coef32))) return st;
-    // divergence tables, SELL-32 over internal real vertices
+    // divergence tables, SELL-32 over internal real vertices: position i of
+    // a slice order holds vertex order[i]; entry j of lane l at off + 32 j + l
     m->nslice = (nr + kSell - 1) / kSell;
-    std::vector<int64_t> svo(m->nslice + 1, 0), seo(m->nslice + 1, 0);
-    for (int64_t s = 0; s < m->nslice; ++s) {
-        int64_t mj = 0, mk = 0;
-        for (int64_t v = s * kSell; v < std::min(nr, (s + 1) * kSell); ++v) {
-            const int64_t o = T.v_new2old[v];
-            mj = std::max(mj, T.voff[o + 1] - T.voff[o]);
-            mk = std::max(mk, T.eoff[o + 1] - T.eoff[o]);
+    struct Sell {
+        std::vector<int64_t> svo, seo;
+        std::vector<int32_t> vid, eid;
+        std::vector<double> wf, wg, we;
+    };
+    auto build_sell = [&](const std::vector<int32_t> &order, Sell &S) {
+        S.svo.assign(m->nslice + 1, 0);
+        S.seo.assign(m->nslice + 1, 0);
+        for (int64_t sl = 0; sl < m->nslice; ++sl) {
+            int64_t mj = 0, mk = 0;
+            for (int64_t i = sl * kSell; i < std::min(nr, (sl + 1) * kSell); ++i) {
+                const int64_t o = T.v_new2old[order[i]];
+                mj = std::max(mj, T.voff[o + 1] - T.voff[o]);
+                mk = std::max(mk, T.eoff[o + 1] - T.eoff[o]);
+            }
+            S.svo[sl + 1] = S.svo[sl] + mj * kSell;
+            S.seo[sl + 1] = S.seo[sl] + mk * kSell;
         }
-        svo[s + 1] = svo[s] + mj * kSell;
-        seo[s + 1] = seo[s] + mk * kSell;
-    }
-    m->vert_nnz_sell = svo[m->nslice];
-    m->edge_nnz_sell = seo[m->nslice];
-    std::vector<int32_t> vid(m->vert_nnz_sell, 0), eid(m->edge_nnz_sell, 0);
-    std::vector<double> wf(m->vert_nnz_sell, 0.0), wg(m->vert_nnz_sell, 0.0), we(m->edge_nnz_sell, 0.0);
+        S.vid.assign(S.svo[m->nslice], 0);
+        S.eid.assign(S.seo[m->nslice], 0);
+        S.wf.assign(S.svo[m->nslice], 0.0);
+        S.wg.assign(S.svo[m->nslice], 0.0);
+        S.we.assign(S.seo[m->nslice], 0.0);
+        for (int64_t i = 0; i < nr; ++i) {
+            const int32_t v = order[i];
+            const int64_t o = T.v_new2old[v], sl = i / kSell, lane = i % kSell;
+            const int64_t J = T.voff[o + 1] - T.voff[o], K = T.eoff[o + 1] - T.eoff[o];
+            const int64_t mj = (S.svo[sl + 1] - S.svo[sl]) / kSell, mk = (S.seo[sl + 1] - S.seo[sl]) / kSell;
+            for (int64_t j = 0; j < mj; ++j) {
+                const int64_t p = S.svo[sl] + j * kSell + lane;
+                if (j < J) {
+                    const int64_t q = T.voff[o] + j;
+                    S.vid[p] = T.v_old2new[T.vid[q]];
+                    S.wf[p] = T.wf[q];
+                    S.wg[p] = T.wg[q];
+                } else {
+                    S.vid[p] = v;  // padding: weight 0 on the vertex itself
+                }
+            }
+            for (int64_t k = 0; k < mk; ++k) {
+                const int64_t p = S.seo[sl] + k * kSell + lane;
+                if (k < K) {
+                    const int64_t q = T.eoff[o] + k;
+                    S.eid[p] = T.e_old2new[T.eid[q]];
+                    S.we[p] = T.we[q];
+                } else {
+                    S.eid[p] = K > 0 ? T.e_old2new[T.eid[T.eoff[o]]] : 0;
+                }
+            }
+        }
+    };
+    // centre weights per vertex
     std::vector<double> cfg(2 * std::max<int64_t>(nr, 1), 0.0);
     for (int64_t v = 0; v < nr; ++v) {
-        const int64_t o = T.v_new2old[v], s = v / kSell, lane = v % kSell;
-        const int64_t J = T.voff[o + 1] - T.voff[o], K = T.eoff[o + 1] - T.eoff[o];
-        const int64_t mj = (svo[s + 1] - svo[s]) / kSell, mk = (seo[s + 1] - seo[s]) / kSell;
+        const int64_t o = T.v_new2old[v];
         double sf = 0, sg = 0, sx = 0, sy = 0;
-        for (int64_t j = 0; j < mj; ++j) {
-            const int64_t p = svo[s] + j * kSell + lane;
-            if (j < J) {
-                const int64_t q = T.voff[o] + j;
-                vid[p] = T.v_old2new[T.vid[q]];
-                wf[p] = T.wf[q];
-                wg[p] = T.wg[q];
-                sf += T.wf[q];
-                sg += T.wg[q];
-            } else {
-                vid[p] = (int32_t)v;  // padding: weight 0 on the vertex itself
-            }
+        for (int64_t q = T.voff[o]; q < T.voff[o + 1]; ++q) {
+            sf += T.wf[q];
+            sg += T.wg[q];
         }
-        for (int64_t k = 0; k < mk; ++k) {
-            const int64_t p = seo[s] + k * kSell + lane;
-            if (k < K) {
-                const int64_t q = T.eoff[o] + k;
-                const int32_t e = T.eid[q];
-                eid[p] = T.e_old2new[e];
-                we[p] = T.we[q];
-                sx += T.we[q] * T.nrm[2 * e];
-                sy += T.we[q] * T.nrm[2 * e + 1];
-            } else {
-                eid[p] = K > 0 ? T.e_old2new[T.eid[T.eoff[o]]] : 0;
-            }
+        for (int64_t q = T.eoff[o]; q < T.eoff[o + 1]; ++q) {
+            const int32_t e = T.eid[q];
+            sx += T.we[q] * T.nrm[2 * e];
+            sy += T.we[q] * T.nrm[2 * e + 1];
         }
         cfg[v] = -(sf + sx);
         cfg[nr + v] = -(sg + sy);
     }
-    if ((st = m->upload(m->slice_voff, svo))) return st;
-    if ((st = m->upload(m->slice_eoff, seo))) return st;
-    if ((st = m->upload(m->svid, vid))) return st;
-    if ((st = m->upload(m->seid, eid))) return st;
-    if ((st = m->upload(m->swf64, wf))) return st;
-    if ((st = m->upload(m->swg64, wg))) return st;
-    if ((st = m->upload(m->swe64, we))) return st;
-    if ((st = m->upload(m->cfg64, cfg))) return st;
+    // FP32: natural (Hilbert) order, which keeps the flux gathers of a warp
+    // local; FP64: inside windows of 256 positions the vertices are sorted
+    // by decreasing stencil size, so a slice's lanes have nearly equal entry
+    // counts and little padding (the FP64 loops are bound by the FP64 pipe,
+    // which padding entries occupy like real ones)
+    std::vector<int32_t> natural(std::max<int64_t>(nr, 1)), sorted;
+    std::iota(natural.begin(), natural.end(), 0);
+    sorted = natural;
+    for (int64_t w0 = 0; w0 < nr; w0 += 256) {
+        const int64_t w1 = std::min<int64_t>(nr, w0 + 256);
+        std::stable_sort(sorted.begin() + w0, sorted.begin() + w1, [&](int32_t x, int32_t y) {
+            const int64_t ox = T.v_new2old[x], oy = T.v_new2old[y];
+            const int64_t jx = T.voff[ox + 1] - T.voff[ox], jy = T.voff[oy + 1] - T.voff[oy];
+            if (jx != jy) return jx > jy;
+            return T.eoff[ox + 1] - T.eoff[ox] > T.eoff[oy + 1] - T.eoff[oy];
+        });
+    }
+    Sell S32, S64;
+    build_sell(natural, S32);
+    build_sell(sorted, S64);
+    m->vert_nnz_sell = S32.svo[m->nslice];
+    m->edge_nnz_sell = S32.seo[m->nslice];
+    m->vert_nnz_sell64 = S64.svo[m->nslice];
+    m->edge_nnz_sell64 = S64.seo[m->nslice];
+    if ((st = m->upload(m->slice_voff, S32.svo))) return st;
+    if ((st = m->upload(m->slice_eoff, S32.seo))) return st;
+    if ((st = m->upload(m->svid, S32.vid))) return st;
+    if ((st = m->upload(m->seid, S32.eid))) return st;
     auto to32 = [](const std::vector<double> &a) { return std::vector<float>(a.begin(), a.end()); };
-    if ((st = m->upload(m->swf32, to32(wf)))) return st;
-    if ((st = m->upload(m->swg32, to32(wg)))) return st;
-    if ((st = m->upload(m->swe32, to32(we)))) return st;
+    if ((st = m->upload(m->swf32, to32(S32.wf)))) return st;
+    if ((st = m->upload(m->swg32, to32(S32.wg)))) return st;
+    if ((st = m->upload(m->swe32, to32(S32.we)))) return st;
     if ((st = m->upload(m->cfg32, to32(cfg)))) return st;
+    if ((st = m->upload(m->slice_voff64, S64.svo))) return st;
+    if ((st = m->upload(m->slice_eoff64, S64.seo))) return st;
+    if ((st = m->upload(m->svid64, S64.vid))) return st;
+    if ((st = m->upload(m->seid64, S64.eid))) return st;
+    if ((st = m->upload(m->swf64, S64.wf))) return st;
+    if ((st = m->upload(m->swg64, S64.wg))) return st;
+    if ((st = m->upload(m->swe64, S64.we))) return st;
+    if ((st = m->upload(m->cfg64, cfg))) return st;
+    if ((st = m->upload(m->perm64, sorted))) return st;
     if ((st = m->upload(m->new2old, T.v_new2old))) return st;
     std::vector<int32_t> donor(std::max<int64_t>(m->n_ghost, 1), 0);
     for (int64_t i = 0; i < m->n_ghost; ++i) donor[i] = T.v_old2new[T.ghost[T.v_new2old[nr + i]]];
@@ -250,10 +301,12 @@ fdu_status upload_tables(fdu_mesh *m) {
     std::vector<double> hm(std::max<int64_t>(nr, 1), 0.0);
     for (int64_t v = 0; v < nr; ++v) hm[v] = T.hmin[T.v_new2old[v]];
     if ((st = m->upload(m->hmin, hm))) return st;
-    m->table_bytes_f64 = (int64_t)(sten.size() * 4 + coef.size() * 8 + (svo.size() + seo.size()) * 8 + vid.size() * 4 +
-                                   eid.size() * 4 + (wf.size() + wg.size() + we.size() + cfg.size()) * 8);
-    m->table_bytes_f32 = (int64_t)(sten.size() * 4 + coef32.size() * 4 + (svo.size() + seo.size()) * 8 +
-                                   vid.size() * 4 + eid.size() * 4 + (wf.size() + wg.size() + we.size() + cfg.size()) * 4);
+    m->table_bytes_f64 = (int64_t)(sten.size() * 4 + coef.size() * 8 + (S64.svo.size() + S64.seo.size()) * 8 +
+                                   S64.vid.size() * 4 + S64.eid.size() * 4 + sorted.size() * 4 +
+                                   (S64.wf.size() + S64.wg.size() + S64.we.size() + cfg.size()) * 8);
+    m->table_bytes_f32 = (int64_t)(sten.size() * 4 + coef32.size() * 4 + (S32.svo.size() + S32.seo.size()) * 8 +
+                                   S32.vid.size() * 4 + S32.eid.size() * 4 +
+                                   (S32.wf.size() + S32.wg.size() + S32.we.size() + cfg.size()) * 4);
     // state and work buffers
     if ((st = m->alloc(m->wn, 4 * nv))) return st;
     if ((st = m->alloc(m->ws, 4 * nv))) return st;
@@ -303,6 +356,11 @@ DivArgs div_args(fdu_mesh *m, int prec, int fin) {
     a.vid = m->svid;
     a.eid = m->seid;
     if (prec == 64) {
+        a.slice_voff = m->slice_voff64;
+        a.slice_eoff = m->slice_eoff64;
+        a.vid = m->svid64;
+        a.eid = m->seid64;
+        a.perm = m->perm64;
         a.wf = m->swf64; a.wg = m->swg64; a.we = m->swe64; a.cfg = m->cfg64;
         a.F = m->F64[fin]; a.r = m->r64;
     } else {
@@ -708,6 +766,8 @@ fdu_status fdu_mesh_info_get(const fdu_mesh *m, fdu_mesh_info *out) {
     out->sell_width = kSell;
     out->sell_vert_nnz = m->vert_nnz_sell;
     out->sell_edge_nnz = m->edge_nnz_sell;
+    out->sell_vert_nnz64 = m->vert_nnz_sell64;
+    out->sell_edge_nnz64 = m->edge_nnz_sell64;
     return FDU_OK;
 }
 

@@ -150,10 +150,12 @@ __device__ __forceinline__ dbl4 forward_euler(const dbl4 &ws, const dbl4 &L, dou
 }
 
 // ------------------------------------------------------------------ FP64 divergence (+ RK stage)
+// Position i of the SELL tables; the vertex it holds is A.perm[i].
 template <int MODE>
-__device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t v) {
-    const int64_t sl = v / kSell;
-    const int lane = (int)(v % kSell);
+__device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) {
+    const int64_t sl = i / kSell;
+    const int lane = (int)(i % kSell);
+    const int64_t v = A.perm ? (int64_t)__ldg(A.perm + i) : i;
     const double *__restrict__ F = static_cast<const double *>(A.F);
     const double *__restrict__ r = static_cast<const double *>(A.r);
     const double *__restrict__ wf = static_cast<const double *>(A.wf);

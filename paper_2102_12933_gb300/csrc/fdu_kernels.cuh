@@ -29,6 +29,7 @@ struct DivArgs {
     int64_t n_real;              // vertices with a residual (internal ids 0..n_real-1)
     const int64_t *slice_voff;   // [nslice+1] start of each slice's vertex entries
     const int64_t *slice_eoff;   // [nslice+1]
+    const int32_t *perm;         // [n_real] vertex at each SELL position (nullptr = position i is vertex i)
     const int32_t *vid;          // vertex entries (SELL: entry j of lane l at off + 32 j + l)
     const void *wf, *wg;         // weights of f_j and g_j
     const int32_t *eid;          // edge entries

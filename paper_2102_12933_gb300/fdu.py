@@ -62,6 +62,7 @@ class MeshInfo(C.Structure):
         ("device_bytes", C.c_int64), ("table_bytes_f64", C.c_int64), ("table_bytes_f32", C.c_int64),
         ("sell_width", C.c_int32), ("pad0", C.c_int32),
         ("sell_vert_nnz", C.c_int64), ("sell_edge_nnz", C.c_int64),
+        ("sell_vert_nnz64", C.c_int64), ("sell_edge_nnz64", C.c_int64),
     ]
 
     def as_dict(self):

@@ -186,5 +186,27 @@ __device__ __forceinline__ void weno_pair64(const double *k, double a, double b,
 }
 
 
+// The forward kernel's form of weno_pair64 (the adjoint keeps the one above,
+// which its reverse sweep differentiates): the middle linear weights are 1
+// (the block stores C_0/C_1, 1, C_2/C_1), and the right increments are taken
+// from L1 instead of R1 (S_d's value shifted by +c), so that
+// w_R = L1 + R dr: sum r_k (v_k - c) / sum r_k + c = sum r_k v_k' / sum r_k.
+__device__ __forceinline__ void weno_pair64_l1(const double *k, double a, double b, double c, double d, double e,
+                                               double f, double eps, double &dl, double &dr) {
+    const double va = fma(k[0], a, k[1] * b), pa = fma(k[2], a, k[3] * b), qa = fma(k[4], a, k[5] * b);
+    const double vb = fma(k[6], b, k[7] * c), pb = fma(k[8], b, k[9] * c), qb = fma(k[10], b, k[11] * c);
+    const double vc = fma(k[12], c, k[13] * d), pc = fma(k[14], c, k[15] * d), qc = fma(k[16], c, k[17] * d);
+    const double vd = fma(k[18], e, k[19] * f), pd = fma(k[20], e, k[21] * f), qd = fma(k[22], e, k[23] * f);
+    const double ba = fma(pa, pa, fma(qa, qa, eps));
+    const double bb = fma(pb, pb, fma(qb, qb, eps));
+    const double bc = fma(pc, pc, fma(qc, qc, eps));
+    const double bd = fma(pd, pd, fma(qd, qd, eps));
+    const double bbc = bb * bc;
+    const double l0 = k[24] * bbc, l1 = ba * bc, l2 = k[26] * (ba * bb);
+    dl = fma(l0, va, fma(l1, vb, l2 * vc)) * recip64_fast(l0 + l1 + l2);
+    const double r0 = k[27] * bbc, r1 = bd * bb, r2 = k[29] * (bd * bc);
+    dr = fma(r0, vd + c, fma(r1, vc, r2 * vb)) * recip64_fast(r0 + r1 + r2);
+}
+
 }  // namespace dev
 }  // namespace fdu

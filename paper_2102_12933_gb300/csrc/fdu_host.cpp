@@ -627,9 +627,11 @@ int build_host_tables(const double *xy, int64_t nv, const CellList &cells, int a
             put(6, L, 1);   // S_b
             put(12, L, 2);  // S_c
             put(18, R, 0);  // S_d
+            // linear weights divided by the middle one (C_1 > 0 on ordered points):
+            // the nonlinear weights are invariant to a common factor of the C_k
             for (int i = 0; i < 3; ++i) {
-                c[24 + i] = L[18 + i];
-                c[27 + i] = R[18 + i];
+                c[24 + i] = i == 1 ? 1.0 : L[18 + i] / L[19];
+                c[27 + i] = i == 1 ? 1.0 : R[18 + i] / R[19];
             }
             c[30] = T.nrm[2 * k];
             c[31] = T.nrm[2 * k + 1];

@@ -26,7 +26,7 @@ constexpr int kSideCoef = 21;
 // value, slope and curvature coefficients (2 each) of two differences:
 //   [0..5]   S_a of (L3-L1, L2-L1)      [6..11]  S_b of (L2-L1, R1-L1)
 //   [12..17] S_c of (R1-L1, R2-L1)      [18..23] S_d of (R3-R1, R2-R1)
-//   [24..26] C_0..2 of the left state   [27..29] C_0..2 of the right state
+//   [24..26] C_0/C_1, 1, C_2/C_1 of the left state   [27..29] the same of the right state
 //   [30..31] n_x, n_y
 constexpr int kEdgeCoef = 32;
 

@@ -56,13 +56,14 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
     for (int i = 0; i < 30; ++i) k[i] = __ldg(coef + (int64_t)i * ne + e);
     const dbl4 cR2L = add4(cR2, cM);  // R2 - L1
     dbl4 dl, dr;
-    weno_pair64(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps, dl.x, dr.x);
-    weno_pair64(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps, dl.y, dr.y);
-    weno_pair64(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps, dl.z, dr.z);
-    weno_pair64(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps, dl.w, dr.w);
+    weno_pair64_l1(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps, dl.x, dr.x);
+    weno_pair64_l1(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps, dl.y, dr.y);
+    weno_pair64_l1(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps, dl.z, dr.z);
+    weno_pair64_l1(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps, dl.w, dr.w);
 
+    // both interpolated states from L1 (R (R1 - L1)_char = R1 - L1)
     dbl4 wl = add4(L1, unproject64(C, dl));
-    dbl4 wr = add4(R1, unproject64(C, dr));
+    dbl4 wr = add4(L1, unproject64(C, dr));
     Prim64 pl, pr;
     bool ok = wl.x > 0.0 && wr.x > 0.0;
     if (ok) {
@@ -78,22 +79,25 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
         atomicAdd(A.fallback, 1ull);
     }
 
-    // Roe flux with Harten's entropy fix (delta = 0.1 c)
+    // Roe flux with Harten's entropy fix (delta = 0.1 c), in the one-sided
+    // form F_L + R diag((lambda - |lambda|)/2) L (w_R - w_L): equal to
+    // (F_L + F_R)/2 - R |Lambda| L (w_R - w_L)/2 because the Roe matrix
+    // satisfies F_R - F_L = R Lambda L (w_R - w_L)
     const Roe64 Q = roe64(wl, pl, wr, pr, nx, ny, gm1);
     const dbl4 a = project64(Q, sub4(wr, wl));
     const double delta = 0.1 * Q.c, h2d = 5.0 * Q.ic;  // 1 / (2 delta)
-    auto fix = [&](double l) {
+    auto neg = [&](double l) {  // (l - |l|_fixed) / 2
         const double m = fabs(l);
-        return m < delta ? fma(l, l, delta * delta) * h2d : m;
+        return 0.5 * (l - (m < delta ? fma(l, l, delta * delta) * h2d : m));
     };
-    const double lu = fix(Q.qn), lm = fix(Q.qn - Q.c), lp = fix(Q.qn + Q.c);
-    const dbl4 D = unproject64(Q, dbl4_make(lm * a.x, lu * a.y, lu * a.z, lp * a.w));
-    const double qnl = (wl.y * nx + wl.z * ny) * pl.ir, qnr = (wr.y * nx + wr.z * ny) * pr.ir;
+    const double nu = neg(Q.qn), nm = neg(Q.qn - Q.c), np = neg(Q.qn + Q.c);
+    const dbl4 D = unproject64(Q, dbl4_make(nm * a.x, nu * a.y, nu * a.z, np * a.w));
+    const double qnl = (wl.y * nx + wl.z * ny) * pl.ir;
     dbl4 f;
-    f.x = 0.5 * (wl.x * qnl + wr.x * qnr - D.x);
-    f.y = 0.5 * (fma(wl.y, qnl, pl.p * nx) + fma(wr.y, qnr, pr.p * nx) - D.y);
-    f.z = 0.5 * (fma(wl.z, qnl, pl.p * ny) + fma(wr.z, qnr, pr.p * ny) - D.z);
-    f.w = 0.5 * ((wl.w + pl.p) * qnl + (wr.w + pr.p) * qnr - D.w);
+    f.x = fma(wl.x, qnl, D.x);
+    f.y = fma(wl.y, qnl, fma(pl.p, nx, D.y));
+    f.z = fma(wl.z, qnl, fma(pl.p, ny, D.z));
+    f.w = fma(wl.w + pl.p, qnl, D.w);
     st4(static_cast<double *>(A.r), e, f);
 }
 
@@ -302,10 +306,12 @@ __device__ __forceinline__ void weno_pair32(const float *k, float a, float b, fl
     const float ib = rcp32(fmaf(pb, pb, fmaf(qb, qb, eps)));
     const float ic = rcp32(fmaf(pc, pc, fmaf(qc, qc, eps)));
     const float id = rcp32(fmaf(pd, pd, fmaf(qd, qd, eps)));
-    const float l0 = k[24] * ia, l1 = k[25] * ib, l2 = k[26] * ic;
+    // middle linear weights are 1 (the block stores C_0/C_1, 1, C_2/C_1);
+    // right increments from L1 (S_d's value shifted by +c), as in the FP64 kernel
+    const float l0 = k[24] * ia, l1 = ib, l2 = k[26] * ic;
     dl = fmaf(l0, va, fmaf(l1, vb, l2 * vc)) * rcp32(l0 + l1 + l2);
-    const float r0 = k[27] * id, r1 = k[28] * ic, r2 = k[29] * ib;
-    dr = fmaf(r0, vd, fmaf(r1, vc - c, r2 * (vb - c))) * rcp32(r0 + r1 + r2);
+    const float r0 = k[27] * id, r1 = ic, r2 = k[29] * ib;
+    dr = fmaf(r0, vd + c, fmaf(r1, vc, r2 * vb)) * rcp32(r0 + r1 + r2);
 }
 
 __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int64_t e) {
@@ -345,7 +351,7 @@ __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int6
     weno_pair32(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, eps, dl.w, dr.w);
 
     float4 wl = add4f(L1, unproject32(C, dl));
-    float4 wr = add4f(R1, unproject32(C, dr));
+    float4 wr = add4f(L1, unproject32(C, dr));
     Prim32 pl, pr;
     bool ok = wl.x > 0.f && wr.x > 0.f;
     if (ok) {
@@ -360,21 +366,22 @@ __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int6
         pr = pR1;
         atomicAdd(A.fallback, 1ull);
     }
+    // one-sided Roe flux F_L + R diag((lambda - |lambda|)/2) L (w_R - w_L)
     const Roe32 Q = roe32(wl, pl, wr, pr, nx, ny, gm1);
     const float4 a = project32(Q, sub4f(wr, wl));
     const float delta = 0.1f * Q.c, h2d = 5.0f * Q.ic;
-    auto fix = [&](float l) {
+    auto neg = [&](float l) {
         const float m = fabsf(l);
-        return m < delta ? fmaf(l, l, delta * delta) * h2d : m;
+        return 0.5f * (l - (m < delta ? fmaf(l, l, delta * delta) * h2d : m));
     };
-    const float lu = fix(Q.qn), lm = fix(Q.qn - Q.c), lp = fix(Q.qn + Q.c);
-    const float4 D = unproject32(Q, make_float4(lm * a.x, lu * a.y, lu * a.z, lp * a.w));
-    const float qnl = (wl.y * nx + wl.z * ny) * pl.ir, qnr = (wr.y * nx + wr.z * ny) * pr.ir;
+    const float nu = neg(Q.qn), nm = neg(Q.qn - Q.c), np = neg(Q.qn + Q.c);
+    const float4 D = unproject32(Q, make_float4(nm * a.x, nu * a.y, nu * a.z, np * a.w));
+    const float qnl = (wl.y * nx + wl.z * ny) * pl.ir;
     float4 f;
-    f.x = 0.5f * (wl.x * qnl + wr.x * qnr - D.x);
-    f.y = 0.5f * (fmaf(wl.y, qnl, pl.p * nx) + fmaf(wr.y, qnr, pr.p * nx) - D.y);
-    f.z = 0.5f * (fmaf(wl.z, qnl, pl.p * ny) + fmaf(wr.z, qnr, pr.p * ny) - D.z);
-    f.w = 0.5f * ((wl.w + pl.p) * qnl + (wr.w + pr.p) * qnr - D.w);
+    f.x = fmaf(wl.x, qnl, D.x);
+    f.y = fmaf(wl.y, qnl, fmaf(pl.p, nx, D.y));
+    f.z = fmaf(wl.z, qnl, fmaf(pl.p, ny, D.z));
+    f.w = fmaf(wl.w + pl.p, qnl, D.w);
     static_cast<float4 *>(A.r)[e] = f;
 }
 

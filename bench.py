@@ -41,14 +41,14 @@ FLOP_DIV64_PER_EENTRY = 8
 FLOP_DIV64_FIXED = 70
 FP64_PEAK_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), NVIDIA datasheet figure
 # DRAM bytes per edge of edge_flux_f64 from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum = 144.8 + 8.8 MB on the 480k-edge case of the same
+# dram__bytes_write.sum = 137.1 + 7.8 MB on the 480k-edge case of the same
 # workload, scaled per edge); None once the kernel changes after the capture.
-TRAFFIC_EDGE64_B_PER_EDGE = 320.0
+TRAFFIC_EDGE64_B_PER_EDGE = 302.0
 # From the same capture: FP64 pipe busy (sm__pipe_fp64_cycles_active, % of
 # active cycles) and executed FP64 thread instructions (DADD + DFMA + DMUL)
 # per edge of edge_flux_f64.
-NCU_EDGE64_FP64_PIPE_BUSY = 0.886
-NCU_EDGE64_FP64_INSTR_PER_EDGE = 545
+NCU_EDGE64_FP64_PIPE_BUSY = 0.888
+NCU_EDGE64_FP64_INSTR_PER_EDGE = 520
 
 
 def _peaks():

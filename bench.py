@@ -35,7 +35,7 @@ N_LATTICE = 500  # 250,000 vertices
 CFL = 0.5
 # FP64 operations per edge of the edge-flux kernel and per vertex of the
 # divergence + stage kernel (counted from the kernel source; FMA = 2).
-FLOP_EDGE64 = 703
+FLOP_EDGE64 = 672
 FLOP_DIV64_PER_VENTRY = 16
 FLOP_DIV64_PER_EENTRY = 8
 FLOP_DIV64_FIXED = 70

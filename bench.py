@@ -35,20 +35,20 @@ N_LATTICE = 500  # 250,000 vertices
 CFL = 0.5
 # FP64 operations per edge of the edge-flux kernel and per vertex of the
 # divergence + stage kernel (counted from the kernel source; FMA = 2).
-FLOP_EDGE64 = 672
+FLOP_EDGE64 = 648
 FLOP_DIV64_PER_VENTRY = 16
 FLOP_DIV64_PER_EENTRY = 8
 FLOP_DIV64_FIXED = 70
 FP64_PEAK_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), NVIDIA datasheet figure
 # DRAM bytes per edge of edge_flux_f64 from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum = 137.1 + 7.8 MB on the 480k-edge case of the same
+# dram__bytes_write.sum = 121.7 + 6.8 MB on the 480k-edge case of the same
 # workload, scaled per edge); None once the kernel changes after the capture.
-TRAFFIC_EDGE64_B_PER_EDGE = 302.0
+TRAFFIC_EDGE64_B_PER_EDGE = 268.0
 # From the same capture: FP64 pipe busy (sm__pipe_fp64_cycles_active, % of
 # active cycles) and executed FP64 thread instructions (DADD + DFMA + DMUL)
 # per edge of edge_flux_f64.
-NCU_EDGE64_FP64_PIPE_BUSY = 0.888
-NCU_EDGE64_FP64_INSTR_PER_EDGE = 520
+NCU_EDGE64_FP64_PIPE_BUSY = 0.884
+NCU_EDGE64_FP64_INSTR_PER_EDGE = 512
 
 
 def _peaks():
@@ -379,7 +379,7 @@ def run_ours(args):
     vnnz, ennz = info["div_vert_nnz"], info["div_edge_nnz"]
     div_flops = FLOP_DIV64_PER_VENTRY * vnnz + FLOP_DIV64_PER_EENTRY * ennz + FLOP_DIV64_FIXED * nv
     # FP32 kernels are HBM-bound: algorithmic bytes per launch
-    edge32_bytes = ne * (24 + 32 * 4 + 16) + nv * 16
+    edge32_bytes = ne * (24 + 28 * 4 + 16) + nv * 16  # ids, 7 float4 of coefficients, flux; FP32 state once
     div32_bytes = (vnnz * 12 + ennz * 8 + nv * 8) + nv * (32 + 32 + 32 + 32 + 16) + ne * 16 + nv * 32
     hbm = peaks.get("hbm_gbs", 6800.0)
     line = {

@@ -143,46 +143,37 @@ __device__ __forceinline__ void unproject64_vjp(const Roe64 &R, const dbl4 &c, c
 __device__ __forceinline__ void weno_pair64_vjp(const double *k, double a, double b, double c, double d, double e,
                                                 double f, double eps, double dlb, double drb, double &ab, double &bb_,
                                                 double &cb, double &db, double &eb, double &fb) {
-    const double va = fma(k[0], a, k[1] * b), pa = fma(k[2], a, k[3] * b), qa = fma(k[4], a, k[5] * b);
-    const double vb = fma(k[6], b, k[7] * c), pb = fma(k[8], b, k[9] * c), qb = fma(k[10], b, k[11] * c);
-    const double vc = fma(k[12], c, k[13] * d), pc = fma(k[14], c, k[15] * d), qc = fma(k[16], c, k[17] * d);
-    const double vd = fma(k[18], e, k[19] * f), pd = fma(k[20], e, k[21] * f), qd = fma(k[22], e, k[23] * f);
-    const double ba = fma(pa, pa, fma(qa, qa, eps));
-    const double bb = fma(pb, pb, fma(qb, qb, eps));
-    const double bc = fma(pc, pc, fma(qc, qc, eps));
-    const double bd = fma(pd, pd, fma(qd, qd, eps));
-    const double bbc = bb * bc;
-    const double l0 = k[24] * bbc, l1 = k[25] * (ba * bc), l2 = k[26] * (ba * bb);
+    const WenoField W = weno_field64(k, a, b, c, d, e, f, eps);
+    const double C0 = k[20], C2 = k[21], D0 = k[22], D2 = k[23];  // C_1 = 1 on both sides
+    const double bbc = W.bb * W.bc;
+    const double l0 = C0 * bbc, l1 = W.ba * W.bc, l2 = C2 * (W.ba * W.bb);
     const double iDL = recip64(l0 + l1 + l2);
-    const double dl = fma(l0, va, fma(l1, vb, l2 * vc)) * iDL;
-    const double r0 = k[27] * bbc, r1 = k[28] * (bd * bb), r2 = k[29] * (bd * bc);
+    const double dl = fma(l0, W.va, fma(l1, W.vb, l2 * W.vc)) * iDL;
+    const double r0 = D0 * bbc, r1 = W.bd * W.bb, r2 = D2 * (W.bd * W.bc);
     const double iDR = recip64(r0 + r1 + r2);
-    const double vcr = vc - c, vbr = vb - c;
-    const double dr = fma(r0, vd, fma(r1, vcr, r2 * vbr)) * iDR;
+    const double vcr = W.vc - c, vbr = W.vb - c;
+    const double dr = fma(r0, W.vd, fma(r1, vcr, r2 * vbr)) * iDR;
     // reverse
     const double NLb = dlb * iDL, DLb = -dlb * dl * iDL;
     const double NRb = drb * iDR, DRb = -drb * dr * iDR;
-    const double l0b = NLb * va + DLb, l1b = NLb * vb + DLb, l2b = NLb * vc + DLb;
-    const double r0b = NRb * vd + DRb, r1b = NRb * vcr + DRb, r2b = NRb * vbr + DRb;
+    const double l0b = NLb * W.va + DLb, l1b = NLb * W.vb + DLb, l2b = NLb * W.vc + DLb;
+    const double r0b = NRb * W.vd + DRb, r1b = NRb * vcr + DRb, r2b = NRb * vbr + DRb;
     const double vab = NLb * l0;
     const double vbb = NLb * l1 + NRb * r2;
     const double vcb = NLb * l2 + NRb * r1;
     const double vdb = NRb * r0;
-    double cdir = -NRb * (r1 + r2);
-    const double bab = l1b * k[25] * bc + l2b * k[26] * bb;
-    const double bbb = l0b * k[24] * bc + l2b * k[26] * ba + r0b * k[27] * bc + r1b * k[28] * bd;
-    const double bcb = l0b * k[24] * bb + l1b * k[25] * ba + r0b * k[27] * bb + r2b * k[29] * bd;
-    const double bdb = r1b * k[28] * bb + r2b * k[29] * bc;
-    const double pab = 2.0 * pa * bab, qab = 2.0 * qa * bab;
-    const double pbb = 2.0 * pb * bbb, qbb = 2.0 * qb * bbb;
-    const double pcb = 2.0 * pc * bcb, qcb = 2.0 * qc * bcb;
-    const double pdb = 2.0 * pd * bdb, qdb = 2.0 * qd * bdb;
-    ab = k[0] * vab + k[2] * pab + k[4] * qab;
-    bb_ = k[1] * vab + k[3] * pab + k[5] * qab + k[6] * vbb + k[8] * pbb + k[10] * qbb;
-    cb = cdir + k[7] * vbb + k[9] * pbb + k[11] * qbb + k[12] * vcb + k[14] * pcb + k[16] * qcb;
-    db = k[13] * vcb + k[15] * pcb + k[17] * qcb;
-    eb = k[18] * vdb + k[20] * pdb + k[22] * qdb;
-    fb = k[19] * vdb + k[21] * pdb + k[23] * qdb;
+    const double cdir = -NRb * (r1 + r2);
+    const double bab = l1b * W.bc + l2b * C2 * W.bb;
+    const double bbb = l0b * C0 * W.bc + l2b * C2 * W.ba + r0b * D0 * W.bc + r1b * W.bd;
+    const double bcb = l0b * C0 * W.bb + l1b * W.ba + r0b * D0 * W.bb + r2b * D2 * W.bd;
+    const double bdb = r1b * W.bb + r2b * D2 * W.bc;
+    // beta = m0 x^2 + m1 x y + m2 y^2: d/dx = 2 m0 x + m1 y, d/dy = m1 x + 2 m2 y
+    ab = k[0] * vab + bab * (2.0 * k[2] * a + k[3] * b);
+    bb_ = k[1] * vab + bab * (k[3] * a + 2.0 * k[4] * b) + k[5] * vbb + bbb * (2.0 * k[7] * b + k[8] * c);
+    cb = cdir + k[6] * vbb + bbb * (k[8] * b + 2.0 * k[9] * c) + k[10] * vcb + bcb * (2.0 * k[12] * c + k[13] * d);
+    db = k[11] * vcb + bcb * (k[13] * c + 2.0 * k[14] * d);
+    eb = k[15] * vdb + bdb * (2.0 * k[17] * e + k[18] * f);
+    fb = k[16] * vdb + bdb * (k[18] * e + 2.0 * k[19] * f);
 }
 
 // F_n(w) = (rho q, m_x q + p n_x, m_y q + p n_y, (E + p) q), q = m.n / rho,
@@ -249,7 +240,7 @@ __global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
     const dbl4 W0 = ld4(w, s[0]), W1 = ld4(w, s[1]), L1 = ld4(w, s[2]), R1 = ld4(w, s[3]), W4 = ld4(w, s[4]),
                W5 = ld4(w, s[5]);
-    const double nx = __ldg(coef + (int64_t)30 * ne + e), ny = __ldg(coef + (int64_t)31 * ne + e);
+    const double nx = __ldg(coef + (int64_t)kCoefN * ne + e), ny = __ldg(coef + (int64_t)(kCoefN + 1) * ne + e);
     const dbl4 lam = ld4(A.lam_r, e);
 
     // ---------------- forward
@@ -259,9 +250,9 @@ __global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
     const dbl4 cM = project64(C, dM), cL2 = project64(C, dL2), cL3 = project64(C, dL3), cR2 = project64(C, dR2),
                cR3 = project64(C, dR3);
     const dbl4 cR2L = add4(cR2, cM);
-    double k[30];
+    double k[kCoefN];
 #pragma unroll
-    for (int i = 0; i < 30; ++i) k[i] = __ldg(coef + (int64_t)i * ne + e);
+    for (int i = 0; i < kCoefN; ++i) k[i] = __ldg(coef + (int64_t)i * ne + e);
     dbl4 dl, dr;
     weno_pair64(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps, dl.x, dr.x);
     weno_pair64(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps, dl.y, dr.y);

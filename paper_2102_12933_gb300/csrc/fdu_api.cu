@@ -168,7 +168,7 @@ fdu_status upload_tables(fdu_mesh *m) {
     // 1D stencils and coefficient blocks, SoA over internal active edges
     std::vector<int32_t> sten(6 * ne);
     std::vector<double> coef((size_t)kEdgeCoef * ne);
-    std::vector<float> coef32((size_t)kEdgeCoef * ne);
+    std::vector<float> coef32((size_t)kEdgeCoef32 * ne, 0.0f);
     for (int64_t e = 0; e < ne; ++e) {
         const int64_t o = T.e_new2old[e];
         for (int i = 0; i < 6; ++i) sten[i * ne + e] = T.v_old2new[T.sten[6 * o + i]];

@@ -161,51 +161,53 @@ __device__ __forceinline__ dbl4 unproject64(const Roe64 &R, const dbl4 &c) {
 // NU-WENO5 increments of one characteristic field (Appendix), both sides.
 // Differences: a = L3-L1, b = L2-L1, c = R1-L1, d = R2-L1 (left centre L1),
 // e = R3-R1, f = R2-R1 (right centre R1).  k is the edge's coefficient block
-// (fdu_internal.h): four sub-stencils S_a..S_d give values v (increments),
-// and slopes p / curvatures q whose squares sum to the smoothness
-// indicators beta = p^2 + q^2.  The nonlinear weights alpha_k = C_k /
-// (beta_k + eps), omega = alpha / sum(alpha) (p = 1) are applied as
+// (fdu_internal.h, 5 values per sub-stencil): sub-stencils S_a..S_d give
+// values v (increments) and smoothness indicators beta as quadratic forms
+// of their two differences.  The nonlinear weights alpha_k = C_k / (beta_k +
+// eps), omega = alpha / sum(alpha) (p = 1) are applied as
 // C_k prod_{l != k}(beta_l + eps) over their sum: the same quotient with one
-// reciprocal per side.
-__device__ __forceinline__ void weno_pair64(const double *k, double a, double b, double c, double d, double e,
-                                            double f, double eps, double &dl, double &dr) {
-    const double va = fma(k[0], a, k[1] * b), pa = fma(k[2], a, k[3] * b), qa = fma(k[4], a, k[5] * b);
-    const double vb = fma(k[6], b, k[7] * c), pb = fma(k[8], b, k[9] * c), qb = fma(k[10], b, k[11] * c);
-    const double vc = fma(k[12], c, k[13] * d), pc = fma(k[14], c, k[15] * d), qc = fma(k[16], c, k[17] * d);
-    const double vd = fma(k[18], e, k[19] * f), pd = fma(k[20], e, k[21] * f), qd = fma(k[22], e, k[23] * f);
-    const double ba = fma(pa, pa, fma(qa, qa, eps));
-    const double bb = fma(pb, pb, fma(qb, qb, eps));
-    const double bc = fma(pc, pc, fma(qc, qc, eps));
-    const double bd = fma(pd, pd, fma(qd, qd, eps));
-    const double bbc = bb * bc;
-    const double l0 = k[24] * bbc, l1 = k[25] * (ba * bc), l2 = k[26] * (ba * bb);
-    dl = fma(l0, va, fma(l1, vb, l2 * vc)) * recip64_fast(l0 + l1 + l2);
-    const double r0 = k[27] * bbc, r1 = k[28] * (bd * bb), r2 = k[29] * (bd * bc);
-    // right-side increments from R1: S_d's own, S_c's and S_b's shifted by -c
-    dr = fma(r0, vd, fma(r1, vc - c, r2 * (vb - c))) * recip64_fast(r0 + r1 + r2);
+// reciprocal per side; the block stores C_0/C_1, C_2/C_1 (C_1 -> 1).
+struct WenoField {
+    double va, vb, vc, vd, ba, bb, bc, bd;
+};
+__device__ __forceinline__ WenoField weno_field64(const double *k, double a, double b, double c, double d, double e,
+                                                  double f, double eps) {
+    WenoField W;
+    const double b2 = b * b, c2 = c * c;
+    W.va = fma(k[0], a, k[1] * b);
+    W.vb = fma(k[5], b, k[6] * c);
+    W.vc = fma(k[10], c, k[11] * d);
+    W.vd = fma(k[15], e, k[16] * f);
+    W.ba = fma(k[2], a * a, fma(k[3], a * b, fma(k[4], b2, eps)));
+    W.bb = fma(k[7], b2, fma(k[8], b * c, fma(k[9], c2, eps)));
+    W.bc = fma(k[12], c2, fma(k[13], c * d, fma(k[14], d * d, eps)));
+    W.bd = fma(k[17], e * e, fma(k[18], e * f, fma(k[19], f * f, eps)));
+    return W;
 }
 
+// The form the adjoint differentiates: right increments from R1 (S_c's and
+// S_b's values shifted by -c).
+__device__ __forceinline__ void weno_pair64(const double *k, double a, double b, double c, double d, double e,
+                                            double f, double eps, double &dl, double &dr) {
+    const WenoField W = weno_field64(k, a, b, c, d, e, f, eps);
+    const double bbc = W.bb * W.bc;
+    const double l0 = k[20] * bbc, l1 = W.ba * W.bc, l2 = k[21] * (W.ba * W.bb);
+    dl = fma(l0, W.va, fma(l1, W.vb, l2 * W.vc)) * recip64_fast(l0 + l1 + l2);
+    const double r0 = k[22] * bbc, r1 = W.bd * W.bb, r2 = k[23] * (W.bd * W.bc);
+    dr = fma(r0, W.vd, fma(r1, W.vc - c, r2 * (W.vb - c))) * recip64_fast(r0 + r1 + r2);
+}
 
-// The forward kernel's form of weno_pair64 (the adjoint keeps the one above,
-// which its reverse sweep differentiates): the middle linear weights are 1
-// (the block stores C_0/C_1, 1, C_2/C_1), and the right increments are taken
-// from L1 instead of R1 (S_d's value shifted by +c), so that
-// w_R = L1 + R dr: sum r_k (v_k - c) / sum r_k + c = sum r_k v_k' / sum r_k.
+// The forward kernel's form: the right increments are taken from L1 instead
+// (S_d's value shifted by +c), so that w_R = L1 + R dr:
+// sum r_k (v_k - c) / sum r_k + c = sum r_k v_k' / sum r_k.
 __device__ __forceinline__ void weno_pair64_l1(const double *k, double a, double b, double c, double d, double e,
                                                double f, double eps, double &dl, double &dr) {
-    const double va = fma(k[0], a, k[1] * b), pa = fma(k[2], a, k[3] * b), qa = fma(k[4], a, k[5] * b);
-    const double vb = fma(k[6], b, k[7] * c), pb = fma(k[8], b, k[9] * c), qb = fma(k[10], b, k[11] * c);
-    const double vc = fma(k[12], c, k[13] * d), pc = fma(k[14], c, k[15] * d), qc = fma(k[16], c, k[17] * d);
-    const double vd = fma(k[18], e, k[19] * f), pd = fma(k[20], e, k[21] * f), qd = fma(k[22], e, k[23] * f);
-    const double ba = fma(pa, pa, fma(qa, qa, eps));
-    const double bb = fma(pb, pb, fma(qb, qb, eps));
-    const double bc = fma(pc, pc, fma(qc, qc, eps));
-    const double bd = fma(pd, pd, fma(qd, qd, eps));
-    const double bbc = bb * bc;
-    const double l0 = k[24] * bbc, l1 = ba * bc, l2 = k[26] * (ba * bb);
-    dl = fma(l0, va, fma(l1, vb, l2 * vc)) * recip64_fast(l0 + l1 + l2);
-    const double r0 = k[27] * bbc, r1 = bd * bb, r2 = k[29] * (bd * bc);
-    dr = fma(r0, vd + c, fma(r1, vc, r2 * vb)) * recip64_fast(r0 + r1 + r2);
+    const WenoField W = weno_field64(k, a, b, c, d, e, f, eps);
+    const double bbc = W.bb * W.bc;
+    const double l0 = k[20] * bbc, l1 = W.ba * W.bc, l2 = k[21] * (W.ba * W.bb);
+    dl = fma(l0, W.va, fma(l1, W.vb, l2 * W.vc)) * recip64_fast(l0 + l1 + l2);
+    const double r0 = k[22] * bbc, r1 = W.bd * W.bb, r2 = k[23] * (W.bd * W.bc);
+    dr = fma(r0, W.vd + c, fma(r1, W.vc, r2 * W.vb)) * recip64_fast(r0 + r1 + r2);
 }
 
 }  // namespace dev

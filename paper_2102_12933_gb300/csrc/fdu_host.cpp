@@ -614,27 +614,31 @@ int build_host_tables(const double *xy, int64_t nv, const CellList &cells, int a
             double L[kSideCoef], R[kSideCoef];
             side_coefficients(xl, L);
             side_coefficients(xr, R);
-            // sub-stencil k of a side block: value at 2k, slope at 6 + 2k, curvature at 12 + 2k
+            // sub-stencil k of a side block: value coefficients at 2k, slope at 6 + 2k,
+            // curvature at 12 + 2k.  The block keeps the value pair and the
+            // smoothness indicator beta = (p0 x + p1 y)^2 + (q0 x + q1 y)^2 as the
+            // quadratic form m0 x^2 + m1 x y + m2 y^2 of the same two differences
             auto put = [&](int dst, const double *side, int k) {
+                const double p0 = side[6 + 2 * k], p1 = side[6 + 2 * k + 1];
+                const double q0 = side[12 + 2 * k], q1 = side[12 + 2 * k + 1];
                 c[dst + 0] = side[2 * k];
                 c[dst + 1] = side[2 * k + 1];
-                c[dst + 2] = side[6 + 2 * k];
-                c[dst + 3] = side[6 + 2 * k + 1];
-                c[dst + 4] = side[12 + 2 * k];
-                c[dst + 5] = side[12 + 2 * k + 1];
+                c[dst + 2] = p0 * p0 + q0 * q0;
+                c[dst + 3] = 2.0 * (p0 * p1 + q0 * q1);
+                c[dst + 4] = p1 * p1 + q1 * q1;
             };
-            put(0, L, 0);   // S_a
-            put(6, L, 1);   // S_b
-            put(12, L, 2);  // S_c
-            put(18, R, 0);  // S_d
+            put(0 * kSubCoef, L, 0);  // S_a
+            put(1 * kSubCoef, L, 1);  // S_b
+            put(2 * kSubCoef, L, 2);  // S_c
+            put(3 * kSubCoef, R, 0);  // S_d
             // linear weights divided by the middle one (C_1 > 0 on ordered points):
             // the nonlinear weights are invariant to a common factor of the C_k
-            for (int i = 0; i < 3; ++i) {
-                c[24 + i] = i == 1 ? 1.0 : L[18 + i] / L[19];
-                c[27 + i] = i == 1 ? 1.0 : R[18 + i] / R[19];
-            }
-            c[30] = T.nrm[2 * k];
-            c[31] = T.nrm[2 * k + 1];
+            c[kCoefCL] = L[18] / L[19];
+            c[kCoefCL + 1] = L[20] / L[19];
+            c[kCoefCR] = R[18] / R[19];
+            c[kCoefCR + 1] = R[20] / R[19];
+            c[kCoefN] = T.nrm[2 * k];
+            c[kCoefN + 1] = T.nrm[2 * k + 1];
         }
     });
     if (periodic && bad.load() >= 0) {

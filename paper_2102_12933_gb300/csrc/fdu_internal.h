@@ -22,13 +22,19 @@ constexpr int kSideCoef = 21;
 // sub-stencils S_a = {L3,L2,L1}, S_b = {L2,L1,R1}, S_c = {L1,R1,R2}; the
 // right (mirrored) state uses S_d = {R1,R2,R3}, S_c, S_b: S_b and S_c are
 // the same quadratics over the same middle interval on both sides, so their
-// values and smoothness indicators are computed once.  Each 6-block holds
-// value, slope and curvature coefficients (2 each) of two differences:
-//   [0..5]   S_a of (L3-L1, L2-L1)      [6..11]  S_b of (L2-L1, R1-L1)
-//   [12..17] S_c of (R1-L1, R2-L1)      [18..23] S_d of (R3-R1, R2-R1)
-//   [24..26] C_0/C_1, 1, C_2/C_1 of the left state   [27..29] the same of the right state
-//   [30..31] n_x, n_y
-constexpr int kEdgeCoef = 32;
+// values and smoothness indicators are computed once.  Each 5-block holds,
+// for two differences (x, y), the value coefficients (2) and the smoothness
+// indicator as a quadratic form m0 x^2 + m1 x y + m2 y^2 (3):
+//   [0..4]   S_a of (L3-L1, L2-L1)      [5..9]   S_b of (L2-L1, R1-L1)
+//   [10..14] S_c of (R1-L1, R2-L1)      [15..19] S_d of (R3-R1, R2-R1)
+//   [20..21] C_0/C_1, C_2/C_1 of the left state   [22..23] the same of the right state
+//   [24..25] n_x, n_y
+constexpr int kSubCoef = 5;
+constexpr int kCoefCL = 20;
+constexpr int kCoefCR = 22;
+constexpr int kCoefN = 24;
+constexpr int kEdgeCoef = 26;
+constexpr int kEdgeCoef32 = 28;  // FP32 copy padded to seven float4 per edge
 
 struct HostTables {
     int64_t nv = 0, nt = 0, ne = 0, n_real = 0;

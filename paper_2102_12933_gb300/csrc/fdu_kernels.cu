@@ -38,8 +38,8 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
     const dbl4 L1 = ld4(w, s[2]), R1 = ld4(w, s[3]);
-    const double nx = __ldg(coef + (int64_t)30 * ne + e);
-    const double ny = __ldg(coef + (int64_t)31 * ne + e);
+    const double nx = __ldg(coef + (int64_t)kCoefN * ne + e);
+    const double ny = __ldg(coef + (int64_t)(kCoefN + 1) * ne + e);
 
     // characteristic decomposition at the Roe average of the end states
     // (per-vertex Roe records when the stage kernel provided them)
@@ -51,9 +51,9 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
     const dbl4 cR2 = project64(C, sub4(ld4(w, s[4]), R1));    // R2 - R1
     const dbl4 cR3 = project64(C, sub4(ld4(w, s[5]), R1));    // R3 - R1
 
-    double k[30];
+    double k[kCoefN];
 #pragma unroll
-    for (int i = 0; i < 30; ++i) k[i] = __ldg(coef + (int64_t)i * ne + e);
+    for (int i = 0; i < kCoefN; ++i) k[i] = __ldg(coef + (int64_t)i * ne + e);
     const dbl4 cR2L = add4(cR2, cM);  // R2 - L1
     dbl4 dl, dr;
     weno_pair64_l1(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps, dl.x, dr.x);
@@ -293,24 +293,23 @@ __device__ __forceinline__ float4 unproject32(const Roe32 &R, const float4 &c) {
 }
 
 // FP32 NU-WENO5 increments of one field, both sides (same sub-stencil
-// sharing as weno_pair64).  Weights alpha_k = C_k / (beta_k + eps32),
-// omega = alpha / sum(alpha); the four reciprocals of (beta + eps32) serve
-// both sides.
+// sharing and block layout as weno_pair64_l1).  Weights alpha_k = C_k /
+// (beta_k + eps32), omega = alpha / sum(alpha); the four reciprocals of
+// (beta + eps32) serve both sides (a product form would underflow in FP32).
 __device__ __forceinline__ void weno_pair32(const float *k, float a, float b, float c, float d, float e, float f,
                                             float eps, float &dl, float &dr) {
-    const float va = fmaf(k[0], a, k[1] * b), pa = fmaf(k[2], a, k[3] * b), qa = fmaf(k[4], a, k[5] * b);
-    const float vb = fmaf(k[6], b, k[7] * c), pb = fmaf(k[8], b, k[9] * c), qb = fmaf(k[10], b, k[11] * c);
-    const float vc = fmaf(k[12], c, k[13] * d), pc = fmaf(k[14], c, k[15] * d), qc = fmaf(k[16], c, k[17] * d);
-    const float vd = fmaf(k[18], e, k[19] * f), pd = fmaf(k[20], e, k[21] * f), qd = fmaf(k[22], e, k[23] * f);
-    const float ia = rcp32(fmaf(pa, pa, fmaf(qa, qa, eps)));
-    const float ib = rcp32(fmaf(pb, pb, fmaf(qb, qb, eps)));
-    const float ic = rcp32(fmaf(pc, pc, fmaf(qc, qc, eps)));
-    const float id = rcp32(fmaf(pd, pd, fmaf(qd, qd, eps)));
-    // middle linear weights are 1 (the block stores C_0/C_1, 1, C_2/C_1);
+    const float b2 = b * b, c2 = c * c;
+    const float va = fmaf(k[0], a, k[1] * b), vb = fmaf(k[5], b, k[6] * c);
+    const float vc = fmaf(k[10], c, k[11] * d), vd = fmaf(k[15], e, k[16] * f);
+    const float ia = rcp32(fmaf(k[2], a * a, fmaf(k[3], a * b, fmaf(k[4], b2, eps))));
+    const float ib = rcp32(fmaf(k[7], b2, fmaf(k[8], b * c, fmaf(k[9], c2, eps))));
+    const float ic = rcp32(fmaf(k[12], c2, fmaf(k[13], c * d, fmaf(k[14], d * d, eps))));
+    const float id = rcp32(fmaf(k[17], e * e, fmaf(k[18], e * f, fmaf(k[19], f * f, eps))));
+    // middle linear weights are 1 (the block stores C_0/C_1, C_2/C_1);
     // right increments from L1 (S_d's value shifted by +c), as in the FP64 kernel
-    const float l0 = k[24] * ia, l1 = ib, l2 = k[26] * ic;
+    const float l0 = k[20] * ia, l1 = ib, l2 = k[21] * ic;
     dl = fmaf(l0, va, fmaf(l1, vb, l2 * vc)) * rcp32(l0 + l1 + l2);
-    const float r0 = k[27] * id, r1 = ic, r2 = k[29] * ib;
+    const float r0 = k[22] * id, r1 = ic, r2 = k[23] * ib;
     dr = fmaf(r0, vd + c, fmaf(r1, vc, r2 * vb)) * rcp32(r0 + r1 + r2);
 }
 
@@ -323,18 +322,18 @@ __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int6
     int32_t s[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
-    // coefficient block as 8 float4 per edge: [c/4][ne] float4, component c%4
+    // coefficient block as 7 float4 per edge: [c/4][ne] float4, component c%4
     const float4 *__restrict__ g4 = reinterpret_cast<const float4 *>(g);
-    float k[32];
+    float k[kEdgeCoef32];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < kEdgeCoef32 / 4; ++i) {
         const float4 q = __ldg(g4 + (int64_t)i * ne + e);
         k[4 * i] = q.x;
         k[4 * i + 1] = q.y;
         k[4 * i + 2] = q.z;
         k[4 * i + 3] = q.w;
     }
-    const float nx = k[30], ny = k[31];
+    const float nx = k[kCoefN], ny = k[kCoefN + 1];
     const float4 L1 = __ldg(w + s[2]), R1 = __ldg(w + s[3]);
     const Prim32 pL1 = prim32(L1, gm1), pR1 = prim32(R1, gm1);
     const Roe32 C = roe32(L1, pL1, R1, pR1, nx, ny, gm1);

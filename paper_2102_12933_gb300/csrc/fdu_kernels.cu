@@ -233,7 +233,7 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) 
 
 // ================================================================== FP32 path
 // The FP32 residual reads an FP32 copy of the state and an FP32 copy of the
-// edge coefficient block (eight float4 per edge); weights, fluxes and sums
+// edge coefficient block (seven float4 per edge); weights, fluxes and sums
 // are FP32.  Reciprocals use the hardware approximation (rcp.approx, about
 // one ulp), well inside the FP32 path's error against FP64.
 __device__ __forceinline__ float rcp32(float x) {

@@ -139,18 +139,18 @@ __device__ __forceinline__ void unproject64_vjp(const Roe64 &R, const dbl4 &c, c
 }
 
 // Reverse of weno_pair64 for one field: from (dlb, drb) to the cotangents of
-// the six differences (a..f), recomputing the forward values.
-__device__ __forceinline__ void weno_pair64_vjp(const double *k, double a, double b, double c, double d, double e,
-                                                double f, double eps, double dlb, double drb, double &ab, double &bb_,
-                                                double &cb, double &db, double &eb, double &fb) {
-    const WenoField W = weno_field64(k, a, b, c, d, e, f, eps);
+// the six differences (a..f), given the field's values and indicators W
+// from the forward pass (same reciprocals as weno_combine64).
+__device__ __forceinline__ void weno_pair64_vjp(const double *k, const WenoField &W, double a, double b, double c,
+                                                double d, double e, double f, double dlb, double drb, double &ab,
+                                                double &bb_, double &cb, double &db, double &eb, double &fb) {
     const double C0 = k[20], C2 = k[21], D0 = k[22], D2 = k[23];  // C_1 = 1 on both sides
     const double bbc = W.bb * W.bc;
     const double l0 = C0 * bbc, l1 = W.ba * W.bc, l2 = C2 * (W.ba * W.bb);
-    const double iDL = recip64(l0 + l1 + l2);
+    const double iDL = recip64_fast(l0 + l1 + l2);
     const double dl = fma(l0, W.va, fma(l1, W.vb, l2 * W.vc)) * iDL;
     const double r0 = D0 * bbc, r1 = W.bd * W.bb, r2 = D2 * (W.bd * W.bc);
-    const double iDR = recip64(r0 + r1 + r2);
+    const double iDR = recip64_fast(r0 + r1 + r2);
     const double vcr = W.vc - c, vbr = W.vb - c;
     const double dr = fma(r0, W.vd, fma(r1, vcr, r2 * vbr)) * iDR;
     // reverse
@@ -253,11 +253,35 @@ __global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
     double k[kCoefN];
 #pragma unroll
     for (int i = 0; i < kCoefN; ++i) k[i] = __ldg(coef + (int64_t)i * ne + e);
+    // each field's sub-stencil values and indicators, kept in shared memory
+    // (thread-private column) for the reverse sweep
+    __shared__ double wsm[4 * 8][128];
+    const int t = threadIdx.x;
+    auto keep = [&](int fi, const WenoField &W) {
+        wsm[fi * 8 + 0][t] = W.va; wsm[fi * 8 + 1][t] = W.vb; wsm[fi * 8 + 2][t] = W.vc; wsm[fi * 8 + 3][t] = W.vd;
+        wsm[fi * 8 + 4][t] = W.ba; wsm[fi * 8 + 5][t] = W.bb; wsm[fi * 8 + 6][t] = W.bc; wsm[fi * 8 + 7][t] = W.bd;
+    };
+    auto kept = [&](int fi) {
+        WenoField W;
+        W.va = wsm[fi * 8 + 0][t]; W.vb = wsm[fi * 8 + 1][t]; W.vc = wsm[fi * 8 + 2][t]; W.vd = wsm[fi * 8 + 3][t];
+        W.ba = wsm[fi * 8 + 4][t]; W.bb = wsm[fi * 8 + 5][t]; W.bc = wsm[fi * 8 + 6][t]; W.bd = wsm[fi * 8 + 7][t];
+        return W;
+    };
     dbl4 dl, dr;
-    weno_pair64(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps, dl.x, dr.x);
-    weno_pair64(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps, dl.y, dr.y);
-    weno_pair64(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps, dl.z, dr.z);
-    weno_pair64(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps, dl.w, dr.w);
+    {
+        WenoField W = weno_field64(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps);
+        keep(0, W);
+        weno_combine64(k, W, cM.x, dl.x, dr.x);
+        W = weno_field64(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps);
+        keep(1, W);
+        weno_combine64(k, W, cM.y, dl.y, dr.y);
+        W = weno_field64(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps);
+        keep(2, W);
+        weno_combine64(k, W, cM.z, dl.z, dr.z);
+        W = weno_field64(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps);
+        keep(3, W);
+        weno_combine64(k, W, cM.w, dl.w, dr.w);
+    }
     dbl4 wl = add4(L1, unproject64(C, dl));
     dbl4 wr = add4(R1, unproject64(C, dr));
     Prim64 pl, pr;
@@ -330,13 +354,13 @@ __global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
         unproject64_vjp(C, dl, wlb, dlb, Cb);
         unproject64_vjp(C, dr, wrb, drb, Cb);
         dbl4 cL3b, cL2b, cMb, cR2Lb, cR3b, cR2b;
-        weno_pair64_vjp(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps, dlb.x, drb.x, cL3b.x, cL2b.x, cMb.x,
+        weno_pair64_vjp(k, kept(0), cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, dlb.x, drb.x, cL3b.x, cL2b.x, cMb.x,
                         cR2Lb.x, cR3b.x, cR2b.x);
-        weno_pair64_vjp(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps, dlb.y, drb.y, cL3b.y, cL2b.y, cMb.y,
+        weno_pair64_vjp(k, kept(1), cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, dlb.y, drb.y, cL3b.y, cL2b.y, cMb.y,
                         cR2Lb.y, cR3b.y, cR2b.y);
-        weno_pair64_vjp(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps, dlb.z, drb.z, cL3b.z, cL2b.z, cMb.z,
+        weno_pair64_vjp(k, kept(2), cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, dlb.z, drb.z, cL3b.z, cL2b.z, cMb.z,
                         cR2Lb.z, cR3b.z, cR2b.z);
-        weno_pair64_vjp(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps, dlb.w, drb.w, cL3b.w, cL2b.w, cMb.w,
+        weno_pair64_vjp(k, kept(3), cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, dlb.w, drb.w, cL3b.w, cL2b.w, cMb.w,
                         cR2Lb.w, cR3b.w, cR2b.w);
         add_to(cR2b, cR2Lb);
         add_to(cMb, cR2Lb);

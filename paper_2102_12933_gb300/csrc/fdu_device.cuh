@@ -186,10 +186,10 @@ __device__ __forceinline__ WenoField weno_field64(const double *k, double a, dou
 }
 
 // The form the adjoint differentiates: right increments from R1 (S_c's and
-// S_b's values shifted by -c).
-__device__ __forceinline__ void weno_pair64(const double *k, double a, double b, double c, double d, double e,
-                                            double f, double eps, double &dl, double &dr) {
-    const WenoField W = weno_field64(k, a, b, c, d, e, f, eps);
+// S_b's values shifted by -c), from a field's values and indicators
+// (weno_field64).
+__device__ __forceinline__ void weno_combine64(const double *k, const WenoField &W, double c, double &dl,
+                                               double &dr) {
     const double bbc = W.bb * W.bc;
     const double l0 = k[20] * bbc, l1 = W.ba * W.bc, l2 = k[21] * (W.ba * W.bb);
     dl = fma(l0, W.va, fma(l1, W.vb, l2 * W.vc)) * recip64_fast(l0 + l1 + l2);

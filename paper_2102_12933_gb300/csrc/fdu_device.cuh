@@ -90,12 +90,6 @@ struct Roe64 {
     double u, v, H, c, ic, b1, qn, qt, hq2, nx, ny;
     double b1h, ich;  // b1 / 2 and ic / 2, the factors project64 applies
 };
-// Roe-weighted record of a state: (s, s u, s v, s H) with s = sqrt(rho),
-// computed with the same operations roe64 applies to each side.
-__device__ __forceinline__ dbl4 roe_record64(const dbl4 &w, double gm1) {
-    const Prim64 p = prim64(w, gm1);
-    return dbl4_make(w.x * p.r, w.y * p.r, w.z * p.r, (w.w + p.p) * p.r);
-}
 // Roe average from the two sides' records (same result as roe64).
 __device__ __forceinline__ Roe64 roe64_from_records(const dbl4 &qa, const dbl4 &qb, double nx, double ny, double gm1) {
     Roe64 R;

@@ -102,12 +102,17 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
 }
 
 // ------------------------------------------------------------------ vertex fluxes
-__device__ __forceinline__ void euler_fg(const dbl4 &w, double gm1, dbl4 &f, dbl4 &g) {
-    const double ir = 1.0 / w.x;
-    const double u = w.y * ir, v = w.z * ir;
-    const double p = gm1 * (w.w - 0.5 * (w.y * u + w.z * v));
-    f = dbl4_make(w.y, fma(w.y, u, p), w.z * u, (w.w + p) * u);
-    g = dbl4_make(w.z, w.y * v, fma(w.z, v, p), (w.w + p) * v);
+// f, g of a state from its primitives (1/rho, p): the same quantities the
+// Roe record needs, so the two share one reciprocal square root.
+__device__ __forceinline__ void euler_fg(const dbl4 &w, const Prim64 &P, dbl4 &f, dbl4 &g) {
+    const double u = w.y * P.ir, v = w.z * P.ir;
+    f = dbl4_make(w.y, fma(w.y, u, P.p), w.z * u, (w.w + P.p) * u);
+    g = dbl4_make(w.z, w.y * v, fma(w.z, v, P.p), (w.w + P.p) * v);
+}
+// Roe-weighted record of a state: (s, s u, s v, s H) with s = sqrt(rho),
+// computed with the same operations roe64 applies to each side.
+__device__ __forceinline__ dbl4 roe_record64(const dbl4 &w, const Prim64 &P) {
+    return dbl4_make(w.x * P.r, w.y * P.r, w.z * P.r, (w.w + P.p) * P.r);
 }
 
 __global__ void vertex_flux_f64_kernel(const double *__restrict__ w, double *__restrict__ F, double *__restrict__ Q,
@@ -115,11 +120,12 @@ __global__ void vertex_flux_f64_kernel(const double *__restrict__ w, double *__r
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     const dbl4 s = ld4(w, v);
+    const Prim64 P = prim64(s, gm1);
     dbl4 f, g;
-    euler_fg(s, gm1, f, g);
+    euler_fg(s, P, f, g);
     st4(F, 2 * v, f);
     st4(F, 2 * v + 1, g);
-    if (Q) st4(Q, v, roe_record64(s, gm1));
+    if (Q) st4(Q, v, roe_record64(s, P));
 }
 
 // Forward-Euler part of an SSP-RK3 stage, fe = ws + theta dt L.  Without
@@ -223,12 +229,13 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) 
         o.w = fma(cn, wn.w, cs * fe.w);
     }
     st4(A.wout, v, o);
+    const Prim64 P = prim64(o, A.gm1);
     dbl4 f, g;
-    euler_fg(o, A.gm1, f, g);
+    euler_fg(o, P, f, g);
     double *Fo = static_cast<double *>(A.Fout);
     st4(Fo, 2 * v, f);
     st4(Fo, 2 * v + 1, g);
-    if (A.Qout) st4(A.Qout, v, roe_record64(o, A.gm1));
+    if (A.Qout) st4(A.Qout, v, roe_record64(o, P));
 }
 
 // ================================================================== FP32 path

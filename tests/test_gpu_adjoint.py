@@ -125,9 +125,10 @@ def test_checkpoint_interval_does_not_change_the_gradient(case):
     dt = M.max_dt(0.5)
     lam = np.random.default_rng(4).standard_normal(w.shape)
     outs = []
-    for k in (1, 3, 10, 12):
+    for k in (1, 3, 5, 10, 12, 20):  # uneven last segments, one segment, interval beyond the run
         M.set_state(w)
         outs.append(M.adjoint_rk(dt, 12, lam, checkpoint_every=k))
+        assert np.array_equal(M.get_state(), w)  # the mesh is back at the initial state
     for o in outs[1:]:
         assert np.array_equal(o, outs[0])
 

@@ -278,3 +278,14 @@ def test_smallest_meshes(n):
         assert rel_l2(got[:, k] - w0[:, k], w[:, k] - w0[:, k]) <= 1e-12
     M.rk_steps(dt, 0, 64)  # zero steps: a no-op
     assert np.array_equal(M.get_state(), got)
+
+
+def test_sell_layouts_and_padding(c40):
+    """FP32 tables keep the vertex order; the FP64 tables sort each window of
+    256 vertices by stencil size, so their slices carry little padding."""
+    i = c40.M.info()
+    assert i["sell_width"] == 32
+    for kind in ("vert", "edge"):
+        nnz = i[f"div_{kind}_nnz"]
+        assert nnz <= i[f"sell_{kind}_nnz64"] <= i[f"sell_{kind}_nnz"]
+        assert i[f"sell_{kind}_nnz64"] <= 1.06 * nnz

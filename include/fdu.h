@@ -17,8 +17,9 @@
  *     Outputs go to caller-owned buffers of the stated size.
  *   - Vertex and edge ids in and out are ORIGINAL ids: vertex ids index
  *     the caller's xy array; edge ids index the edge list of
- *     fdu_get_edges (unique triangle sides (v0, v1), v0 < v1, sorted by
- *     (v0, v1)).  Any internal renumbering stays internal.
+ *     fdu_get_edges (the unique cell sides and artificial edges (v0, v1),
+ *     v0 < v1, sorted by (v0, v1)).  Any internal renumbering stays
+ *     internal.
  *   - States are conservative records w[nv][4] = (rho, rho u, rho v,
  *     rho E), row-major FP64, with E = e + (u^2 + v^2)/2 and
  *     p = (gamma - 1) rho e (Section 2.1).
@@ -42,7 +43,7 @@ extern "C" {
 typedef int fdu_status;
 #define FDU_OK 0
 #define FDU_ERR_ARG (-1)            /* bad argument (null pointer, size, option) */
-#define FDU_ERR_MESH (-2)           /* bad mesh: bad ids, degenerate or inverted triangle */
+#define FDU_ERR_MESH (-2)           /* bad mesh: bad ids, degenerate, inverted or non-convex cell */
 #define FDU_ERR_STENCIL (-3)        /* a 1D stencil walk found no forward neighbour */
 #define FDU_ERR_RANK_DEFICIENT (-4) /* least-squares system with too few conditions or rank loss */
 #define FDU_ERR_CUDA (-5)           /* a CUDA runtime call failed (message has the CUDA error) */
@@ -165,7 +166,13 @@ fdu_status fdu_get_div_sizes(const fdu_mesh *mesh, int64_t *vert_nnz, int64_t *e
 fdu_status fdu_get_div_stencils(const fdu_mesh *mesh, int64_t *voff, int32_t *vid, double *wf, double *wg,
                                 int64_t *eoff, int32_t *eid, double *we);
 
-/* Copy a state w[nv][4] into / out of the mesh (original vertex order). */
+/* Copy a state w[nv][4] into / out of the mesh (original vertex order).
+ * fdu_set_state from host memory (on_device = 0) copies the rows once (a
+ * DMA transfer when they are pinned), checks them on the device and
+ * synchronises `stream`: FDU_ERR_NONPHYSICAL names the first row with
+ * rho <= 0 or a non-finite value, and the mesh keeps its previous state.
+ * From device memory the rows are taken as they are, without the check.
+ * Both reset the mesh time of fdu_advance to 0. */
 fdu_status fdu_set_state(fdu_mesh *mesh, const double *w, int on_device, void *stream);
 fdu_status fdu_get_state(const fdu_mesh *mesh, double *w, int on_device, void *stream);
 

@@ -269,9 +269,12 @@ fdu_status fdu_rk_step_vjp(fdu_mesh *mesh, double dt, const double *lam_next, do
 /* Gradient with respect to the current state w0 of a function of the state
  * after n_steps SSP-RK3 steps of size dt, given lam_final = its gradient
  * with respect to that final state: grad = (dw_T/dw0)^T lam_final.  The
- * forward pass keeps a checkpoint every `checkpoint_every` steps and each
- * segment's step states are recomputed in the reverse pass.  The mesh state
- * is w0 again afterwards. */
+ * forward pass keeps a checkpoint every `checkpoint_every` = K steps and
+ * the stage states of the last segment; the reverse pass recomputes the
+ * stage states of each earlier segment from its checkpoint.  Device memory:
+ * ceil(n_steps / K) + 3 K states of nv x 4 doubles (K >= n_steps: one
+ * segment, nothing recomputed).  The gradient does not depend on K.  The
+ * mesh state is w0 again afterwards. */
 fdu_status fdu_adjoint_rk(fdu_mesh *mesh, double dt, int n_steps, int checkpoint_every, const double *lam_final,
                           double *grad, int on_device, void *stream);
 

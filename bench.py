@@ -612,6 +612,15 @@ def run_batch(args):
         ms = ev0.elapsed_time(ev1)
         res[prec] = {"value": round(B.nv * 3 * args.steps / (ms / 1e3) / 1e6, 2), "ms_per_step": round(ms / args.steps, 4),
                      "launch": {"threads": t, "blocks_per_sm": b, "autotune_ms_per_step": round(ms_tune, 4)}}
+    # FP32 error against FP64 after the same steps from the same state, over all meshes
+    err_steps = 100
+    states = {}
+    for prec in (64, 32):
+        B.set_state(w0)
+        B.batch_rk_steps(err_steps, prec, stream=stream)
+        states[prec] = B.get_state()
+    res[32]["error_vs_f64"] = {"rho": _rel_l2(states[32][:, 0], states[64][:, 0]),
+                               "rhoE": _rel_l2(states[32][:, 3], states[64][:, 3]), "steps": err_steps}
     line = {
         "metric": METRIC, "value": res[32]["value"], "unit": "Mvertex/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res[32]["ms_per_step"], "higher_is_better": True, "scaling": "weak",

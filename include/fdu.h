@@ -254,12 +254,18 @@ fdu_status fdu_batch_autotune(fdu_mesh *batch, int precision, int *threads, int 
  * or hang is involved: the wait is bounded and the kernel returns. */
 fdu_status fdu_batch_barrier_selftest(fdu_mesh *batch, int *status);
 
-/* ---- Adjoint (hand-written vector-Jacobian products, FP64, periodic meshes) ----
+/* ---- Adjoint (hand-written vector-Jacobian products, FP64, all single meshes) ----
  * Derivatives of the residual and the RK step as defined above, taking the
  * same branch as the forward pass at the piecewise choices (positivity
  * fallback, entropy-fix band, |lambda|); the WENO weights are
  * differentiable wherever beta_k + eps > 0.  Arrays are [nv][4] in original
- * vertex order, device (on_device = 1) or host pointers. */
+ * vertex order, device (on_device = 1) or host pointers.
+ * Ghost layers: the state is taken through the ghost fill first, so the
+ * rows of a transmissive ghost carry nothing (its cotangent is added to its
+ * donor's row) and the rows of a Dirichlet ghost are the derivative with
+ * respect to its fixed value.  fdu_rk_step_vjp and fdu_adjoint_rk return
+ * FDU_ERR_ARG when the stage positivity safeguard is on (positivity_alpha
+ * > 0): the safeguard is not differentiated. */
 /* grad = (dL/dw)^T lam at the current state. */
 fdu_status fdu_residual_vjp(fdu_mesh *mesh, const double *lam, double *grad, int on_device, void *stream);
 /* lam_prev = (dw_{n+1}/dw_n)^T lam_next for one SSP-RK3 step of size dt from

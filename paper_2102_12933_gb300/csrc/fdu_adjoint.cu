@@ -447,9 +447,31 @@ __global__ void axpby_kernel(double *__restrict__ out, double a, const double *_
     out[i] = v;
 }
 
+// Transpose of the transmissive ghost fill (ghost rows copy their donor's):
+// each donor adds its ghosts' cotangents, in ascending ghost order, and the
+// ghost rows become 0.  One thread per donor, so the sums are deterministic.
+__global__ void ghost_fold_kernel(double *__restrict__ x, const int32_t *__restrict__ donor,
+                                  const int64_t *__restrict__ off, const int32_t *__restrict__ ghost, int64_t nd) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nd) return;
+    const int64_t d = __ldg(donor + i);
+    dbl4 acc = ld4(x, d);
+    for (int64_t p = __ldg(off + i); p < __ldg(off + i + 1); ++p) {
+        const int64_t g = __ldg(ghost + p);
+        add_to(acc, ld4(x, g));
+        st4(x, g, dbl4_make(0, 0, 0, 0));
+    }
+    st4(x, d, acc);
+}
+
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
+
+void launch_ghost_fold(double *x, const int32_t *donor, const int64_t *off, const int32_t *ghost, int64_t nd,
+                       cudaStream_t s) {
+    if (nd > 0) ghost_fold_kernel<<<nblk(nd, 128), 128, 0, s>>>(x, donor, off, ghost, nd);
+}
 
 void launch_residual_vjp(const AdjEdgeArgs &ea, const AdjTables &t, const AdjVertexArgs &va, cudaStream_t s) {
     if (ea.ne > 0) {

@@ -45,6 +45,10 @@ struct AdjVertexArgs {
 // grad = (dL/dw)^T lam at state w: transpose gathers, edge-flux VJP, per-vertex
 // flux Jacobians; three launches on s.
 void launch_residual_vjp(const AdjEdgeArgs &ea, const AdjTables &t, const AdjVertexArgs &va, cudaStream_t s);
+// x <- (transmissive ghost fill)^T x: donor[i] += sum of x over its ghosts
+// ghost[off[i] .. off[i+1]-1], which are then zeroed (nd donors, internal ids)
+void launch_ghost_fold(double *x, const int32_t *donor, const int64_t *off, const int32_t *ghost, int64_t nd,
+                       cudaStream_t s);
 // out = a x + b y + c z over n4 doubles (y, z may be null)
 void launch_axpby(double *out, double a, const double *x, double b, const double *y, double c, const double *z,
                   int64_t n4, cudaStream_t s);

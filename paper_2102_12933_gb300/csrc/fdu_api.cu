@@ -103,6 +103,10 @@ struct fdu_mesh {
     double *adj_ewt = nullptr, *adj_wf = nullptr, *adj_wg = nullptr;
     double *adj_lam_r = nullptr, *adj_G = nullptr;
     double *adj_S1 = nullptr, *adj_buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // transpose of the transmissive ghost fill: donors with their ghosts (CSR, internal ids)
+    int64_t adj_nfold = 0;
+    int32_t *adj_fold_donor = nullptr, *adj_fold_ghost = nullptr;
+    int64_t *adj_fold_off = nullptr;
     std::vector<double *> adj_states;  // checkpoints and recomputed step states
     // kernel timing: event pairs per kind (0 edge64, 1 div64, 2 edge32, 3 div32)
     bool prof_on = false;
@@ -453,7 +457,6 @@ void enqueue_step(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaSt
 // ---------------------------------------------------------------- adjoint
 fdu_status adjoint_setup(fdu_mesh *m) {
     if (m->adj_ready) return FDU_OK;
-    if (m->n_ghost > 0) return set_err(FDU_ERR_ARG, "the adjoint supports periodic meshes (no ghost vertices)");
     const HostTables &T = m->T;
     const int64_t nv = m->nv, ne = m->ne_act;
     // edge transpose and vertex transpose (with centre weights), internal ids
@@ -516,8 +519,39 @@ fdu_status adjoint_setup(fdu_mesh *m) {
     if ((st = m->alloc(m->adj_S1, 4 * nv))) return st;
     for (int i = 0; i < 5; ++i)
         if ((st = m->alloc(m->adj_buf[i], 4 * nv))) return st;
+    // transmissive ghosts grouped by donor (a Dirichlet ghost is its own
+    // donor: its state is an input of its own, nothing to fold)
+    {
+        std::vector<std::pair<int32_t, int32_t>> dg;  // (donor, ghost), internal ids
+        for (int64_t g = m->n_real; g < nv; ++g) {
+            const int32_t o = T.v_new2old[g], od = T.ghost[o];
+            if (od >= 0 && od != o) dg.push_back({T.v_old2new[od], (int32_t)g});
+        }
+        std::sort(dg.begin(), dg.end());
+        std::vector<int32_t> donor, ghost;
+        std::vector<int64_t> off{0};
+        for (size_t i = 0; i < dg.size(); ++i) {
+            if (donor.empty() || donor.back() != dg[i].first) {
+                if (!donor.empty()) off.push_back((int64_t)ghost.size());
+                donor.push_back(dg[i].first);
+            }
+            ghost.push_back(dg[i].second);
+        }
+        if (!donor.empty()) off.push_back((int64_t)ghost.size());
+        m->adj_nfold = (int64_t)donor.size();
+        if (m->adj_nfold > 0) {
+            if ((st = m->upload(m->adj_fold_donor, donor))) return st;
+            if ((st = m->upload(m->adj_fold_off, off))) return st;
+            if ((st = m->upload(m->adj_fold_ghost, ghost))) return st;
+        }
+    }
     m->adj_ready = true;
     return FDU_OK;
+}
+
+// x <- (ghost fill)^T x (no-op without transmissive ghosts)
+void fold_ghosts(fdu_mesh *m, double *x, cudaStream_t s) {
+    launch_ghost_fold(x, m->adj_fold_donor, m->adj_fold_off, m->adj_fold_ghost, m->adj_nfold, s);
 }
 
 // out = (dL/dw)^T lam at state w (all internal order)
@@ -550,8 +584,9 @@ void enqueue_residual_vjp(fdu_mesh *m, const double *w, const double *lam, doubl
 }
 
 // lam_prev = (dw'/dw)^T lam_next for one SSP-RK3 step from the state wn
-// (internal order; wn is not changed, ws and the stage flux buffers are).
-void enqueue_rk_step_vjp(fdu_mesh *m, double dt, const double *lam_next, double *lam_prev, cudaStream_t s,
+// (internal order; wn is not changed, ws and the stage flux buffers are, and
+// lam_next is folded in place).
+void enqueue_rk_step_vjp(fdu_mesh *m, double dt, double *lam_next, double *lam_prev, cudaStream_t s,
                          const double *S0 = nullptr, const double *S1 = nullptr, const double *S2 = nullptr) {
     const int64_t n4 = 4 * m->nv;
     double *t = m->adj_buf[2], *ls2 = m->adj_buf[3], *ls1 = m->adj_buf[4];
@@ -564,16 +599,25 @@ void enqueue_rk_step_vjp(fdu_mesh *m, double dt, const double *lam_next, double 
         S1 = m->adj_S1;
         S2 = m->ws;
     }
-    // w' = 1/3 S0 + 2/3 (S2 + dt L(S2))
+    // Each stage output is P(.), P the ghost fill (transmissive ghosts copy
+    // their donors; Dirichlet ghosts keep their value, which the stage
+    // combination of ghost rows with zero residual reproduces), so each
+    // stage's cotangent goes through P^T (fold_ghosts, in place) first.
+    // w' = P(1/3 S0 + 2/3 (S2 + dt L(S2)))
+    fold_ghosts(m, lam_next, s);
     enqueue_residual_vjp(m, S2, lam_next, t, s);
     launch_axpby(ls2, 2.0 / 3.0, lam_next, 2.0 / 3.0 * dt, t, 0.0, nullptr, n4, s);
-    // S2 = 3/4 S0 + 1/4 (S1 + dt L(S1))
+    // S2 = P(3/4 S0 + 1/4 (S1 + dt L(S1)))
+    fold_ghosts(m, ls2, s);
     enqueue_residual_vjp(m, S1, ls2, t, s);
     launch_axpby(ls1, 0.25, ls2, 0.25 * dt, t, 0.0, nullptr, n4, s);
-    // S1 = S0 + dt L(S0)
+    // S1 = P(S0 + dt L(S0))
+    fold_ghosts(m, ls1, s);
     enqueue_residual_vjp(m, S0, ls1, t, s);
     launch_axpby(lam_prev, 1.0 / 3.0, lam_next, 0.75, ls2, 1.0, ls1, n4, s);
     launch_axpby(lam_prev, 1.0, lam_prev, dt, t, 0.0, nullptr, n4, s);
+    // S0 = P(w): the caller's ghost rows are overwritten by the fill
+    fold_ghosts(m, lam_prev, s);
 }
 
 // One SSP-RK3 step of a batch: three cooperative persistent launches.
@@ -1392,6 +1436,7 @@ fdu_status fdu_residual_vjp(fdu_mesh *m, const double *lam, double *grad, int on
     cudaStream_t s = m->stream(stream);
     if ((st = to_internal(m, lam, on_device, m->adj_buf[0], s))) return st;
     enqueue_residual_vjp(m, m->wn, m->adj_buf[0], m->adj_buf[1], s);
+    fold_ghosts(m, m->adj_buf[1], s);  // the residual is taken at P(w)
     CK_LAUNCH();
     return from_internal(m, m->adj_buf[1], grad, on_device, s);
 }
@@ -1401,6 +1446,8 @@ fdu_status fdu_rk_step_vjp(fdu_mesh *m, double dt, const double *lam_next, doubl
     fdu_status st = need_device(m);
     if (st) return st;
     if (!lam_next || !lam_prev || !(dt > 0)) return set_err(FDU_ERR_ARG, "null argument or dt <= 0");
+    if (m->opts.positivity_alpha > 0)
+        return set_err(FDU_ERR_ARG, "the RK adjoint does not differentiate the stage positivity safeguard");
     if ((st = adjoint_setup(m))) return st;
     cudaStream_t s = m->stream(stream);
     if ((st = to_internal(m, lam_next, on_device, m->adj_buf[0], s))) return st;
@@ -1416,6 +1463,8 @@ fdu_status fdu_adjoint_rk(fdu_mesh *m, double dt, int n_steps, int checkpoint_ev
     if (st) return st;
     if (!lam_final || !grad || !(dt > 0) || n_steps < 1 || checkpoint_every < 1)
         return set_err(FDU_ERR_ARG, "need dt > 0, n_steps >= 1, checkpoint_every >= 1 and both arrays");
+    if (m->opts.positivity_alpha > 0)
+        return set_err(FDU_ERR_ARG, "the RK adjoint does not differentiate the stage positivity safeguard");
     if ((st = adjoint_setup(m))) return st;
     cudaStream_t s = m->stream(stream);
     const int K = checkpoint_every, nseg = (n_steps + K - 1) / K;

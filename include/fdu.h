@@ -180,8 +180,16 @@ fdu_status fdu_get_state(const fdu_mesh *mesh, double *w, int on_device, void *s
  * state (Section 2.2.1), with edge fluxes from characteristic NU-WENO5
  * and a Roe flux (Section 2.3.1, Appendix).  precision = 64 computes in
  * FP64; precision = 32 reads FP32 copies of the state and tables and
- * computes in FP32.  Ghost vertices get 0.  With on_device = 0 the call
- * synchronises `stream` before returning. */
+ * computes in FP32; precision = 48 is the FP64 computation with the edge
+ * flux's increments (characteristic projection, WENO, flux increment and
+ * Roe dissipation) in double-word FP32 arithmetic (FP32 pairs, about 48
+ * significant bits) and its state-sized terms (stencil differences, the
+ * vertex flux at the edge's left end, the final sum) in FP64: the same
+ * function to the FP64 path's tolerance, faster on parts whose FP64 rate
+ * is a small fraction of their FP32 rate.  Its first use builds a
+ * double-word copy of the edge coefficient block (192 bytes per edge).
+ * Ghost vertices get 0.  With on_device = 0 the call synchronises `stream`
+ * before returning.  The RK calls below accept the same three values. */
 fdu_status fdu_residual(fdu_mesh *mesh, int precision, double *dwdt, int on_device, void *stream);
 
 /* dt = cfl * min over real vertices of h_v / (|u_v| + c_v), h_v the
@@ -191,7 +199,7 @@ fdu_status fdu_max_dt(fdu_mesh *mesh, double cfl, double *dt, void *stream);
 /* One SSP-RK3 step of the current state in place (Shu & Osher):
  * w1 = w + dt L(w); w2 = 3/4 w + 1/4 (w1 + dt L(w1));
  * w <- 1/3 w + 2/3 (w2 + dt L(w2)).  The state and the stage combination
- * stay FP64 for both precisions; `precision` selects the residual.
+ * stay FP64 for every precision; `precision` selects the residual.
  * dt > 0 is required. */
 fdu_status fdu_rk_step(fdu_mesh *mesh, double dt, int precision, void *stream);
 
@@ -295,7 +303,7 @@ fdu_status fdu_fallback_count(fdu_mesh *mesh, int64_t *count, int reset, void *s
  * of fdu_rk_steps are not instrumented).  fdu_profile_read synchronises the
  * recorded events and returns the summed device time (ms) and the launch
  * count of one kernel kind: FDU_KERNEL_EDGE or FDU_KERNEL_DIV at
- * precision 64 or 32; reset = 1 clears that kind's record. */
+ * precision 64, 48 or 32; reset = 1 clears that kind's record. */
 #define FDU_KERNEL_EDGE 0
 #define FDU_KERNEL_DIV 1
 fdu_status fdu_profile(fdu_mesh *mesh, int enable);

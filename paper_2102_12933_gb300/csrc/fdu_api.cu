@@ -61,6 +61,7 @@ struct fdu_mesh {
     int32_t *sten = nullptr;          // [6][ne_act]
     double *coef64 = nullptr;         // [32][ne_act]
     float *coef32 = nullptr;          // [32][ne_act]
+    float2 *coefdw = nullptr;         // [kCoefN][ne_act] double words (built on first precision-48 use)
     int64_t *slice_voff = nullptr, *slice_eoff = nullptr;       // FP32 layout (natural order)
     int64_t *slice_voff64 = nullptr, *slice_eoff64 = nullptr;   // FP64 layout (stencil-size order in windows)
     int32_t *svid64 = nullptr, *seid64 = nullptr, *perm64 = nullptr;
@@ -108,10 +109,10 @@ struct fdu_mesh {
     int32_t *adj_fold_donor = nullptr, *adj_fold_ghost = nullptr;
     int64_t *adj_fold_off = nullptr;
     std::vector<double *> adj_states;  // checkpoints and recomputed step states
-    // kernel timing: event pairs per kind (0 edge64, 1 div64, 2 edge32, 3 div32)
+    // kernel timing: event pairs per kind (0 edge64, 1 div64, 2 edge32, 3 div32, 4 edge48, 5 div at precision 48)
     bool prof_on = false;
-    std::vector<cudaEvent_t> prof_ev[4];
-    size_t prof_used[4] = {0, 0, 0, 0};
+    std::vector<cudaEvent_t> prof_ev[6];
+    size_t prof_used[6] = {0, 0, 0, 0, 0, 0};
 
     template <class T>
     fdu_status alloc(T *&p, size_t count) {
@@ -335,12 +336,52 @@ fdu_status upload_tables(fdu_mesh *m) {
     return FDU_OK;
 }
 
+// Precision 48: the FP64 state pipeline (FP64 divergence and stage) with
+// the double-word edge flux.
+inline bool fp64_state(int prec) { return prec != 32; }
+inline int prof_kind(int prec) { return prec == 64 ? 0 : prec == 32 ? 2 : 4; }
+
+// Precision 64, 32 or 48; the first use of 48 builds the double-word
+// coefficient block (hi = the FP32 rounding of each FP64 coefficient, lo =
+// the FP32 rounding of the remainder).
+fdu_status check_precision(fdu_mesh *m, int prec) {
+    if (prec != 64 && prec != 32 && prec != 48) return set_err(FDU_ERR_ARG, "precision must be 64, 48 or 32");
+    if (prec != 48 || m->coefdw) return FDU_OK;
+    const HostTables &T = m->T;
+    const int64_t ne = m->ne_act;
+    std::vector<float2> k((size_t)kCoefN * ne);
+    for (int64_t e = 0; e < ne; ++e) {
+        const int64_t o = T.e_new2old[e];
+        for (int c = 0; c < kCoefN; ++c) {
+            const double x = T.coef[(size_t)kEdgeCoef * o + c];
+            const float h = (float)x;
+            k[(size_t)c * ne + e] = make_float2(h, (float)(x - (double)h));
+        }
+    }
+    return m->upload(m->coefdw, k);
+}
+
+// Double-word constants of the precision-48 edge flux.
+void dw_split(double x, float out[2]) {
+    out[0] = (float)x;
+    out[1] = (float)(x - (double)out[0]);
+}
+
 EdgeArgs edge_args(fdu_mesh *m, int prec, const void *w) {
     EdgeArgs a{};
     a.sten = m->sten;
-    a.coef = prec == 64 ? (const void *)m->coef64 : (const void *)m->coef32;
+    a.coef = fp64_state(prec) ? (const void *)m->coef64 : (const void *)m->coef32;
     a.w = w;
-    a.r = prec == 64 ? (void *)m->r64 : (void *)m->r32;
+    a.r = fp64_state(prec) ? (void *)m->r64 : (void *)m->r32;
+    if (prec == 48) {
+        a.coefdw = m->coefdw;
+        dw_split(m->opts.gamma - 1.0, a.dw_gm1);
+        dw_split(0.1, a.dw_tenth);
+        int ee = 0;
+        const double mant = std::frexp(m->opts.weno_eps, &ee);  // eps = mant 2^ee, mant in [1/2, 1)
+        dw_split(2.0 * mant, a.dw_eps);
+        a.dw_eps_e = ee - 1;
+    }
     a.ne = m->ne_act;
     a.gm1 = m->opts.gamma - 1.0;
     a.eps = m->opts.weno_eps;
@@ -359,7 +400,7 @@ DivArgs div_args(fdu_mesh *m, int prec, int fin) {
     a.slice_eoff = m->slice_eoff;
     a.vid = m->svid;
     a.eid = m->seid;
-    if (prec == 64) {
+    if (fp64_state(prec)) {
         a.slice_voff = m->slice_voff64;
         a.slice_eoff = m->slice_eoff64;
         a.vid = m->svid64;
@@ -401,7 +442,7 @@ void timed(fdu_mesh *m, int kind, bool allowed, cudaStream_t s, F &&launch) {
 
 // Make F64[0] (or w32 and F32[0]) describe the current state wn.
 void ensure_fluxes(fdu_mesh *m, int prec, cudaStream_t s) {
-    if (prec == 64 && !m->f64_valid) {
+    if (fp64_state(prec) && !m->f64_valid) {
         launch_vertex_flux_f64(m->wn, m->F64[0], m->nv, m->opts.gamma, s, m->Q64[0]);
         m->f64_valid = true;
     }
@@ -416,33 +457,36 @@ void ensure_fluxes(fdu_mesh *m, int prec, cudaStream_t s) {
 // the new state at the end and a captured step can be replayed as is.
 void enqueue_stages(fdu_mesh *m, int prec, double dt, const double *dt_dev, cudaStream_t s, bool prof, int first,
                     int last) {
-    const int fq = prec == 64 ? 4 : 2;  // 16-byte words of vertex fluxes per vertex
-    const int kd = prec == 64 ? 0 : 2;
+    const bool f64 = fp64_state(prec);
+    const int fq = f64 ? 4 : 2;  // 16-byte words of vertex fluxes per vertex
+    const int kd = prof_kind(prec);
     for (int stage = first; stage <= last; ++stage) {
         const double *win = stage == 1 ? m->wn : m->ws;
         timed(m, kd, prof, s, [&] {
-            EdgeArgs ea = edge_args(m, prec, prec == 64 ? (const void *)win : (const void *)m->w32);
+            EdgeArgs ea = edge_args(m, prec, f64 ? (const void *)win : (const void *)m->w32);
             ea.dt_dev = dt_dev;
-            if (prec == 64) ea.Q = m->Q64[stage - 1];
+            if (f64) ea.Q = m->Q64[stage - 1];
+            ea.F64v = m->F64[stage - 1];
             if (prec == 64) launch_edge_flux_f64(ea, s);
+            else if (prec == 48) launch_edge_flux_dw(ea, s);
             else launch_edge_flux_f32(ea, s);
         });
         DivArgs a = div_args(m, prec, stage - 1);
         a.wn = m->wn;
         a.ws = win;
         a.wout = stage == 3 ? m->wn : m->ws;
-        a.Fout = prec == 64 ? (void *)m->F64[stage % 3] : (void *)m->F32[stage % 3];
-        a.Qout = prec == 64 ? m->Q64[stage % 3] : nullptr;
+        a.Fout = f64 ? (void *)m->F64[stage % 3] : (void *)m->F32[stage % 3];
+        a.Qout = f64 ? m->Q64[stage % 3] : nullptr;
         a.w32out = prec == 32 ? m->w32 : nullptr;
         a.dt = dt;
         a.dt_dev = dt_dev;
         timed(m, kd + 1, prof, s, [&] {
-            if (prec == 64) launch_div_f64(a, stage, s);
+            if (f64) launch_div_f64(a, stage, s);
             else launch_div_f32(a, stage, s);
         });
         if (m->n_ghost > 0) {
             // Dirichlet ghosts take their fixed values from the step's start buffers (wn, F[0], Q[0])
-            const void *F0 = prec == 64 ? (const void *)m->F64[0] : (const void *)m->F32[0];
+            const void *F0 = f64 ? (const void *)m->F64[0] : (const void *)m->F32[0];
             launch_ghost_fill(a.wout, m->wn, a.Fout, F0, fq, prec == 32 ? m->w32 : nullptr, m->donor, m->n_real,
                               m->n_ghost, s);
             if (a.Qout) launch_ghost_fill(nullptr, nullptr, a.Qout, m->Q64[0], 2, nullptr, m->donor, m->n_real, m->n_ghost, s);
@@ -906,26 +950,26 @@ fdu_status fdu_residual(fdu_mesh *m, int precision, double *dwdt, int on_device,
     fdu_status st = need_device(m);
     if (st) return st;
     if (!dwdt) return set_err(FDU_ERR_ARG, "null output");
-    if (precision != 64 && precision != 32) return set_err(FDU_ERR_ARG, "precision must be 64 or 32");
+    if ((st = check_precision(m, precision))) return st;
     cudaStream_t s = m->stream(stream);
     ensure_fluxes(m, precision, s);
     double *out = on_device ? dwdt : m->scratch;
     if (m->n_ghost > 0) CK(cudaMemsetAsync(out, 0, 4 * m->nv * sizeof(double), s));
-    const int kd = precision == 64 ? 0 : 2;
+    const int kd = prof_kind(precision);
+    const bool f64 = fp64_state(precision);
     timed(m, kd, true, s, [&] {
-        EdgeArgs ea = edge_args(m, precision, precision == 64 ? (const void *)m->wn : (const void *)m->w32);
-        if (precision == 64) {
-            ea.Q = m->Q64[0];
-            launch_edge_flux_f64(ea, s);
-        } else {
-            launch_edge_flux_f32(ea, s);
-        }
+        EdgeArgs ea = edge_args(m, precision, f64 ? (const void *)m->wn : (const void *)m->w32);
+        ea.Q = f64 ? m->Q64[0] : nullptr;
+        ea.F64v = m->F64[0];
+        if (precision == 64) launch_edge_flux_f64(ea, s);
+        else if (precision == 48) launch_edge_flux_dw(ea, s);
+        else launch_edge_flux_f32(ea, s);
     });
     DivArgs a = div_args(m, precision, 0);
     a.out = out;
     a.out_map = m->new2old;
     timed(m, kd + 1, true, s, [&] {
-        if (precision == 64) launch_div_f64(a, 0, s);
+        if (f64) launch_div_f64(a, 0, s);
         else launch_div_f32(a, 0, s);
     });
     CK_LAUNCH();
@@ -959,12 +1003,12 @@ fdu_status fdu_rk_step(fdu_mesh *m, double dt, int precision, void *stream) {
     fdu_status st = need_device(m);
     if (st) return st;
     if (!(dt > 0) || !std::isfinite(dt)) return set_err(FDU_ERR_ARG, "dt must be positive and finite");
-    if (precision != 64 && precision != 32) return set_err(FDU_ERR_ARG, "precision must be 64 or 32");
+    if ((st = check_precision(m, precision))) return st;
     cudaStream_t s = m->stream(stream);
     ensure_fluxes(m, precision, s);
     enqueue_step(m, precision, dt, nullptr, s, true);
     CK_LAUNCH();
-    if (precision == 64) m->f32_valid = false;
+    if (fp64_state(precision)) m->f32_valid = false;
     else m->f64_valid = false;
     return FDU_OK;
 }
@@ -973,7 +1017,7 @@ fdu_status fdu_rk_steps(fdu_mesh *m, double dt, int precision, int n_steps, void
     fdu_status st = need_device(m);
     if (st) return st;
     if (!(dt > 0) || !std::isfinite(dt) || n_steps < 0) return set_err(FDU_ERR_ARG, "need dt > 0 and n_steps >= 0");
-    if (precision != 64 && precision != 32) return set_err(FDU_ERR_ARG, "precision must be 64 or 32");
+    if ((st = check_precision(m, precision))) return st;
     if (n_steps == 0) return FDU_OK;
     cudaStream_t s = m->stream(stream);
     ensure_fluxes(m, precision, s);
@@ -1000,7 +1044,7 @@ fdu_status fdu_rk_steps(fdu_mesh *m, double dt, int precision, int n_steps, void
         it = m->graphs.emplace(key, ge).first;
     }
     for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(it->second, s));
-    if (precision == 64) m->f32_valid = false;
+    if (fp64_state(precision)) m->f32_valid = false;
     else m->f64_valid = false;
     return FDU_OK;
 }
@@ -1009,8 +1053,9 @@ fdu_status fdu_advance(fdu_mesh *m, double cfl, double t_end, int precision, int
                        double *t_out, void *stream) {
     fdu_status st = need_device(m);
     if (st) return st;
-    if (!(cfl > 0) || !std::isfinite(t_end) || max_steps < 0 || (precision != 64 && precision != 32))
-        return set_err(FDU_ERR_ARG, "need cfl > 0, a finite t_end, max_steps >= 0, precision 64 or 32");
+    if (!(cfl > 0) || !std::isfinite(t_end) || max_steps < 0)
+        return set_err(FDU_ERR_ARG, "need cfl > 0, a finite t_end and max_steps >= 0");
+    if ((st = check_precision(m, precision))) return st;
     cudaStream_t s = m->stream(stream);
     ensure_fluxes(m, precision, s);
     CK_LAUNCH();
@@ -1054,7 +1099,7 @@ fdu_status fdu_advance(fdu_mesh *m, double cfl, double t_end, int precision, int
         CK(cudaStreamSynchronize(s));
         if (host[1] == 0.0 && host[0] < t_end && host[2] == 0.0) break;  // no progress
     }
-    if (precision == 64) m->f32_valid = false;
+    if (fp64_state(precision)) m->f32_valid = false;
     else m->f64_valid = false;
     if (steps_done) *steps_done = (int64_t)(n1 - n0);
     if (t_out) *t_out = host[0];
@@ -1279,7 +1324,7 @@ fdu_status fdu_batch_rk_steps(fdu_mesh *m, int precision, int n_steps, void *str
         it = m->batch_graphs.emplace(key, ge).first;
     }
     for (int i = 0; i < n_steps; ++i) CK(cudaGraphLaunch(it->second, s));
-    if (precision == 64) m->f32_valid = false;
+    if (fp64_state(precision)) m->f32_valid = false;
     else m->f64_valid = false;
     return check_barrier(m, s);
 }
@@ -1581,9 +1626,9 @@ fdu_status fdu_profile_read(fdu_mesh *m, int kernel, int precision, double *tota
     fdu_status st = need_device(m);
     if (st) return st;
     if (!total_ms || !launches || (kernel != FDU_KERNEL_EDGE && kernel != FDU_KERNEL_DIV) ||
-        (precision != 64 && precision != 32))
+        (precision != 64 && precision != 32 && precision != 48))
         return set_err(FDU_ERR_ARG, "bad kernel kind, precision or output pointer");
-    const int kind = (precision == 64 ? 0 : 2) + kernel;
+    const int kind = prof_kind(precision) + kernel;
     double tot = 0;
     const size_t n = m->prof_used[kind];
     for (size_t i = 0; i < n; ++i) {

@@ -22,6 +22,13 @@ struct EdgeArgs {
     unsigned long long *fallback;  // edges that fell back to first order (device counter)
     const double *dt_dev; // adaptive stepping: a zero time step here skips the launch
     const double *Q;      // FP64: per-vertex Roe records of the stage state (nullptr = compute per edge)
+    // double-word edge flux (precision 48; Q is required there)
+    const float2 *coefdw; // [kCoefN][ne] (hi, lo) of the WENO coefficients
+    const double *F64v;   // [nv][8] FP64 vertex fluxes (f, g) of the stage state
+    float dw_gm1[2];      // gamma - 1 as a double word
+    float dw_tenth[2];    // 0.1 as a double word
+    float dw_eps[2];      // WENO epsilon = dw_eps * 2^dw_eps_e, dw_eps in [1, 2)
+    int dw_eps_e;
 };
 
 // Divergence (+ optional SSP-RK3 stage) inputs.
@@ -62,6 +69,7 @@ void launch_vertex_flux_f64(const double *w, double *F, int64_t n, double gamma,
 void launch_vertex_flux_f32(const double *w, float4 *F, float4 *w32, int64_t n, double gamma, cudaStream_t s);
 void launch_edge_flux_f64(const EdgeArgs &a, cudaStream_t s);
 void launch_edge_flux_f32(const EdgeArgs &a, cudaStream_t s);
+void launch_edge_flux_dw(const EdgeArgs &a, cudaStream_t s);
 void launch_div_f64(const DivArgs &a, int mode, cudaStream_t s);
 void launch_div_f32(const DivArgs &a, int mode, cudaStream_t s);
 // *bad = min(*bad, first row of w[n][4] with rho <= 0 or a non-finite value)

@@ -61,7 +61,13 @@ struct fdu_mesh {
     int32_t *sten = nullptr;          // [6][ne_act]
     double *coef64 = nullptr;         // [32][ne_act]
     float *coef32 = nullptr;          // [32][ne_act]
-    float2 *coefdw = nullptr;         // [kCoefN][ne_act] double words (built on first precision-48 use)
+    // precision 48 (built on first use): double-word coefficient block
+    // [kEdgeCoef][ne_act]; FP64 divergence tables with the left vertex flux
+    // of each edge folded into the vertex weights; edge weights as double words
+    float2 *coefdw = nullptr;
+    double *swf48 = nullptr, *swg48 = nullptr, *cfg48 = nullptr;
+    float2 *swe48 = nullptr;
+    std::vector<int32_t> order64;     // vertex at each position of the FP64 SELL layout
     int64_t *slice_voff = nullptr, *slice_eoff = nullptr;       // FP32 layout (natural order)
     int64_t *slice_voff64 = nullptr, *slice_eoff64 = nullptr;   // FP64 layout (stencil-size order in windows)
     int32_t *svid64 = nullptr, *seid64 = nullptr, *perm64 = nullptr;
@@ -165,6 +171,64 @@ fdu_status need_device(const fdu_mesh *m) {
     return FDU_OK;
 }
 
+// Divergence tables, SELL-32 over internal real vertices: position i of a
+// slice order holds vertex order[i]; entry j of lane l at off + 32 j + l.
+// The weights come from wf, wg, we (indexed like the host tables' entries).
+struct Sell {
+    std::vector<int64_t> svo, seo;
+    std::vector<int32_t> vid, eid;
+    std::vector<double> wf, wg, we;
+};
+void sell_tables(const fdu_mesh *m, const std::vector<int32_t> &order, const double *wf, const double *wg,
+                 const double *we, Sell &S) {
+    const HostTables &T = m->T;
+    const int64_t nr = m->n_real;
+    S.svo.assign(m->nslice + 1, 0);
+    S.seo.assign(m->nslice + 1, 0);
+    for (int64_t sl = 0; sl < m->nslice; ++sl) {
+        int64_t mj = 0, mk = 0;
+        for (int64_t i = sl * kSell; i < std::min(nr, (sl + 1) * kSell); ++i) {
+            const int64_t o = T.v_new2old[order[i]];
+            mj = std::max(mj, T.voff[o + 1] - T.voff[o]);
+            mk = std::max(mk, T.eoff[o + 1] - T.eoff[o]);
+        }
+        S.svo[sl + 1] = S.svo[sl] + mj * kSell;
+        S.seo[sl + 1] = S.seo[sl] + mk * kSell;
+    }
+    S.vid.assign(S.svo[m->nslice], 0);
+    S.eid.assign(S.seo[m->nslice], 0);
+    S.wf.assign(S.svo[m->nslice], 0.0);
+    S.wg.assign(S.svo[m->nslice], 0.0);
+    S.we.assign(S.seo[m->nslice], 0.0);
+    for (int64_t i = 0; i < nr; ++i) {
+        const int32_t v = order[i];
+        const int64_t o = T.v_new2old[v], sl = i / kSell, lane = i % kSell;
+        const int64_t J = T.voff[o + 1] - T.voff[o], K = T.eoff[o + 1] - T.eoff[o];
+        const int64_t mj = (S.svo[sl + 1] - S.svo[sl]) / kSell, mk = (S.seo[sl + 1] - S.seo[sl]) / kSell;
+        for (int64_t j = 0; j < mj; ++j) {
+            const int64_t p = S.svo[sl] + j * kSell + lane;
+            if (j < J) {
+                const int64_t q = T.voff[o] + j;
+                S.vid[p] = T.v_old2new[T.vid[q]];
+                S.wf[p] = wf[q];
+                S.wg[p] = wg[q];
+            } else {
+                S.vid[p] = v;  // padding: weight 0 on the vertex itself
+            }
+        }
+        for (int64_t k = 0; k < mk; ++k) {
+            const int64_t p = S.seo[sl] + k * kSell + lane;
+            if (k < K) {
+                const int64_t q = T.eoff[o] + k;
+                S.eid[p] = T.e_old2new[T.eid[q]];
+                S.we[p] = we[q];
+            } else {
+                S.eid[p] = K > 0 ? T.e_old2new[T.eid[T.eoff[o]]] : 0;
+            }
+        }
+    }
+}
+
 // Pack host tables into device layouts.
 fdu_status upload_tables(fdu_mesh *m) {
     const HostTables &T = m->T;
@@ -186,60 +250,8 @@ fdu_status upload_tables(fdu_mesh *m) {
     if ((st = m->upload(m->sten, sten))) return st;
     if ((st = m->upload(m->coef64, coef))) return st;
     if ((st = m->upload(m->coef32, coef32))) return st;
-    // divergence tables, SELL-32 over internal real vertices: position i of
-    // a slice order holds vertex order[i]; entry j of lane l at off + 32 j + l
+    // divergence tables, SELL-32 over internal real vertices (sell_tables)
     m->nslice = (nr + kSell - 1) / kSell;
-    struct Sell {
-        std::vector<int64_t> svo, seo;
-        std::vector<int32_t> vid, eid;
-        std::vector<double> wf, wg, we;
-    };
-    auto build_sell = [&](const std::vector<int32_t> &order, Sell &S) {
-        S.svo.assign(m->nslice + 1, 0);
-        S.seo.assign(m->nslice + 1, 0);
-        for (int64_t sl = 0; sl < m->nslice; ++sl) {
-            int64_t mj = 0, mk = 0;
-            for (int64_t i = sl * kSell; i < std::min(nr, (sl + 1) * kSell); ++i) {
-                const int64_t o = T.v_new2old[order[i]];
-                mj = std::max(mj, T.voff[o + 1] - T.voff[o]);
-                mk = std::max(mk, T.eoff[o + 1] - T.eoff[o]);
-            }
-            S.svo[sl + 1] = S.svo[sl] + mj * kSell;
-            S.seo[sl + 1] = S.seo[sl] + mk * kSell;
-        }
-        S.vid.assign(S.svo[m->nslice], 0);
-        S.eid.assign(S.seo[m->nslice], 0);
-        S.wf.assign(S.svo[m->nslice], 0.0);
-        S.wg.assign(S.svo[m->nslice], 0.0);
-        S.we.assign(S.seo[m->nslice], 0.0);
-        for (int64_t i = 0; i < nr; ++i) {
-            const int32_t v = order[i];
-            const int64_t o = T.v_new2old[v], sl = i / kSell, lane = i % kSell;
-            const int64_t J = T.voff[o + 1] - T.voff[o], K = T.eoff[o + 1] - T.eoff[o];
-            const int64_t mj = (S.svo[sl + 1] - S.svo[sl]) / kSell, mk = (S.seo[sl + 1] - S.seo[sl]) / kSell;
-            for (int64_t j = 0; j < mj; ++j) {
-                const int64_t p = S.svo[sl] + j * kSell + lane;
-                if (j < J) {
-                    const int64_t q = T.voff[o] + j;
-                    S.vid[p] = T.v_old2new[T.vid[q]];
-                    S.wf[p] = T.wf[q];
-                    S.wg[p] = T.wg[q];
-                } else {
-                    S.vid[p] = v;  // padding: weight 0 on the vertex itself
-                }
-            }
-            for (int64_t k = 0; k < mk; ++k) {
-                const int64_t p = S.seo[sl] + k * kSell + lane;
-                if (k < K) {
-                    const int64_t q = T.eoff[o] + k;
-                    S.eid[p] = T.e_old2new[T.eid[q]];
-                    S.we[p] = T.we[q];
-                } else {
-                    S.eid[p] = K > 0 ? T.e_old2new[T.eid[T.eoff[o]]] : 0;
-                }
-            }
-        }
-    };
     // centre weights per vertex
     std::vector<double> cfg(2 * std::max<int64_t>(nr, 1), 0.0);
     for (int64_t v = 0; v < nr; ++v) {
@@ -275,8 +287,9 @@ fdu_status upload_tables(fdu_mesh *m) {
         });
     }
     Sell S32, S64;
-    build_sell(natural, S32);
-    build_sell(sorted, S64);
+    sell_tables(m, natural, T.wf.data(), T.wg.data(), T.we.data(), S32);
+    sell_tables(m, sorted, T.wf.data(), T.wg.data(), T.we.data(), S64);
+    m->order64 = sorted;
     m->vert_nnz_sell = S32.svo[m->nslice];
     m->edge_nnz_sell = S32.seo[m->nslice];
     m->vert_nnz_sell64 = S64.svo[m->nslice];
@@ -341,23 +354,74 @@ fdu_status upload_tables(fdu_mesh *m) {
 inline bool fp64_state(int prec) { return prec != 32; }
 inline int prof_kind(int prec) { return prec == 64 ? 0 : prec == 32 ? 2 : 4; }
 
-// Precision 64, 32 or 48; the first use of 48 builds the double-word
-// coefficient block (hi = the FP32 rounding of each FP64 coefficient, lo =
-// the FP32 rounding of the remainder).
+// Precision 64, 32 or 48.  The first use of 48 builds its tables:
+//  - the double-word edge coefficient block (hi = the FP32 rounding of each
+//    FP64 coefficient, lo = the FP32 rounding of the remainder);
+//  - divergence tables in the FP64 SELL layout where the edge flux, which
+//    the precision-48 edge kernel leaves as the increment
+//    r_k - F_n(L1_k) = r_k - (n_x f + n_y g)(L1_k), has its left-vertex part
+//    folded into the weights of that vertex's fluxes:
+//      sum_k w_k r_k = sum_k w_k (n_x,k f_L1k + n_y,k g_L1k) + sum_k w_k (r_k - F_n(L1_k)),
+//    the first sum going into w_f, w_g (or the centre weights when L1_k is
+//    the vertex itself) and the second taken in double words.
+//    Both ends of every stencil edge are in the vertex's own stencil, so
+//    the folding adds no entries; a mesh where that fails is refused.
 fdu_status check_precision(fdu_mesh *m, int prec) {
     if (prec != 64 && prec != 32 && prec != 48) return set_err(FDU_ERR_ARG, "precision must be 64, 48 or 32");
     if (prec != 48 || m->coefdw) return FDU_OK;
     const HostTables &T = m->T;
-    const int64_t ne = m->ne_act;
-    std::vector<float2> k((size_t)kCoefN * ne);
+    const int64_t ne = m->ne_act, nr = m->n_real;
+    fdu_status st;
+    auto split = [](double x) {
+        const float h = (float)x;
+        return make_float2(h, (float)(x - (double)h));
+    };
+    std::vector<double> wf(T.wf), wg(T.wg), cfg(2 * std::max<int64_t>(nr, 1), 0.0);
+    for (int64_t v = 0; v < nr; ++v) {
+        const int64_t o = T.v_new2old[v];
+        double sf = 0, sg = 0, sx = 0, sy = 0;
+        for (int64_t q = T.voff[o]; q < T.voff[o + 1]; ++q) {
+            sf += T.wf[q];
+            sg += T.wg[q];
+        }
+        for (int64_t q = T.eoff[o]; q < T.eoff[o + 1]; ++q) {
+            const int32_t e = T.eid[q];
+            sx += T.we[q] * T.nrm[2 * e];
+            sy += T.we[q] * T.nrm[2 * e + 1];
+        }
+        double cf = -(sf + sx), cg = -(sg + sy);
+        for (int64_t q = T.eoff[o]; q < T.eoff[o + 1]; ++q) {
+            const int32_t e = T.eid[q];
+            const int32_t L = T.sten[6 * (int64_t)e + 2];
+            const double ax = T.we[q] * T.nrm[2 * e], ay = T.we[q] * T.nrm[2 * e + 1];
+            if (L == o) {
+                cf += ax;
+                cg += ay;
+                continue;
+            }
+            int64_t j = T.voff[o];
+            while (j < T.voff[o + 1] && T.vid[j] != L) ++j;
+            if (j == T.voff[o + 1])
+                return set_err(FDU_ERR_MESH, "precision 48: an edge's left vertex is outside the vertex's stencil");
+            wf[j] += ax;
+            wg[j] += ay;
+        }
+        cfg[v] = cf;
+        cfg[nr + v] = cg;
+    }
+    Sell S;
+    sell_tables(m, m->order64, wf.data(), wg.data(), T.we.data(), S);
+    std::vector<float2> we2(S.we.size());
+    for (size_t i = 0; i < we2.size(); ++i) we2[i] = split(S.we[i]);
+    std::vector<float2> k((size_t)kEdgeCoef * ne);
     for (int64_t e = 0; e < ne; ++e) {
         const int64_t o = T.e_new2old[e];
-        for (int c = 0; c < kCoefN; ++c) {
-            const double x = T.coef[(size_t)kEdgeCoef * o + c];
-            const float h = (float)x;
-            k[(size_t)c * ne + e] = make_float2(h, (float)(x - (double)h));
-        }
+        for (int c = 0; c < kEdgeCoef; ++c) k[(size_t)c * ne + e] = split(T.coef[(size_t)kEdgeCoef * o + c]);
     }
+    if ((st = m->upload(m->swf48, S.wf))) return st;
+    if ((st = m->upload(m->swg48, S.wg))) return st;
+    if ((st = m->upload(m->cfg48, cfg))) return st;
+    if ((st = m->upload(m->swe48, we2))) return st;
     return m->upload(m->coefdw, k);
 }
 
@@ -408,6 +472,10 @@ DivArgs div_args(fdu_mesh *m, int prec, int fin) {
         a.perm = m->perm64;
         a.wf = m->swf64; a.wg = m->swg64; a.we = m->swe64; a.cfg = m->cfg64;
         a.F = m->F64[fin]; a.r = m->r64;
+        if (prec == 48) {  // folded vertex weights, double-word edge increments (in r64's storage)
+            a.wf = m->swf48; a.wg = m->swg48; a.we = m->swe48; a.cfg = m->cfg48;
+            a.dw_edges = true;
+        }
     } else {
         a.wf = m->swf32; a.wg = m->swg32; a.we = m->swe32; a.cfg = m->cfg32;
         a.F = m->F32[fin]; a.r = m->r32;
@@ -466,7 +534,6 @@ void enqueue_stages(fdu_mesh *m, int prec, double dt, const double *dt_dev, cuda
             EdgeArgs ea = edge_args(m, prec, f64 ? (const void *)win : (const void *)m->w32);
             ea.dt_dev = dt_dev;
             if (f64) ea.Q = m->Q64[stage - 1];
-            ea.F64v = m->F64[stage - 1];
             if (prec == 64) launch_edge_flux_f64(ea, s);
             else if (prec == 48) launch_edge_flux_dw(ea, s);
             else launch_edge_flux_f32(ea, s);
@@ -960,7 +1027,6 @@ fdu_status fdu_residual(fdu_mesh *m, int precision, double *dwdt, int on_device,
     timed(m, kd, true, s, [&] {
         EdgeArgs ea = edge_args(m, precision, f64 ? (const void *)m->wn : (const void *)m->w32);
         ea.Q = f64 ? m->Q64[0] : nullptr;
-        ea.F64v = m->F64[0];
         if (precision == 64) launch_edge_flux_f64(ea, s);
         else if (precision == 48) launch_edge_flux_dw(ea, s);
         else launch_edge_flux_f32(ea, s);

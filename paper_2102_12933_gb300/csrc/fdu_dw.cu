@@ -62,31 +62,7 @@ __device__ __forceinline__ d4v ldd4(const double *p, int64_t i) {
     return d4v{a.x, a.y, b.x, b.y};
 }
 
-// ---- conversions by bit manipulation (no FP64 pipe)
-// double -> double word; magnitudes below 2^-126 flush to zero (the data
-// stay far above); the high word keeps the top 24 bits, the low word the
-// next 24 of the remaining 29 (relative error below 2^-47).
-__device__ __forceinline__ dw d2dw(double d) {
-    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-    const int e = (int)((hi >> 20) & 0x7ffu);
-    if (e <= 896) return dw_make(0.0f, 0.0f);
-    const unsigned sgn = hi & 0x80000000u;
-    const float h = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
-    const unsigned m = lo & 0x1fffffffu;  // value m 2^(e - 1075)
-    const unsigned lb = __float_as_uint(__uint2float_rn(m));
-    const int le = (int)((lb >> 23) & 0xffu) + (e - 1075);
-    const float l = (m != 0u && le > 0) ? __uint_as_float(sgn | ((unsigned)le << 23) | (lb & 0x7fffffu)) : 0.0f;
-    return fast_two_sum(h, l);
-}
 __device__ __forceinline__ dw4 d2dw4(const d4v &v) { return d4(d2dw(v.x), d2dw(v.y), d2dw(v.z), d2dw(v.w)); }
-
-// float -> double, exact for normal floats (zero and subnormals -> 0)
-__device__ __forceinline__ double f2d(float x) {
-    const unsigned b = __float_as_uint(x);
-    const unsigned e = (b >> 23) & 0xffu;
-    if (e == 0u) return 0.0;
-    return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)), (int)(b << 29));
-}
 
 // ---- Roe average and characteristic projections (double words)
 struct RoeW {
@@ -200,15 +176,13 @@ __device__ __forceinline__ dw4 ld_dw4(const float2 *S, int j) {
 
 __device__ __forceinline__ void edge_flux_dw_body(const EdgeArgs &A, const int64_t e, float2 *S) {
     const double *__restrict__ w = static_cast<const double *>(A.w);
-    const double *__restrict__ coef = static_cast<const double *>(A.coef);
     const int64_t ne = A.ne;
     const dw gm1 = dw_make(A.dw_gm1[0], A.dw_gm1[1]);
     int32_t s[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
-    const double nx64 = __ldg(coef + (int64_t)kCoefN * ne + e);
-    const double ny64 = __ldg(coef + (int64_t)(kCoefN + 1) * ne + e);
-    const dw nx = d2dw(nx64), ny = d2dw(ny64);
+    const float2 nq = __ldg(A.coefdw + (int64_t)kCoefN * ne + e), mq = __ldg(A.coefdw + (int64_t)(kCoefN + 1) * ne + e);
+    const dw nx = dw_make(nq.x, nq.y), ny = dw_make(mq.x, mq.y);
     const d4v L1 = ldd4(w, s[2]);
     dw4 b;  // L1 in double words
     {
@@ -317,16 +291,11 @@ __device__ __forceinline__ void edge_flux_dw_body(const EdgeArgs &A, const int64
         out = add4_sl(out, D);
     }
 
-    // r = F_n(L1) + increment, in FP64
-    const double *__restrict__ F = A.F64v;
-    const d4v f = ldd4(F, 2 * (int64_t)s[2]), g = ldd4(F, 2 * (int64_t)s[2] + 1);
-    double *r = static_cast<double *>(A.r);
-    const double2 o0 = make_double2(fma(f.x, nx64, g.x * ny64) + (f2d(out.x.h) + f2d(out.x.l)),
-                                    fma(f.y, nx64, g.y * ny64) + (f2d(out.y.h) + f2d(out.y.l)));
-    const double2 o1 = make_double2(fma(f.z, nx64, g.z * ny64) + (f2d(out.z.h) + f2d(out.z.l)),
-                                    fma(f.w, nx64, g.w * ny64) + (f2d(out.w.h) + f2d(out.w.l)));
-    reinterpret_cast<double2 *>(r)[2 * e] = o0;
-    reinterpret_cast<double2 *>(r)[2 * e + 1] = o1;
+    // the increment r - F_n(L1); the divergence adds F_n(L1) through its
+    // folded vertex weights
+    float4 *r = static_cast<float4 *>(A.r);
+    r[2 * e] = make_float4(out.x.h, out.x.l, out.y.h, out.y.l);
+    r[2 * e + 1] = make_float4(out.z.h, out.z.l, out.w.h, out.w.l);
 }
 
 __global__ void __launch_bounds__(kEdgeBlock, 4) edge_flux_dw_kernel(EdgeArgs A) {

@@ -104,12 +104,48 @@ __device__ __forceinline__ dw rsqrt(dw x) {
     return fast_two_sum(y, __fmul_rn(__fmul_rn(y, e), __fmaf_rn(0.375f, e, 0.5f)));
 }
 
-// FP64 <-> double word
-__device__ __forceinline__ dw from_double(double x) {
-    const float h = __double2float_rn(x);
-    return dw{h, __double2float_rn(x - (double)h)};
+// Compensated dot product (Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26(6), 2005, algorithm Dot2, extended to
+// double-word factors): s carries the running FP32 sum, c the sum of the
+// exact errors of each product and sum plus the low-word cross terms; the
+// result s + c has an absolute error of about u^2 times the sum of |terms|.
+struct dot2 {
+    float s, c;
+};
+__device__ __forceinline__ void dot2_add(dot2 &A, dw a, dw x) {
+    const float p = __fmul_rn(a.h, x.h);
+    const float e1 = __fmaf_rn(a.h, x.h, -p);
+    const dw t = two_sum(A.s, p);
+    A.s = t.h;
+    A.c = __fadd_rn(A.c, __fadd_rn(__fadd_rn(e1, t.l), __fmaf_rn(a.h, x.l, __fmul_rn(a.l, x.h))));
 }
-__device__ __forceinline__ double to_double(dw x) { return (double)x.h + (double)x.l; }
+__device__ __forceinline__ dw dot2_result(const dot2 &A) { return two_sum(A.s, A.c); }
+
+// FP64 <-> double word by bit manipulation (GB300 runs float <-> double
+// conversions on its FP64 pipe)
+// double -> double word; magnitudes below 2^-126 flush to zero (the data
+// stay far above); the high word keeps the top 24 bits, the low word the
+// next 24 of the remaining 29 (relative error below 2^-47).
+__device__ __forceinline__ dw d2dw(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e <= 896) return dw_make(0.0f, 0.0f);
+    const unsigned sgn = hi & 0x80000000u;
+    const float h = __uint_as_float(sgn | ((unsigned)(e - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    const unsigned m = lo & 0x1fffffffu;  // value m 2^(e - 1075)
+    const unsigned lb = __float_as_uint(__uint2float_rn(m));
+    const int le = (int)((lb >> 23) & 0xffu) + (e - 1075);
+    const float l = (m != 0u && le > 0) ? __uint_as_float(sgn | ((unsigned)le << 23) | (lb & 0x7fffffu)) : 0.0f;
+    return fast_two_sum(h, l);
+}
+// float -> double, exact for normal floats (zero and subnormals -> 0)
+__device__ __forceinline__ double f2d(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)), (int)(b << 29));
+}
+
 
 }  // namespace dwa
 }  // namespace fdu

@@ -22,6 +22,7 @@
 #include "fdu_internal.h"
 #include "fdu_kernels.cuh"
 #include "fdu_device.cuh"
+#include "fdu_dw.cuh"
 
 namespace fdu {
 namespace {
@@ -160,8 +161,12 @@ __device__ __forceinline__ dbl4 forward_euler(const dbl4 &ws, const dbl4 &L, dou
 }
 
 // ------------------------------------------------------------------ FP64 divergence (+ RK stage)
-// Position i of the SELL tables; the vertex it holds is A.perm[i].
-template <int MODE>
+// Position i of the SELL tables; the vertex it holds is A.perm[i].  With
+// DWE (precision 48) the edge entries are double-word increments
+// r_k - F_n(L1_k) with double-word weights, summed in double words (terms of
+// the size of the increments), and the vertex weights carry the folded
+// F_n(L1_k) parts.
+template <int MODE, bool DWE = false>
 __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) {
     const int64_t sl = i / kSell;
     const int lane = (int)(i % kSell);
@@ -185,7 +190,29 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) 
             acc.w = fma(a, f.w, fma(c, g.w, acc.w));
         }
     }
-    {
+    if (DWE) {
+        using namespace dwa;
+        const float2 *__restrict__ we2 = static_cast<const float2 *>(A.we);
+        const float4 *__restrict__ rd = static_cast<const float4 *>(A.r);
+        dot2 sx{0.0f, 0.0f}, sy = sx, sz = sx, sw = sx;
+        const int64_t b = __ldg(A.slice_eoff + sl) + lane, e = __ldg(A.slice_eoff + sl + 1);
+#pragma unroll 4
+        for (int64_t p = b; p < e; p += kSell) {
+            const int32_t k = __ldg(A.eid + p);
+            const float2 wq = __ldg(we2 + p);
+            const dw a = dw_make(wq.x, wq.y);
+            const float4 q0 = __ldg(rd + 2 * (int64_t)k), q1 = __ldg(rd + 2 * (int64_t)k + 1);
+            dot2_add(sx, a, dw_make(q0.x, q0.y));
+            dot2_add(sy, a, dw_make(q0.z, q0.w));
+            dot2_add(sz, a, dw_make(q1.x, q1.y));
+            dot2_add(sw, a, dw_make(q1.z, q1.w));
+        }
+        const dw rx = dot2_result(sx), ry = dot2_result(sy), rz = dot2_result(sz), rw = dot2_result(sw);
+        acc.x += f2d(rx.h) + f2d(rx.l);
+        acc.y += f2d(ry.h) + f2d(ry.l);
+        acc.z += f2d(rz.h) + f2d(rz.l);
+        acc.w += f2d(rw.h) + f2d(rw.l);
+    } else {
         const int64_t b = __ldg(A.slice_eoff + sl) + lane, e = __ldg(A.slice_eoff + sl + 1);
 #pragma unroll 4
         for (int64_t p = b; p < e; p += kSell) {
@@ -508,12 +535,12 @@ __global__ void __launch_bounds__(kEdgeBlock, 6) edge_flux_f32_kernel(EdgeArgs A
     if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
     edge_flux_f32_body(A, e);
 }
-template <int MODE>
+template <int MODE, bool DWE>
 __global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= A.n_real) return;
     if (MODE != 0 && A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
-    div_f64_body<MODE>(A, v);
+    div_f64_body<MODE, DWE>(A, v);
 }
 template <int MODE>
 __global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
@@ -699,15 +726,20 @@ void launch_edge_flux_f64(const EdgeArgs &a, cudaStream_t s) {
 void launch_edge_flux_f32(const EdgeArgs &a, cudaStream_t s) {
     if (a.ne > 0) edge_flux_f32_kernel<<<blocks(a.ne, kEdgeBlock), kEdgeBlock, 0, s>>>(a);
 }
-void launch_div_f64(const DivArgs &a, int mode, cudaStream_t s) {
-    if (a.n_real <= 0) return;
+template <bool DWE>
+void launch_div_f64_t(const DivArgs &a, int mode, cudaStream_t s) {
     const unsigned g = blocks(a.n_real, kDivBlock);
     switch (mode) {
-        case 0: div_f64_kernel<0><<<g, kDivBlock, 0, s>>>(a); break;
-        case 1: div_f64_kernel<1><<<g, kDivBlock, 0, s>>>(a); break;
-        case 2: div_f64_kernel<2><<<g, kDivBlock, 0, s>>>(a); break;
-        default: div_f64_kernel<3><<<g, kDivBlock, 0, s>>>(a); break;
+        case 0: div_f64_kernel<0, DWE><<<g, kDivBlock, 0, s>>>(a); break;
+        case 1: div_f64_kernel<1, DWE><<<g, kDivBlock, 0, s>>>(a); break;
+        case 2: div_f64_kernel<2, DWE><<<g, kDivBlock, 0, s>>>(a); break;
+        default: div_f64_kernel<3, DWE><<<g, kDivBlock, 0, s>>>(a); break;
     }
+}
+void launch_div_f64(const DivArgs &a, int mode, cudaStream_t s) {
+    if (a.n_real <= 0) return;
+    if (a.dw_edges) launch_div_f64_t<true>(a, mode, s);
+    else launch_div_f64_t<false>(a, mode, s);
 }
 void launch_div_f32(const DivArgs &a, int mode, cudaStream_t s) {
     if (a.n_real <= 0) return;

@@ -22,9 +22,10 @@ struct EdgeArgs {
     unsigned long long *fallback;  // edges that fell back to first order (device counter)
     const double *dt_dev; // adaptive stepping: a zero time step here skips the launch
     const double *Q;      // FP64: per-vertex Roe records of the stage state (nullptr = compute per edge)
-    // double-word edge flux (precision 48; Q is required there)
-    const float2 *coefdw; // [kCoefN][ne] (hi, lo) of the WENO coefficients
-    const double *F64v;   // [nv][8] FP64 vertex fluxes (f, g) of the stage state
+    // double-word edge flux (precision 48; Q is required there): r receives
+    // the increment r_k - F_n(L1_k) as double words, [ne] x two float4
+    // (h0, l0, h1, l1), (h2, l2, h3, l3)
+    const float2 *coefdw; // [kEdgeCoef][ne] (hi, lo) of the coefficient block
     float dw_gm1[2];      // gamma - 1 as a double word
     float dw_tenth[2];    // 0.1 as a double word
     float dw_eps[2];      // WENO epsilon = dw_eps * 2^dw_eps_e, dw_eps in [1, 2)
@@ -40,10 +41,11 @@ struct DivArgs {
     const int32_t *vid;          // vertex entries (SELL: entry j of lane l at off + 32 j + l)
     const void *wf, *wg;         // weights of f_j and g_j
     const int32_t *eid;          // edge entries
-    const void *we;              // weights of r_k
+    const void *we;              // weights of r_k (double words when dw_edges)
     const void *cfg;             // [2][n_real] centre weights: -(sum wf + sum we nx), -(sum wg + sum we ny)
     const void *F;               // vertex fluxes of the stage state: FP64 [nv][8] (f0..3, g0..3); FP32 [nv][2] float4 pairs
-    const void *r;               // edge fluxes
+    const void *r;               // edge fluxes (dw_edges: the precision-48 edge increments)
+    bool dw_edges;               // precision 48: folded vertex weights, double-word edge part
     // residual output (mode 0)
     double *out;                 // [nv][4] FP64
     const int32_t *out_map;      // internal -> output row (nullptr = internal order)

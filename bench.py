@@ -3,9 +3,10 @@
 One step = one SSP-RK3 time step = three (edge flux, divergence + stage)
 passes over the 250,000-vertex periodic isentropic-vortex mesh (jittered
 500x500 torus lattice split on random diagonals, two-level stencils,
-degree-2 least squares, NU-WENO5).  The headline is the FP64 path; the FP32
-residual path (FP64 state accumulation) is measured beside it with its
-error against FP64.
+degree-2 least squares, NU-WENO5).  The headline is the FP64 path; beside it
+are precision 48 (the same FP64 computation with the edge-flux increments in
+double-word FP32 arithmetic) and the FP32 residual path (FP64 state
+accumulation), each with its error against FP64.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -49,6 +50,14 @@ TRAFFIC_EDGE64_B_PER_EDGE = 268.0
 # per edge of edge_flux_f64.
 NCU_EDGE64_FP64_PIPE_BUSY = 0.884
 NCU_EDGE64_FP64_INSTR_PER_EDGE = 512
+# edge_flux_dw (precision 48) from one ncu capture on the 480k-edge case:
+# issue slots busy, FMA (FP32) pipe busy, FP64 pipe busy (% of active
+# cycles), thread instructions per edge, DRAM bytes per edge.
+NCU_EDGE48_ISSUE_ACTIVE = 0.727
+NCU_EDGE48_FMA_PIPE = 0.596
+NCU_EDGE48_FP64_PIPE = 0.132
+NCU_EDGE48_THREAD_INSTR_PER_EDGE = 104959417 * 32 / 480000
+TRAFFIC_EDGE48_B_PER_EDGE = (121.782784 + 7.462912) * 1e6 / 480000
 
 
 def _peaks():
@@ -327,6 +336,21 @@ def run_ours(args):
     M.profile(False)
     w64 = M.get_state()
 
+    # ---------------- precision 48 (FP64 state, double-word edge increments), same steps from w0
+    M.set_state(w0)
+    for _ in range(args.warmup):
+        M.rk_step(dt, 48, stream=stream)
+    M.set_state(w0)
+    M.profile(True)
+    M.profile_read("edge", 48)
+    M.profile_read("div", 48)
+    ms48 = timed_steps(48, args.steps)
+    e48_ms, e48_n = M.profile_read("edge", 48)
+    d48_ms, d48_n = M.profile_read("div", 48)
+    M.profile(False)
+    M.set_state(w0)
+    res_diff48 = _rel_l2(M.residual(48), M.residual(64))
+
     # ---------------- FP32 residual path (FP64 accumulation), same steps from w0
     M.set_state(w0)
     for _ in range(args.warmup):
@@ -351,6 +375,11 @@ def run_ours(args):
     w32b = M.get_state()
     err32 = {"rho": _rel_l2(w32b[:, 0], w64b[:, 0]), "rhoE": _rel_l2(w32b[:, 3], w64b[:, 3]),
              "steps": err_steps}
+    M.set_state(w0)
+    M.rk_steps(dt, err_steps, 48, stream=stream)
+    w48b = M.get_state()
+    err48 = {"rho": _rel_l2(w48b[:, 0], w64b[:, 0]), "rhoE": _rel_l2(w48b[:, 3], w64b[:, 3]),
+             "steps": err_steps}
 
     # ---------------- end to end through the C-ABI with host buffers
     # pinned host buffers: the copies are DMA transfers of the caller's rows
@@ -370,6 +399,9 @@ def run_ours(args):
     stages = 3
     value = replica_throughput(nv * stages * args.steps, ws_, ms64 / 1e3) / 1e6
     value32 = replica_throughput(nv * stages * (args.warmup + args.steps), ws_, ms32 / 1e3) / 1e6
+    value48 = replica_throughput(nv * stages * args.steps, ws_, ms48 / 1e3) / 1e6
+    e48_avg_ms = e48_ms / max(e48_n, 1)
+    tf48 = FLOP_EDGE64 * ne / (e48_avg_ms / 1e3) / 1e12
     e2e_value = replica_throughput(nv * stages * e2e_steps, ws_, e2e_s) / 1e6
     edge_avg_ms = edge_ms / max(edge_n, 1)
     div_avg_ms = div_ms / max(div_n, 1)
@@ -418,6 +450,23 @@ def run_ours(args):
             "div_kernel": {"avg_launch_ms": round(div_avg_ms, 4),
                            "achieved_tflops": round(div_flops / (div_avg_ms / 1e3) / 1e12, 4)},
         },
+        "f64_dw": {
+            "precision": 48,
+            "value": round(value48, 3), "unit": "Mvertex/s", "ms_per_step": round(ms48 / args.steps, 4),
+            "speedup_vs_f64": round(value48 / value, 3),
+            "dtype": "f64 state, divergence and state-sized flux terms; edge-flux increments in f32x2 double words",
+            "residual_vs_f64": res_diff48,
+            "error_vs_f64": err48,
+            "edge_kernel": {"kernel": "edge_flux_dw", "bound": "alu (FP32 issue)",
+                            "avg_launch_ms": round(e48_avg_ms, 4),
+                            "fp64_equivalent_tflops": round(tf48, 4),
+                            "frac_of_fp64_peak": round(tf48 / FP64_PEAK_NOMINAL_TFLOPS, 4),
+                            "ncu_issue_active": NCU_EDGE48_ISSUE_ACTIVE, "ncu_fma_pipe": NCU_EDGE48_FMA_PIPE,
+                            "ncu_fp64_pipe": NCU_EDGE48_FP64_PIPE,
+                            "ncu_thread_instr_per_edge": round(NCU_EDGE48_THREAD_INSTR_PER_EDGE),
+                            "traffic": round(TRAFFIC_EDGE48_B_PER_EDGE * ne), "traffic_unit": "bytes per launch"},
+            "div_kernel": {"avg_launch_ms": round(d48_ms / max(d48_n, 1), 4)},
+        },
         "fp32": {
             "value": round(value32, 3), "unit": "Mvertex/s", "speedup_vs_f64": round(value32 / value, 3),
             "error_vs_f64": err32,
@@ -453,16 +502,17 @@ def run_ours(args):
 
 
 def _advance_both(M, w0, real, t_end, max_steps, err_steps=16):
-    """FP64 then FP32 adaptive runs from w0 to t_end (at most max_steps steps),
-    wall-clock timed between the host's time checks every 8 steps; the
-    FP32 state is compared with the FP64 one after err_steps steps."""
+    """FP64, precision-48 and FP32 adaptive runs from w0 to t_end (at most
+    max_steps steps), wall-clock timed between the host's time checks every
+    8 steps; the other states are compared with the FP64 one after
+    err_steps steps."""
     import torch
 
     from paper_2102_12933_gb300 import fdu
 
     n_real = int(real.sum())
     out, states = {}, {}
-    for prec in (64, 32):
+    for prec in (64, 48, 32):
         M.set_state(w0)
         M.advance(0.5, t_end, prec, max_steps=8)  # warm-up (graph capture)
         M.set_state(w0)
@@ -487,10 +537,11 @@ def _advance_both(M, w0, real, t_end, max_steps, err_steps=16):
         out[prec] = {"steps": steps, "t": t, "seconds": round(el, 3), "status": status,
                      "value": round(n_real * 3 * steps / el / 1e6, 2) if el > 0 else None,
                      "fallback_edges": M.fallback_count(), "safeguarded_vertex_stages": M.limited_count()}
-    err = None
-    if 64 in states and 32 in states:
-        err = {"rho": _rel_l2(states[32][real, 0], states[64][real, 0]),
-               "rhoE": _rel_l2(states[32][real, 3], states[64][real, 3]), "steps": err_steps}
+    err = {}
+    for prec in (48, 32):
+        if 64 in states and prec in states:
+            err[prec] = {"rho": _rel_l2(states[prec][real, 0], states[64][real, 0]),
+                         "rhoE": _rel_l2(states[prec][real, 3], states[64][real, 3]), "steps": err_steps}
     return out, err
 
 
@@ -501,9 +552,13 @@ def _ghost_line(out, err, workload, t_build):
         "ms_per_step": round(1e3 * out[64]["seconds"] / max(out[64]["steps"], 1), 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload, "host_build_s": round(t_build, 2)},
-        "fp64": out[64], "fp32": dict(out[32], speedup_vs_f64=(round(out[32]["value"] / out[64]["value"], 3)
-                                                               if out[32]["value"] and out[64]["value"] else None),
-                                      error_vs_f64=err),
+        "fp64": out[64],
+        "f64_dw": dict(out[48], speedup_vs_f64=(round(out[48]["value"] / out[64]["value"], 3)
+                                                if out[48]["value"] and out[64]["value"] else None),
+                       error_vs_f64=err.get(48)),
+        "fp32": dict(out[32], speedup_vs_f64=(round(out[32]["value"] / out[64]["value"], 3)
+                                              if out[32]["value"] and out[64]["value"] else None),
+                     error_vs_f64=err.get(32)),
     }
 
 

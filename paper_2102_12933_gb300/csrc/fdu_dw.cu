@@ -92,8 +92,9 @@ __device__ __forceinline__ RoeW roe_records(const dw4 &qa, const dw4 &qb, dw nx,
                       ny, gm1);
 }
 // fields q_n - c, q_n (entropy), q_n (shear), q_n + c
-// Sums of increments take the sloppy sum: its absolute error, about
-// u^2 (|x| + |y|), is of the order of the increments' own rounding.
+// Sums of increments (here and in the WENO values and weighted sums) take
+// the sloppy sum: its absolute error, about u^2 (|x| + |y|), is of the
+// order of the increments' own rounding.
 __device__ __forceinline__ dw4 project(const RoeW &R, const dw4 &d) {
     const dw phh = mul(R.b1h, add_sl(sub_sl(sub_sl(mul_u(R.hq2, d.x), mul_u(R.u, d.y)), mul_u(R.v, d.z)), d.w));
     const dw psh = mul(sub_sl(sub_sl(mul_u(R.qn, d.x), mul_u(R.nx, d.y)), mul_u(R.ny, d.z)), R.ich);
@@ -115,11 +116,11 @@ __device__ __forceinline__ int bexp(float x) { return (int)((__float_as_uint(x) 
 
 __device__ __forceinline__ void weno_pair_dw(const dw *k, dw a, dw b, dw c, dw d, dw e, dw f, dw eps_m, int eps_e,
                                              dw &dl, dw &dr) {
-    const dw va = add(mul_u(k[0], a), mul_u(k[1], b));
-    const dw vb = add(mul_u(k[5], b), mul_u(k[6], c));
-    const dw vc = add(mul_u(k[10], c), mul_u(k[11], d));
-    const dw vd = add(mul_u(k[15], e), mul_u(k[16], f));
-    const dw vdc = add(vd, c);  // S_d's value from L1
+    const dw va = add_sl(mul_u(k[0], a), mul_u(k[1], b));
+    const dw vb = add_sl(mul_u(k[5], b), mul_u(k[6], c));
+    const dw vc = add_sl(mul_u(k[10], c), mul_u(k[11], d));
+    const dw vd = add_sl(mul_u(k[15], e), mul_u(k[16], f));
+    const dw vdc = add_sl(vd, c);  // S_d's value from L1
     // common power-of-two scale of the six differences: max |.| in [1/2, 1)
     const float mx = fmaxf(fmaxf(fmaxf(fabsf(a.h), fabsf(b.h)), fmaxf(fabsf(c.h), fabsf(d.h))),
                            fmaxf(fabsf(e.h), fabsf(f.h)));
@@ -147,9 +148,9 @@ __device__ __forceinline__ void weno_pair_dw(const dw *k, dw a, dw b, dw c, dw d
     const dw rd = recip(beta(k[17], k[18], k[19], mul_u(e, e), mul_u(e, f), mul_u(f, f)));
     // alpha_k = C_k / (beta_k + eps); the block stores C_0/C_1, C_2/C_1 (C_1 -> 1)
     const dw l0 = mul(k[20], ra), l2 = mul(k[21], rc);
-    dl = mul(add(add(mul_u(l0, va), mul_u(rb, vb)), mul_u(l2, vc)), recip(add_sl(add_sl(l0, rb), l2)));
+    dl = mul(add_sl(add_sl(mul_u(l0, va), mul_u(rb, vb)), mul_u(l2, vc)), recip(add_sl(add_sl(l0, rb), l2)));
     const dw r0 = mul(k[22], rd), r2 = mul(k[23], rb);
-    dr = mul(add(add(mul_u(r0, vdc), mul_u(rc, vc)), mul_u(r2, vb)), recip(add_sl(add_sl(r0, rc), r2)));
+    dr = mul(add_sl(add_sl(mul_u(r0, vdc), mul_u(rc, vc)), mul_u(r2, vb)), recip(add_sl(add_sl(r0, rc), r2)));
 }
 
 // ---- the edge flux
@@ -212,7 +213,7 @@ __device__ __forceinline__ void edge_flux_dw_body(const EdgeArgs &A, const int64
         for (int i = 0; i < 4; ++i) {
             const dw c = ld_dw(S, i), f = ld_dw(S, 12 + i);
             dw dl, dr;
-            weno_pair_dw(k, ld_dw(S, 8 + i), ld_dw(S, 4 + i), c, add(f, c), ld_dw(S, 16 + i), f, eps_m, A.dw_eps_e,
+            weno_pair_dw(k, ld_dw(S, 8 + i), ld_dw(S, 4 + i), c, add_sl(f, c), ld_dw(S, 16 + i), f, eps_m, A.dw_eps_e,
                          dl, dr);
             st_dw(S, 20 + i, dl);
             st_dw(S, 24 + i, dr);

@@ -124,8 +124,10 @@ __device__ __forceinline__ dw dot2_result(const dot2 &A) { return two_sum(A.s, A
 // FP64 <-> double word by bit manipulation (GB300 runs float <-> double
 // conversions on its FP64 pipe)
 // double -> double word; magnitudes below 2^-126 flush to zero (the data
-// stay far above); the high word keeps the top 24 bits, the low word the
-// next 24 of the remaining 29 (relative error below 2^-47).
+// stay far above); the high word keeps the top 24 bits (truncated), the low
+// word the next 24 of the remaining 29 (relative error below 2^-47).  The
+// pair is not renormalised (|l| < ulp(h) instead of ulp(h)/2): the
+// operations that take it renormalise their results.
 __device__ __forceinline__ dw d2dw(double d) {
     const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
     const int e = (int)((hi >> 20) & 0x7ffu);
@@ -136,7 +138,7 @@ __device__ __forceinline__ dw d2dw(double d) {
     const unsigned lb = __float_as_uint(__uint2float_rn(m));
     const int le = (int)((lb >> 23) & 0xffu) + (e - 1075);
     const float l = (m != 0u && le > 0) ? __uint_as_float(sgn | ((unsigned)le << 23) | (lb & 0x7fffffu)) : 0.0f;
-    return fast_two_sum(h, l);
+    return dw_make(h, l);  // |l| < ulp(h): the truncated split, not renormalised
 }
 // float -> double, exact for normal floats (zero and subnormals -> 0)
 __device__ __forceinline__ double f2d(float x) {

@@ -344,6 +344,15 @@ fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n);
  * Roe weights): y[i] = 1/sqrt(x[i]) by Newton-Raphson refinement of the
  * hardware approximation, for host arrays of positive normal doubles. */
 fdu_status fdu_check_rsqrt64(int device, const double *x, double *y, int64_t n);
+/* Accuracy check of the double-word primitives of precision 48 (no
+ * counterpart in the paper).  Host arrays x[n], y[n]; each value is split
+ * into a double word as the precision-48 kernels split FP64 inputs, `op`
+ * is applied and the double-word result is returned exactly as a double:
+ * 0 the split of x, 1 x + y (accurate sum), 2 x + y (sloppy sum), 3 x * y,
+ * 4 x * y before renormalisation, 5 1/x, 6 1/sqrt(x) (x > 0 normal), 7 the
+ * compensated dot product of each 8 consecutive pairs (n a multiple of 8;
+ * z[n/8]).  FDU_ERR_ARG for a bad op or size. */
+fdu_status fdu_check_dw(int device, int op, const double *x, const double *y, double *z, int64_t n);
 
 /* Measurement helper with no counterpart in the paper: the FMA throughput
  * (TFLOP/s, FMA = 2 flops) of `device` at precision 64 or 32, from a short

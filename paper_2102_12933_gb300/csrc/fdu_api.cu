@@ -1665,6 +1665,26 @@ fdu_status fdu_check_rsqrt64(int device, const double *x, double *y, int64_t n) 
     return check_special(device, x, y, n, 1);
 }
 
+fdu_status fdu_check_dw(int device, int op, const double *x, const double *y, double *z, int64_t n) {
+    if (!x || !y || !z || n < 0 || op < 0 || op > 7 || (op == 7 && n % 8 != 0))
+        return set_err(FDU_ERR_ARG, "bad arguments");
+    if (n == 0) return FDU_OK;
+    CK(cudaSetDevice(device));
+    double *d = nullptr;
+    CK(cudaMalloc(&d, 3 * n * sizeof(double)));
+    cudaError_t e = cudaMemcpy(d, x, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + n, y, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch_dw_check(op, d, d + n, d + 2 * n, n, nullptr);
+        e = cudaGetLastError();
+    }
+    const int64_t nz = op == 7 ? n / 8 : n;
+    if (e == cudaSuccess) e = cudaMemcpy(z, d + 2 * n, nz * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("double-word check: ") + cudaGetErrorString(e));
+    return FDU_OK;
+}
+
 fdu_status fdu_probe_fma(int device, int precision, double *tflops) {
     if (!tflops || (precision != 64 && precision != 32)) return set_err(FDU_ERR_ARG, "bad precision or output");
     CK(cudaSetDevice(device));

@@ -307,7 +307,37 @@ __global__ void __launch_bounds__(kEdgeBlock, 4) edge_flux_dw_kernel(EdgeArgs A)
     edge_flux_dw_body(A, e, stage + threadIdx.x);
 }
 
+// Accuracy check of the double-word primitives: inputs and outputs as
+// doubles (inputs split by d2dw, outputs recombined exactly by f2d).
+__global__ void dw_check_kernel(int op, const double *__restrict__ x, const double *__restrict__ y,
+                                double *__restrict__ z, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    auto out = [&](dw r) { z[i] = f2d(r.h) + f2d(r.l); };
+    if (op == 7) {  // compensated dot product of 8 consecutive pairs
+        if (i >= n / 8) return;
+        dot2 A{0.0f, 0.0f};
+        for (int j = 0; j < 8; ++j) dot2_add(A, d2dw(x[8 * i + j]), d2dw(y[8 * i + j]));
+        out(dot2_result(A));
+        return;
+    }
+    if (i >= n) return;
+    const dw a = d2dw(x[i]), b = d2dw(y[i]);
+    switch (op) {
+        case 0: out(a); break;
+        case 1: out(add(a, b)); break;
+        case 2: out(add_sl(a, b)); break;
+        case 3: out(mul(a, b)); break;
+        case 4: out(mul_u(a, b)); break;
+        case 5: out(recip(a)); break;
+        default: out(rsqrt(a)); break;
+    }
+}
+
 }  // namespace
+
+void launch_dw_check(int op, const double *x, const double *y, double *z, int64_t n, cudaStream_t s) {
+    if (n > 0) dw_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(op, x, y, z, n);
+}
 
 void launch_edge_flux_dw(const EdgeArgs &a, cudaStream_t s) {
     if (a.ne > 0) edge_flux_dw_kernel<<<(unsigned)((a.ne + kEdgeBlock - 1) / kEdgeBlock), kEdgeBlock, 0, s>>>(a);

@@ -72,6 +72,8 @@ void launch_vertex_flux_f32(const double *w, float4 *F, float4 *w32, int64_t n, 
 void launch_edge_flux_f64(const EdgeArgs &a, cudaStream_t s);
 void launch_edge_flux_f32(const EdgeArgs &a, cudaStream_t s);
 void launch_edge_flux_dw(const EdgeArgs &a, cudaStream_t s);
+// z = double-word primitive `op` of x (and y), device pointers (accuracy check)
+void launch_dw_check(int op, const double *x, const double *y, double *z, int64_t n, cudaStream_t s);
 void launch_div_f64(const DivArgs &a, int mode, cudaStream_t s);
 void launch_div_f32(const DivArgs &a, int mode, cudaStream_t s);
 // *bad = min(*bad, first row of w[n][4] with rho <= 0 or a non-finite value)

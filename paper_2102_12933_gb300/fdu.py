@@ -33,7 +33,7 @@ EXPORTS = (
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
     "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
-    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_mesh_create_cells", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
+    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_check_dw", "fdu_mesh_create_cells", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
     "fdu_batch_max_dt", "fdu_batch_set_dt", "fdu_batch_rk_steps", "fdu_batch_set_launch", "fdu_batch_autotune",
     "fdu_batch_barrier_selftest", "fdu_residual_vjp", "fdu_rk_step_vjp", "fdu_adjoint_rk",
 )
@@ -108,6 +108,7 @@ def load():
         L.fdu_residual_noalloc.argtypes = [P, P, P, P]
         L.fdu_check_recip64.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_check_rsqrt64.argtypes = [C.c_int, dp, dp, i64]
+        L.fdu_check_dw.argtypes = [C.c_int, C.c_int, dp, dp, dp, i64]
         L.fdu_mesh_create_cells.argtypes = [dp, i64, lp, ip, i64, C.c_int, C.POINTER(MeshOpts), C.POINTER(P)]
         L.fdu_advance.argtypes = [P, C.c_double, C.c_double, C.c_int, i64, lp, dp, P]
         L.fdu_limited_count.argtypes = [P, lp, C.c_int, P]
@@ -208,6 +209,21 @@ def check_recip64(x, device=0):
     y = np.zeros_like(x)
     _check(load().fdu_check_recip64(int(device), _dp(x), _dp(y), x.size))
     return y
+
+
+DW_OPS = {"split": 0, "add": 1, "add_sloppy": 2, "mul": 3, "mul_unnormalised": 4, "recip": 5, "rsqrt": 6,
+          "dot8": 7}
+
+
+def check_dw(op, x, y=None, device=0):
+    """A double-word primitive of precision 48 applied to x (and y), the
+    result returned exactly as doubles (accuracy check)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x) if y is None else np.ascontiguousarray(y, dtype=np.float64)
+    k = DW_OPS[op]
+    z = np.zeros(x.size // 8 if k == 7 else x.size)
+    _check(load().fdu_check_dw(int(device), k, _dp(x), _dp(y), _dp(z), x.size))
+    return z
 
 
 def check_rsqrt64(x, device=0):

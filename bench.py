@@ -53,11 +53,11 @@ NCU_EDGE64_FP64_INSTR_PER_EDGE = 512
 # edge_flux_dw (precision 48) from one ncu capture on the 480k-edge case:
 # issue slots busy, FMA (FP32) pipe busy, FP64 pipe busy (% of active
 # cycles), thread instructions per edge, DRAM bytes per edge.
-NCU_EDGE48_ISSUE_ACTIVE = 0.727
-NCU_EDGE48_FMA_PIPE = 0.596
-NCU_EDGE48_FP64_PIPE = 0.132
-NCU_EDGE48_THREAD_INSTR_PER_EDGE = 104959417 * 32 / 480000
-TRAFFIC_EDGE48_B_PER_EDGE = (121.782784 + 7.462912) * 1e6 / 480000
+NCU_EDGE48_ISSUE_ACTIVE = 0.718
+NCU_EDGE48_FMA_PIPE = 0.585
+NCU_EDGE48_FP64_PIPE = 0.141
+NCU_EDGE48_THREAD_INSTR_PER_EDGE = 97722617 * 32 / 480000
+TRAFFIC_EDGE48_B_PER_EDGE = (121.78432 + 6.677504) * 1e6 / 480000
 
 
 def _peaks():

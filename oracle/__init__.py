@@ -17,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fdu_oracle.c")
+_SRC_STATE = os.path.join(_HERE, "fdu_oracle_state.h")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libfdu_oracle.so")
 _lock = threading.Lock()
@@ -29,7 +30,8 @@ GAMMA = 1.4  # ratio of specific heats (Section 2.1)
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_STATE))
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
@@ -76,6 +78,12 @@ def lib():
             L.om_max_dt.argtypes = [P, dp, C.c_double]
             L.om_max_dt.restype = C.c_double
             L.om_fill_ghosts.argtypes = [P, dp]
+            # complex-step copies (double complex arrays passed as pointers)
+            L.om_residual_cs.argtypes = [P, P, C.c_double, up, P, lp]
+            L.om_residual_cs.restype = C.c_int
+            L.om_rk3_step_cs.argtypes = [P, P, C.c_double, C.c_double, lp]
+            L.om_rk3_step_cs.restype = C.c_int
+            L.om_fill_ghosts_cs.argtypes = [P, P]
             L.om_walk_edge.argtypes = [P, i64, ip]
             L.om_walk_edge.restype = C.c_int
             L.om_curve_coords.argtypes = [dp, dp]
@@ -296,6 +304,35 @@ class OracleMesh:
         nf = C.c_int64()
         _check(lib().om_rk3_step(self._h, _d(w), float(dt), float(eps), C.byref(nf)))
         return (w, nf.value) if return_fallbacks else w
+
+    # ---- complex-step tangents (directional derivatives of the same functions)
+    # Im F(w + i h d) / h = J d for a function analytic in the state, with no
+    # subtraction (Squire & Trapp 1998); the branches are those of F at w.
+    CS_STEP = 1e-30
+
+    def _complex_state(self, w, d):
+        z = np.ascontiguousarray(_f64(w, (self.nv, 4)) + 1j * self.CS_STEP * _f64(d, (self.nv, 4)))
+        return z
+
+    def residual_jvp(self, w, d, eps=EPS, return_value=False):
+        """J d, J the Jacobian of ``residual`` at w (ghost fill included)."""
+        z = self._complex_state(w, d)
+        if self._ghost is not None:
+            lib().om_fill_ghosts_cs(self._h, z.ctypes.data)
+        out = np.zeros((self.nv, 4), np.complex128)
+        nf = C.c_int64()
+        _check(lib().om_residual_cs(self._h, z.ctypes.data, float(eps), None, out.ctypes.data, C.byref(nf)))
+        jd = out.imag / self.CS_STEP
+        return (out.real.copy(), jd) if return_value else jd
+
+    def rk3_steps_jvp(self, w, d, dt, n=1, eps=EPS):
+        """(state, J d) after n SSP-RK3 steps of size dt from w, J the
+        Jacobian of the n-step map (``rk3_step`` applied n times)."""
+        z = self._complex_state(w, d)
+        nf = C.c_int64()
+        for _ in range(n):
+            _check(lib().om_rk3_step_cs(self._h, z.ctypes.data, float(dt), float(eps), C.byref(nf)))
+        return z.real.copy(), z.imag / self.CS_STEP
 
     def set_positivity(self, alpha):
         """Enable the stage positivity safeguard (alpha > 0) or disable it (0)."""

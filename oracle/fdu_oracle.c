@@ -33,6 +33,7 @@
  * for characteristics are readings: the tests pin their properties, not
  * printed values.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -304,110 +305,49 @@ void om_s5_coeffs(const double *x, double *l /*[5]*/) {
     }
 }
 
-/* Smoothness indicator of a quadratic through (p[3], q[3]) on [a, b]:
- * sum_{l=1,2} int_a^b dx^{2l-1} (d^l u/dx^l)^2 dx with dx = b - a. */
-static double smoothness(const double *p, const double *q, double a, double b) {
-    double A = 0, B = 0; /* u'(0) and u'' of the interpolating quadratic */
-    for (int j = 0; j < 3; ++j) {
-        double pa = p[(j + 1) % 3], pb = p[(j + 2) % 3];
-        double D = (p[j] - pa) * (p[j] - pb);
-        A += q[j] * (-(pa + pb)) / D;
-        B += q[j] * 2.0 / D;
-    }
-    double dx = b - a;
-    double i1 = A * A * (b - a) + A * B * (b * b - a * a) + B * B * (b * b * b - a * a * a) / 3.0;
-    double i2 = B * B * (b - a);
-    return dx * i1 + dx * dx * dx * i2;
-}
-
-/* Left-state interpolation at 0 (mode 0: nonlinear weights, 1: linear). */
-double om_nuweno(const double *x, const double *u, double eps, int mode) {
-    double lag[9], C[3], ut[3], beta[3];
-    om_substencil_coeffs(x, lag);
-    om_linear_weights(x, C);
-    for (int k = 0; k < 3; ++k) {
-        ut[k] = lag[3 * k] * u[k] + lag[3 * k + 1] * u[k + 1] + lag[3 * k + 2] * u[k + 2];
-        beta[k] = smoothness(x + k, u + k, x[2], x[3]);
-    }
-    if (mode == 1) return C[0] * ut[0] + C[1] * ut[1] + C[2] * ut[2];
-    double alpha[3], sa = 0;
-    for (int k = 0; k < 3; ++k) {
-        alpha[k] = C[k] / (beta[k] + eps); /* p = 1 */
-        sa += alpha[k];
-    }
-    double r = 0;
-    for (int k = 0; k < 3; ++k) r += alpha[k] / sa * ut[k];
-    return r;
-}
-
 /* ------------------------------------------------------------------ */
-/* Euler (Section 2.1) and the Riemann flux                            */
+/* State-dependent arithmetic (fdu_oracle_state.h), instantiated twice.  */
+/* REAL = double: the oracle.  REAL = double complex: complex-step       */
+/* tangents (Squire & Trapp, SIAM Review 40(1), 1998): for a function F  */
+/* analytic in the state, F(w + i h d) = F(w) + i h J d + O(h^2), so     */
+/* Im F(w + i h d) / h is the directional derivative J d with no         */
+/* subtraction, exact to rounding for h = 1e-30.  The complex copy takes */
+/* every branch (positivity fallback, entropy-fix band, pivot choice) on */
+/* real parts and uses the analytic |x| = sign(Re x) x, so its real part */
+/* is the oracle's value and its derivative is that of the same branch.  */
 /* ------------------------------------------------------------------ */
-static double pressure(const double *w, double g) {
-    return (g - 1.0) * (w[3] - 0.5 * (w[1] * w[1] + w[2] * w[2]) / w[0]);
-}
-static void flux_fg(const double *w, double g, double *f, double *gg) {
-    double rho = w[0], u = w[1] / rho, v = w[2] / rho, p = pressure(w, g);
-    f[0] = rho * u; f[1] = rho * u * u + p; f[2] = rho * u * v; f[3] = (w[3] + p) * u;
-    gg[0] = rho * v; gg[1] = rho * v * u; gg[2] = rho * v * v + p; gg[3] = (w[3] + p) * v;
-}
+int om_build_weights(om_mesh *m, const uint8_t *mask);
+#define OM_CAT2(a, b) a##b
+#define OM_CAT(a, b) OM_CAT2(a, b)
+#define OMS(name) OM_CAT(name, OM_SUFFIX)
 
-/* Roe average of a and b, then the right eigenvectors of dF_n/dw as
- * columns (order: q_n - c, q_n (entropy), q_n (shear), q_n + c) and the
- * eigenvalues.  Reading: the paper names neither the average nor the
- * eigenvector normalisation. */
-static int roe_eigen(const double *a, const double *b, const double *n, double g, double R[4][4], double lam[4], double *cout) {
-    double ra = a[0], rb = b[0];
-    if (!(ra > 0) || !(rb > 0)) return OM_ERR_NONPHYSICAL;
-    double ua = a[1] / ra, va = a[2] / ra, ub = b[1] / rb, vb = b[2] / rb;
-    double Ha = (a[3] + pressure(a, g)) / ra, Hb = (b[3] + pressure(b, g)) / rb;
-    double sa = sqrt(ra), sb = sqrt(rb);
-    double u = (sa * ua + sb * ub) / (sa + sb);
-    double v = (sa * va + sb * vb) / (sa + sb);
-    double H = (sa * Ha + sb * Hb) / (sa + sb);
-    double q2 = u * u + v * v;
-    double c2 = (g - 1.0) * (H - 0.5 * q2);
-    if (!(c2 > 0)) return OM_ERR_NONPHYSICAL;
-    double c = sqrt(c2);
-    double nx = n[0], ny = n[1];
-    double qn = u * nx + v * ny, qt = -u * ny + v * nx;
-    double col[4][4] = {
-        {1, u - c * nx, v - c * ny, H - c * qn},
-        {1, u, v, 0.5 * q2},
-        {0, -ny, nx, qt},
-        {1, u + c * nx, v + c * ny, H + c * qn},
-    };
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) R[i][j] = col[j][i];
-    lam[0] = qn - c; lam[1] = qn; lam[2] = qn; lam[3] = qn + c;
-    if (cout) *cout = c;
-    return OM_OK;
-}
+#define OM_SUFFIX
+#define REAL double
+#define RE(x) (x)
+#define SQRT(x) sqrt(x)
+#define ABSV(x) fabs(x)
+#define MAGR(x) fabs(x)
+#include "fdu_oracle_state.h"
+#undef OM_SUFFIX
+#undef REAL
+#undef RE
+#undef SQRT
+#undef ABSV
+#undef MAGR
 
-/* Gauss-Jordan inverse with partial pivoting (a plain library-style step) */
-static int inverse4(double A[4][4], double X[4][4]) {
-    double M[4][8];
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 8; ++j) M[i][j] = j < 4 ? A[i][j] : (j - 4 == i);
-    for (int col = 0; col < 4; ++col) {
-        int piv = col;
-        for (int i = col + 1; i < 4; ++i)
-            if (fabs(M[i][col]) > fabs(M[piv][col])) piv = i;
-        if (M[piv][col] == 0) return -1;
-        if (piv != col)
-            for (int j = 0; j < 8; ++j) { double t = M[col][j]; M[col][j] = M[piv][j]; M[piv][j] = t; }
-        double inv = 1.0 / M[col][col];
-        for (int j = 0; j < 8; ++j) M[col][j] *= inv;
-        for (int i = 0; i < 4; ++i) {
-            if (i == col) continue;
-            double f = M[i][col];
-            for (int j = 0; j < 8; ++j) M[i][j] -= f * M[col][j];
-        }
-    }
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) X[i][j] = M[i][j + 4];
-    return 0;
-}
+#define OM_SUFFIX _cs
+#define REAL double complex
+#define RE(x) creal(x)
+#define SQRT(x) csqrt(x)
+#define ABSV(x) (creal(x) < 0 ? -(x) : (x))
+#define MAGR(x) fabs(creal(x))
+#include "fdu_oracle_state.h"
+#undef OM_SUFFIX
+#undef REAL
+#undef RE
+#undef SQRT
+#undef ABSV
+#undef MAGR
 
 /* exported for the tests: R (row-major 4x4) and its inverse */
 int om_eigvec(const double *a, const double *b, const double *n, double gamma, double *Rout, double *Lout, double *lam) {
@@ -418,89 +358,6 @@ int om_eigvec(const double *a, const double *b, const double *n, double gamma, d
     memcpy(Rout, R, sizeof R);
     memcpy(Lout, L, sizeof L);
     return OM_OK;
-}
-
-/* Reading (the paper does not name the solver for its method; Roe is the
- * one it pairs with WENO for WCNS in Section 3.2): Roe flux with Harten's
- * entropy fix |l| -> (l^2 + d^2)/(2d) for |l| < d, d = 0.1 c. */
-int om_roe_flux(const double *wl, const double *wr, const double *n, double g, double *out) {
-    double R[4][4], L[4][4], lam[4], c;
-    int st = roe_eigen(wl, wr, n, g, R, lam, &c);
-    if (st) return st;
-    if (inverse4(R, L)) return OM_ERR_NONPHYSICAL;
-    double fl[4], gl[4], fr[4], gr[4];
-    flux_fg(wl, g, fl, gl);
-    flux_fg(wr, g, fr, gr);
-    double dw[4], al[4];
-    for (int i = 0; i < 4; ++i) dw[i] = wr[i] - wl[i];
-    for (int k = 0; k < 4; ++k) {
-        al[k] = 0;
-        for (int j = 0; j < 4; ++j) al[k] += L[k][j] * dw[j];
-    }
-    double delta = 0.1 * c;
-    for (int k = 0; k < 4; ++k) {
-        double a = fabs(lam[k]);
-        if (a < delta) a = (lam[k] * lam[k] + delta * delta) / (2 * delta);
-        lam[k] = a;
-    }
-    for (int i = 0; i < 4; ++i) {
-        double diss = 0;
-        for (int k = 0; k < 4; ++k) diss += lam[k] * al[k] * R[i][k];
-        double fn_l = n[0] * fl[i] + n[1] * gl[i];
-        double fn_r = n[0] * fr[i] + n[1] * gr[i];
-        out[i] = 0.5 * (fn_l + fn_r) - 0.5 * diss;
-    }
-    return OM_OK;
-}
-
-/* ------------------------------------------------------------------ */
-/* Edge flux: characteristic NU-WENO5 + Roe (Section 2.3.1, Appendix)  */
-/* Reading: characteristics at the Roe average of the two edge end     */
-/* states; the right state uses the mirrored stencil.  Positivity      */
-/* reading: if an interpolated density or pressure is not positive,    */
-/* the edge falls back to the end states (first order) and is counted. */
-/* ------------------------------------------------------------------ */
-static int edge_flux(const om_mesh *m, const double *w, int64_t k, double eps, double *r, int *fallback) {
-    const int32_t *s = m->sten + 6 * k;
-    const double *xi = m->xi + 6 * k;
-    const double *W[6];
-    for (int i = 0; i < 6; ++i) W[i] = w + 4 * (int64_t)s[i];
-    const double *n = m->nrm + 2 * k;
-    double R[4][4], L[4][4], lam[4];
-    int st = roe_eigen(W[2], W[3], n, m->gamma, R, lam, NULL);
-    if (st) return st;
-    if (inverse4(R, L)) return OM_ERR_NONPHYSICAL;
-    double ch[6][4];
-    for (int i = 0; i < 6; ++i)
-        for (int f = 0; f < 4; ++f) {
-            ch[i][f] = 0;
-            for (int j = 0; j < 4; ++j) ch[i][f] += L[f][j] * W[i][j];
-        }
-    double xl[5] = {xi[0], xi[1], xi[2], xi[3], xi[4]};
-    double xr[5] = {-xi[5], -xi[4], -xi[3], -xi[2], -xi[1]};
-    double cl[4], cr[4];
-    for (int f = 0; f < 4; ++f) {
-        double ul[5] = {ch[0][f], ch[1][f], ch[2][f], ch[3][f], ch[4][f]};
-        double ur[5] = {ch[5][f], ch[4][f], ch[3][f], ch[2][f], ch[1][f]};
-        cl[f] = om_nuweno(xl, ul, eps, 0);
-        cr[f] = om_nuweno(xr, ur, eps, 0);
-    }
-    double wl[4], wr[4];
-    for (int i = 0; i < 4; ++i) {
-        wl[i] = 0;
-        wr[i] = 0;
-        for (int f = 0; f < 4; ++f) {
-            wl[i] += R[i][f] * cl[f];
-            wr[i] += R[i][f] * cr[f];
-        }
-    }
-    *fallback = 0;
-    if (!(wl[0] > 0) || !(wr[0] > 0) || !(pressure(wl, m->gamma) > 0) || !(pressure(wr, m->gamma) > 0)) {
-        memcpy(wl, W[2], sizeof wl);
-        memcpy(wr, W[3], sizeof wr);
-        *fallback = 1;
-    }
-    return om_roe_flux(wl, wr, n, m->gamma, r);
 }
 
 /* ------------------------------------------------------------------ */
@@ -991,157 +848,7 @@ void om_get_div(const om_mesh *m, int64_t *voff, int32_t *vid, double *wf, doubl
 /* ------------------------------------------------------------------ */
 /* Residual (Section 2.2.1): dw/dt = -(a1 + b2) per component          */
 /* ------------------------------------------------------------------ */
-/* r[ne][4] for edges with emask[k] (NULL = all) */
-int om_edge_fluxes(const om_mesh *m, const double *w, double eps, const uint8_t *emask, double *r, int64_t *nfallback) {
-    int64_t nf = 0;
-    for (int64_t k = 0; k < m->ne; ++k) {
-        if (emask && !emask[k]) continue;
-        if (m->sten[6 * k] < 0) return fail(OM_ERR_STENCIL, "an edge in a divergence stencil has no 1D stencil");
-        int fb = 0;
-        int st = edge_flux(m, w, k, eps, r + 4 * k, &fb);
-        if (st) return fail(st, "non-physical state in an edge flux");
-        nf += fb;
-    }
-    if (nfallback) *nfallback = nf;
-    return OM_OK;
-}
-
-/* ghost fill: a transmissive ghost copies its donor (reading); a ghost
- * that is its own donor is a Dirichlet vertex and keeps its state */
-void om_fill_ghosts(const om_mesh *m, double *w) {
-    if (!m->ghost) return;
-    for (int64_t v = 0; v < m->nv; ++v)
-        if (m->ghost[v] >= 0 && m->ghost[v] != v) memcpy(w + 4 * v, w + 4 * (int64_t)m->ghost[v], 4 * sizeof(double));
-}
-
-/* dwdt[nv][4] at vertices with vmask[v] (NULL = all real vertices);
- * w must already hold the ghost states.  The edge fluxes needed are
- * computed from scratch. */
-int om_residual(om_mesh *m, const double *w, double eps, const uint8_t *vmask, double *dwdt, int64_t *nfallback) {
-    int st = om_build_weights(m, vmask);
-    if (st) return st;
-    uint8_t *emask = (uint8_t *)calloc(m->ne, 1);
-    for (int64_t o = 0; o < m->nv; ++o) {
-        if (vmask && !vmask[o]) continue;
-        for (int64_t i = m->de_off[o]; i < m->de_off[o + 1]; ++i) emask[m->de_id[i]] = 1;
-    }
-    double *r = (double *)calloc(m->ne * 4, sizeof(double));
-    st = om_edge_fluxes(m, w, eps, emask, r, nfallback);
-    if (st) { free(emask); free(r); return st; }
-    for (int64_t o = 0; o < m->nv; ++o) {
-        if (vmask && !vmask[o]) continue;
-        if (m->ghost && m->ghost[o] >= 0) { for (int c = 0; c < 4; ++c) dwdt[4 * o + c] = 0; continue; }
-        double f0[4], g0[4], fj[4], gj[4];
-        flux_fg(w + 4 * o, m->gamma, f0, g0);
-        double div[4] = {0, 0, 0, 0};
-        for (int64_t i = m->dv_off[o]; i < m->dv_off[o + 1]; ++i) {
-            flux_fg(w + 4 * (int64_t)m->dv_id[i], m->gamma, fj, gj);
-            for (int c = 0; c < 4; ++c) div[c] += m->wf[i] * (fj[c] - f0[c]) + m->wg[i] * (gj[c] - g0[c]);
-        }
-        for (int64_t i = m->de_off[o]; i < m->de_off[o + 1]; ++i) {
-            int32_t e = m->de_id[i];
-            for (int c = 0; c < 4; ++c)
-                div[c] += m->we[i] * (r[4 * e + c] - (m->nrm[2 * e] * f0[c] + m->nrm[2 * e + 1] * g0[c]));
-        }
-        for (int c = 0; c < 4; ++c) dwdt[4 * o + c] = -div[c];
-    }
-    free(emask);
-    free(r);
-    return OM_OK;
-}
-
-/* SSP-RK3 stage combination (Shu & Osher), stage = 1, 2, 3:
- *   1: out = wn + dt L
- *   2: out = 3/4 wn + 1/4 (ws + dt L)
- *   3: out = 1/3 wn + 2/3 (ws + dt L)                                  */
-void om_stage_combine(int64_t n, int stage, const double *wn, const double *ws, const double *L, double dt,
-                      double *out) {
-    for (int64_t i = 0; i < n; ++i) {
-        if (stage == 1) out[i] = wn[i] + dt * L[i];
-        else if (stage == 2) out[i] = 0.75 * wn[i] + 0.25 * (ws[i] + dt * L[i]);
-        else out[i] = (1.0 / 3.0) * wn[i] + (2.0 / 3.0) * (ws[i] + dt * L[i]);
-    }
-}
-
-/* Positivity safeguard of a stage (a reading: the paper has none, its Sod
- * run overshoots).  The forward-Euler part fe = ws + theta dt L of each
- * vertex's stage uses the largest theta in {1, 1/2, ..., 2^-20, 0} with
- * rho(fe) >= alpha rho(ws) and p(fe) >= alpha p(ws); the stage is then the
- * SSP combination of w_n and fe, which stays physical because the set of
- * physical states is convex.  Returns the number of limited vertices. */
-static int64_t pos_limit(const om_mesh *m, int64_t nv, const double *ws, const double *L, double dt, double *fe) {
-    int64_t lim = 0;
-    for (int64_t v = 0; v < nv; ++v) {
-        const double *s = ws + 4 * v;
-        const double *l = L + 4 * v;
-        double *f = fe + 4 * v;
-        if (m->ghost && m->ghost[v] >= 0) {
-            for (int c = 0; c < 4; ++c) f[c] = s[c] + dt * l[c];
-            continue;
-        }
-        double ps = pressure(s, m->gamma);
-        double theta = 1.0;
-        int ok = 0;
-        for (int k = 0; k <= 20; ++k) {
-            for (int c = 0; c < 4; ++c) f[c] = s[c] + theta * dt * l[c];
-            if (f[0] >= m->pos_alpha * s[0] && pressure(f, m->gamma) >= m->pos_alpha * ps) {
-                ok = 1;
-                break;
-            }
-            theta *= 0.5;
-        }
-        if (!ok) {
-            theta = 0.0;
-            for (int c = 0; c < 4; ++c) f[c] = s[c];
-        }
-        lim += theta < 1.0;
-    }
-    return lim;
-}
-
 void om_set_positivity(om_mesh *m, double alpha) { m->pos_alpha = alpha; }
-
-/* one SSP-RK3 step in place on w[nv][4] */
-int om_rk3_step(om_mesh *m, double *w, double dt, double eps, int64_t *nfallback) {
-    int64_t n = m->nv * 4, nf = 0, f;
-    double *wn = (double *)malloc(n * sizeof(double));
-    double *L = (double *)malloc(n * sizeof(double));
-    double *ws = (double *)malloc(n * sizeof(double));
-    memcpy(wn, w, n * sizeof(double));
-    memcpy(ws, w, n * sizeof(double));
-    int st = OM_OK;
-    for (int stage = 1; stage <= 3 && st == OM_OK; ++stage) {
-        om_fill_ghosts(m, ws);
-        st = om_residual(m, ws, eps, NULL, L, &f);
-        nf += f;
-        if (st) break;
-        if (m->pos_alpha > 0) {
-            /* fe = ws + theta dt L, then the stage combination with dt L -> fe - ws */
-            double *fe = (double *)malloc(n * sizeof(double));
-            m->pos_limited += pos_limit(m, m->nv, ws, L, dt, fe);
-            for (int64_t i = 0; i < n; ++i) L[i] = fe[i];
-            free(fe);
-            for (int64_t i = 0; i < n; ++i) {
-                if (stage == 1) ws[i] = L[i];
-                else if (stage == 2) ws[i] = 0.75 * wn[i] + 0.25 * L[i];
-                else ws[i] = (1.0 / 3.0) * wn[i] + (2.0 / 3.0) * L[i];
-            }
-        } else {
-            om_stage_combine(n, stage, wn, ws, L, dt, ws);
-        }
-        if (m->ghost)
-            for (int64_t v = 0; v < m->nv; ++v)
-                if (m->ghost[v] >= 0) memcpy(ws + 4 * v, wn + 4 * v, 4 * sizeof(double));
-    }
-    if (st == OM_OK) {
-        om_fill_ghosts(m, ws);
-        memcpy(w, ws, n * sizeof(double));
-    }
-    free(wn); free(L); free(ws);
-    if (nfallback) *nfallback = nf;
-    return st;
-}
-
 /* Reading (the paper uses a CFL number without defining it):
  * dt = cfl * min over real vertices of h_v / (|u_v| + c_v), h_v the
  * shortest edge at v. */

@@ -20,7 +20,10 @@
  *   - one- and two-level divergence stencils (Section 2.2.2) and the
  *     least-squares flux divergence by the SVD pseudo-inverse
  *     (Section 2.2.1, Eqs. ef, eg, eLinearSystem and the a1+b2 weights);
- *   - third-order TVD Runge-Kutta (Section 3, Shu & Osher).
+ *   - third-order TVD Runge-Kutta (Section 3, Shu & Osher);
+ *   - directional derivatives of the residual and of RK steps by the
+ *     complex step (the state arithmetic of fdu_oracle_state.h compiled a
+ *     second time for double complex), the reference for the adjoint.
  *
  * Readings where the paper is silent (stencil-walk rule, curve tangents,
  * arc-length quadrature, Riemann solver, characteristic average, positivity

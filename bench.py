@@ -394,6 +394,15 @@ def run_ours(args):
         M.rk_step(dt, 64)
         M.get_state(out=host_out)  # D2H of the step's result (synchronises)
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    # the same through precision 48
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        M.set_state(host_in)
+        M.rk_step(dt, 48)
+        M.get_state(out=host_out)
+    e2e48_s = max_over_ranks(time.perf_counter() - t0, dist)
 
     # ---------------- figures
     stages = 3
@@ -466,6 +475,9 @@ def run_ours(args):
                             "ncu_thread_instr_per_edge": round(NCU_EDGE48_THREAD_INSTR_PER_EDGE),
                             "traffic": round(TRAFFIC_EDGE48_B_PER_EDGE * ne), "traffic_unit": "bytes per launch"},
             "div_kernel": {"avg_launch_ms": round(d48_ms / max(d48_n, 1), 4)},
+            "e2e": {"value": round(replica_throughput(nv * stages * e2e_steps, ws_, e2e48_s) / 1e6, 3),
+                    "unit": "Mvertex/s", "h2d_bytes_per_step": nv * 32, "d2h_bytes_per_step": nv * 32,
+                    "steps": e2e_steps},
         },
         "fp32": {
             "value": round(value32, 3), "unit": "Mvertex/s", "speedup_vs_f64": round(value32 / value, 3),

@@ -234,8 +234,8 @@ def test_fast_rsqrt_within_two_ulp_of_exact():
 def test_four_million_vertex_mesh_sampled_parity_and_free_stream():
     """The largest case of the suite: a 2000 x 2000 torus lattice (4M vertices,
     12M edges, ~290M divergence entries with 64-bit offsets).  Sampled FP64
-    parity with the oracle, and free-stream preservation on the whole mesh
-    (a property that holds at any size)."""
+    parity with the oracle (FP64 and precision 48), and free-stream
+    preservation on the whole mesh (a property that holds at any size)."""
     m, w0 = inputs.vortex_case(2000, seed=1011)
     M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0)
     assert M.ne == 3 * m.nv
@@ -250,9 +250,13 @@ def test_four_million_vertex_mesh_sampled_parity_and_free_stream():
     sel = mask.astype(bool)
     for k in range(4):
         assert rel_l2(got[sel, k], want[sel, k]) <= 1e-12
+    got48 = M.residual(48)  # precision 48 at the largest size (its tables built on first use)
+    for k in range(4):
+        assert rel_l2(got48[sel, k], want[sel, k]) <= 1e-12
     one = np.ones(m.nv)
     M.set_state(inputs.primitive_to_conservative(1.3 * one, 0.7 * one, -0.4 * one, 2.1 * one))
     assert np.abs(M.residual(64)).max() < 1e-10
+    assert np.abs(M.residual(48)).max() < 1e-10
     assert np.abs(M.residual(32)).max() < 1e-2
 
 

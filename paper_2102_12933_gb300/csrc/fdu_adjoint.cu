@@ -476,7 +476,8 @@ void launch_ghost_fold(double *x, const int32_t *donor, const int64_t *off, cons
 void launch_residual_vjp(const AdjEdgeArgs &ea, const AdjTables &t, const AdjVertexArgs &va, cudaStream_t s) {
     if (ea.ne > 0) {
         adj_edge_lambda_kernel<<<nblk(ea.ne, 256), 256, 0, s>>>(t.eoff, t.evid, t.ewt, va.lam, ea.lam_r_mut, ea.ne);
-        edge_flux_vjp_kernel<<<nblk(ea.ne, 128), 128, 0, s>>>(ea);
+        if (ea.prec == 48) launch_edge_flux_vjp_dw(ea, s);
+        else edge_flux_vjp_kernel<<<nblk(ea.ne, 128), 128, 0, s>>>(ea);
     }
     if (va.nv > 0) adj_vertex_kernel<<<nblk(va.nv, 256), 256, 0, s>>>(va);
 }

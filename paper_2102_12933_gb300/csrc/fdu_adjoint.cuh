@@ -16,6 +16,11 @@ struct AdjEdgeArgs {
     double *G;            // [6][ne][4] cotangents of the stencil states, per slot
     int64_t ne;
     double gm1, eps;
+    // precision 48 (double-word edge VJP, fdu_adjoint_dw.cu)
+    int prec;              // 64 or 48
+    const float2 *coefdw;  // [kEdgeCoef][ne] double-word coefficient block
+    float dw_gm1[2], dw_tenth[2], dw_eps[2];
+    int dw_eps_e;          // WENO epsilon = dw_eps * 2^dw_eps_e
 };
 
 // Edge transpose: for each active edge, the vertices whose divergence
@@ -42,8 +47,10 @@ struct AdjVertexArgs {
     double *grad;         // [nv][4] output
 };
 
-// grad = (dL/dw)^T lam at state w: transpose gathers, edge-flux VJP, per-vertex
-// flux Jacobians; three launches on s.
+// The double-word edge-flux VJP (precision 48) of the same edge flux.
+void launch_edge_flux_vjp_dw(const AdjEdgeArgs &a, cudaStream_t s);
+// grad = (dL/dw)^T lam at state w: transpose gathers, edge-flux VJP (FP64, or
+// double words when ea.prec == 48), per-vertex flux Jacobians; three launches on s.
 void launch_residual_vjp(const AdjEdgeArgs &ea, const AdjTables &t, const AdjVertexArgs &va, cudaStream_t s);
 // x <- (transmissive ghost fill)^T x: donor[i] += sum of x over its ghosts
 // ghost[off[i] .. off[i+1]-1], which are then zeroed (nd donors, internal ids)

@@ -105,6 +105,7 @@ struct fdu_mesh {
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> batch_graphs;
     // adjoint workspace (built on first use)
     bool adj_ready = false;
+    int adj_prec = 64;                // edge-flux VJP arithmetic: 64 (FP64) or 48 (double words)
     int64_t *adj_eoff = nullptr, *adj_voff = nullptr, *adj_soff = nullptr, *adj_slot = nullptr;
     int32_t *adj_evid = nullptr, *adj_vvid = nullptr;
     double *adj_ewt = nullptr, *adj_wf = nullptr, *adj_wg = nullptr;
@@ -677,6 +678,17 @@ void enqueue_residual_vjp(fdu_mesh *m, const double *w, const double *lam, doubl
     ea.ne = m->ne_act;
     ea.gm1 = m->opts.gamma - 1.0;
     ea.eps = m->opts.weno_eps;
+    ea.prec = m->adj_prec;
+    if (m->adj_prec == 48) {
+        const EdgeArgs e48 = edge_args(m, 48, w);
+        ea.coefdw = e48.coefdw;
+        for (int i = 0; i < 2; ++i) {
+            ea.dw_gm1[i] = e48.dw_gm1[i];
+            ea.dw_tenth[i] = e48.dw_tenth[i];
+            ea.dw_eps[i] = e48.dw_eps[i];
+        }
+        ea.dw_eps_e = e48.dw_eps_e;
+    }
     AdjTables t{m->adj_eoff, m->adj_evid, m->adj_ewt};
     AdjVertexArgs va{};
     va.nv = m->nv;
@@ -1663,6 +1675,15 @@ fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n) 
 
 fdu_status fdu_check_rsqrt64(int device, const double *x, double *y, int64_t n) {
     return check_special(device, x, y, n, 1);
+}
+
+fdu_status fdu_set_adjoint_precision(fdu_mesh *m, int precision) {
+    fdu_status st = need_device(m);
+    if (st) return st;
+    if (precision != 64 && precision != 48) return set_err(FDU_ERR_ARG, "adjoint precision must be 64 or 48");
+    if (precision == 48 && (st = check_precision(m, 48))) return st;
+    m->adj_prec = precision;
+    return FDU_OK;
 }
 
 fdu_status fdu_check_dw(int device, int op, const double *x, const double *y, double *z, int64_t n) {

@@ -33,7 +33,7 @@ EXPORTS = (
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
     "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
-    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_check_dw", "fdu_mesh_create_cells", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
+    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_check_dw", "fdu_set_adjoint_precision", "fdu_mesh_create_cells", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
     "fdu_batch_max_dt", "fdu_batch_set_dt", "fdu_batch_rk_steps", "fdu_batch_set_launch", "fdu_batch_autotune",
     "fdu_batch_barrier_selftest", "fdu_residual_vjp", "fdu_rk_step_vjp", "fdu_adjoint_rk",
 )
@@ -109,6 +109,7 @@ def load():
         L.fdu_check_recip64.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_check_rsqrt64.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_check_dw.argtypes = [C.c_int, C.c_int, dp, dp, dp, i64]
+        L.fdu_set_adjoint_precision.argtypes = [C.c_void_p, C.c_int]
         L.fdu_mesh_create_cells.argtypes = [dp, i64, lp, ip, i64, C.c_int, C.POINTER(MeshOpts), C.POINTER(P)]
         L.fdu_advance.argtypes = [P, C.c_double, C.c_double, C.c_int, i64, lp, dp, P]
         L.fdu_limited_count.argtypes = [P, lp, C.c_int, P]
@@ -388,6 +389,10 @@ class Mesh:
         _check(load().fdu_advance(self._h, float(cfl), float(t_end), int(precision), int(max_steps), C.byref(n),
                                   C.byref(t), _stream_ptr(stream)))
         return n.value, t.value
+
+    def set_adjoint_precision(self, precision):
+        """Arithmetic of the adjoint's edge-flux VJP: 64 (FP64) or 48 (double words)."""
+        _check(load().fdu_set_adjoint_precision(self._h, int(precision)))
 
     def residual_vjp(self, lam, out=None, stream=None):
         """(dL/dw)^T lam at the current state."""

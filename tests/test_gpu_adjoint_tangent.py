@@ -5,7 +5,8 @@ vector-Jacobian products.  Both linearise the same function at the same
 state, so the two agree to rounding; the bound is 1e-10 relative, for the
 residual, one RK3 step and a checkpointed run of several steps, on a
 periodic, a transmissive and a Dirichlet mesh, over several seeded
-directions each.  (Central differences reach only about 1e-8 here; they
+directions each, with the edge-flux VJP in FP64 and in double words
+(precision 48).  (Central differences reach only about 1e-8 here; they
 are the check in tests/test_gpu_adjoint.py.)
 """
 import numpy as np
@@ -58,6 +59,12 @@ def case(request):
     return request.param, m, w, om, M
 
 
+@pytest.fixture(params=[64, 48], ids=["adjoint64", "adjoint48"])
+def aprec(request):
+    """Arithmetic of the edge-flux VJP: FP64, or double words (precision 48)."""
+    return request.param
+
+
 def _pairs(w, seed):
     rng = np.random.default_rng(seed)
     for _ in range(DIRECTIONS):
@@ -70,15 +77,17 @@ def _check(adj, tan):
     assert abs(adj - tan) <= TOL * abs(tan), (adj, tan, abs(adj - tan) / abs(tan))
 
 
-def test_residual_vjp_against_tangents(case):
+def test_residual_vjp_against_tangents(case, aprec):
     kind, m, w, om, M = case
+    M.set_adjoint_precision(aprec)
     M.set_state(w)
     for d, lam in _pairs(w, 21):
         _check(float(np.sum(M.residual_vjp(lam) * d)), float(np.sum(lam * om.residual_jvp(w, d))))
 
 
-def test_rk_step_vjp_against_tangents(case):
+def test_rk_step_vjp_against_tangents(case, aprec):
     kind, m, w, om, M = case
+    M.set_adjoint_precision(aprec)
     M.set_state(w)
     dt = M.max_dt(0.5)
     for d, lam in _pairs(w, 22):
@@ -88,8 +97,9 @@ def test_rk_step_vjp_against_tangents(case):
         _check(float(np.sum(g * d)), float(np.sum(lam * jd)))
 
 
-def test_adjoint_rk_against_tangents(case):
+def test_adjoint_rk_against_tangents(case, aprec):
     kind, m, w, om, M = case
+    M.set_adjoint_precision(aprec)
     M.set_state(w)
     dt = 0.5 * M.max_dt(0.5)
     n = 5
@@ -100,7 +110,8 @@ def test_adjoint_rk_against_tangents(case):
         _check(float(np.sum(g * d)), float(np.sum(lam * jd)))
 
 
-def test_fifty_step_density_misfit_gradient():
+@pytest.mark.parametrize("aprec", [64, 48], ids=["adjoint64", "adjoint48"])
+def test_fifty_step_density_misfit_gradient(aprec):
     """The adjoint workload's shape on the 1600-vertex vortex mesh: gradient
     of J = 1/2 sum (rho(T) - rho_exact(T))^2 after 50 SSP-RK3 steps with a
     checkpoint every 10 steps, against the oracle's tangent of the 50-step
@@ -112,6 +123,7 @@ def test_fifty_step_density_misfit_gradient():
     mesh, w0 = inputs.vortex_case(40, seed=1005)
     eps = 1e-6
     M = fdu.Mesh(mesh.xy, mesh.tri, mesh.Lx, mesh.Ly, device=0, weno_eps=eps)
+    M.set_adjoint_precision(aprec)
     M.set_state(w0)
     dt = M.max_dt(0.5)
     n_steps = 50

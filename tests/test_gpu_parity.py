@@ -282,6 +282,16 @@ def test_smallest_meshes(n):
         assert rel_l2(got[:, k] - w0[:, k], w[:, k] - w0[:, k]) <= 1e-12
     M.rk_steps(dt, 0, 64)  # zero steps: a no-op
     assert np.array_equal(M.get_state(), got)
+    # precision 48 on the same small meshes (a single partial edge block
+    # of its kernel, folded weights on wrapping stencils)
+    M.set_state(w0)
+    got48 = M.residual(48)
+    for k in range(4):
+        assert rel_l2(got48[:, k], want[:, k]) <= 1e-12
+    M.rk_steps(dt, 3, 48)
+    got48 = M.get_state()
+    for k in range(4):
+        assert rel_l2(got48[:, k] - w0[:, k], w[:, k] - w0[:, k]) <= 1e-12
 
 
 def test_sell_layouts_and_padding(c40):

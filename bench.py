@@ -792,10 +792,36 @@ def run_adjoint(args):
                     e = abs(fd - a) / abs(a)
                     best = e if best is None else min(best, e)
             errs.append(best)
+        # the same with the double-word edge-flux VJP (precision 48)
+        M.set_adjoint_precision(48)
+        M.set_state(w0d)
+        t_vjp48 = timed(lambda: M.residual_vjp(lam_r, out=out, stream=stream), 20)
+        t_adj48 = timed(adj, 3)
+        g48 = grad.clone()
+        errs48 = []
+        gen = torch.Generator(device="cuda").manual_seed(5005)
+        for _ in range(8):
+            d = torch.randn(w0d.shape, generator=gen, device="cuda", dtype=torch.float64)
+            a = float((g48 * d).sum())
+            best = None
+            for h in steps_h:
+                jp, jm = J_and_lam(w0d + h * d)[0], J_and_lam(w0d - h * d)[0]
+                jp2, jm2 = J_and_lam(w0d + 2 * h * d)[0], J_and_lam(w0d - 2 * h * d)[0]
+                for fd in ((jp - jm) / (2 * h), (8 * (jp - jm) - (jp2 - jm2)) / (12 * h)):
+                    e = abs(fd - a) / abs(a)
+                    best = e if best is None else min(best, e)
+            errs48.append(best)
+        M.set_adjoint_precision(64)
+        adjoint48 = {"residual_vjp_ms": round(t_vjp48, 4), "residual_vjp_over_residual": round(t_vjp48 / t_res, 3),
+                     "adjoint_ms": round(t_adj48, 3), "adjoint_over_forward": round(t_adj48 / t_fwd, 3),
+                     "gradient_rel_diff_vs_f64": float((g48 - g).norm() / g.norm()),
+                     "fd_check": {"directions": 8, "max_rel_err": float(np.max(errs48)),
+                                  "median_rel_err": float(np.median(errs48)),
+                                  "within_1e-6": int(np.sum(np.array(errs48) <= 1e-6))}}
         result[label] = {"residual_ms": round(t_res, 4), "residual_vjp_ms": round(t_vjp, 4),
                          "residual_vjp_over_residual": round(t_vjp / t_res, 3), "forward_ms": round(t_fwd, 3),
                          "adjoint_ms": round(t_adj, 3), "adjoint_over_forward": round(t_adj / t_fwd, 3),
-                         "one_segment": one_seg, "J": J0,
+                         "one_segment": one_seg, "J": J0, "precision48_vjp": adjoint48,
                          "fd_check": {"directions": 32, "steps_h": list(steps_h),
                                       "differences": "central, 2nd and 4th order; best per direction",
                                       "max_rel_err": float(np.max(errs)), "median_rel_err": float(np.median(errs)),

@@ -812,8 +812,12 @@ def run_adjoint(args):
                     best = e if best is None else min(best, e)
             errs48.append(best)
         M.set_adjoint_precision(64)
+        t_fwd48 = timed(lambda: (M.set_state(w0d, stream=stream), M.rk_steps(dt, n_steps, 48, stream=stream)), 3)
         adjoint48 = {"residual_vjp_ms": round(t_vjp48, 4), "residual_vjp_over_residual": round(t_vjp48 / t_res, 3),
                      "adjoint_ms": round(t_adj48, 3), "adjoint_over_forward": round(t_adj48 / t_fwd, 3),
+                     "forward48_ms": round(t_fwd48, 3), "adjoint_over_forward48": round(t_adj48 / t_fwd48, 3),
+                     "note": "adjoint precision 48: double-word edge-flux VJP and precision-48 forward and "
+                             "recomputed steps; adjoint_over_forward is against the FP64 forward",
                      "gradient_rel_diff_vs_f64": float((g48 - g).norm() / g.norm()),
                      "fd_check": {"directions": 8, "max_rel_err": float(np.max(errs48)),
                                   "median_rel_err": float(np.median(errs48)),

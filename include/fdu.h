@@ -274,10 +274,11 @@ fdu_status fdu_batch_barrier_selftest(fdu_mesh *batch, int *status);
  * respect to its fixed value.  fdu_rk_step_vjp and fdu_adjoint_rk return
  * FDU_ERR_ARG when the stage positivity safeguard is on (positivity_alpha
  * > 0): the safeguard is not differentiated. */
-/* Arithmetic of the edge-flux VJP that the three calls below use: 64 (FP64,
- * the default) or 48 (double-word FP32, as the precision-48 residual; the
- * same derivative to about 1e-13, on the FP32 pipes).  The first use of 48
- * builds the double-word coefficient block. */
+/* Precision of the adjoint calls below: 64 (FP64, the default) or 48.  With
+ * 48 the edge-flux VJP runs in double-word FP32 (the same derivative to about
+ * 1e-13, on the FP32 pipes) and the steps that fdu_rk_step_vjp and
+ * fdu_adjoint_rk take or recompute are precision-48 steps (the trajectory of
+ * fdu_rk_step(..., 48)).  The first use of 48 builds its tables. */
 fdu_status fdu_set_adjoint_precision(fdu_mesh *mesh, int precision);
 /* grad = (dL/dw)^T lam at the current state. */
 fdu_status fdu_residual_vjp(fdu_mesh *mesh, const double *lam, double *grad, int on_device, void *stream);

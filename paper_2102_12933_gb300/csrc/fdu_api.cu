@@ -105,7 +105,7 @@ struct fdu_mesh {
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> batch_graphs;
     // adjoint workspace (built on first use)
     bool adj_ready = false;
-    int adj_prec = 64;                // edge-flux VJP arithmetic: 64 (FP64) or 48 (double words)
+    int adj_prec = 64;                // adjoint precision: 64, or 48 (double-word VJP, precision-48 steps)
     int64_t *adj_eoff = nullptr, *adj_voff = nullptr, *adj_soff = nullptr, *adj_slot = nullptr;
     int32_t *adj_evid = nullptr, *adj_vvid = nullptr;
     double *adj_ewt = nullptr, *adj_wf = nullptr, *adj_wg = nullptr;
@@ -714,10 +714,10 @@ void enqueue_rk_step_vjp(fdu_mesh *m, double dt, double *lam_next, double *lam_p
     const int64_t n4 = 4 * m->nv;
     double *t = m->adj_buf[2], *ls2 = m->adj_buf[3], *ls1 = m->adj_buf[4];
     if (!S0) {  // recompute the stage states from wn
-        ensure_fluxes(m, 64, s);
-        enqueue_stages(m, 64, dt, nullptr, s, false, 1, 1);
+        ensure_fluxes(m, m->adj_prec, s);
+        enqueue_stages(m, m->adj_prec, dt, nullptr, s, false, 1, 1);
         cudaMemcpyAsync(m->adj_S1, m->ws, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        enqueue_stages(m, 64, dt, nullptr, s, false, 2, 2);  // ws = S2
+        enqueue_stages(m, m->adj_prec, dt, nullptr, s, false, 2, 2);  // ws = S2
         S0 = m->wn;
         S1 = m->adj_S1;
         S2 = m->ws;
@@ -1606,12 +1606,12 @@ fdu_status fdu_adjoint_rk(fdu_mesh *m, double dt, int n_steps, int checkpoint_ev
             double *const *S = stp + 3 * (i - i0);
             cudaError_t e = cudaMemcpyAsync(S[0], m->wn, bytes, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) return e;
-            ensure_fluxes(m, 64, s);
-            enqueue_stages(m, 64, dt, nullptr, s, false, 1, 1);
+            ensure_fluxes(m, m->adj_prec, s);
+            enqueue_stages(m, m->adj_prec, dt, nullptr, s, false, 1, 1);
             if ((e = cudaMemcpyAsync(S[1], m->ws, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-            enqueue_stages(m, 64, dt, nullptr, s, false, 2, 2);
+            enqueue_stages(m, m->adj_prec, dt, nullptr, s, false, 2, 2);
             if ((e = cudaMemcpyAsync(S[2], m->ws, bytes, cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-            if (i + 1 < i1) enqueue_stages(m, 64, dt, nullptr, s, false, 3, 3);
+            if (i + 1 < i1) enqueue_stages(m, m->adj_prec, dt, nullptr, s, false, 3, 3);
         }
         return cudaSuccess;
     };
@@ -1619,10 +1619,10 @@ fdu_status fdu_adjoint_rk(fdu_mesh *m, double dt, int n_steps, int checkpoint_ev
     // steps; the last segment keeps its stage inputs at once, so the reverse
     // pass recomputes only the segments before it
     const int last0 = (nseg - 1) * K;
-    ensure_fluxes(m, 64, s);
+    ensure_fluxes(m, m->adj_prec, s);
     for (int i = 0; i < last0; ++i) {
         if (i % K == 0) CK(cudaMemcpyAsync(ck[i / K], m->wn, bytes, cudaMemcpyDeviceToDevice, s));
-        enqueue_step(m, 64, dt, nullptr, s, false);
+        enqueue_step(m, m->adj_prec, dt, nullptr, s, false);
     }
     CK(cudaMemcpyAsync(ck[nseg - 1], m->wn, bytes, cudaMemcpyDeviceToDevice, s));
     CK(segment_states(last0, n_steps));

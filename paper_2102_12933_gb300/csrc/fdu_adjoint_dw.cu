@@ -31,13 +31,12 @@ namespace {
 using namespace dwa;
 
 constexpr int kVjpBlock = 64;
-constexpr int kVjpSlots = 84;
+constexpr int kVjpSlots = 64;
 // per-thread shared-memory slots (float2 double words), slot j of thread t at [j][t]
-constexpr int kSlotD = 0;     // raw differences R1-L1, L2-L1, L3-L1, R2-R1, R3-R1 (5 x 4)
-constexpr int kSlotC = 20;    // their characteristic projections (5 x 4)
-constexpr int kSlotW = 40;    // per field: va vb vc vd B'a B'b B'c B'd (4 x 8); reverse: the six cotangents
-constexpr int kSlotS = 72;    // per field: (lambda, clamp bits)
-constexpr int kSlotLR = 76;   // per field: dl, dr
+constexpr int kSlotC = 0;     // characteristic projections of R1-L1, L2-L1, L3-L1, R2-R1, R3-R1 (5 x 4)
+constexpr int kSlotW = 20;    // per field: va vb vc vd B'a B'b B'c B'd (4 x 8); reverse: the six cotangents
+constexpr int kSlotS = 52;    // per field: (lambda, clamp bits)
+constexpr int kSlotLR = 56;   // per field: dl, dr
 
 __device__ __forceinline__ void st_s(float2 *S, int j, dw v) { S[j * kVjpBlock] = make_float2(v.h, v.l); }
 __device__ __forceinline__ dw ld_s(const float2 *S, int j) {
@@ -354,20 +353,19 @@ __global__ void __launch_bounds__(kVjpBlock, 6) edge_flux_vjp_dw_kernel(AdjEdgeA
     const dw nx = kc(kp, ne, kCoefN), ny = kc(kp, ne, kCoefN + 1);
 
     // ---------------- forward
-    const d4v L1v = ldd4(w, s[2]), R1v = ldd4(w, s[3]);
-    {
-        auto diff = [](const d4v &p, const d4v &q) { return d2dw4(d4v{p.x - q.x, p.y - q.y, p.z - q.z, p.w - q.w}); };
-        st_s4(S, kSlotD + 0, diff(R1v, L1v));
-        st_s4(S, kSlotD + 4, diff(ldd4(w, s[1]), L1v));
-        st_s4(S, kSlotD + 8, diff(ldd4(w, s[0]), L1v));
-        st_s4(S, kSlotD + 12, diff(ldd4(w, s[4]), R1v));
-        st_s4(S, kSlotD + 16, diff(ldd4(w, s[5]), R1v));
-    }
-    const dw4 L1 = d2dw4(L1v), R1 = d2dw4(R1v);
+    const dw4 L1 = d2dw4(ldd4(w, s[2])), R1 = d2dw4(ldd4(w, s[3]));
+    // difference j (R1-L1, L2-L1, L3-L1, R2-R1, R3-R1) in FP64, then double
+    // words; taken again in the reverse sweep instead of being kept
+    auto diff_j = [&](int j) {
+        const int32_t p = j == 0 ? s[3] : j == 1 ? s[1] : j == 2 ? s[0] : j == 3 ? s[4] : s[5];
+        const int32_t q = j == 0 || j == 1 || j == 2 ? s[2] : s[3];
+        const d4v a = ldd4(w, p), b = ldd4(w, q);
+        return d2dw4(d4v{a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w});
+    };
     const PrimW pL1 = prim_w(L1, gm1), pR1 = prim_w(R1, gm1);
     const RoeW C = roe_w(L1, pL1, R1, pR1, nx, ny, gm1);
 #pragma unroll 1
-    for (int j = 0; j < 20; j += 4) st_s4(S, kSlotC + j, project(C, ld_s4(S, kSlotD + j)));
+    for (int j = 0; j < 5; ++j) st_s4(S, kSlotC + 4 * j, project(C, diff_j(j)));
     // fields: a = L3-L1, b = L2-L1, c = R1-L1, d = R2-L1, e = R3-R1, f = R2-R1 (characteristic)
 #pragma unroll 1
     for (int i = 0; i < 4; ++i) {
@@ -477,7 +475,7 @@ __global__ void __launch_bounds__(kVjpBlock, 6) edge_flux_vjp_dw_kernel(AdjEdgeA
                 cbv[i] = v;
             }
             dw4 db = zero4();
-            project_vjp_w(C, ld_s4(S, kSlotD + 4 * j), d4(cbv[0], cbv[1], cbv[2], cbv[3]), db, Cb);
+            project_vjp_w(C, diff_j(j), d4(cbv[0], cbv[1], cbv[2], cbv[3]), db, Cb);
             if (j == 0) {
                 acc4(GR1, db);
                 GL1 = sub4_sl(GL1, db);

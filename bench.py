@@ -644,7 +644,8 @@ def run_batch(args):
     5k..200k vertices, strengths in [1,5], centres in [3,7]^2, each with its
     own CFL time step, advanced by one persistent launch per RK stage
     (CUDA-graph replays), launch shape picked by the autotuner; FP32
-    residual with FP64 state accumulation (FP64 residual timed beside it)."""
+    residual with FP64 state accumulation (FP64 and precision-48 residuals
+    timed beside it)."""
     import torch
 
     from paper_2102_12933_gb300 import fdu, inputs
@@ -666,7 +667,7 @@ def run_batch(args):
     B.set_dt(dts)
     stream = torch.cuda.current_stream()
     res = {}
-    for prec in (32, 64):
+    for prec in (32, 64, 48):
         B.set_state(w0)
         t, b, ms_tune = B.autotune(prec)
         B.batch_rk_steps(args.warmup, prec, stream=stream)
@@ -682,12 +683,14 @@ def run_batch(args):
     # FP32 error against FP64 after the same steps from the same state, over all meshes
     err_steps = 100
     states = {}
-    for prec in (64, 32):
+    for prec in (64, 48, 32):
+        B.set_launch(res[prec]["launch"]["threads"], res[prec]["launch"]["blocks_per_sm"])  # its tuned shape
         B.set_state(w0)
         B.batch_rk_steps(err_steps, prec, stream=stream)
         states[prec] = B.get_state()
-    res[32]["error_vs_f64"] = {"rho": _rel_l2(states[32][:, 0], states[64][:, 0]),
-                               "rhoE": _rel_l2(states[32][:, 3], states[64][:, 3]), "steps": err_steps}
+    for prec in (48, 32):
+        res[prec]["error_vs_f64"] = {"rho": _rel_l2(states[prec][:, 0], states[64][:, 0]),
+                                     "rhoE": _rel_l2(states[prec][:, 3], states[64][:, 3]), "steps": err_steps}
     line = {
         "metric": METRIC, "value": res[32]["value"], "unit": "Mvertex/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res[32]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -697,6 +700,7 @@ def run_batch(args):
                                "persistent launch per RK stage, CUDA-graph replays, autotuned launch shape",
                    "host_build_s": round(t_build, 2)},
         "fp32": res[32], "fp64": res[64],
+        "f64_dw": dict(res[48], speedup_vs_f64=round(res[48]["value"] / res[64]["value"], 3)),
     }
     print(json.dumps(line), flush=True)
     B.close()

@@ -242,8 +242,10 @@ fdu_status fdu_batch_max_dt(fdu_mesh *batch, double cfl, double *dt, void *strea
 /* Per-mesh time steps used by fdu_batch_rk_steps (host array [n_meshes]). */
 fdu_status fdu_batch_set_dt(fdu_mesh *batch, const double *dt, void *stream);
 /* n_steps SSP-RK3 steps of every mesh (FP64 state accumulation; the
- * residual at `precision`).  FDU_ERR_TIMEOUT if a grid barrier's bounded
- * wait ran out (the state is then not advanced past that stage). */
+ * residual at `precision`, 64, 48 or 32 as for fdu_residual; precision 48
+ * runs a kernel of its own with its double-word staging in dynamic shared
+ * memory).  FDU_ERR_TIMEOUT if a grid barrier's bounded wait ran out (the
+ * state is then not advanced past that stage). */
 fdu_status fdu_batch_rk_steps(fdu_mesh *batch, int precision, int n_steps, void *stream);
 /* Persistent launch shape: threads per block (128, 256 or 512) and
  * co-resident blocks per SM (1 .. the larger of the FP32 and FP64 stage

@@ -21,7 +21,7 @@ ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 HOST_SRC = ["fdu_host.cpp"]
 CUDA_SRC = ["fdu_kernels.cu", "fdu_api.cu", "fdu_adjoint.cu", "fdu_dw.cu", "fdu_adjoint_dw.cu"]
-HEADERS = ["fdu_internal.h", "fdu_kernels.cuh", "fdu_device.cuh", "fdu_adjoint.cuh", "fdu_dw.cuh", "fdu_dw_euler.cuh"]
+HEADERS = ["fdu_internal.h", "fdu_kernels.cuh", "fdu_device.cuh", "fdu_adjoint.cuh", "fdu_dw.cuh", "fdu_dw_euler.cuh", "fdu_dw_edge.cuh"]
 
 
 def _nvcc():

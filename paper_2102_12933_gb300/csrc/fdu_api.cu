@@ -748,14 +748,15 @@ cudaError_t enqueue_step_persistent(fdu_mesh *m, int prec, cudaStream_t s, unsig
                                     unsigned long long spin_limit) {
     for (int stage = 1; stage <= 3; ++stage) {
         const double *win = stage == 1 ? m->wn : m->ws;
-        EdgeArgs ea = edge_args(m, prec, prec == 64 ? (const void *)win : (const void *)m->w32);
+        const bool f64 = fp64_state(prec);
+        EdgeArgs ea = edge_args(m, prec, f64 ? (const void *)win : (const void *)m->w32);
         DivArgs a = div_args(m, prec, stage - 1);
         a.wn = m->wn;
         a.ws = win;
         a.wout = stage == 3 ? m->wn : m->ws;
-        a.Fout = prec == 64 ? (void *)m->F64[stage % 3] : (void *)m->F32[stage % 3];
-        a.Qout = prec == 64 ? m->Q64[stage % 3] : nullptr;
-        if (prec == 64) ea.Q = m->Q64[stage - 1];
+        a.Fout = f64 ? (void *)m->F64[stage % 3] : (void *)m->F32[stage % 3];
+        a.Qout = f64 ? m->Q64[stage % 3] : nullptr;
+        if (f64) ea.Q = m->Q64[stage - 1];
         a.w32out = prec == 32 ? m->w32 : nullptr;
         a.comp = m->comp;
         a.dt_comp = m->dt_comp;
@@ -1369,7 +1370,8 @@ constexpr unsigned long long kSpinLimit = 1ull << 24;
 fdu_status fdu_batch_rk_steps(fdu_mesh *m, int precision, int n_steps, void *stream) {
     fdu_status st = need_batch(m);
     if (st) return st;
-    if (n_steps < 0 || (precision != 64 && precision != 32)) return set_err(FDU_ERR_ARG, "bad precision or n_steps");
+    if (n_steps < 0) return set_err(FDU_ERR_ARG, "bad n_steps");
+    if ((st = check_precision(m, precision))) return st;
     if (n_steps == 0) return FDU_OK;
     cudaStream_t s = m->stream(stream);
     const int occ = persistent_blocks_per_sm(precision, m->pl_threads);
@@ -1410,7 +1412,7 @@ fdu_status fdu_batch_rk_steps(fdu_mesh *m, int precision, int n_steps, void *str
 fdu_status fdu_batch_autotune(fdu_mesh *m, int precision, int *threads, int *blocks_per_sm, double *ms_per_step) {
     fdu_status st = need_batch(m);
     if (st) return st;
-    if (precision != 64 && precision != 32) return set_err(FDU_ERR_ARG, "precision must be 64 or 32");
+    if ((st = check_precision(m, precision))) return st;
     cudaStream_t s = m->own_stream;
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device));

@@ -23,6 +23,7 @@
 #include "fdu_kernels.cuh"
 #include "fdu_device.cuh"
 #include "fdu_dw.cuh"
+#include "fdu_dw_edge.cuh"
 
 namespace fdu {
 namespace {
@@ -604,6 +605,23 @@ __global__ void stage_persistent_kernel(EdgeArgs EA, DivArgs DA, unsigned int *b
     }
 }
 
+// Precision 48: the same stage with the double-word edge flux (its staging in
+// dynamic shared memory, kDwSlots double words per thread) and the folded
+// divergence.  At most 512 threads a block, so at most 128 registers.
+template <int MODE>
+__global__ void __launch_bounds__(512, 1)
+    stage_persistent_dw_kernel(EdgeArgs EA, DivArgs DA, unsigned int *bar_count, unsigned int *bar_gen,
+                               unsigned int nblocks_expected, unsigned long long spin_limit, int *err) {
+    extern __shared__ float2 dw_stage[];
+    const dwa::Stage T{dw_stage + threadIdx.x, (int)blockDim.x};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t e = t0; e < EA.ne; e += stride) dwa::edge_flux_dw_body(EA, e, T);
+    __threadfence();
+    if (!grid_barrier(bar_count, bar_gen, nblocks_expected, spin_limit, err)) return;
+    for (int64_t v = t0; v < DA.n_real; v += stride) div_f64_body<MODE, true>(DA, v);
+}
+
 // ------------------------------------------------------------------ support kernels
 // Smallest row index whose state has rho <= 0 (or NaN) or a non-finite
 // momentum or energy (set_state's physical check).
@@ -781,10 +799,32 @@ cudaError_t coop(const EdgeArgs &ea, const DivArgs &da, unsigned int *c, unsigne
 }
 }  // namespace
 
+namespace {
+size_t dw_stage_bytes(int threads) { return (size_t)dwa::kDwSlots * sizeof(float2) * threads; }
+template <int MODE>
+cudaError_t coop48(const EdgeArgs &ea, const DivArgs &da, unsigned int *c, unsigned int *g, unsigned int ne,
+                   unsigned long long lim, int *err, int threads, int nb, cudaStream_t s) {
+    EdgeArgs a = ea;
+    DivArgs d = da;
+    void *args[] = {&a, &d, &c, &g, &ne, &lim, &err};
+    const size_t bytes = dw_stage_bytes(threads);
+    cudaError_t e = cudaFuncSetAttribute((const void *)stage_persistent_dw_kernel<MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel((const void *)stage_persistent_dw_kernel<MODE>, dim3(nb), dim3(threads), args,
+                                       bytes, s);
+}
+}  // namespace
+
 cudaError_t launch_stage_persistent(int prec, int mode, const EdgeArgs &ea, const DivArgs &da, unsigned int *bar_count,
                                     unsigned int *bar_gen, unsigned int nblocks_expected,
                                     unsigned long long spin_limit, int *err, int threads, int nb, cudaStream_t s) {
     const unsigned int ne = nblocks_expected;
+    if (prec == 48) {
+        if (mode == 1) return coop48<1>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
+        if (mode == 2) return coop48<2>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
+        return coop48<3>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
+    }
     if (prec == 64) {
         if (mode == 1) return coop<64, 1>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
         if (mode == 2) return coop<64, 2>(ea, da, bar_count, bar_gen, ne, spin_limit, err, threads, nb, s);
@@ -798,7 +838,14 @@ cudaError_t launch_stage_persistent(int prec, int mode, const EdgeArgs &ea, cons
 int persistent_blocks_per_sm(int prec, int threads) {
     int n = 0;
     // the three stage modes share their register footprint; mode 3 stands for all
-    if (prec == 64)
+    if (prec == 48) {
+        const size_t bytes = dw_stage_bytes(threads);
+        for (auto k : {stage_persistent_dw_kernel<1>, stage_persistent_dw_kernel<2>, stage_persistent_dw_kernel<3>})
+            if (cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+                cudaSuccess)
+                return 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_persistent_dw_kernel<3>, threads, bytes);
+    } else if (prec == 64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_persistent_kernel<64, 3>, threads, 0);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_persistent_kernel<32, 3>, threads, 0);

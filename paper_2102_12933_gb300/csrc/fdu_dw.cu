@@ -8,17 +8,19 @@
 // pipes at 64 times the FP64 instruction rate.
 //
 //   FP64 : the five stencil differences R1-L1, L2-L1, L3-L1, R2-R1, R3-R1
-//          (exact or correctly rounded), the normal flux F_n(L1) from the
-//          vertex fluxes (f, g) of L1, and the final sum
-//          r = F_n(L1) + [F_n(w_L) - F_n(L1)] + D.
+//          (exact or correctly rounded); the normal flux F_n(L1) of the
+//          edge's left vertex, which the divergence adds through its folded
+//          FP64 vertex weights (div_f64_body<MODE, true>).
 //   DW   : characteristic projection at the Roe average of (L1, R1), the
 //          WENO increments, the flux increment F_n(w_L) - F_n(L1) in a
 //          cancellation-free form, and the Roe dissipation
-//          D = R diag((lambda - |lambda|_fix)/2) L (w_R - w_L).
+//          D = R diag((lambda - |lambda|_fix)/2) L (w_R - w_L); the kernel
+//          writes r - F_n(L1) = [F_n(w_L) - F_n(L1)] + D as double words.
 // An error of relative size 2^-46 in an increment of size h |grad w| gives
 // an error of that size times h in the flux, which the least-squares
 // divergence (weights of size 1/h) does not amplify beyond the FP64 path's
-// own rounding.
+// own rounding.  The NU-WENO5 and edge-flux bodies are in fdu_dw_edge.cuh
+// (shared with the batched persistent stage).
 //
 // FP32 has a narrower exponent range than FP64.  The smoothness indicators
 // are formed from the differences of each field scaled by a power of two

@@ -391,8 +391,14 @@ class Mesh:
         return n.value, t.value
 
     def set_adjoint_precision(self, precision):
-        """Arithmetic of the adjoint's edge-flux VJP: 64 (FP64) or 48 (double words)."""
+        """Precision of the adjoint calls: 64 (FP64) or 48 (double-word edge-flux
+        VJP and precision-48 steps)."""
         _check(load().fdu_set_adjoint_precision(self._h, int(precision)))
+        self._adjoint_precision = int(precision)
+
+    @property
+    def adjoint_precision(self):
+        return getattr(self, "_adjoint_precision", 64)
 
     def residual_vjp(self, lam, out=None, stream=None):
         """(dL/dw)^T lam at the current state."""

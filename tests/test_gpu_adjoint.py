@@ -155,3 +155,39 @@ def test_autograd_functions(case):
     lam2 = 2 * M.residual(64)
     M.set_state(w)
     assert np.array_equal(w1.grad.cpu().numpy(), M.residual_vjp(lam2))
+
+
+def test_autograd_functions_precision48(case):
+    """precision = 48 runs the forward in precision 48 and the backward with
+    the adjoint precision 48 (restored afterwards); the gradients are the
+    direct calls' bits, and within 1e-10 of the FP64 ones."""
+    from paper_2102_12933_gb300.autograd import Residual, RKSteps
+
+    m, w, M = case
+    w0 = torch.tensor(w, device="cuda", requires_grad=True)
+    M.set_state(w)
+    dt = M.max_dt(0.5)
+    wT = RKSteps.apply(w0, M, dt, 6, 3, 48)
+    loss = 0.5 * (wT[:, 0] ** 2).sum()
+    loss.backward()
+    assert M.adjoint_precision == 64
+    lam = np.zeros_like(w)
+    lam[:, 0] = wT[:, 0].detach().cpu().numpy()
+    M.set_adjoint_precision(48)
+    M.set_state(w)
+    ref = M.adjoint_rk(dt, 6, lam, checkpoint_every=3)
+    M.set_adjoint_precision(64)
+    assert np.array_equal(w0.grad.cpu().numpy(), ref)
+    M.set_state(w)
+    ref64 = M.adjoint_rk(dt, 6, lam, checkpoint_every=3)
+    assert np.linalg.norm(ref - ref64) <= 1e-10 * np.linalg.norm(ref64)
+    w1 = torch.tensor(w, device="cuda", requires_grad=True)
+    r = Residual.apply(w1, M, 48)
+    (r * r).sum().backward()
+    M.set_state(w)
+    lam2 = 2 * M.residual(48)
+    M.set_adjoint_precision(48)
+    M.set_state(w)
+    want = M.residual_vjp(lam2)
+    M.set_adjoint_precision(64)
+    assert np.array_equal(w1.grad.cpu().numpy(), want)

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
 
     // ---------------- forward
     const Prim64 pL1 = prim64(L1, gm1), pR1 = prim64(R1, gm1);
-    const Roe64 C = roe64(L1, pL1, R1, pR1, nx, ny, gm1);
+    const Roe64 C = roe64(L1, pL1, R1, pR1, nx, ny, gm1, 0.5 * gm1);
     const dbl4 dM = sub4(R1, L1), dL2 = sub4(W1, L1), dL3 = sub4(W0, L1), dR2 = sub4(W4, R1), dR3 = sub4(W5, R1);
     const dbl4 cM = project64(C, dM), cL2 = project64(C, dL2), cL3 = project64(C, dL3), cR2 = project64(C, dR2),
                cR3 = project64(C, dR3);
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
         pl = pL1;
         pr = pR1;
     }
-    const Roe64 Q = roe64(wl, pl, wr, pr, nx, ny, gm1);
+    const Roe64 Q = roe64(wl, pl, wr, pr, nx, ny, gm1, 0.5 * gm1);
     const dbl4 dw = sub4(wr, wl);
     const dbl4 a = project64(Q, dw);
     const double delta = 0.1 * Q.c;

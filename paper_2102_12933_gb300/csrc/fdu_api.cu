@@ -449,6 +449,7 @@ EdgeArgs edge_args(fdu_mesh *m, int prec, const void *w) {
     }
     a.ne = m->ne_act;
     a.gm1 = m->opts.gamma - 1.0;
+    a.hgm1 = 0.5 * a.gm1;
     a.eps = m->opts.weno_eps;
     a.gm1f = (float)(m->opts.gamma - 1.0);
     a.epsf = (float)m->opts.weno_eps32;

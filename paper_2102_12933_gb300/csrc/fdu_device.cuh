@@ -31,6 +31,14 @@ __device__ __forceinline__ dbl4 add4(dbl4 a, dbl4 b) {
 }
 __device__ __forceinline__ dbl4 neg4(dbl4 a) { return dbl4_make(-a.x, -a.y, -a.z, -a.w); }
 
+// x > 0 decided on the integer pipe from the bit pattern (positive doubles
+// order as their bits; NaN and -0 give false, as the FP64 comparison does),
+// which keeps the comparison off GB300's narrow FP64 pipe.
+__device__ __forceinline__ bool pos64(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7FF0000000000000LL;
+}
+
 // Reciprocal of a positive normal double by Newton-Raphson iteration
 // y <- y + y (1 - x y), started from the hardware's approximate FP64
 // reciprocal (PTX rcp.approx.ftz.f64); two iterations bring the relative
@@ -83,15 +91,25 @@ __device__ __forceinline__ Prim64 prim64(const dbl4 &w, double gm1) {
     q.p = gm1 * (w.w - 0.5 * (w.y * w.y + w.z * w.z) * q.ir);
     return q;
 }
+// The same with hgm1 = (gamma - 1) / 2 given: p = (gamma - 1) E - hgm1 |m|^2 / rho,
+// one product fewer.
+__device__ __forceinline__ Prim64 prim64(const dbl4 &w, double gm1, double hgm1) {
+    Prim64 q;
+    q.r = rsqrt64(w.x);
+    q.ir = q.r * q.r;
+    q.p = fma(-(hgm1 * fma(w.z, w.z, w.y * w.y)), q.ir, gm1 * w.w);
+    return q;
+}
 
 // Roe average of two states (weights sqrt(rho)) and the eigen-quantities
-// of the flux Jacobian along n.
+// of the flux Jacobian along n; hgm1 = (gamma - 1) / 2.
 struct Roe64 {
     double u, v, H, c, ic, b1, qn, qt, hq2, nx, ny;
     double b1h, ich;  // b1 / 2 and ic / 2, the factors project64 applies
 };
 // Roe average from the two sides' records (same result as roe64).
-__device__ __forceinline__ Roe64 roe64_from_records(const dbl4 &qa, const dbl4 &qb, double nx, double ny, double gm1) {
+__device__ __forceinline__ Roe64 roe64_from_records(const dbl4 &qa, const dbl4 &qb, double nx, double ny, double gm1,
+                                                    double hgm1) {
     Roe64 R;
     const double inv = recip64(qa.x + qb.x);
     R.u = (qa.y + qb.y) * inv;
@@ -101,8 +119,9 @@ __device__ __forceinline__ Roe64 roe64_from_records(const dbl4 &qa, const dbl4 &
     const double c2 = gm1 * (R.H - R.hq2);
     R.ic = rsqrt64(c2);
     R.c = c2 * R.ic;
-    R.b1 = gm1 * R.ic * R.ic;
-    R.b1h = 0.5 * R.b1;
+    const double ic2 = R.ic * R.ic;
+    R.b1 = gm1 * ic2;
+    R.b1h = hgm1 * ic2;  // hgm1 = (gamma - 1) / 2
     R.ich = 0.5 * R.ic;
     R.nx = nx;
     R.ny = ny;
@@ -112,7 +131,7 @@ __device__ __forceinline__ Roe64 roe64_from_records(const dbl4 &qa, const dbl4 &
 }
 
 __device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const dbl4 &b, const Prim64 &pb,
-                                      double nx, double ny, double gm1) {
+                                      double nx, double ny, double gm1, double hgm1) {
     Roe64 R;
     const double sa = a.x * pa.r, sb = b.x * pb.r;
     const double inv = recip64(sa + sb);
@@ -123,8 +142,9 @@ __device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const db
     const double c2 = gm1 * (R.H - R.hq2);
     R.ic = rsqrt64(c2);
     R.c = c2 * R.ic;
-    R.b1 = gm1 * R.ic * R.ic;
-    R.b1h = 0.5 * R.b1;
+    const double ic2 = R.ic * R.ic;
+    R.b1 = gm1 * ic2;
+    R.b1h = hgm1 * ic2;  // hgm1 = (gamma - 1) / 2
     R.ich = 0.5 * R.ic;
     R.nx = nx;
     R.ny = ny;
@@ -152,6 +172,18 @@ __device__ __forceinline__ dbl4 unproject64(const Roe64 &R, const dbl4 &c) {
                         R.H * ac + R.hq2 * c.y + R.qn * dd + R.qt * c.z);
 }
 
+// base + the conservative difference of unproject64, with base taken into
+// the fused multiply-add chains (three additions fewer than add4 after
+// unproject64).
+__device__ __forceinline__ dbl4 unproject_add64(const Roe64 &R, const dbl4 &c, const dbl4 &base) {
+    const double ac = c.x + c.w;
+    const double rho = ac + c.y;
+    const double dd = R.c * (c.w - c.x);
+    return dbl4_make(base.x + rho, fma(R.u, rho, fma(R.nx, dd, fma(-R.ny, c.z, base.y))),
+                     fma(R.v, rho, fma(R.ny, dd, fma(R.nx, c.z, base.z))),
+                     fma(R.H, ac, fma(R.hq2, c.y, fma(R.qn, dd, fma(R.qt, c.z, base.w)))));
+}
+
 // NU-WENO5 increments of one characteristic field (Appendix), both sides.
 // Differences: a = L3-L1, b = L2-L1, c = R1-L1, d = R2-L1 (left centre L1),
 // e = R3-R1, f = R2-R1 (right centre R1).  k is the edge's coefficient block
@@ -172,10 +204,13 @@ __device__ __forceinline__ WenoField weno_field64(const double *k, double a, dou
     W.vb = fma(k[5], b, k[6] * c);
     W.vc = fma(k[10], c, k[11] * d);
     W.vd = fma(k[15], e, k[16] * f);
-    W.ba = fma(k[2], a * a, fma(k[3], a * b, fma(k[4], b2, eps)));
-    W.bb = fma(k[7], b2, fma(k[8], b * c, fma(k[9], c2, eps)));
-    W.bc = fma(k[12], c2, fma(k[13], c * d, fma(k[14], d * d, eps)));
-    W.bd = fma(k[17], e * e, fma(k[18], e * f, fma(k[19], f * f, eps)));
+    // m0 x^2 + m1 x y + m2 y^2 + eps as x (m0 x + m1 y) + m2 y^2 + eps, with
+    // y^2 shared between neighbouring sub-stencils: three products per field
+    // fewer than the expanded form
+    W.ba = fma(a, fma(k[2], a, k[3] * b), fma(k[4], b2, eps));
+    W.bb = fma(b, fma(k[7], b, k[8] * c), fma(k[9], c2, eps));
+    W.bc = fma(d, fma(k[14], d, k[13] * c), fma(k[12], c2, eps));
+    W.bd = fma(e, fma(k[17], e, k[18] * f), fma(k[19], f * f, eps));
     return W;
 }
 
@@ -197,11 +232,14 @@ __device__ __forceinline__ void weno_combine64(const double *k, const WenoField 
 __device__ __forceinline__ void weno_pair64_l1(const double *k, double a, double b, double c, double d, double e,
                                                double f, double eps, double &dl, double &dr) {
     const WenoField W = weno_field64(k, a, b, c, d, e, f, eps);
-    const double bbc = W.bb * W.bc;
-    const double l0 = k[20] * bbc, l1 = W.ba * W.bc, l2 = k[21] * (W.ba * W.bb);
-    dl = fma(l0, W.va, fma(l1, W.vb, l2 * W.vc)) * recip64_fast(l0 + l1 + l2);
-    const double r0 = k[22] * bbc, r1 = W.bd * W.bb, r2 = k[23] * (W.bd * W.bc);
-    dr = fma(r0, W.vd + c, fma(r1, W.vc, r2 * W.vb)) * recip64_fast(r0 + r1 + r2);
+    // left: (C0 bb bc va + ba bc vb + C2 ba bb vc) / (C0 bb bc + ba bc + C2 ba bb)
+    // with bc factored from the first two terms; right: (D0 bb bc vd' + bd bb vc
+    // + D2 bd bc vb) / (D0 bb bc + bd bb + D2 bd bc) with bb factored from the
+    // first two (one product fewer per field than the term-by-term sums)
+    const double g = k[20] * W.bb, m = k[21] * (W.ba * W.bb);
+    dl = fma(W.bc, fma(g, W.va, W.ba * W.vb), m * W.vc) * recip64_fast(fma(W.bc, g + W.ba, m));
+    const double s = k[22] * W.bc, q = k[23] * (W.bd * W.bc);
+    dr = fma(W.bb, fma(s, W.vd + c, W.bd * W.vc), q * W.vb) * recip64_fast(fma(W.bb, s + W.bd, q));
 }
 
 }  // namespace dev

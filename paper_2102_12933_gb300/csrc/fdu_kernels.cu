@@ -34,7 +34,7 @@ using namespace dev;
 __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int64_t e) {
     const double *__restrict__ w = static_cast<const double *>(A.w);
     const double *__restrict__ coef = static_cast<const double *>(A.coef);
-    const double gm1 = A.gm1;
+    const double gm1 = A.gm1, hgm1 = A.hgm1;
     const int64_t ne = A.ne;
     int32_t s[6];
 #pragma unroll
@@ -45,8 +45,8 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
 
     // characteristic decomposition at the Roe average of the end states
     // (per-vertex Roe records when the stage kernel provided them)
-    const Roe64 C = A.Q ? roe64_from_records(ld4(A.Q, s[2]), ld4(A.Q, s[3]), nx, ny, gm1)
-                        : roe64(L1, prim64(L1, gm1), R1, prim64(R1, gm1), nx, ny, gm1);
+    const Roe64 C = A.Q ? roe64_from_records(ld4(A.Q, s[2]), ld4(A.Q, s[3]), nx, ny, gm1, hgm1)
+                        : roe64(L1, prim64(L1, gm1, hgm1), R1, prim64(R1, gm1, hgm1), nx, ny, gm1, hgm1);
     const dbl4 cM = project64(C, sub4(R1, L1));               // R1 - L1
     const dbl4 cL2 = project64(C, sub4(ld4(w, s[1]), L1));    // L2 - L1
     const dbl4 cL3 = project64(C, sub4(ld4(w, s[0]), L1));    // L3 - L1
@@ -64,20 +64,20 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
     weno_pair64_l1(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps, dl.w, dr.w);
 
     // both interpolated states from L1 (R (R1 - L1)_char = R1 - L1)
-    dbl4 wl = add4(L1, unproject64(C, dl));
-    dbl4 wr = add4(L1, unproject64(C, dr));
+    dbl4 wl = unproject_add64(C, dl, L1);
+    dbl4 wr = unproject_add64(C, dr, L1);
     Prim64 pl, pr;
-    bool ok = wl.x > 0.0 && wr.x > 0.0;
+    bool ok = pos64(wl.x) && pos64(wr.x);
     if (ok) {
-        pl = prim64(wl, gm1);
-        pr = prim64(wr, gm1);
-        ok = pl.p > 0.0 && pr.p > 0.0;
+        pl = prim64(wl, gm1, hgm1);
+        pr = prim64(wr, gm1, hgm1);
+        ok = pos64(pl.p) && pos64(pr.p);
     }
     if (!ok) {  // positivity fallback: first-order end states
         wl = L1;
         wr = R1;
-        pl = prim64(L1, gm1);
-        pr = prim64(R1, gm1);
+        pl = prim64(L1, gm1, hgm1);
+        pr = prim64(R1, gm1, hgm1);
         atomicAdd(A.fallback, 1ull);
     }
 
@@ -85,12 +85,23 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
     // form F_L + R diag((lambda - |lambda|)/2) L (w_R - w_L): equal to
     // (F_L + F_R)/2 - R |Lambda| L (w_R - w_L)/2 because the Roe matrix
     // satisfies F_R - F_L = R Lambda L (w_R - w_L)
-    const Roe64 Q = roe64(wl, pl, wr, pr, nx, ny, gm1);
+    const Roe64 Q = roe64(wl, pl, wr, pr, nx, ny, gm1, hgm1);
     const dbl4 a = project64(Q, sub4(wr, wl));
-    const double delta = 0.1 * Q.c, h2d = 5.0 * Q.ic;  // 1 / (2 delta)
-    auto neg = [&](double l) {  // (l - |l|_fixed) / 2
-        const double m = fabs(l);
-        return 0.5 * (l - (m < delta ? fma(l, l, delta * delta) * h2d : m));
+    // (l - |l|_fixed) / 2 is min(l, 0) where |l| >= delta and, where Harten's
+    // |l|_fixed = (l^2 + delta^2) / (2 delta) applies, -(l - delta)^2 / (4 delta).
+    // Both tests run on the integer pipe: |l| < delta compares the bit
+    // patterns of two non-negative doubles (delta = 0.1 c is positive), and
+    // a NaN l is passed through as the FP64 form would.
+    const double delta = 0.1 * Q.c, h4d = 2.5 * Q.ic;  // 1 / (4 delta)
+    const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
+    auto neg = [&](double l) {
+        const long long b = __double_as_longlong(l);
+        const unsigned long long ab = (unsigned long long)b & 0x7FFFFFFFFFFFFFFFULL;
+        if (ab < dbits) {
+            const double s = l - delta;
+            return -(s * s) * h4d;
+        }
+        return (b < 0 || ab > 0x7FF0000000000000ULL) ? l : 0.0;
     };
     const double nu = neg(Q.qn), nm = neg(Q.qn - Q.c), np = neg(Q.qn + Q.c);
     const dbl4 D = unproject64(Q, dbl4_make(nm * a.x, nu * a.y, nu * a.z, np * a.w));

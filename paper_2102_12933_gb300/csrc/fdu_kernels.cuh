@@ -18,6 +18,7 @@ struct EdgeArgs {
     void *r;              // FP64: [ne][4] double; FP32: [ne] float4
     int64_t ne;
     double gm1, eps;      // gamma - 1 and the WENO epsilon (FP64 path)
+    double hgm1;          // (gamma - 1) / 2
     float gm1f, epsf;     // the same for the FP32 path
     unsigned long long *fallback;  // edges that fell back to first order (device counter)
     const double *dt_dev; // adaptive stepping: a zero time step here skips the launch

@@ -406,6 +406,35 @@ def test_roe_flux_consistency_symmetry_and_upwinding():
     assert np.allclose(_flux_n(wr, n) - _flux_n(wl, n), Aroe @ (wr - wl), atol=1e-13)
 
 
+@pytest.mark.parametrize("qn_over_c", [0.0, 0.03, -0.07, 0.0999, -0.1001, 0.25, -0.6])
+def test_roe_flux_of_a_moving_contact_with_the_entropy_fix(qn_over_c):
+    """A contact discontinuity: uniform velocity and pressure, a density jump.
+    Worked by hand: w_R - w_L = (rho_R - rho_L) (1, u, v, |q|^2 / 2), which is
+    the entropy eigenvector, so the other three wave strengths vanish; the
+    Roe-averaged sound speed is c^2 = gamma p / sqrt(rho_L rho_R) (the Roe
+    average of the enthalpy minus |q|^2 / 2); the wave speed is q_n.  The flux
+    is then (F_L + F_R) / 2 - |q_n|_fix (rho_R - rho_L) (1, u, v, |q|^2 / 2) / 2
+    with Harten's |q_n|_fix = (q_n^2 + d^2) / (2 d) for |q_n| < d = c / 10 and
+    |q_n| outside that band: the stationary contact (q_n = 0) carries the
+    mass flux -(c / 40) (rho_R - rho_L), and outside the band the flux is the
+    upwind side's."""
+    n = np.array([0.28, -0.96])
+    t = np.array([-n[1], n[0]])
+    rl, rr, p = 0.7, 1.9, 1.3
+    c = math.sqrt(G * p / math.sqrt(rl * rr))
+    qn = qn_over_c * c
+    vel = qn * n + 0.4 * t  # a tangential part as well
+    wl, wr = _state(rl, vel[0], vel[1], p), _state(rr, vel[0], vel[1], p)
+    d = 0.1 * c
+    fix = (qn * qn + d * d) / (2 * d) if abs(qn) < d else abs(qn)
+    r2 = np.array([1.0, vel[0], vel[1], 0.5 * vel @ vel])
+    want = 0.5 * (_flux_n(wl, n) + _flux_n(wr, n)) - 0.5 * fix * (rr - rl) * r2
+    got = oracle.roe_flux(wl, wr, n)
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-13)
+    if abs(qn) >= d:  # upwinding outside the band
+        assert np.allclose(got, _flux_n(wl if qn > 0 else wr, n), atol=1e-13)
+
+
 # ----------------------------------------------------------- residual, RK3
 def test_free_stream_preserved():
     m, _ = inputs.vortex_case(20, seed=12)

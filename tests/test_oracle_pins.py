@@ -435,6 +435,59 @@ def test_roe_flux_of_a_moving_contact_with_the_entropy_fix(qn_over_c):
         assert np.allclose(got, _flux_n(wl if qn > 0 else wr, n), atol=1e-13)
 
 
+# ----------------------------------------------------------- time step
+def _edge_min_lengths(m):
+    """Shortest triangle edge at each vertex, by brute force over the
+    triangles (minimum image on the torus)."""
+    h = np.full(m.nv, np.inf)
+    for a, b in ((0, 1), (1, 2), (2, 0)):
+        i, j = m.tri[:, a], m.tri[:, b]
+        d = m.xy[j] - m.xy[i]
+        for k, L in enumerate((m.Lx, m.Ly)):
+            if L > 0:
+                d[:, k] -= L * np.round(d[:, k] / L)
+        ln = np.hypot(d[:, 0], d[:, 1])
+        np.minimum.at(h, i, ln)
+        np.minimum.at(h, j, ln)
+    return h
+
+
+def test_max_dt_is_the_cfl_bound():
+    """dt = CFL min_v h_v / (|q_v| + c_v), h_v the shortest edge at v (the
+    reading of the CFL condition used in Section 3.1)."""
+    # regular lattice, uniform state: h = L / n, |q| = 0.5, c = 1
+    m = inputs.torus_lattice(12, L=6.0, jitter=0.0, seed=3)
+    one = np.ones(m.nv)
+    w = inputs.primitive_to_conservative(1.4 * one, 0.3 * one, -0.4 * one, 1.0 * one)
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly)
+    assert abs(om.max_dt(w, 0.5) - 0.5 * 0.5 / 1.5) < 1e-15
+    # jittered lattice, varied state: brute force
+    m = inputs.torus_lattice(9, L=6.0, jitter=0.3, seed=4)
+    rng = np.random.default_rng(5)
+    r, u, v, p = (rng.uniform(0.5, 2, m.nv), rng.uniform(-1, 1, m.nv), rng.uniform(-1, 1, m.nv),
+                  rng.uniform(0.5, 2, m.nv))
+    w = inputs.primitive_to_conservative(r, u, v, p)
+    want = 0.3 * np.min(_edge_min_lengths(m) / (np.hypot(u, v) + np.sqrt(G * p / r)))
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly)
+    assert abs(om.max_dt(w, 0.3) - want) <= 1e-14 * want
+
+
+def test_max_dt_ignores_ghost_vertices():
+    m = inputs.box_lattice(12, ghost_layers=5, jitter=0.1, seed=6)
+    one = np.ones(m.nv)
+    w = inputs.primitive_to_conservative(one, 0.2 * one, 0.1 * one, one)
+    om = oracle.OracleMesh(m.xy, m.tri, 0.0, 0.0, ghost=m.ghost_donor)
+    base = om.max_dt(w, 0.5)
+    ghost = m.ghost_donor >= 0
+    w2 = w.copy()
+    w2[ghost] = inputs.primitive_to_conservative(one[ghost], 50.0 * one[ghost], 0 * one[ghost], one[ghost])
+    assert om.max_dt(w2, 0.5) == base
+    real = np.nonzero(~ghost)[0]
+    h = _edge_min_lengths(m)[real]
+    c = math.sqrt(G)
+    assert abs(base - 0.5 * np.min(h / (math.hypot(0.2, 0.1) + c))) <= 1e-14 * base
+
+
 # ----------------------------------------------------------- residual, RK3
 def test_free_stream_preserved():
     m, _ = inputs.vortex_case(20, seed=12)

@@ -133,11 +133,26 @@ int build_edges(const CellList &cells, int artificial, int degree, int64_t nv, c
             keys.push_back(edge_key(v[1], v[3]));
         }
     }
-    std::sort(keys.begin(), keys.end());
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    if (artificial >= 2) far_apex_edges(cells, nv, degree, keys);
-    std::sort(keys.begin(), keys.end());
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    {  // sort and deduplicate: bucket by the smaller id, then sort each short bucket
+        std::vector<int64_t> cnt(nv + 1, 0);
+        for (uint64_t k : keys) cnt[(k >> 32) + 1]++;
+        for (int64_t v = 0; v < nv; ++v) cnt[v + 1] += cnt[v];
+        std::vector<uint32_t> q(keys.size());
+        std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+        for (uint64_t k : keys) q[fill[k >> 32]++] = (uint32_t)(k & 0xffffffffu);
+        keys.clear();
+        for (int64_t v = 0; v < nv; ++v) {
+            auto b = q.begin() + cnt[v], e = q.begin() + cnt[v + 1];
+            std::sort(b, e);
+            e = std::unique(b, e);
+            for (auto it = b; it != e; ++it) keys.push_back(((uint64_t)v << 32) | *it);
+        }
+    }
+    if (artificial >= 2) {
+        far_apex_edges(cells, nv, degree, keys);
+        std::sort(keys.begin(), keys.end());
+        keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    }
     T.ne = (int64_t)keys.size();
     T.edge.resize(2 * T.ne);
     T.nrm.resize(2 * T.ne);
@@ -154,22 +169,29 @@ int build_edges(const CellList &cells, int artificial, int degree, int64_t nv, c
         T.nrm[2 * k] = d[0] / l;
         T.nrm[2 * k + 1] = d[1] / l;
     }
-    // adjacency: (vertex, neighbour, edge) triples sorted by (vertex, neighbour)
-    std::vector<std::array<int32_t, 3>> trip(2 * T.ne);
-    for (int64_t k = 0; k < T.ne; ++k) {
-        trip[2 * k] = {T.edge[2 * k], T.edge[2 * k + 1], (int32_t)k};
-        trip[2 * k + 1] = {T.edge[2 * k + 1], T.edge[2 * k], (int32_t)k};
-    }
-    std::sort(trip.begin(), trip.end());
+    // adjacency (CSR): each vertex's (neighbour, edge) pairs in ascending
+    // neighbour order; bucketed by vertex, then each short list sorted
     T.adj_off.assign(nv + 1, 0);
-    T.adj.resize(trip.size());
-    T.adj_edge.resize(trip.size());
-    for (size_t i = 0; i < trip.size(); ++i) {
-        T.adj_off[trip[i][0] + 1]++;
-        T.adj[i] = trip[i][1];
-        T.adj_edge[i] = trip[i][2];
-    }
+    for (int64_t k = 0; k < 2 * T.ne; ++k) T.adj_off[T.edge[k] + 1]++;
     for (int64_t v = 0; v < nv; ++v) T.adj_off[v + 1] += T.adj_off[v];
+    {
+        std::vector<std::pair<int32_t, int32_t>> nbr(2 * T.ne);  // (neighbour, edge)
+        std::vector<int64_t> fill(T.adj_off.begin(), T.adj_off.end() - 1);
+        for (int64_t k = 0; k < T.ne; ++k) {
+            const int32_t a = T.edge[2 * k], b = T.edge[2 * k + 1];
+            nbr[fill[a]++] = {b, (int32_t)k};
+            nbr[fill[b]++] = {a, (int32_t)k};
+        }
+        T.adj.resize(2 * T.ne);
+        T.adj_edge.resize(2 * T.ne);
+        for (int64_t v = 0; v < nv; ++v) {
+            std::sort(nbr.begin() + T.adj_off[v], nbr.begin() + T.adj_off[v + 1]);
+            for (int64_t i = T.adj_off[v]; i < T.adj_off[v + 1]; ++i) {
+                T.adj[i] = nbr[i].first;
+                T.adj_edge[i] = nbr[i].second;
+            }
+        }
+    }
     for (int64_t v = 0; v < nv; ++v)
         if (T.adj_off[v + 1] - T.adj_off[v] < 2) {
             err = "vertex " + std::to_string(v) + " has fewer than two neighbours";
@@ -534,6 +556,8 @@ uint64_t hilbert_index(uint32_t x, uint32_t y, int order) {
     return d;
 }
 
+// f(b, e, thread) over [0, n) in ranges that start at multiples of 256 and
+// end at the next multiple or at n (one range [0, n) when run serially).
 template <class F>
 void parallel_for(int64_t n, int threads, F &&f) {
     if (threads <= 1 || n < 1024) {
@@ -646,27 +670,58 @@ int build_host_tables(const double *xy, int64_t nv, const CellList &cells, int a
         return FDU_ERR_STENCIL;
     }
 
-    // divergence stencils (serial: cheap) and weights (parallel)
+    // divergence stencils and weights (both parallel).  Each chunk of
+    // vertices collects its stencils in its own buffers; concatenating the
+    // chunks in vertex order gives the tables a serial loop would build.
     T.voff.assign(nv + 1, 0);
     T.eoff.assign(nv + 1, 0);
     T.vid.clear();
     T.eid.clear();
     {
-        std::vector<int32_t> V, E;
-        for (int32_t v = 0; v < nv; ++v) {
-            if (T.ghost.empty() || T.ghost[v] < 0) {
-                stencil_of(T, v, V, E);
-                for (int32_t e : E)
-                    if (T.sten[6 * (int64_t)e] < 0) {
-                        err = "edge " + std::to_string(e) + " in the divergence stencil of vertex " +
-                              std::to_string(v) + " has no 1D stencil";
-                        return FDU_ERR_STENCIL;
+        const int64_t chunk = 256, nchunk = (nv + chunk - 1) / chunk;
+        std::vector<std::vector<int32_t>> cv(nchunk), ce(nchunk);
+        std::atomic<int64_t> first_bad(INT64_MAX);  // lowest vertex with an edge lacking a 1D stencil
+        std::vector<int32_t> bad_edge(nchunk, -1);
+        // parallel_for hands out vertex ranges that start at multiples of 256
+        // and hold whole chunks
+        parallel_for(nv, threads, [&](int64_t b, int64_t e, int) {
+            std::vector<int32_t> V, E;
+            for (int64_t c = b / chunk; c * chunk < e; ++c)
+                for (int64_t v = c * chunk; v < std::min(nv, (c + 1) * chunk); ++v) {
+                    if (!T.ghost.empty() && T.ghost[v] >= 0) {
+                        T.voff[v + 1] = 0;
+                        T.eoff[v + 1] = 0;
+                        continue;
                     }
-                T.vid.insert(T.vid.end(), V.begin(), V.end());
-                T.eid.insert(T.eid.end(), E.begin(), E.end());
-            }
-            T.voff[v + 1] = (int64_t)T.vid.size();
-            T.eoff[v + 1] = (int64_t)T.eid.size();
+                    stencil_of(T, (int32_t)v, V, E);
+                    for (int32_t k : E)
+                        if (T.sten[6 * (int64_t)k] < 0 && bad_edge[c] < 0) {
+                            bad_edge[c] = k;
+                            int64_t cur = first_bad.load();
+                            while (v < cur && !first_bad.compare_exchange_weak(cur, v)) {
+                            }
+                        }
+                    cv[c].insert(cv[c].end(), V.begin(), V.end());
+                    ce[c].insert(ce[c].end(), E.begin(), E.end());
+                    T.voff[v + 1] = (int64_t)V.size();  // counts, summed below
+                    T.eoff[v + 1] = (int64_t)E.size();
+                }
+        });
+        if (first_bad.load() != INT64_MAX) {
+            const int64_t v = first_bad.load();
+            err = "edge " + std::to_string(bad_edge[v / chunk]) + " in the divergence stencil of vertex " +
+                  std::to_string(v) + " has no 1D stencil";
+            return FDU_ERR_STENCIL;
+        }
+        for (int64_t v = 0; v < nv; ++v) {
+            T.voff[v + 1] += T.voff[v];
+            T.eoff[v + 1] += T.eoff[v];
+        }
+        T.vid.reserve(T.voff[nv]);
+        T.eid.reserve(T.eoff[nv]);
+        for (int64_t c = 0; c < nchunk; ++c) {
+            T.vid.insert(T.vid.end(), cv[c].begin(), cv[c].end());
+            T.eid.insert(T.eid.end(), ce[c].begin(), ce[c].end());
         }
     }
     T.wf.assign(T.vid.size(), 0.0);

@@ -54,6 +54,46 @@ def test_info_counts():
     assert 12 <= info["J_min"] <= info["J_max"] <= 30
 
 
+@pytest.mark.parametrize("kind", ["torus", "ghost box"])
+def test_host_tables_do_not_depend_on_the_thread_count(kind):
+    """Edges, 1D stencils and divergence stencils are built in parallel
+    chunks; every thread count gives the same bits.  The meshes have more
+    than 1024 vertices so that the tables are built by several threads."""
+    if kind == "torus":
+        m, _ = inputs.vortex_case(48, seed=21)
+        build = lambda t: fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=-1, host_threads=t)
+    else:
+        m = inputs.box_lattice(40, ghost_layers=5, seed=22)
+        build = lambda t: fdu.Mesh(m.xy, m.tri, 0.0, 0.0, device=-1, host_threads=t, ghost_donor=m.ghost_donor)
+    ref = build(1)
+    for t in (2, 5):
+        M = build(t)
+        assert np.array_equal(M.edges(), ref.edges())
+        for x, y in zip(M.edge_stencils(), ref.edge_stencils()):
+            assert np.array_equal(x, y)
+        for x, y in zip(M.div_stencils(), ref.div_stencils()):
+            assert np.array_equal(x, y)
+
+
+def test_stencil_error_names_the_same_vertex_for_any_thread_count():
+    """An open box whose first ten rows are (Dirichlet) ghosts and whose
+    other sides have none: the parallel divergence-stencil build reports the
+    lowest vertex whose stencil holds an edge without a 1D stencil, as a
+    serial build does (here a vertex several 256-vertex chunks in)."""
+    b = inputs.box_lattice(40, ghost_layers=0, seed=23)
+    donor = np.full(b.nv, -1, np.int32)
+    low = np.arange(b.nv) < 400
+    donor[low] = np.nonzero(low)[0]
+    msgs = set()
+    for t in (1, 3, 8):
+        with pytest.raises(fdu.FduError) as e:
+            fdu.Mesh(b.xy, b.tri, 0.0, 0.0, device=-1, host_threads=t, ghost_donor=donor)
+        assert e.value.status == -3
+        msgs.add(str(e.value))
+    assert len(msgs) == 1, msgs
+    assert re.search(r"vertex (\d+)", msgs.pop()).group(1) != "0"
+
+
 def test_renumbering_is_invisible():
     """Permuting the caller's vertex ids permutes the outputs and nothing else."""
     m, _ = inputs.vortex_case(24, seed=5)

@@ -51,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for f in HOST_SRC:
         o = os.path.join(OUT_DIR, f + ".o")
         objs.append(o)
-        jobs.append(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-pthread", *inc, "-c",
+        jobs.append(["g++", "-std=c++17", "-O3", "-ffp-contract=off", "-fPIC", "-pthread", *inc, "-c",
                      os.path.join(CSRC, f), "-o", o])
     for f in CUDA_SRC:
         o = os.path.join(OUT_DIR, f + ".o")

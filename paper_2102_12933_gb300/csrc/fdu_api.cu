@@ -1211,7 +1211,8 @@ fdu_status fdu_limited_count(fdu_mesh *m, int64_t *count, int reset, void *strea
 fdu_status fdu_batch_create(int32_t n_meshes, const double *const *xy, const int64_t *nv, const int32_t *const *tri,
                             const int64_t *nt, const fdu_mesh_opts *opts, fdu_mesh **out) {
     if (out) *out = nullptr;
-    if (n_meshes < 1 || !xy || !nv || !tri || !nt || !opts || !out) return set_err(FDU_ERR_ARG, "null argument");
+    if (n_meshes < 1) return set_err(FDU_ERR_ARG, "a batch needs at least one mesh");
+    if (!xy || !nv || !tri || !nt || !opts || !out) return set_err(FDU_ERR_ARG, "null argument");
     if (opts->ghost_donor || opts->bc != FDU_BC_PERIODIC)
         return set_err(FDU_ERR_ARG, "batches hold periodic meshes (without ghost vertices)");
     if (opts->device < 0) return set_err(FDU_ERR_ARG, "batches need a device");

@@ -145,6 +145,30 @@ def test_error_statuses():
     assert e.value.status == -8
 
 
+def test_degenerate_inputs_fail_cleanly():
+    """Empty and minimal inputs return error statuses (no crash, no
+    partial object)."""
+    tri1 = np.array([[0, 1, 2]], np.int32)
+    xy1 = np.array([[0, 0], [1, 0], [0, 1.0]])
+    cases = [
+        ("no vertices", np.zeros((0, 2)), np.zeros((0, 3), np.int32), 0.0, 0.0, -1),
+        ("no triangles", np.random.default_rng(0).random((5, 2)), np.zeros((0, 3), np.int32), 0.0, 0.0, -1),
+        ("one triangle, non-periodic without ghost vertices", xy1, tri1, 0.0, 0.0, -1),
+        ("one triangle, periodic: no walk finds a forward neighbour", xy1, tri1, 2.0, 2.0, -3),
+    ]
+    for name, xy, tri, Lx, Ly, status in cases:
+        with pytest.raises(fdu.FduError) as e:
+            fdu.Mesh(xy, tri, Lx, Ly, device=-1)
+        assert e.value.status == status, (name, e.value)
+    m, _ = inputs.vortex_case(12, seed=3)
+    with pytest.raises(fdu.FduError) as e:
+        fdu.Batch([], 10.0, device=-1)
+    assert e.value.status == -1 and "at least one mesh" in str(e.value)
+    with pytest.raises(fdu.FduError) as e:
+        fdu.Batch([(m.xy, m.tri)], 10.0, device=-1)  # batches live on a device
+    assert e.value.status == -1
+
+
 def test_transmissive_box_tables_match_oracle():
     """Four-quadrant Riemann box with 5 ghost layers: real vertices carry
     stencils, ghosts do not; every active edge has a full 1D stencil."""

@@ -500,7 +500,24 @@ int lsq_weights(const HostTables &T, const Geo &g, int32_t o, const int64_t vb, 
         for (int i = k; i < m; ++i) vv += v[i] * v[i];
         beta[k] = vv > 0 ? 2.0 / vv : 0.0;
         rdiag[k] = alpha;
-        for (int c = k; c < n; ++c) {
+        // two columns per pass: two independent dot products in flight, each
+        // summed in the same order as alone (same bits)
+        int c = k;
+        for (; c + 1 < n; c += 2) {
+            double *a = &A[(size_t)c * m], *a2 = &A[(size_t)(c + 1) * m];
+            double dot = 0, dot2 = 0;
+            for (int i = k; i < m; ++i) {
+                dot += v[i] * a[i];
+                dot2 += v[i] * a2[i];
+            }
+            dot *= beta[k];
+            dot2 *= beta[k];
+            for (int i = k; i < m; ++i) {
+                a[i] -= dot * v[i];
+                a2[i] -= dot2 * v[i];
+            }
+        }
+        if (c < n) {
             double *a = &A[(size_t)c * m];
             double dot = 0;
             for (int i = k; i < m; ++i) dot += v[i] * a[i];

@@ -336,6 +336,12 @@ class Mesh:
         return out
 
     def residual(self, precision=64, out=None, stream=None):
+        """dw/dt of the current state, [nv, 4] in the caller's vertex order
+        (edge fluxes by characteristic NU-WENO5 and a Roe flux, Section 2.3.1;
+        least-squares divergence, Section 2.2.1).  precision 64: FP64;
+        48: the FP64 result with the edge-flux increments in double-word FP32;
+        32: FP32 fluxes with FP64 accumulation.  out: a host array or a CUDA
+        tensor of that shape (None: a new host array)."""
         if out is None:
             out = np.zeros((self.nv, 4))
         p, dev = _buffer(out, self.nv, writable=True)
@@ -343,14 +349,19 @@ class Mesh:
         return out
 
     def max_dt(self, cfl, stream=None) -> float:
+        """CFL time step of the current state: cfl * min over real vertices of
+        h_v / (|q_v| + c_v), h_v the shortest edge at v."""
         dt = C.c_double()
         _check(load().fdu_max_dt(self._h, float(cfl), C.byref(dt), _stream_ptr(stream)))
         return dt.value
 
     def rk_step(self, dt, precision=64, stream=None):
+        """One SSP-RK3 step (three stages, Shu-Osher form) of size dt;
+        precision as for residual."""
         _check(load().fdu_rk_step(self._h, float(dt), int(precision), _stream_ptr(stream)))
 
     def rk_steps(self, dt, n_steps, precision=64, stream=None):
+        """n_steps SSP-RK3 steps of size dt, replayed from a captured CUDA graph."""
         _check(load().fdu_rk_steps(self._h, float(dt), int(precision), int(n_steps), _stream_ptr(stream)))
 
     def fallback_count(self, reset=False, stream=None) -> int:
@@ -482,6 +493,8 @@ class Batch(Mesh):
         _check(load().fdu_batch_set_dt(self._h, _dp(dt), _stream_ptr(stream)))
 
     def batch_rk_steps(self, n_steps, precision=32, stream=None):
+        """n_steps SSP-RK3 steps of every mesh with its own dt (set_dt), one
+        persistent launch per stage; precision 32, 48 or 64."""
         _check(load().fdu_batch_rk_steps(self._h, int(precision), int(n_steps), _stream_ptr(stream)))
 
     def set_launch(self, threads, blocks_per_sm):

@@ -232,7 +232,11 @@ fdu_status fdu_limited_count(fdu_mesh *mesh, int64_t *count, int reset, void *st
  * in ONE cooperative persistent launch per RK stage (edge fluxes of all
  * meshes, a bounded grid barrier, then every vertex's divergence and stage
  * update), captured once into a CUDA graph per (precision, launch shape).
- * xy[i], tri[i], nv[i], nt[i] describe mesh i as for fdu_mesh_create. */
+ * xy[i], tri[i], nv[i], nt[i] describe mesh i as for fdu_mesh_create.
+ * Errors: FDU_ERR_ARG for n_meshes < 1, a null array, a mesh with fewer
+ * than 3 vertices or no triangle, ghost vertices or non-periodic options,
+ * or opts->device < 0 (batches live on a device); FDU_ERR_MESH and the
+ * preprocessing errors of fdu_mesh_create for a bad member mesh. */
 fdu_status fdu_batch_create(int32_t n_meshes, const double *const *xy, const int64_t *nv, const int32_t *const *tri,
                             const int64_t *nt, const fdu_mesh_opts *opts, fdu_mesh **out);
 /* Number of meshes and vertex_offsets[n_meshes+1] (may be NULL). */

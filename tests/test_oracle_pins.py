@@ -105,6 +105,33 @@ def test_nonlinear_weno_exact_for_quadratics():
             assert abs(oracle.nuweno(x, u, eps=eps) - q[0]) < 1e-12
 
 
+def test_uniform_nonlinear_weights_combine_the_classical_pieces():
+    """On unit spacing the nonlinear interpolation is the classical WENO5
+    midpoint value with the paper's weights: alpha_k = C_k / (beta_k + eps)
+    (power 1), omega = alpha / sum(alpha), value = sum omega_k v_k, with the
+    sub-stencil values, linear weights and indicators in the closed forms
+    pinned above.  Checked to tell the power 1 from 2 on the same data."""
+    rng = np.random.default_rng(17)
+    C = np.array([1, 10, 5]) / 16.0
+    for eps in (1e-40, 1e-3, 0.5):
+        for _ in range(20):
+            u = rng.standard_normal(5)
+            a, b, c, d, e = u
+            v = np.array([(3 * a - 10 * b + 15 * c) / 8, (-b + 6 * c + 3 * d) / 8, (3 * c + 6 * d - e) / 8])
+            beta = np.array([(a - 3 * b + 2 * c) ** 2 + 13 / 12 * (a - 2 * b + c) ** 2,
+                             (d - c) ** 2 + 13 / 12 * (b - 2 * c + d) ** 2,
+                             (d - c) ** 2 + 13 / 12 * (c - 2 * d + e) ** 2])
+
+            def value(power):
+                al = C / (beta + eps) ** power
+                return float(al @ v / al.sum())
+
+            got = oracle.nuweno(UNIFORM, u, eps=eps)
+            assert abs(got - value(1)) <= 1e-13 * max(1.0, abs(got))
+            if eps < 1e-2:  # the power matters where eps does not swamp beta
+                assert abs(value(2) - value(1)) > 1e-9
+
+
 def test_nonlinear_weno_avoids_a_jump():
     """Across a jump the sub-stencil containing it gets (almost) no weight."""
     x = UNIFORM

@@ -81,6 +81,40 @@ def test_other_stencils_and_degrees():
             assert rel_l2(got[:, k], want[:, k]) <= 1e-12
 
 
+def test_degree5_one_step_measure_matches_oracle():
+    """Section 3.1's accuracy measure on the GPU path: one SSP-RK3 step at CFL
+    0.01 from the exact vortex on the regular diagonalised 80x80 lattice,
+    degree-5 least squares on two-level stencils, in FP64 and precision 48.
+    The residual matches the oracle within 1e-12 relative L2.  The step's
+    increment (about 1e-4 against states of size 1) matches within 1e-12
+    plus the rounding of the new state (2 ulp of |w|, relative to the
+    increment), and the L1 error of rho against the translated vortex
+    agrees to 1e-6 relative (that error is about 1e-8, so one ulp of the
+    state is already 1e-8 of it)."""
+    m = inputs.torus_lattice(80, L=10.0, jitter=0.0, random_diagonals=False)
+    w0 = inputs.isentropic_vortex(m.xy)
+    om = oracle.OracleMesh(m.xy, m.tri, 10.0, 10.0, degree=5)
+    dt = om.max_dt(w0, 0.01)
+    want = om.rk3_step(w0, dt)
+    res_want = om.residual(w0)
+    ex = inputs.isentropic_vortex(m.xy, t=dt)
+    e_want = np.mean(np.abs(want[:, 0] - ex[:, 0]))
+    M = fdu.Mesh(m.xy, m.tri, 10.0, 10.0, lsq_degree=5, lsq_levels=2, device=0)
+    for prec in (64, 48):
+        M.set_state(w0)
+        res = M.residual(prec)
+        M.rk_step(dt, prec)
+        got = M.get_state()
+        for k in range(4):
+            assert rel_l2(res[:, k], res_want[:, k]) <= 1e-12, (prec, k)
+            inc = want[:, k] - w0[:, k]
+            tol = 1e-12 + 2 * 2.0 ** -52 * np.linalg.norm(want[:, k]) / np.linalg.norm(inc)
+            assert rel_l2(got[:, k] - w0[:, k], inc) <= tol, (prec, k)
+        e_got = np.mean(np.abs(got[:, 0] - ex[:, 0]))
+        assert abs(e_got - e_want) <= 1e-6 * e_want, prec
+    M.close()
+
+
 def test_rk_steps_f64_match_oracle(c40):
     dt = c40.om.max_dt(c40.w0, 0.5)
     c40.M.set_state(c40.w0)

@@ -639,19 +639,54 @@ def test_positivity_safeguard_keeps_states_physical_and_is_inert_on_smooth_flow(
     assert np.abs(wa - wb).max() <= 1e-15 * np.abs(wa).max()
 
 
-@pytest.mark.slow
-def test_vortex_residual_degree5_regular_meshes():
-    """Section 3.1 with the paper's degree-5 least squares on regular
-    diagonalised meshes: the rate climbs past 3.5 by n = 80 -> 160 (the
-    nonlinear weights cap it near 4 at critical points, reading 14)."""
-    errs, hs = [], []
+@pytest.fixture(scope="module")
+def degree5_regular_lattices():
+    """The regular diagonalised torus lattices n = 40, 80, 160 of Section 3.1
+    with the paper's degree-5 least squares on two-level stencils (built once
+    for the two degree-5 pins)."""
+    out = []
     for n in (40, 80, 160):
         m = inputs.torus_lattice(n, L=10.0, jitter=0.0, random_diagonals=False)
+        out.append((10.0 / n, m, oracle.OracleMesh(m.xy, m.tri, 10.0, 10.0, degree=5)))
+    return out
+
+
+@pytest.mark.slow
+def test_vortex_one_step_degree5_regular_meshes(degree5_regular_lattices):
+    """Section 3.1's own accuracy measure: the L1 error of rho after one SSP-RK3
+    step at CFL 0.01 from the exact vortex, against the vortex translated by
+    dt, on regular diagonalised meshes.  The paper reports about fifth order;
+    the rate climbs towards 5 (4.42, then 4.77 on these lattices)."""
+    errs, hs = [], []
+    for h, m, om in degree5_regular_lattices:
         w0 = inputs.isentropic_vortex(m.xy)
-        d = 1e-5
+        dt = om.max_dt(w0, 0.01)
+        w1 = om.rk3_step(w0, dt)
+        ex = inputs.isentropic_vortex(m.xy, t=dt)
+        errs.append(np.mean(np.abs(w1[:, 0] - ex[:, 0])))
+        hs.append(h)
+    assert math.log(errs[0] / errs[1]) / math.log(2) > 4.2
+    assert math.log(errs[1] / errs[2]) / math.log(2) > 4.5
+    assert errs[2] < 1e-9
+
+
+@pytest.mark.slow
+def test_vortex_residual_degree5_regular_meshes(degree5_regular_lattices):
+    """A different quantity from the paper's measure: the residual itself
+    against the exact dw/dt of the translating vortex, degree 5 on regular
+    diagonalised meshes.  Its rate is about 4 (3.42, then 3.77), and it is
+    about 4 with linear weights too, so the nonlinear weights are not what
+    holds it there.  The midpoint interpolation error is O(h^5) but depends
+    on each edge's direction and stencil, so it is not the normal component
+    of one smooth flux; the least-squares weights scale as 1/h and turn it
+    into an O(h^4) residual error.  One step at a fixed CFL multiplies that
+    error by dt ~ h, which is why the one-step measure approaches 5."""
+    errs, hs = [], []
+    d = 1e-5
+    for h, m, om in degree5_regular_lattices:
+        w0 = inputs.isentropic_vortex(m.xy)
         ex = (inputs.isentropic_vortex(m.xy, t=d) - inputs.isentropic_vortex(m.xy, t=-d)) / (2 * d)
-        om = oracle.OracleMesh(m.xy, m.tri, 10.0, 10.0, degree=5)
         errs.append(np.mean(np.abs(om.residual(w0)[:, 0] - ex[:, 0])))
-        hs.append(10.0 / n)
+        hs.append(h)
     assert math.log(errs[1] / errs[2]) / math.log(2) > 3.5
     assert errs[2] < 3e-6

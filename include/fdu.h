@@ -248,8 +248,13 @@ fdu_status fdu_batch_set_dt(fdu_mesh *batch, const double *dt, void *stream);
 /* n_steps SSP-RK3 steps of every mesh (FP64 state accumulation; the
  * residual at `precision`, 64, 48 or 32 as for fdu_residual; precision 48
  * runs a kernel of its own with its double-word staging in dynamic shared
- * memory).  FDU_ERR_TIMEOUT if a grid barrier's bounded wait ran out (the
- * state is then not advanced past that stage). */
+ * memory).  FDU_ERR_TIMEOUT if a grid barrier's bounded wait ran out.  The
+ * batch's state is then undefined: blocks that were still waiting may have
+ * given up while the others went on with their part of that stage.  Every
+ * later launch of the call finds the error flag set and returns without
+ * work or arrival, so no later barrier can release on the count the failed
+ * one left; the library resets the barrier before returning.  Set the
+ * state again (fdu_set_state) before the next step. */
 fdu_status fdu_batch_rk_steps(fdu_mesh *batch, int precision, int n_steps, void *stream);
 /* Persistent launch shape: threads per block (128, 256 or 512) and
  * co-resident blocks per SM (1 .. the larger of the FP32 and FP64 stage
@@ -263,7 +268,9 @@ fdu_status fdu_batch_set_launch(fdu_mesh *batch, int threads, int blocks_per_sm)
 fdu_status fdu_batch_autotune(fdu_mesh *batch, int precision, int *threads, int *blocks_per_sm, double *ms_per_step);
 /* Failure-path check of the bounded grid barrier: launches one persistent
  * stage whose barrier waits for one block more than the grid holds, so
- * every block's bounded wait runs out; *status gets the resulting status
+ * every block's bounded wait runs out, then one ordinary RK3 step (three
+ * persistent launches) before the error is read: those launches must find
+ * the flag set and do nothing.  *status gets the resulting status
  * (FDU_ERR_TIMEOUT expected) and the state is left unchanged.  No GPU fault
  * or hang is involved: the wait is bounded and the kernel returns. */
 fdu_status fdu_batch_barrier_selftest(fdu_mesh *batch, int *status);
@@ -338,11 +345,16 @@ fdu_status fdu_profile_read(fdu_mesh *mesh, int kernel, int precision, double *t
  * Limit: nv <= FDU_NOALLOC_MAX_VERTICES and active edges <=
  * FDU_NOALLOC_MAX_EDGES, otherwise FDU_ERR_ARG.  The array takes
  * 12.6 MB on every GPU that loads the library, for the life of the
- * process.  The first call on each device looks up the array's device
- * address with that device current.  Every call uses the same array, which
- * keeps the last call's contents: calls whose work overlaps on the GPU
- * (on different streams or for different meshes) race on it and must be
- * serialised by the caller.  The mesh's fallback counter still counts. */
+ * process.  Each call looks up the array's device address with the mesh's
+ * device current (a lookup in the already loaded module, no allocation),
+ * so a context torn down and created again is followed.  A null stream is
+ * the legacy default stream (cudaStreamLegacy), not the mesh's own stream,
+ * so calls a caller issues one after the other from one thread with a
+ * null stream are ordered even when they are for different meshes.  Every
+ * call uses the same array, which keeps the last call's contents: calls
+ * whose work overlaps on the GPU (on different non-null streams, or from
+ * different threads) race on it and must be serialised by the caller.
+ * The mesh's fallback counter still counts. */
 #define FDU_NOALLOC_MAX_VERTICES 65536
 #define FDU_NOALLOC_MAX_EDGES 196608
 fdu_status fdu_residual_noalloc(const fdu_mesh *mesh, const double *w, double *dwdt, void *stream);

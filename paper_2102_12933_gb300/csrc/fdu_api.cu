@@ -6,7 +6,6 @@
 #include <cmath>
 #include <cstring>
 #include <map>
-#include <mutex>
 #include <new>
 #include <tuple>
 #include <string>
@@ -789,22 +788,16 @@ constexpr int64_t kNoallocDoubles = 4 * (int64_t)FDU_NOALLOC_MAX_VERTICES + 8 * 
                                     4 * (int64_t)FDU_NOALLOC_MAX_EDGES;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double *g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once per device).
-fdu_status noalloc_scratch(int device, double **out) {
-    if (device < 0 || device >= kMaxDevices) return set_err(FDU_ERR_ARG, "device ordinal out of range");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess)
-            return set_err(FDU_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-        g_noalloc_ptr[device] = static_cast<double *>(p);
-    }
-    *out = g_noalloc_ptr[device];
+// Device address of the scratch array on the current device.  Looked up on
+// every call: the lookup reads the loaded module's symbol table and
+// allocates nothing, and it follows a context that was reset and created
+// again (a cached address would then be stale).
+fdu_status noalloc_scratch(double **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+        return set_err(FDU_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    *out = static_cast<double *>(p);
     return FDU_OK;
 }
 }  // namespace
@@ -1488,6 +1481,13 @@ fdu_status fdu_batch_barrier_selftest(fdu_mesh *m, int *status) {
     const int nb = std::min(m->pl_blocks, persistent_blocks_per_sm(32, m->pl_threads) * sms);
     CK(launch_stage_persistent(32, 1, ea, a, m->bar, m->bar + 1, (unsigned)nb + 1, 20000, m->bar_err, m->pl_threads,
                                nb, s));
+    // an ordinary step enqueued behind the failed launch, before the error is
+    // read: each of its launches finds the flag set and returns at entry (it
+    // neither arrives on the count the failed barrier left nor writes the state)
+    const int keep_blocks = m->pl_blocks;
+    m->pl_blocks = nb;
+    CK(enqueue_step_persistent(m, 32, s, (unsigned)nb, kSpinLimit));
+    m->pl_blocks = keep_blocks;
     m->f32_valid = false;  // w32 may hold nothing else than the state, but be conservative
     *status = check_barrier(m, s);
     return FDU_OK;
@@ -1504,12 +1504,14 @@ fdu_status fdu_residual_noalloc(const fdu_mesh *mc, const double *w, double *dwd
                                         std::to_string(FDU_NOALLOC_MAX_VERTICES) + " and " +
                                         std::to_string(FDU_NOALLOC_MAX_EDGES));
     double *base = nullptr;
-    st = noalloc_scratch(m->device, &base);
+    st = noalloc_scratch(&base);  // need_device made the mesh's device current
     if (st) return st;
     double *wi = base;                                       // [MAX_V][4]
     double *F = base + 4 * (int64_t)FDU_NOALLOC_MAX_VERTICES;  // [MAX_V][8]
     double *r = F + 8 * (int64_t)FDU_NOALLOC_MAX_VERTICES;     // [MAX_E][4]
-    cudaStream_t s = m->stream(stream);
+    // a null stream is the legacy default stream (not the mesh's own), so
+    // serial calls with a null stream stay ordered across meshes
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : cudaStreamLegacy;
     // every scratch word read below is written first in this call; only the
     // ghost rows of the output must start at zero
     if (m->n_ghost > 0) CK(cudaMemsetAsync(dwdt, 0, 4 * m->nv * sizeof(double), s));

@@ -565,29 +565,37 @@ __global__ void __launch_bounds__(kDivBlock) div_f32_kernel(DivArgs A) {
 // Grid-wide barrier for a cooperative launch, with a bounded wait: thread 0
 // of each block arrives on *count; the last arrival resets it and advances
 // *gen; the others spin on *gen at most `limit` times (with a short sleep).
-// Returns false (and sets *err) if the wait ran out.
+// Returns false (and sets *err) if the wait ran out.  Once *err is set no
+// block arrives any more (a block finding it set at entry, or while it
+// waits, gives up), so a count left short by a timed-out barrier is never
+// completed by a later barrier of the same call; the host resets count,
+// gen and err before the next call.
 __device__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen, unsigned int nblocks,
                              unsigned long long limit, int *err) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        ok = 1;
-        const unsigned int g = *gen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(count, 1u);
-        if (arrived == nblocks - 1) {
-            *count = 0;
+        volatile int *verr = err;
+        ok = 0;
+        if (*verr == 0) {
+            ok = 1;
+            const unsigned int g = *gen;
             __threadfence();
-            atomicAdd((unsigned int *)gen, 1u);
-        } else {
-            unsigned long long it = 0;
-            while (*gen == g) {
-                if (++it > limit) {
-                    ok = 0;
-                    atomicExch(err, 1);
-                    break;
+            const unsigned int arrived = atomicAdd(count, 1u);
+            if (arrived == nblocks - 1) {
+                *count = 0;
+                __threadfence();
+                atomicAdd((unsigned int *)gen, 1u);
+            } else {
+                unsigned long long it = 0;
+                while (*gen == g) {
+                    if (*verr != 0 || ++it > limit) {
+                        ok = 0;
+                        atomicExch(err, 1);
+                        break;
+                    }
+                    __nanosleep(64);
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();
@@ -596,12 +604,23 @@ __device__ bool grid_barrier(unsigned int *count, volatile unsigned int *gen, un
     return ok != 0;
 }
 
+// A persistent launch after a timed-out barrier of the same call does no
+// work: its state would rest on a stage that did not complete.  Thread 0
+// reads the flag for its block, so the whole block takes the same branch.
+__device__ __forceinline__ bool barrier_failed(const int *err) {
+    __shared__ int failed;
+    if (threadIdx.x == 0) failed = *(const volatile int *)err;
+    __syncthreads();
+    return failed != 0;
+}
+
 // One SSP-RK3 stage over every mesh of a batch in one cooperative launch:
 // all edge fluxes, a grid barrier, then every vertex's divergence and stage
 // update (grid-stride loops; MODE = stage 1..3).
 template <int PREC, int MODE>
 __global__ void stage_persistent_kernel(EdgeArgs EA, DivArgs DA, unsigned int *bar_count, unsigned int *bar_gen,
                                         unsigned int nblocks_expected, unsigned long long spin_limit, int *err) {
+    if (barrier_failed(err)) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t e = t0; e < EA.ne; e += stride) {
@@ -623,6 +642,7 @@ template <int MODE>
 __global__ void __launch_bounds__(512, 1)
     stage_persistent_dw_kernel(EdgeArgs EA, DivArgs DA, unsigned int *bar_count, unsigned int *bar_gen,
                                unsigned int nblocks_expected, unsigned long long spin_limit, int *err) {
+    if (barrier_failed(err)) return;
     extern __shared__ float2 dw_stage[];
     const dwa::Stage T{dw_stage + threadIdx.x, (int)blockDim.x};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;

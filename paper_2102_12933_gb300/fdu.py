@@ -384,7 +384,13 @@ class Mesh:
     def residual_noalloc(self, w, out, stream=None):
         """FP64 residual of the device state `w` into the device tensor `out`
         (both [nv][4] float64, original vertex order) using the library's fixed
-        scratch array: no device memory is allocated by this call."""
+        scratch array: no device memory is allocated by this call.  With
+        stream=None the call goes to torch's current stream (a null handle,
+        torch's default stream, is the legacy default stream in the library),
+        so calls made one after the other from one thread are ordered, for
+        any mesh.  Every call shares the one scratch array: calls on different
+        streams, or from different threads, that overlap on the GPU race on it
+        and must be serialised by the caller."""
         pw, dw = _buffer(w, self.nv)
         po, do = _buffer(out, self.nv, writable=True)
         if not (dw and do):

@@ -6,9 +6,12 @@ array inside the library, so the call itself allocates nothing.
 
 Checked through the C-ABI against fdu_residual (the existing entry point)
 within the FP64 parity tolerance (1e-12 relative L2 per component), on two
-calls in a row with different states, and for the size limit.  This file
-is collected last so that a run stopping at the first failure has already
-run every other test.
+calls in a row with different states, on periodic meshes and on meshes with
+ghost layers (transmissive and Dirichlet: the call fills the ghost rows of
+its scratch state and returns ghost rows of exactly 0), for calls on two
+meshes issued one after the other with the default stream, and for the size
+limit.  This file is collected last so that a run stopping at the first
+failure has already run every other test.
 """
 import numpy as np
 import pytest
@@ -72,3 +75,57 @@ def test_noalloc_rejects_meshes_over_the_limit():
         M.residual_noalloc(w, out)
     assert e.value.status == -1
     assert "at most 65536" in str(e.value)
+
+
+def _ghost_mesh(kind):
+    if kind == "transmissive":
+        m, w0 = inputs.riemann_case(41, ghost_layers=5, seed=17)
+        return m, w0, fdu.Mesh(m.xy, m.tri, 0.0, 0.0, device=0, ghost_donor=m.ghost_donor)
+    m, w0 = inputs.shock_vortex_case(80)
+    return m, w0, fdu.Mesh(m.xy, m.tri, 0.0, 80.0, device=0, ghost_donor=m.ghost_donor)
+
+
+@pytest.mark.parametrize("kind", ["transmissive", "dirichlet"])
+def test_noalloc_matches_residual_on_ghost_layer_meshes(kind):
+    m, w0, M = _ghost_mesh(kind)
+    real = torch.tensor(m.ghost_donor < 0, device="cuda")
+    assert int((~real).sum()) > 0
+    w_a = torch.tensor(w0, device="cuda")
+    x = torch.tensor(m.xy, device="cuda")
+    w_b = w_a.clone()  # a second, different state (smooth relative change)
+    w_b[:, 3] *= 1.0 + 0.03 * torch.sin(0.7 * x[:, 0]) * torch.cos(0.3 * x[:, 1])
+    for w in (w_a, w_b):
+        M.set_state(w)
+        ref = torch.empty_like(w)
+        M.residual(64, out=ref)
+        got = torch.full_like(w, float("nan"))
+        M.residual_noalloc(w, got)
+        torch.cuda.synchronize()
+        for k in range(4):
+            assert _rel(got[real, k], ref[real, k]) <= 1e-12, (kind, k)
+        assert bool((got[~real] == 0).all()), kind
+
+
+def test_noalloc_serial_calls_on_two_meshes_are_ordered():
+    # two meshes, each large enough for its launches to overlap the other's
+    # if the two calls went to unordered streams; issued back to back with
+    # the default stream, they run in order and both results are right
+    cases = [inputs.vortex_case(200, seed=s) for s in (51, 52)]
+    Ms = [fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0) for m, _ in cases]
+    ws = [torch.tensor(w, device="cuda") for _, w in cases]
+    ws[1][:, 3] *= 1.02
+    refs = []
+    for M, w in zip(Ms, ws):
+        M.set_state(w)
+        r = torch.empty_like(w)
+        M.residual(64, out=r)
+        refs.append(r)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        outs = [torch.full_like(w, float("nan")) for w in ws]
+        for M, w, o in zip(Ms, ws, outs):
+            M.residual_noalloc(w, o)
+        torch.cuda.synchronize()
+        for o, r in zip(outs, refs):
+            for k in range(4):
+                assert _rel(o[:, k], r[:, k]) <= 1e-12

@@ -29,7 +29,7 @@ struct Prim64Bar {
     double r = 0, ir = 0, p = 0;
 };
 struct Roe64Bar {
-    double u = 0, v = 0, H = 0, c = 0, ic = 0, b1 = 0, qn = 0, qt = 0, hq2 = 0;
+    double u = 0, v = 0, H = 0, c = 0, b1h = 0, ich = 0, qn = 0, qt = 0, hq2 = 0;
 };
 
 __device__ __forceinline__ void add_to(dbl4 &a, const dbl4 &b) {
@@ -50,58 +50,52 @@ __device__ __forceinline__ void prim64_vjp(const dbl4 &w, const Prim64 &P, const
     wb.w += B.p * gm1;
 }
 
-// Roe average (a, b) -> R; accumulates into the primitives' cotangents and
-// the states' direct cotangents.
+// Roe average (a, b) -> R of roe64 (b1h = hgm1 ic^2, ich = ic / 2, c = c2 ic
+// with ic = c2^-1/2); accumulates into the primitives' cotangents and the
+// states' direct cotangents.  R.u = U inv, R.v = V inv, R.H = Hn inv with
+// inv = 1 / (sa + sb), so the cotangent of inv, ub U + vb V + Hb Hn, times
+// -inv^2 is -(ub u + vb v + Hb H) inv: the sums U, V, Hn and the reciprocal
+// are not formed again.
 __device__ __forceinline__ void roe64_vjp(const dbl4 &a, const Prim64 &pa, const dbl4 &b, const Prim64 &pb,
                                           const Roe64 &R, const Roe64Bar &Rb, double gm1, dbl4 &ab, Prim64Bar &pab,
                                           dbl4 &bb, Prim64Bar &pbb) {
     double ub = Rb.u + Rb.qn * R.nx - Rb.qt * R.ny;
     double vb = Rb.v + Rb.qn * R.ny + Rb.qt * R.nx;
-    const double icb = Rb.ic + Rb.b1 * gm1 * 2.0 * R.ic;
-    const double c2b = Rb.c * 0.5 * R.ic - icb * 0.5 * R.ic * R.ic * R.ic;
+    const double icb = fma(0.5, Rb.ich, gm1 * R.ic * Rb.b1h);  // d b1h / d ic = 2 hgm1 ic = gm1 ic
+    const double c2b = 0.5 * R.ic * fma(-icb, R.ic * R.ic, Rb.c);
     const double Hb = Rb.H + c2b * gm1;
     const double hq2b = Rb.hq2 - c2b * gm1;
     ub += hq2b * R.u;
     vb += hq2b * R.v;
-    const double sa = a.x * pa.r, sb = b.x * pb.r;
-    const double inv = recip64(sa + sb);
-    const double U = a.y * pa.r + b.y * pb.r;
-    const double V = a.z * pa.r + b.z * pb.r;
-    const double Hn = (a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r;
-    const double invb = ub * U + vb * V + Hb * Hn;
+    const double inv = R.inv;
     const double Ub = ub * inv, Vb = vb * inv, Hnb = Hb * inv;
-    const double sbar = -invb * inv * inv;
+    const double sbar = -(ub * R.u + vb * R.v + Hb * R.H) * inv;
     ab.x += sbar * pa.r;
-    pab.r += sbar * a.x;
     bb.x += sbar * pb.r;
-    pbb.r += sbar * b.x;
     ab.y += Ub * pa.r;
-    pab.r += Ub * a.y;
     bb.y += Ub * pb.r;
-    pbb.r += Ub * b.y;
     ab.z += Vb * pa.r;
-    pab.r += Vb * a.z;
     bb.z += Vb * pb.r;
-    pbb.r += Vb * b.z;
     ab.w += Hnb * pa.r;
     pab.p += Hnb * pa.r;
-    pab.r += Hnb * (a.w + pa.p);
     bb.w += Hnb * pb.r;
     pbb.p += Hnb * pb.r;
-    pbb.r += Hnb * (b.w + pb.p);
+    pab.r += sbar * a.x + Ub * a.y + Vb * a.z + Hnb * (a.w + pa.p);
+    pbb.r += sbar * b.x + Ub * b.y + Vb * b.z + Hnb * (b.w + pb.p);
 }
 
-// c = project64(R, d): accumulates d's and R's cotangents
+// c = project64(R, d) = (phh + psh, d.x - 2 phh, nx d.z - ny d.y - qt d.x,
+// phh - psh) with phh = b1h (hq2 d.x - u d.y - v d.z + d.w) and psh = ich
+// (qn d.x - nx d.y - ny d.z): accumulates d's and R's cotangents
 __device__ __forceinline__ void project64_vjp(const Roe64 &R, const dbl4 &d, const dbl4 &cb, dbl4 &db, Roe64Bar &Rb) {
-    const double phib = 0.5 * cb.x - cb.y + 0.5 * cb.w;
-    const double psib = 0.5 * cb.x - 0.5 * cb.w;
+    const double phhb = fma(-2.0, cb.y, cb.x + cb.w);
+    const double pshb = cb.x - cb.w;
     db.x += cb.y - R.qt * cb.z;
     db.y += -R.ny * cb.z;
     db.z += R.nx * cb.z;
     Rb.qt += -d.x * cb.z;
-    const double inner_phi = R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w;
-    Rb.b1 += phib * inner_phi;
-    const double t = phib * R.b1;
+    Rb.b1h += phhb * (R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w);
+    const double t = phhb * R.b1h;
     Rb.hq2 += t * d.x;
     Rb.u += -t * d.y;
     Rb.v += -t * d.z;
@@ -109,13 +103,12 @@ __device__ __forceinline__ void project64_vjp(const Roe64 &R, const dbl4 &d, con
     db.y += -t * R.u;
     db.z += -t * R.v;
     db.w += t;
-    const double inner_psi = R.qn * d.x - R.nx * d.y - R.ny * d.z;
-    Rb.ic += psib * inner_psi;
-    const double s = psib * R.ic;
-    Rb.qn += s * d.x;
-    db.x += s * R.qn;
-    db.y += -s * R.nx;
-    db.z += -s * R.ny;
+    Rb.ich += pshb * (R.qn * d.x - R.nx * d.y - R.ny * d.z);
+    const double u = pshb * R.ich;
+    Rb.qn += u * d.x;
+    db.x += u * R.qn;
+    db.y += -u * R.nx;
+    db.z += -u * R.ny;
 }
 
 // d = unproject64(R, c): accumulates c's and R's cotangents
@@ -138,31 +131,44 @@ __device__ __forceinline__ void unproject64_vjp(const Roe64 &R, const dbl4 &c, c
     cb.w += rhob + R.H * dbar.w + R.c * ddb;
 }
 
-// Reverse of weno_pair64 for one field: from (dlb, drb) to the cotangents of
-// the six differences (a..f), given the field's values and indicators W
-// from the forward pass (same reciprocals as weno_combine64).
-__device__ __forceinline__ void weno_pair64_vjp(const double *k, const WenoField &W, double a, double b, double c,
-                                                double d, double e, double f, double dlb, double drb, double &ab,
-                                                double &bb_, double &cb, double &db, double &eb, double &fb) {
-    const double C0 = k[20], C2 = k[21], D0 = k[22], D2 = k[23];  // C_1 = 1 on both sides
+// The R1-based combination of one field's values and indicators (the form
+// the reverse sweep differentiates; dl, dr as weno_combine64), keeping the
+// products and reciprocals the reverse sweep needs.
+struct WenoKeep {
+    double l0, l1, l2, iDL, dl, r0, r1, r2, iDR, dr;
+};
+__device__ __forceinline__ void weno_combine64_keep(const double *k, const WenoField &W, double c, WenoKeep &K) {
     const double bbc = W.bb * W.bc;
-    const double l0 = C0 * bbc, l1 = W.ba * W.bc, l2 = C2 * (W.ba * W.bb);
-    const double iDL = recip64_fast(l0 + l1 + l2);
-    const double dl = fma(l0, W.va, fma(l1, W.vb, l2 * W.vc)) * iDL;
-    const double r0 = D0 * bbc, r1 = W.bd * W.bb, r2 = D2 * (W.bd * W.bc);
-    const double iDR = recip64_fast(r0 + r1 + r2);
+    K.l0 = k[20] * bbc;
+    K.l1 = W.ba * W.bc;
+    K.l2 = k[21] * (W.ba * W.bb);
+    K.iDL = recip64_fast(K.l0 + K.l1 + K.l2);
+    K.dl = fma(K.l0, W.va, fma(K.l1, W.vb, K.l2 * W.vc)) * K.iDL;
+    K.r0 = k[22] * bbc;
+    K.r1 = W.bd * W.bb;
+    K.r2 = k[23] * (W.bd * W.bc);
+    K.iDR = recip64_fast(K.r0 + K.r1 + K.r2);
+    K.dr = fma(K.r0, W.vd, fma(K.r1, W.vc - c, K.r2 * (W.vb - c))) * K.iDR;
+}
+
+// Reverse of the combination for one field: from (dlb, drb) to the
+// cotangents of the six differences (a..f), given the field's values and
+// indicators W and the kept products K of the forward pass.
+__device__ __forceinline__ void weno_pair64_vjp(const double *k, const WenoField &W, const WenoKeep &K, double a,
+                                                double b, double c, double d, double e, double f, double dlb,
+                                                double drb, double &ab, double &bb_, double &cb, double &db,
+                                                double &eb, double &fb) {
+    const double C0 = k[20], C2 = k[21], D0 = k[22], D2 = k[23];  // C_1 = 1 on both sides
     const double vcr = W.vc - c, vbr = W.vb - c;
-    const double dr = fma(r0, W.vd, fma(r1, vcr, r2 * vbr)) * iDR;
-    // reverse
-    const double NLb = dlb * iDL, DLb = -dlb * dl * iDL;
-    const double NRb = drb * iDR, DRb = -drb * dr * iDR;
+    const double NLb = dlb * K.iDL, DLb = -NLb * K.dl;
+    const double NRb = drb * K.iDR, DRb = -NRb * K.dr;
     const double l0b = NLb * W.va + DLb, l1b = NLb * W.vb + DLb, l2b = NLb * W.vc + DLb;
     const double r0b = NRb * W.vd + DRb, r1b = NRb * vcr + DRb, r2b = NRb * vbr + DRb;
-    const double vab = NLb * l0;
-    const double vbb = NLb * l1 + NRb * r2;
-    const double vcb = NLb * l2 + NRb * r1;
-    const double vdb = NRb * r0;
-    const double cdir = -NRb * (r1 + r2);
+    const double vab = NLb * K.l0;
+    const double vbb = NLb * K.l1 + NRb * K.r2;
+    const double vcb = NLb * K.l2 + NRb * K.r1;
+    const double vdb = NRb * K.r0;
+    const double cdir = -NRb * (K.r1 + K.r2);
     const double bab = l1b * W.bc + l2b * C2 * W.bb;
     const double bbb = l0b * C0 * W.bc + l2b * C2 * W.ba + r0b * D0 * W.bc + r1b * W.bd;
     const double bcb = l0b * C0 * W.bb + l1b * W.ba + r0b * D0 * W.bb + r2b * D2 * W.bd;
@@ -227,13 +233,18 @@ __device__ __forceinline__ dbl4 vertex_flux_vjp(const dbl4 &w, double gm1, const
 }
 
 // Edge-flux VJP: recompute edge e's forward pass at state w, then reverse
-// from lam (cotangent of r_e) to the six stencil states; G[slot][e].
-__global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
+// from lam (cotangent of r_e) to the six stencil states; G[slot][e].  The
+// flux is reversed in the one-sided Roe form F_n(w_L) + R diag(nu) L (w_R -
+// w_L), nu = (lambda - |lambda|_fixed) / 2, which equals the symmetric form
+// (F_L + F_R)/2 - R |Lambda|_fixed L (w_R - w_L)/2 by Roe's property, so only
+// the left physical flux is differentiated.
+constexpr int kVjpBlock = 64;
+__global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= A.ne) return;
     const double *__restrict__ w = A.w;
     const double *__restrict__ coef = A.coef;
-    const double gm1 = A.gm1;
+    const double gm1 = A.gm1, hgm1 = 0.5 * A.gm1;
     const int64_t ne = A.ne;
     int32_t s[6];
 #pragma unroll
@@ -244,8 +255,8 @@ __global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
     const dbl4 lam = ld4(A.lam_r, e);
 
     // ---------------- forward
-    const Prim64 pL1 = prim64(L1, gm1), pR1 = prim64(R1, gm1);
-    const Roe64 C = roe64(L1, pL1, R1, pR1, nx, ny, gm1, 0.5 * gm1);
+    const Prim64 pL1 = prim64(L1, gm1, hgm1), pR1 = prim64(R1, gm1, hgm1);
+    const Roe64 C = roe64(L1, pL1, R1, pR1, nx, ny, gm1, hgm1);
     const dbl4 dM = sub4(R1, L1), dL2 = sub4(W1, L1), dL3 = sub4(W0, L1), dR2 = sub4(W4, R1), dR3 = sub4(W5, R1);
     const dbl4 cM = project64(C, dM), cL2 = project64(C, dL2), cL3 = project64(C, dL3), cR2 = project64(C, dR2),
                cR3 = project64(C, dR3);
@@ -253,43 +264,58 @@ __global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
     double k[kCoefN];
 #pragma unroll
     for (int i = 0; i < kCoefN; ++i) k[i] = __ldg(coef + (int64_t)i * ne + e);
-    // each field's sub-stencil values and indicators, kept in shared memory
-    // (thread-private column) for the reverse sweep
-    __shared__ double wsm[4 * 8][128];
+    // each field's sub-stencil values and indicators and the combination's
+    // products, kept in shared memory (thread-private column) for the
+    // reverse sweep
+    __shared__ double wsm[4 * 18][kVjpBlock];
     const int t = threadIdx.x;
-    auto keep = [&](int fi, const WenoField &W) {
-        wsm[fi * 8 + 0][t] = W.va; wsm[fi * 8 + 1][t] = W.vb; wsm[fi * 8 + 2][t] = W.vc; wsm[fi * 8 + 3][t] = W.vd;
-        wsm[fi * 8 + 4][t] = W.ba; wsm[fi * 8 + 5][t] = W.bb; wsm[fi * 8 + 6][t] = W.bc; wsm[fi * 8 + 7][t] = W.bd;
+    auto keep = [&](int fi, const WenoField &W, const WenoKeep &K) {
+        double *q = &wsm[fi * 18][t];
+        const double v[18] = {W.va, W.vb, W.vc, W.vd, W.ba, W.bb, W.bc, W.bd, K.l0,
+                              K.l1, K.l2, K.iDL, K.dl, K.r0, K.r1, K.r2, K.iDR, K.dr};
+#pragma unroll
+        for (int i = 0; i < 18; ++i) q[i * kVjpBlock] = v[i];
     };
-    auto kept = [&](int fi) {
-        WenoField W;
-        W.va = wsm[fi * 8 + 0][t]; W.vb = wsm[fi * 8 + 1][t]; W.vc = wsm[fi * 8 + 2][t]; W.vd = wsm[fi * 8 + 3][t];
-        W.ba = wsm[fi * 8 + 4][t]; W.bb = wsm[fi * 8 + 5][t]; W.bc = wsm[fi * 8 + 6][t]; W.bd = wsm[fi * 8 + 7][t];
-        return W;
+    auto kept = [&](int fi, WenoField &W, WenoKeep &K) {
+        const double *q = &wsm[fi * 18][t];
+        W.va = q[0 * kVjpBlock]; W.vb = q[1 * kVjpBlock]; W.vc = q[2 * kVjpBlock]; W.vd = q[3 * kVjpBlock];
+        W.ba = q[4 * kVjpBlock]; W.bb = q[5 * kVjpBlock]; W.bc = q[6 * kVjpBlock]; W.bd = q[7 * kVjpBlock];
+        K.l0 = q[8 * kVjpBlock]; K.l1 = q[9 * kVjpBlock]; K.l2 = q[10 * kVjpBlock]; K.iDL = q[11 * kVjpBlock];
+        K.dl = q[12 * kVjpBlock]; K.r0 = q[13 * kVjpBlock]; K.r1 = q[14 * kVjpBlock]; K.r2 = q[15 * kVjpBlock];
+        K.iDR = q[16 * kVjpBlock]; K.dr = q[17 * kVjpBlock];
     };
     dbl4 dl, dr;
     {
+        WenoKeep K;
         WenoField W = weno_field64(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps);
-        keep(0, W);
-        weno_combine64(k, W, cM.x, dl.x, dr.x);
+        weno_combine64_keep(k, W, cM.x, K);
+        keep(0, W, K);
+        dl.x = K.dl;
+        dr.x = K.dr;
         W = weno_field64(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps);
-        keep(1, W);
-        weno_combine64(k, W, cM.y, dl.y, dr.y);
+        weno_combine64_keep(k, W, cM.y, K);
+        keep(1, W, K);
+        dl.y = K.dl;
+        dr.y = K.dr;
         W = weno_field64(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps);
-        keep(2, W);
-        weno_combine64(k, W, cM.z, dl.z, dr.z);
+        weno_combine64_keep(k, W, cM.z, K);
+        keep(2, W, K);
+        dl.z = K.dl;
+        dr.z = K.dr;
         W = weno_field64(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps);
-        keep(3, W);
-        weno_combine64(k, W, cM.w, dl.w, dr.w);
+        weno_combine64_keep(k, W, cM.w, K);
+        keep(3, W, K);
+        dl.w = K.dl;
+        dr.w = K.dr;
     }
-    dbl4 wl = add4(L1, unproject64(C, dl));
-    dbl4 wr = add4(R1, unproject64(C, dr));
+    dbl4 wl = unproject_add64(C, dl, L1);
+    dbl4 wr = unproject_add64(C, dr, R1);
     Prim64 pl, pr;
-    bool ok = wl.x > 0.0 && wr.x > 0.0;
+    bool ok = pos64(wl.x) && pos64(wr.x);
     if (ok) {
-        pl = prim64(wl, gm1);
-        pr = prim64(wr, gm1);
-        ok = pl.p > 0.0 && pr.p > 0.0;
+        pl = prim64(wl, gm1, hgm1);
+        pr = prim64(wr, gm1, hgm1);
+        ok = pos64(pl.p) && pos64(pr.p);
     }
     if (!ok) {
         wl = L1;
@@ -297,43 +323,49 @@ __global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
         pl = pL1;
         pr = pR1;
     }
-    const Roe64 Q = roe64(wl, pl, wr, pr, nx, ny, gm1, 0.5 * gm1);
+    const Roe64 Q = roe64(wl, pl, wr, pr, nx, ny, gm1, hgm1);
     const dbl4 dw = sub4(wr, wl);
     const dbl4 a = project64(Q, dw);
-    const double delta = 0.1 * Q.c;
-    const double l_u = Q.qn, l_m = Q.qn - Q.c, l_p = Q.qn + Q.c;
-    auto fixv = [&](double l) { return fabs(l) < delta ? (l * l + delta * delta) * (5.0 * Q.ic) : fabs(l); };
-    const double lu = fixv(l_u), lm = fixv(l_m), lp = fixv(l_p);
-    const dbl4 sv = dbl4_make(lm * a.x, lu * a.y, lu * a.z, lp * a.w);
-
-    // ---------------- reverse
-    const dbl4 Db = dbl4_make(-0.5 * lam.x, -0.5 * lam.y, -0.5 * lam.z, -0.5 * lam.w);
-    const dbl4 Fb = dbl4_make(0.5 * lam.x, 0.5 * lam.y, 0.5 * lam.z, 0.5 * lam.w);
-    dbl4 wlb = dbl4_make(0, 0, 0, 0), wrb = dbl4_make(0, 0, 0, 0);
-    Prim64Bar plb, prb;
-    fluxn_vjp(wl, pl, nx, ny, Fb, wlb, plb);
-    fluxn_vjp(wr, pr, nx, ny, Fb, wrb, prb);
-    Roe64Bar Qb;
-    dbl4 svb = dbl4_make(0, 0, 0, 0);
-    unproject64_vjp(Q, sv, Db, svb, Qb);
-    dbl4 ab = dbl4_make(lm * svb.x, lu * svb.y, lu * svb.z, lp * svb.w);
-    const double lmb = a.x * svb.x, lub = a.y * svb.y + a.z * svb.z, lpb = a.w * svb.w;
-    // entropy fix: |l| or (l^2 + delta^2) / (2 delta), delta = 0.1 c
-    double deltab = 0.0;
-    auto fix_vjp = [&](double l, double fb, double &lb) {
-        if (fabs(l) < delta) {
-            lb += fb * l / delta;
-            deltab += fb * (0.5 - 0.5 * l * l / (delta * delta));
+    // nu = (l - |l|_fixed) / 2: -(l - delta)^2 / (4 delta) inside Harten's
+    // band |l| < delta = 0.1 c (decided on the integer pipe, as the forward
+    // kernel does), min(l, 0) outside; with the derivatives d nu / d l and
+    // d nu / d delta = (l^2 - delta^2) / (4 delta^2) (0 outside the band)
+    const double delta = 0.1 * Q.c, h4d = 2.5 * Q.ic;  // 1 / (4 delta)
+    const unsigned long long dbits = (unsigned long long)__double_as_longlong(delta);
+    auto wave = [&](double l, double &nu, double &dnu_l, double &dnu_d) {
+        const long long b = __double_as_longlong(l);
+        const unsigned long long ab_ = (unsigned long long)b & 0x7FFFFFFFFFFFFFFFULL;
+        if (ab_ < dbits) {
+            const double sd = l - delta;
+            nu = -(sd * sd) * h4d;
+            dnu_l = -2.0 * sd * h4d;
+            dnu_d = sd * (l + delta) * (10.0 * Q.ic) * h4d;
         } else {
-            lb += fb * (l >= 0.0 ? 1.0 : -1.0);
+            const bool neg = b < 0 || ab_ > 0x7FF0000000000000ULL;
+            nu = neg ? l : 0.0;
+            dnu_l = neg ? 1.0 : 0.0;
+            dnu_d = 0.0;
         }
     };
-    double lub_ = 0, lmb_ = 0, lpb_ = 0;
-    fix_vjp(l_u, lub, lub_);
-    fix_vjp(l_m, lmb, lmb_);
-    fix_vjp(l_p, lpb, lpb_);
-    Qb.qn += lub_ + lmb_ + lpb_;
-    Qb.c += -lmb_ + lpb_ + 0.1 * deltab;
+    double nu_u, nu_m, nu_p, gu, gm, gp, hu, hm, hp;
+    wave(Q.qn, nu_u, gu, hu);
+    wave(Q.qn - Q.c, nu_m, gm, hm);
+    wave(Q.qn + Q.c, nu_p, gp, hp);
+    const dbl4 sv = dbl4_make(nu_m * a.x, nu_u * a.y, nu_u * a.z, nu_p * a.w);
+
+    // ---------------- reverse
+    dbl4 wlb = dbl4_make(0, 0, 0, 0), wrb = dbl4_make(0, 0, 0, 0);
+    Prim64Bar plb, prb;
+    fluxn_vjp(wl, pl, nx, ny, lam, wlb, plb);
+    Roe64Bar Qb;
+    dbl4 svb = dbl4_make(0, 0, 0, 0);
+    unproject64_vjp(Q, sv, lam, svb, Qb);
+    const dbl4 ab = dbl4_make(nu_m * svb.x, nu_u * svb.y, nu_u * svb.z, nu_p * svb.w);
+    const double nmb = a.x * svb.x, nub = a.y * svb.y + a.z * svb.z, npb = a.w * svb.w;
+    const double lub = nub * gu, lmb = nmb * gm, lpb = npb * gp;
+    const double deltab = nub * hu + nmb * hm + npb * hp;
+    Qb.qn += lub + lmb + lpb;
+    Qb.c += lpb - lmb + 0.1 * deltab;
     dbl4 dwb = dbl4_make(0, 0, 0, 0);
     project64_vjp(Q, dw, ab, dwb, Qb);
     add_to(wrb, dwb);
@@ -342,25 +374,26 @@ __global__ void __launch_bounds__(128) edge_flux_vjp_kernel(AdjEdgeArgs A) {
     prim64_vjp(wl, pl, plb, gm1, wlb);
     prim64_vjp(wr, pr, prb, gm1, wrb);
 
-    dbl4 G0 = dbl4_make(0, 0, 0, 0), G1 = G0, GL1 = G0, GR1 = G0, G4 = G0, G5 = G0;
-    if (!ok) {
-        GL1 = wlb;
-        GR1 = wrb;
-    } else {
-        GL1 = wlb;
-        GR1 = wrb;
+    dbl4 G0 = dbl4_make(0, 0, 0, 0), G1 = G0, GL1 = wlb, GR1 = wrb, G4 = G0, G5 = G0;
+    if (ok) {
         Roe64Bar Cb;
         dbl4 dlb = dbl4_make(0, 0, 0, 0), drb = dbl4_make(0, 0, 0, 0);
         unproject64_vjp(C, dl, wlb, dlb, Cb);
         unproject64_vjp(C, dr, wrb, drb, Cb);
         dbl4 cL3b, cL2b, cMb, cR2Lb, cR3b, cR2b;
-        weno_pair64_vjp(k, kept(0), cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, dlb.x, drb.x, cL3b.x, cL2b.x, cMb.x,
+        WenoField W;
+        WenoKeep K;
+        kept(0, W, K);
+        weno_pair64_vjp(k, W, K, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, dlb.x, drb.x, cL3b.x, cL2b.x, cMb.x,
                         cR2Lb.x, cR3b.x, cR2b.x);
-        weno_pair64_vjp(k, kept(1), cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, dlb.y, drb.y, cL3b.y, cL2b.y, cMb.y,
+        kept(1, W, K);
+        weno_pair64_vjp(k, W, K, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, dlb.y, drb.y, cL3b.y, cL2b.y, cMb.y,
                         cR2Lb.y, cR3b.y, cR2b.y);
-        weno_pair64_vjp(k, kept(2), cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, dlb.z, drb.z, cL3b.z, cL2b.z, cMb.z,
+        kept(2, W, K);
+        weno_pair64_vjp(k, W, K, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, dlb.z, drb.z, cL3b.z, cL2b.z, cMb.z,
                         cR2Lb.z, cR3b.z, cR2b.z);
-        weno_pair64_vjp(k, kept(3), cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, dlb.w, drb.w, cL3b.w, cL2b.w, cMb.w,
+        kept(3, W, K);
+        weno_pair64_vjp(k, W, K, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, dlb.w, drb.w, cL3b.w, cL2b.w, cMb.w,
                         cR2Lb.w, cR3b.w, cR2b.w);
         add_to(cR2b, cR2Lb);
         add_to(cMb, cR2Lb);
@@ -477,7 +510,7 @@ void launch_residual_vjp(const AdjEdgeArgs &ea, const AdjTables &t, const AdjVer
     if (ea.ne > 0) {
         adj_edge_lambda_kernel<<<nblk(ea.ne, 256), 256, 0, s>>>(t.eoff, t.evid, t.ewt, va.lam, ea.lam_r_mut, ea.ne);
         if (ea.prec == 48) launch_edge_flux_vjp_dw(ea, s);
-        else edge_flux_vjp_kernel<<<nblk(ea.ne, 128), 128, 0, s>>>(ea);
+        else edge_flux_vjp_kernel<<<nblk(ea.ne, kVjpBlock), kVjpBlock, 0, s>>>(ea);
     }
     if (va.nv > 0) adj_vertex_kernel<<<nblk(va.nv, 256), 256, 0, s>>>(va);
 }

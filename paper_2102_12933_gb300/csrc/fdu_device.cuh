@@ -106,12 +106,14 @@ __device__ __forceinline__ Prim64 prim64(const dbl4 &w, double gm1, double hgm1)
 struct Roe64 {
     double u, v, H, c, ic, b1, qn, qt, hq2, nx, ny;
     double b1h, ich;  // b1 / 2 and ic / 2, the factors project64 applies
+    double inv;       // 1 / (sum of the sides' sqrt(rho)), kept for the adjoint
 };
 // Roe average from the two sides' records (same result as roe64).
 __device__ __forceinline__ Roe64 roe64_from_records(const dbl4 &qa, const dbl4 &qb, double nx, double ny, double gm1,
                                                     double hgm1) {
     Roe64 R;
     const double inv = recip64(qa.x + qb.x);
+    R.inv = inv;
     R.u = (qa.y + qb.y) * inv;
     R.v = (qa.z + qb.z) * inv;
     R.H = (qa.w + qb.w) * inv;
@@ -135,6 +137,7 @@ __device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const db
     Roe64 R;
     const double sa = a.x * pa.r, sb = b.x * pb.r;
     const double inv = recip64(sa + sb);
+    R.inv = inv;
     R.u = (a.y * pa.r + b.y * pb.r) * inv;
     R.v = (a.z * pa.r + b.z * pb.r) * inv;
     R.H = ((a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r) * inv;

@@ -203,7 +203,7 @@ __device__ __forceinline__ void fluxn_vjp(const dbl4 &w, const Prim64 &P, double
 
 // (df/dw)^T fb + (dg/dw)^T gb at state w
 __device__ __forceinline__ dbl4 vertex_flux_vjp(const dbl4 &w, double gm1, const dbl4 &fb, const dbl4 &gb) {
-    const double ir = 1.0 / w.x;
+    const double ir = recip64(w.x);  // within 2 ulp of 1 / rho, without the FP64 division sequence
     const double u = w.y * ir, v = w.z * ir;
     const double p = gm1 * (w.w - 0.5 * (w.y * u + w.z * v));
     dbl4 wb = dbl4_make(0, 0, 0, 0);

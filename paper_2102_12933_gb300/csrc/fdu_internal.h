@@ -34,7 +34,10 @@ constexpr int kCoefCL = 20;
 constexpr int kCoefCR = 22;
 constexpr int kCoefN = 24;
 constexpr int kEdgeCoef = 26;
-constexpr int kEdgeCoef32 = 28;  // FP32 copy padded to seven float4 per edge
+// FP32 copy: values 0..23 as six float4 per edge ([6][ne] float4), then
+// (n_x, n_y) as one float2 per edge ([ne] float2): 104 bytes, no padding
+constexpr int kEdgeCoef32 = 26;
+constexpr int kEdgeCoef32Vec = 6;  // float4 blocks before the normals
 
 struct HostTables {
     int64_t nv = 0, nt = 0, ne = 0, n_real = 0;

@@ -368,16 +368,22 @@ __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int6
     int32_t s[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
-    // coefficient block as 7 float4 per edge: [c/4][ne] float4, component c%4
+    // coefficient block: six float4 per edge ([c/4][ne] float4, component
+    // c%4) and the normal as one float2 ([ne] float2 after them)
     const float4 *__restrict__ g4 = reinterpret_cast<const float4 *>(g);
     float k[kEdgeCoef32];
 #pragma unroll
-    for (int i = 0; i < kEdgeCoef32 / 4; ++i) {
+    for (int i = 0; i < kEdgeCoef32Vec; ++i) {
         const float4 q = __ldg(g4 + (int64_t)i * ne + e);
         k[4 * i] = q.x;
         k[4 * i + 1] = q.y;
         k[4 * i + 2] = q.z;
         k[4 * i + 3] = q.w;
+    }
+    {
+        const float2 q = __ldg(reinterpret_cast<const float2 *>(g + (int64_t)4 * kEdgeCoef32Vec * ne) + e);
+        k[kCoefN] = q.x;
+        k[kCoefN + 1] = q.y;
     }
     const float nx = k[kCoefN], ny = k[kCoefN + 1];
     const float4 L1 = __ldg(w + s[2]), R1 = __ldg(w + s[3]);

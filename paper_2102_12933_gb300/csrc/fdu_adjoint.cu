@@ -28,8 +28,14 @@ using namespace dev;
 struct Prim64Bar {
     double r = 0, ir = 0, p = 0;
 };
+// Cotangents of a Roe64.  The projections' parts through b1h and ich are
+// kept as the raw sums sphi = sum phh_bar (c.x + c.w) and spsi = sum psh_bar
+// (c.x - c.w) of the projected values c (c.x + c.w = 2 phh, c.x - c.w = 2 psh),
+// which roe64_vjp turns into the cotangent of ic: with b1h = hgm1 ic^2 and
+// ich = ic / 2, sum phh_bar phh / b1h * d b1h / d ic = c sphi and sum psh_bar
+// psh / ich * d ich / d ic = c spsi / 2.
 struct Roe64Bar {
-    double u = 0, v = 0, H = 0, c = 0, b1h = 0, ich = 0, qn = 0, qt = 0, hq2 = 0;
+    double u = 0, v = 0, H = 0, c = 0, qn = 0, qt = 0, hq2 = 0, sphi = 0, spsi = 0;
 };
 
 __device__ __forceinline__ void add_to(dbl4 &a, const dbl4 &b) {
@@ -39,15 +45,16 @@ __device__ __forceinline__ void add_to(dbl4 &a, const dbl4 &b) {
     a.w += b.w;
 }
 
-// w -> (r = rho^-1/2, ir = 1/rho, p)
+// w -> (r = rho^-1/2, ir = 1/rho = r^2, p = (gamma - 1) E - (gamma - 1)/2 |m|^2 ir)
 __device__ __forceinline__ void prim64_vjp(const dbl4 &w, const Prim64 &P, const Prim64Bar &B, double gm1, dbl4 &wb) {
-    const double ke2 = w.y * w.y + w.z * w.z;
-    const double irb = B.ir - B.p * gm1 * 0.5 * ke2;
-    const double rb = B.r + irb * 2.0 * P.r;
-    wb.x += rb * (-0.5 * P.r * P.r * P.r);
-    wb.y += -B.p * gm1 * w.y * P.ir;
-    wb.z += -B.p * gm1 * w.z * P.ir;
-    wb.w += B.p * gm1;
+    const double pg = B.p * gm1;
+    const double irb = fma(-0.5 * pg, fma(w.y, w.y, w.z * w.z), B.ir);
+    const double rb = fma(2.0 * P.r, irb, B.r);
+    wb.x = fma(rb, -0.5 * P.ir * P.r, wb.x);  // d r / d rho = -r^3 / 2
+    const double t = pg * P.ir;
+    wb.y = fma(-t, w.y, wb.y);
+    wb.z = fma(-t, w.z, wb.z);
+    wb.w += pg;
 }
 
 // Roe average (a, b) -> R of roe64 (b1h = hgm1 ic^2, ich = ic / 2, c = c2 ic
@@ -61,7 +68,7 @@ __device__ __forceinline__ void roe64_vjp(const dbl4 &a, const Prim64 &pa, const
                                           dbl4 &bb, Prim64Bar &pbb) {
     double ub = Rb.u + Rb.qn * R.nx - Rb.qt * R.ny;
     double vb = Rb.v + Rb.qn * R.ny + Rb.qt * R.nx;
-    const double icb = fma(0.5, Rb.ich, gm1 * R.ic * Rb.b1h);  // d b1h / d ic = 2 hgm1 ic = gm1 ic
+    const double icb = R.c * fma(0.5, Rb.spsi, Rb.sphi);
     const double c2b = 0.5 * R.ic * fma(-icb, R.ic * R.ic, Rb.c);
     const double Hb = Rb.H + c2b * gm1;
     const double hq2b = Rb.hq2 - c2b * gm1;
@@ -86,15 +93,17 @@ __device__ __forceinline__ void roe64_vjp(const dbl4 &a, const Prim64 &pa, const
 
 // c = project64(R, d) = (phh + psh, d.x - 2 phh, nx d.z - ny d.y - qt d.x,
 // phh - psh) with phh = b1h (hq2 d.x - u d.y - v d.z + d.w) and psh = ich
-// (qn d.x - nx d.y - ny d.z): accumulates d's and R's cotangents
-__device__ __forceinline__ void project64_vjp(const Roe64 &R, const dbl4 &d, const dbl4 &cb, dbl4 &db, Roe64Bar &Rb) {
+// (qn d.x - nx d.y - ny d.z): accumulates d's and R's cotangents, given the
+// forward's c (for the parts through b1h and ich, Roe64Bar)
+__device__ __forceinline__ void project64_vjp(const Roe64 &R, const dbl4 &d, const dbl4 &c, const dbl4 &cb, dbl4 &db,
+                                              Roe64Bar &Rb) {
     const double phhb = fma(-2.0, cb.y, cb.x + cb.w);
     const double pshb = cb.x - cb.w;
     db.x += cb.y - R.qt * cb.z;
     db.y += -R.ny * cb.z;
     db.z += R.nx * cb.z;
     Rb.qt += -d.x * cb.z;
-    Rb.b1h += phhb * (R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w);
+    Rb.sphi = fma(phhb, c.x + c.w, Rb.sphi);
     const double t = phhb * R.b1h;
     Rb.hq2 += t * d.x;
     Rb.u += -t * d.y;
@@ -103,7 +112,7 @@ __device__ __forceinline__ void project64_vjp(const Roe64 &R, const dbl4 &d, con
     db.y += -t * R.u;
     db.z += -t * R.v;
     db.w += t;
-    Rb.ich += pshb * (R.qn * d.x - R.nx * d.y - R.ny * d.z);
+    Rb.spsi = fma(pshb, c.x - c.w, Rb.spsi);
     const double u = pshb * R.ich;
     Rb.qn += u * d.x;
     db.x += u * R.qn;
@@ -131,6 +140,31 @@ __device__ __forceinline__ void unproject64_vjp(const Roe64 &R, const dbl4 &c, c
     cb.w += rhob + R.H * dbar.w + R.c * ddb;
 }
 
+// weno_field64 (the same arithmetic) with the inner Horner terms of the four
+// indicators: h_a = m0 a + m1 b of S_a and likewise h_b, h_c (of d and c),
+// h_d; the reverse sweep takes the indicators' slopes as h + m0 x.
+struct WenoHorner {
+    double ha, hb, hc, hd;
+};
+__device__ __forceinline__ WenoField weno_field64_h(const double *k, double a, double b, double c, double d, double e,
+                                                   double f, double eps, WenoHorner &H) {
+    WenoField W;
+    const double b2 = b * b, c2 = c * c;
+    W.va = fma(k[0], a, k[1] * b);
+    W.vb = fma(k[5], b, k[6] * c);
+    W.vc = fma(k[10], c, k[11] * d);
+    W.vd = fma(k[15], e, k[16] * f);
+    H.ha = fma(k[2], a, k[3] * b);
+    H.hb = fma(k[7], b, k[8] * c);
+    H.hc = fma(k[14], d, k[13] * c);
+    H.hd = fma(k[17], e, k[18] * f);
+    W.ba = fma(a, H.ha, fma(k[4], b2, eps));
+    W.bb = fma(b, H.hb, fma(k[9], c2, eps));
+    W.bc = fma(d, H.hc, fma(k[12], c2, eps));
+    W.bd = fma(e, H.hd, fma(k[19], f * f, eps));
+    return W;
+}
+
 // The R1-based combination of one field's values and indicators (the form
 // the reverse sweep differentiates; dl, dr as weno_combine64), keeping the
 // products and reciprocals the reverse sweep needs.
@@ -154,10 +188,10 @@ __device__ __forceinline__ void weno_combine64_keep(const double *k, const WenoF
 // Reverse of the combination for one field: from (dlb, drb) to the
 // cotangents of the six differences (a..f), given the field's values and
 // indicators W and the kept products K of the forward pass.
-__device__ __forceinline__ void weno_pair64_vjp(const double *k, const WenoField &W, const WenoKeep &K, double a,
-                                                double b, double c, double d, double e, double f, double dlb,
-                                                double drb, double &ab, double &bb_, double &cb, double &db,
-                                                double &eb, double &fb) {
+__device__ __forceinline__ void weno_pair64_vjp(const double *k, const WenoField &W, const WenoKeep &K,
+                                                const WenoHorner &H, double a, double b, double c, double d, double e,
+                                                double f, double dlb, double drb, double &ab, double &bb_, double &cb,
+                                                double &db, double &eb, double &fb) {
     const double C0 = k[20], C2 = k[21], D0 = k[22], D2 = k[23];  // C_1 = 1 on both sides
     const double vcr = W.vc - c, vbr = W.vb - c;
     const double NLb = dlb * K.iDL, DLb = -NLb * K.dl;
@@ -169,16 +203,19 @@ __device__ __forceinline__ void weno_pair64_vjp(const double *k, const WenoField
     const double vcb = NLb * K.l2 + NRb * K.r1;
     const double vdb = NRb * K.r0;
     const double cdir = -NRb * (K.r1 + K.r2);
-    const double bab = l1b * W.bc + l2b * C2 * W.bb;
-    const double bbb = l0b * C0 * W.bc + l2b * C2 * W.ba + r0b * D0 * W.bc + r1b * W.bd;
-    const double bcb = l0b * C0 * W.bb + l1b * W.ba + r0b * D0 * W.bb + r2b * D2 * W.bd;
-    const double bdb = r1b * W.bb + r2b * D2 * W.bc;
-    // beta = m0 x^2 + m1 x y + m2 y^2: d/dx = 2 m0 x + m1 y, d/dy = m1 x + 2 m2 y
-    ab = k[0] * vab + bab * (2.0 * k[2] * a + k[3] * b);
-    bb_ = k[1] * vab + bab * (k[3] * a + 2.0 * k[4] * b) + k[5] * vbb + bbb * (2.0 * k[7] * b + k[8] * c);
+    // l0 = C0 bb bc, l1 = ba bc, l2 = C2 ba bb; r0 = D0 bb bc, r1 = bd bb, r2 = D2 bd bc
+    const double t0 = l0b * C0, t2 = l2b * C2, u0 = r0b * D0, u2 = r2b * D2;
+    const double bab = fma(l1b, W.bc, t2 * W.bb);
+    const double bbb = fma(t0, W.bc, fma(t2, W.ba, fma(u0, W.bc, r1b * W.bd)));
+    const double bcb = fma(t0, W.bb, fma(l1b, W.ba, fma(u0, W.bb, u2 * W.bd)));
+    const double bdb = fma(r1b, W.bb, u2 * W.bc);
+    // beta = m0 x^2 + m1 x y + m2 y^2: d/dx = 2 m0 x + m1 y = h + m0 x with the
+    // forward's h = m0 x + m1 y, d/dy = m1 x + 2 m2 y
+    ab = k[0] * vab + bab * fma(k[2], a, H.ha);
+    bb_ = k[1] * vab + bab * (k[3] * a + 2.0 * k[4] * b) + k[5] * vbb + bbb * fma(k[7], b, H.hb);
     cb = cdir + k[6] * vbb + bbb * (k[8] * b + 2.0 * k[9] * c) + k[10] * vcb + bcb * (2.0 * k[12] * c + k[13] * d);
-    db = k[11] * vcb + bcb * (k[13] * c + 2.0 * k[14] * d);
-    eb = k[15] * vdb + bdb * (2.0 * k[17] * e + k[18] * f);
+    db = k[11] * vcb + bcb * fma(k[14], d, H.hc);
+    eb = k[15] * vdb + bdb * fma(k[17], e, H.hd);
     fb = k[16] * vdb + bdb * (k[18] * e + 2.0 * k[19] * f);
 }
 
@@ -267,44 +304,46 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     // each field's sub-stencil values and indicators and the combination's
     // products, kept in shared memory (thread-private column) for the
     // reverse sweep
-    __shared__ double wsm[4 * 18][kVjpBlock];
+    __shared__ double wsm[4 * 22][kVjpBlock];
     const int t = threadIdx.x;
-    auto keep = [&](int fi, const WenoField &W, const WenoKeep &K) {
-        double *q = &wsm[fi * 18][t];
-        const double v[18] = {W.va, W.vb, W.vc, W.vd, W.ba, W.bb, W.bc, W.bd, K.l0,
-                              K.l1, K.l2, K.iDL, K.dl, K.r0, K.r1, K.r2, K.iDR, K.dr};
+    auto keep = [&](int fi, const WenoField &W, const WenoKeep &K, const WenoHorner &H) {
+        double *q = &wsm[fi * 22][t];
+        const double v[22] = {W.va, W.vb, W.vc, W.vd, W.ba, W.bb, W.bc, W.bd, K.l0, K.l1, K.l2,
+                              K.iDL, K.dl, K.r0, K.r1, K.r2, K.iDR, K.dr, H.ha, H.hb, H.hc, H.hd};
 #pragma unroll
-        for (int i = 0; i < 18; ++i) q[i * kVjpBlock] = v[i];
+        for (int i = 0; i < 22; ++i) q[i * kVjpBlock] = v[i];
     };
-    auto kept = [&](int fi, WenoField &W, WenoKeep &K) {
-        const double *q = &wsm[fi * 18][t];
+    auto kept = [&](int fi, WenoField &W, WenoKeep &K, WenoHorner &H) {
+        const double *q = &wsm[fi * 22][t];
         W.va = q[0 * kVjpBlock]; W.vb = q[1 * kVjpBlock]; W.vc = q[2 * kVjpBlock]; W.vd = q[3 * kVjpBlock];
         W.ba = q[4 * kVjpBlock]; W.bb = q[5 * kVjpBlock]; W.bc = q[6 * kVjpBlock]; W.bd = q[7 * kVjpBlock];
         K.l0 = q[8 * kVjpBlock]; K.l1 = q[9 * kVjpBlock]; K.l2 = q[10 * kVjpBlock]; K.iDL = q[11 * kVjpBlock];
         K.dl = q[12 * kVjpBlock]; K.r0 = q[13 * kVjpBlock]; K.r1 = q[14 * kVjpBlock]; K.r2 = q[15 * kVjpBlock];
         K.iDR = q[16 * kVjpBlock]; K.dr = q[17 * kVjpBlock];
+        H.ha = q[18 * kVjpBlock]; H.hb = q[19 * kVjpBlock]; H.hc = q[20 * kVjpBlock]; H.hd = q[21 * kVjpBlock];
     };
     dbl4 dl, dr;
     {
         WenoKeep K;
-        WenoField W = weno_field64(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps);
+        WenoHorner H;
+        WenoField W = weno_field64_h(k, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, A.eps, H);
         weno_combine64_keep(k, W, cM.x, K);
-        keep(0, W, K);
+        keep(0, W, K, H);
         dl.x = K.dl;
         dr.x = K.dr;
-        W = weno_field64(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps);
+        W = weno_field64_h(k, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, A.eps, H);
         weno_combine64_keep(k, W, cM.y, K);
-        keep(1, W, K);
+        keep(1, W, K, H);
         dl.y = K.dl;
         dr.y = K.dr;
-        W = weno_field64(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps);
+        W = weno_field64_h(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, A.eps, H);
         weno_combine64_keep(k, W, cM.z, K);
-        keep(2, W, K);
+        keep(2, W, K, H);
         dl.z = K.dl;
         dr.z = K.dr;
-        W = weno_field64(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps);
+        W = weno_field64_h(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, A.eps, H);
         weno_combine64_keep(k, W, cM.w, K);
-        keep(3, W, K);
+        keep(3, W, K, H);
         dl.w = K.dl;
         dr.w = K.dr;
     }
@@ -367,7 +406,7 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     Qb.qn += lub + lmb + lpb;
     Qb.c += lpb - lmb + 0.1 * deltab;
     dbl4 dwb = dbl4_make(0, 0, 0, 0);
-    project64_vjp(Q, dw, ab, dwb, Qb);
+    project64_vjp(Q, dw, a, ab, dwb, Qb);
     add_to(wrb, dwb);
     wlb = sub4(wlb, dwb);
     roe64_vjp(wl, pl, wr, pr, Q, Qb, gm1, wlb, plb, wrb, prb);
@@ -383,26 +422,27 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
         dbl4 cL3b, cL2b, cMb, cR2Lb, cR3b, cR2b;
         WenoField W;
         WenoKeep K;
-        kept(0, W, K);
-        weno_pair64_vjp(k, W, K, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, dlb.x, drb.x, cL3b.x, cL2b.x, cMb.x,
+        WenoHorner H;
+        kept(0, W, K, H);
+        weno_pair64_vjp(k, W, K, H, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, dlb.x, drb.x, cL3b.x, cL2b.x, cMb.x,
                         cR2Lb.x, cR3b.x, cR2b.x);
-        kept(1, W, K);
-        weno_pair64_vjp(k, W, K, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, dlb.y, drb.y, cL3b.y, cL2b.y, cMb.y,
+        kept(1, W, K, H);
+        weno_pair64_vjp(k, W, K, H, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, dlb.y, drb.y, cL3b.y, cL2b.y, cMb.y,
                         cR2Lb.y, cR3b.y, cR2b.y);
-        kept(2, W, K);
-        weno_pair64_vjp(k, W, K, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, dlb.z, drb.z, cL3b.z, cL2b.z, cMb.z,
+        kept(2, W, K, H);
+        weno_pair64_vjp(k, W, K, H, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, dlb.z, drb.z, cL3b.z, cL2b.z, cMb.z,
                         cR2Lb.z, cR3b.z, cR2b.z);
-        kept(3, W, K);
-        weno_pair64_vjp(k, W, K, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, dlb.w, drb.w, cL3b.w, cL2b.w, cMb.w,
+        kept(3, W, K, H);
+        weno_pair64_vjp(k, W, K, H, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, dlb.w, drb.w, cL3b.w, cL2b.w, cMb.w,
                         cR2Lb.w, cR3b.w, cR2b.w);
         add_to(cR2b, cR2Lb);
         add_to(cMb, cR2Lb);
         dbl4 dMb = dbl4_make(0, 0, 0, 0), dL2b = dMb, dL3b = dMb, dR2b = dMb, dR3b = dMb;
-        project64_vjp(C, dM, cMb, dMb, Cb);
-        project64_vjp(C, dL2, cL2b, dL2b, Cb);
-        project64_vjp(C, dL3, cL3b, dL3b, Cb);
-        project64_vjp(C, dR2, cR2b, dR2b, Cb);
-        project64_vjp(C, dR3, cR3b, dR3b, Cb);
+        project64_vjp(C, dM, cM, cMb, dMb, Cb);
+        project64_vjp(C, dL2, cL2, cL2b, dL2b, Cb);
+        project64_vjp(C, dL3, cL3, cL3b, dL3b, Cb);
+        project64_vjp(C, dR2, cR2, cR2b, dR2b, Cb);
+        project64_vjp(C, dR3, cR3, cR3b, dR3b, Cb);
         add_to(GR1, dMb);
         GL1 = sub4(GL1, dMb);
         add_to(G1, dL2b);

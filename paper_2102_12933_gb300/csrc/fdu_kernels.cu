@@ -514,6 +514,14 @@ __device__ __forceinline__ float ld_stream(const float *p) {
     asm("ld.global.nc.L1::no_allocate.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
+// Vertex fluxes (f, g) of vertex j from the FP32 [nv][2] float4 buffer as one
+// 32-byte load (the buffer is 32-byte aligned and read-only in the kernel).
+__device__ __forceinline__ void ld_fg32(const float4 *F, int64_t j, float4 &f, float4 &g) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(f.x), "=f"(f.y), "=f"(f.z), "=f"(f.w), "=f"(g.x), "=f"(g.y), "=f"(g.z), "=f"(g.w)
+        : "l"(F + 2 * j));
+}
+
 // Table loads of the FP32 divergence: streaming loads in the fused stage
 // (modes 1..3: 0.066 -> 0.062 ms at 250k vertices), plain cached loads for
 // the residual alone (mode 0, where the streaming form measured slower).
@@ -539,7 +547,8 @@ __device__ __forceinline__ void div_f32_body(const DivArgs &A, const int64_t v) 
         for (int64_t p = b; p < e; p += kSell) {
             const int32_t j = ld_table<MODE>(A.vid + p);
             const float a = ld_table<MODE>(wf + p), c = ld_table<MODE>(wg + p);
-            const float4 f = __ldg(F + 2 * (int64_t)j), g = __ldg(F + 2 * (int64_t)j + 1);
+            float4 f, g;
+            ld_fg32(F, j, f, g);
             acc.x = fmaf(a, f.x, fmaf(c, g.x, acc.x));
             acc.y = fmaf(a, f.y, fmaf(c, g.y, acc.y));
             acc.z = fmaf(a, f.z, fmaf(c, g.z, acc.z));

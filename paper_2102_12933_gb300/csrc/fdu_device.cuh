@@ -18,6 +18,13 @@ __device__ __forceinline__ dbl4 ld4(const double *p, int64_t i) {
     const double2 a = __ldg(q), b = __ldg(q + 1);
     return dbl4_make(a.x, a.y, b.x, b.y);
 }
+// The same record as one 256-bit load, for the library's own buffers (their
+// rows are 32-byte aligned) that the kernel only reads.
+__device__ __forceinline__ dbl4 ld4v(const double *p, int64_t i) {
+    dbl4 r;
+    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(r.x), "=d"(r.y), "=d"(r.z), "=d"(r.w) : "l"(p + 4 * i));
+    return r;
+}
 __device__ __forceinline__ void st4(double *p, int64_t i, dbl4 v) {
     double2 *q = reinterpret_cast<double2 *>(p + 4 * i);
     q[0] = make_double2(v.x, v.y);

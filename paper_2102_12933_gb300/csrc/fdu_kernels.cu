@@ -39,19 +39,19 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
     int32_t s[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
-    const dbl4 L1 = ld4(w, s[2]), R1 = ld4(w, s[3]);
+    const dbl4 L1 = ld4v(w, s[2]), R1 = ld4v(w, s[3]);
     const double nx = __ldg(coef + (int64_t)kCoefN * ne + e);
     const double ny = __ldg(coef + (int64_t)(kCoefN + 1) * ne + e);
 
     // characteristic decomposition at the Roe average of the end states
     // (per-vertex Roe records when the stage kernel provided them)
-    const Roe64 C = A.Q ? roe64_from_records(ld4(A.Q, s[2]), ld4(A.Q, s[3]), nx, ny, gm1, hgm1)
+    const Roe64 C = A.Q ? roe64_from_records(ld4v(A.Q, s[2]), ld4v(A.Q, s[3]), nx, ny, gm1, hgm1)
                         : roe64(L1, prim64(L1, gm1, hgm1), R1, prim64(R1, gm1, hgm1), nx, ny, gm1, hgm1);
     const dbl4 cM = project64(C, sub4(R1, L1));               // R1 - L1
-    const dbl4 cL2 = project64(C, sub4(ld4(w, s[1]), L1));    // L2 - L1
-    const dbl4 cL3 = project64(C, sub4(ld4(w, s[0]), L1));    // L3 - L1
-    const dbl4 cR2 = project64(C, sub4(ld4(w, s[4]), R1));    // R2 - R1
-    const dbl4 cR3 = project64(C, sub4(ld4(w, s[5]), R1));    // R3 - R1
+    const dbl4 cL2 = project64(C, sub4(ld4v(w, s[1]), L1));    // L2 - L1
+    const dbl4 cL3 = project64(C, sub4(ld4v(w, s[0]), L1));    // L3 - L1
+    const dbl4 cR2 = project64(C, sub4(ld4v(w, s[4]), R1));    // R2 - R1
+    const dbl4 cR3 = project64(C, sub4(ld4v(w, s[5]), R1));    // R3 - R1
 
     double k[kCoefN];
 #pragma unroll
@@ -195,7 +195,7 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) 
         for (int64_t p = b; p < e; p += kSell) {
             const int32_t j = __ldg(A.vid + p);
             const double a = __ldg(wf + p), c = __ldg(wg + p);
-            const dbl4 f = ld4(F, 2 * (int64_t)j), g = ld4(F, 2 * (int64_t)j + 1);
+            const dbl4 f = ld4v(F, 2 * (int64_t)j), g = ld4v(F, 2 * (int64_t)j + 1);
             acc.x = fma(a, f.x, fma(c, g.x, acc.x));
             acc.y = fma(a, f.y, fma(c, g.y, acc.y));
             acc.z = fma(a, f.z, fma(c, g.z, acc.z));
@@ -230,7 +230,7 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) 
         for (int64_t p = b; p < e; p += kSell) {
             const int32_t k = __ldg(A.eid + p);
             const double a = __ldg(we + p);
-            const dbl4 q = ld4(r, k);
+            const dbl4 q = ld4v(r, k);
             acc.x = fma(a, q.x, acc.x);
             acc.y = fma(a, q.y, acc.y);
             acc.z = fma(a, q.z, acc.z);
@@ -240,7 +240,7 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) 
     {
         const double *cfg = static_cast<const double *>(A.cfg);
         const double cf = __ldg(cfg + v), cg = __ldg(cfg + A.n_real + v);
-        const dbl4 f = ld4(F, 2 * v), g = ld4(F, 2 * v + 1);
+        const dbl4 f = ld4v(F, 2 * v), g = ld4v(F, 2 * v + 1);
         acc.x = fma(cf, f.x, fma(cg, g.x, acc.x));
         acc.y = fma(cf, f.y, fma(cg, g.y, acc.y));
         acc.z = fma(cf, f.z, fma(cg, g.z, acc.z));
@@ -253,13 +253,13 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) 
         return;
     }
     const double dt = A.comp ? __ldg(A.dt_comp + __ldg(A.comp + v)) : (A.dt_dev ? *A.dt_dev : A.dt);
-    const dbl4 ws = ld4(A.ws, v);
+    const dbl4 ws = ld4v(A.ws, v);
     const dbl4 fe = forward_euler(ws, L, dt, A.gm1, A.pos_alpha, A.limited);
     dbl4 o;
     if (MODE == 1) {
         o = fe;
     } else {
-        const dbl4 wn = ld4(A.wn, v);
+        const dbl4 wn = ld4v(A.wn, v);
         const double cn = MODE == 2 ? 0.75 : 1.0 / 3.0;
         const double cs = MODE == 2 ? 0.25 : 2.0 / 3.0;
         o.x = fma(cn, wn.x, cs * fe.x);

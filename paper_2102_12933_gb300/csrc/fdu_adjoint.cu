@@ -286,10 +286,10 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     int32_t s[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
-    const dbl4 W0 = ld4(w, s[0]), W1 = ld4(w, s[1]), L1 = ld4(w, s[2]), R1 = ld4(w, s[3]), W4 = ld4(w, s[4]),
-               W5 = ld4(w, s[5]);
+    const dbl4 W0 = ld4v(w, s[0]), W1 = ld4v(w, s[1]), L1 = ld4v(w, s[2]), R1 = ld4v(w, s[3]), W4 = ld4v(w, s[4]),
+               W5 = ld4v(w, s[5]);
     const double nx = __ldg(coef + (int64_t)kCoefN * ne + e), ny = __ldg(coef + (int64_t)(kCoefN + 1) * ne + e);
-    const dbl4 lam = ld4(A.lam_r, e);
+    const dbl4 lam = ld4v(A.lam_r, e);
 
     // ---------------- forward
     const Prim64 pL1 = prim64(L1, gm1, hgm1), pR1 = prim64(R1, gm1, hgm1);
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     st4(G, 5 * ne + e, G5);
 }
 
-// lam_r[k] = -sum_v we_vk lam_v (CSR over edges)
+// lam_r[k] = -sum_v we_vk lam_v (CSR over edges; the table holds -we)
 __global__ void adj_edge_lambda_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ vid,
                                        const double *__restrict__ wt, const double *__restrict__ lam,
                                        double *__restrict__ lam_r, int64_t ne) {
@@ -476,17 +476,18 @@ __global__ void adj_edge_lambda_kernel(const int64_t *__restrict__ off, const in
     dbl4 acc = dbl4_make(0, 0, 0, 0);
     for (int64_t p = __ldg(off + k); p < __ldg(off + k + 1); ++p) {
         const double a = __ldg(wt + p);
-        const dbl4 l = ld4(lam, __ldg(vid + p));
+        const dbl4 l = ld4v(lam, __ldg(vid + p));
         acc.x = fma(a, l.x, acc.x);
         acc.y = fma(a, l.y, acc.y);
         acc.z = fma(a, l.z, acc.z);
         acc.w = fma(a, l.w, acc.w);
     }
-    st4(lam_r, k, neg4(acc));
+    st4(lam_r, k, acc);
 }
 
 // grad[j] = (df/dw)^T lam_f + (dg/dw)^T lam_g with lam_f = -sum_v wf_vj lam_v
-// (centre weights included as the entry v = j), then + sum of the edge-flux
+// (the table holds -wf, -wg; the centre weights are included as the entry
+// v = j), then + sum of the edge-flux
 // slot cotangents G[slot][k] over the stencil slots that hold j.
 __global__ void adj_vertex_kernel(AdjVertexArgs A) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -494,7 +495,7 @@ __global__ void adj_vertex_kernel(AdjVertexArgs A) {
     dbl4 lf = dbl4_make(0, 0, 0, 0), lg = lf;
     for (int64_t p = __ldg(A.voff + j); p < __ldg(A.voff + j + 1); ++p) {
         const double a = __ldg(A.wf + p), b = __ldg(A.wg + p);
-        const dbl4 l = ld4(A.lam, __ldg(A.vid + p));
+        const dbl4 l = ld4v(A.lam, __ldg(A.vid + p));
         lf.x = fma(a, l.x, lf.x);
         lf.y = fma(a, l.y, lf.y);
         lf.z = fma(a, l.z, lf.z);
@@ -504,8 +505,8 @@ __global__ void adj_vertex_kernel(AdjVertexArgs A) {
         lg.z = fma(b, l.z, lg.z);
         lg.w = fma(b, l.w, lg.w);
     }
-    dbl4 g = vertex_flux_vjp(ld4(A.w, j), A.gm1, neg4(lf), neg4(lg));
-    for (int64_t p = __ldg(A.soff + j); p < __ldg(A.soff + j + 1); ++p) add_to(g, ld4(A.G, __ldg(A.slot + p)));
+    dbl4 g = vertex_flux_vjp(ld4v(A.w, j), A.gm1, lf, lg);
+    for (int64_t p = __ldg(A.soff + j); p < __ldg(A.soff + j + 1); ++p) add_to(g, ld4v(A.G, __ldg(A.slot + p)));
     st4(A.grad, j, g);
 }
 

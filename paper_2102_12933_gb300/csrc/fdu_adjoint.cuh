@@ -28,7 +28,7 @@ struct AdjEdgeArgs {
 struct AdjTables {
     const int64_t *eoff;  // [ne+1]
     const int32_t *evid;
-    const double *ewt;
+    const double *ewt;    // -w_k: the residual's minus sign carried by the weights
 };
 
 // Per-vertex part: vertex transpose (wf, wg of every stencil that holds the
@@ -37,7 +37,7 @@ struct AdjVertexArgs {
     int64_t nv;
     const int64_t *voff;  // [nv+1]
     const int32_t *vid;
-    const double *wf, *wg;
+    const double *wf, *wg;  // -wf, -wg (and minus the centre weights at v = j)
     const double *lam;    // [nv][4] cotangent of the residual
     const double *w;      // [nv][4] state
     double gm1;

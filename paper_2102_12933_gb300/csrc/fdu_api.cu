@@ -602,22 +602,22 @@ fdu_status adjoint_setup(fdu_mesh *m) {
             const int32_t e = T.eid[q];
             const int64_t p = ef[T.e_old2new[e]]++;
             evid[p] = (int32_t)v;
-            ewt[p] = T.we[q];
+            ewt[p] = -T.we[q];  // the residual is minus the divergence: the sign rides on the weights
             sx += T.we[q] * T.nrm[2 * e];
             sy += T.we[q] * T.nrm[2 * e + 1];
         }
         for (int64_t q = T.voff[o]; q < T.voff[o + 1]; ++q) {
             const int64_t p = vf[T.v_old2new[T.vid[q]]]++;
             vvid[p] = (int32_t)v;
-            wf[p] = T.wf[q];
-            wg[p] = T.wg[q];
+            wf[p] = -T.wf[q];
+            wg[p] = -T.wg[q];
             sf_ += T.wf[q];
             sg_ += T.wg[q];
         }
         const int64_t p = vf[v]++;  // centre weights, as in the forward's folded form
         vvid[p] = (int32_t)v;
-        wf[p] = -(sf_ + sx);
-        wg[p] = -(sg_ + sy);
+        wf[p] = sf_ + sx;  // minus the centre weights -(sum wf + sum we nx), likewise g
+        wg[p] = sg_ + sy;
     }
     for (int64_t k = 0; k < ne; ++k)
         for (int i = 0; i < 6; ++i) slot[sf[T.v_old2new[T.sten[6 * (int64_t)T.e_new2old[k] + i]]]++] = i * ne + k;

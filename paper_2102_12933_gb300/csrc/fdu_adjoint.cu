@@ -169,7 +169,7 @@ __device__ __forceinline__ WenoField weno_field64_h(const double *k, double a, d
 // the reverse sweep differentiates; dl, dr as weno_combine64), keeping the
 // products and reciprocals the reverse sweep needs.
 struct WenoKeep {
-    double l0, l1, l2, iDL, dl, r0, r1, r2, iDR, dr;
+    double l0, l1, l2, iDL, dl, r0, r1, r2, iDR, dr, vcr, vbr;  // vcr = vc - c, vbr = vb - c
 };
 __device__ __forceinline__ void weno_combine64_keep(const double *k, const WenoField &W, double c, WenoKeep &K) {
     const double bbc = W.bb * W.bc;
@@ -182,7 +182,9 @@ __device__ __forceinline__ void weno_combine64_keep(const double *k, const WenoF
     K.r1 = W.bd * W.bb;
     K.r2 = k[23] * (W.bd * W.bc);
     K.iDR = recip64_fast(K.r0 + K.r1 + K.r2);
-    K.dr = fma(K.r0, W.vd, fma(K.r1, W.vc - c, K.r2 * (W.vb - c))) * K.iDR;
+    K.vcr = W.vc - c;
+    K.vbr = W.vb - c;
+    K.dr = fma(K.r0, W.vd, fma(K.r1, K.vcr, K.r2 * K.vbr)) * K.iDR;
 }
 
 // Reverse of the combination for one field: from (dlb, drb) to the
@@ -193,7 +195,7 @@ __device__ __forceinline__ void weno_pair64_vjp(const double *k, const WenoField
                                                 double f, double dlb, double drb, double &ab, double &bb_, double &cb,
                                                 double &db, double &eb, double &fb) {
     const double C0 = k[20], C2 = k[21], D0 = k[22], D2 = k[23];  // C_1 = 1 on both sides
-    const double vcr = W.vc - c, vbr = W.vb - c;
+    const double vcr = K.vcr, vbr = K.vbr;
     const double NLb = dlb * K.iDL, DLb = -NLb * K.dl;
     const double NRb = drb * K.iDR, DRb = -NRb * K.dr;
     const double l0b = NLb * W.va + DLb, l1b = NLb * W.vb + DLb, l2b = NLb * W.vc + DLb;
@@ -309,17 +311,20 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     auto keep = [&](int fi, const WenoField &W, const WenoKeep &K, const WenoHorner &H) {
         double *q = &wsm[fi * 22][t];
         const double v[22] = {W.va, W.vb, W.vc, W.vd, W.ba, W.bb, W.bc, W.bd, K.l0, K.l1, K.l2,
-                              K.iDL, K.dl, K.r0, K.r1, K.r2, K.iDR, K.dr, H.ha, H.hb, H.hc, H.hd};
+                              K.iDL, K.vcr, K.r0, K.r1, K.r2, K.iDR, K.vbr, H.ha, H.hb, H.hc, H.hd};
 #pragma unroll
         for (int i = 0; i < 22; ++i) q[i * kVjpBlock] = v[i];
     };
-    auto kept = [&](int fi, WenoField &W, WenoKeep &K, WenoHorner &H) {
+    // dl, dr of the field stay in registers (the dbl4 dl, dr below)
+    auto kept = [&](int fi, double dlf, double drf, WenoField &W, WenoKeep &K, WenoHorner &H) {
         const double *q = &wsm[fi * 22][t];
         W.va = q[0 * kVjpBlock]; W.vb = q[1 * kVjpBlock]; W.vc = q[2 * kVjpBlock]; W.vd = q[3 * kVjpBlock];
         W.ba = q[4 * kVjpBlock]; W.bb = q[5 * kVjpBlock]; W.bc = q[6 * kVjpBlock]; W.bd = q[7 * kVjpBlock];
         K.l0 = q[8 * kVjpBlock]; K.l1 = q[9 * kVjpBlock]; K.l2 = q[10 * kVjpBlock]; K.iDL = q[11 * kVjpBlock];
-        K.dl = q[12 * kVjpBlock]; K.r0 = q[13 * kVjpBlock]; K.r1 = q[14 * kVjpBlock]; K.r2 = q[15 * kVjpBlock];
-        K.iDR = q[16 * kVjpBlock]; K.dr = q[17 * kVjpBlock];
+        K.vcr = q[12 * kVjpBlock]; K.r0 = q[13 * kVjpBlock]; K.r1 = q[14 * kVjpBlock]; K.r2 = q[15 * kVjpBlock];
+        K.iDR = q[16 * kVjpBlock]; K.vbr = q[17 * kVjpBlock];
+        K.dl = dlf;
+        K.dr = drf;
         H.ha = q[18 * kVjpBlock]; H.hb = q[19 * kVjpBlock]; H.hc = q[20 * kVjpBlock]; H.hd = q[21 * kVjpBlock];
     };
     dbl4 dl, dr;
@@ -423,16 +428,16 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
         WenoField W;
         WenoKeep K;
         WenoHorner H;
-        kept(0, W, K, H);
+        kept(0, dl.x, dr.x, W, K, H);
         weno_pair64_vjp(k, W, K, H, cL3.x, cL2.x, cM.x, cR2L.x, cR3.x, cR2.x, dlb.x, drb.x, cL3b.x, cL2b.x, cMb.x,
                         cR2Lb.x, cR3b.x, cR2b.x);
-        kept(1, W, K, H);
+        kept(1, dl.y, dr.y, W, K, H);
         weno_pair64_vjp(k, W, K, H, cL3.y, cL2.y, cM.y, cR2L.y, cR3.y, cR2.y, dlb.y, drb.y, cL3b.y, cL2b.y, cMb.y,
                         cR2Lb.y, cR3b.y, cR2b.y);
-        kept(2, W, K, H);
+        kept(2, dl.z, dr.z, W, K, H);
         weno_pair64_vjp(k, W, K, H, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, dlb.z, drb.z, cL3b.z, cL2b.z, cMb.z,
                         cR2Lb.z, cR3b.z, cR2b.z);
-        kept(3, W, K, H);
+        kept(3, dl.w, dr.w, W, K, H);
         weno_pair64_vjp(k, W, K, H, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, dlb.w, drb.w, cL3b.w, cL2b.w, cMb.w,
                         cR2Lb.w, cR3b.w, cR2b.w);
         add_to(cR2b, cR2Lb);
@@ -469,11 +474,13 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
 
 // lam_r[k] = -sum_v we_vk lam_v (CSR over edges; the table holds -we)
 __global__ void adj_edge_lambda_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ vid,
-                                       const double *__restrict__ wt, const double *__restrict__ lam,
-                                       double *__restrict__ lam_r, int64_t ne) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ne) return;
+                                       const double *__restrict__ wt, const int32_t *__restrict__ perm,
+                                       const double *__restrict__ lam, double *__restrict__ lam_r, int64_t ne) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const int64_t k = perm ? (int64_t)__ldg(perm + i) : i;
     dbl4 acc = dbl4_make(0, 0, 0, 0);
+#pragma unroll 4
     for (int64_t p = __ldg(off + k); p < __ldg(off + k + 1); ++p) {
         const double a = __ldg(wt + p);
         const dbl4 l = ld4v(lam, __ldg(vid + p));
@@ -490,9 +497,11 @@ __global__ void adj_edge_lambda_kernel(const int64_t *__restrict__ off, const in
 // v = j), then + sum of the edge-flux
 // slot cotangents G[slot][k] over the stencil slots that hold j.
 __global__ void adj_vertex_kernel(AdjVertexArgs A) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= A.nv) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.nv) return;
+    const int64_t j = A.perm ? (int64_t)__ldg(A.perm + i) : i;
     dbl4 lf = dbl4_make(0, 0, 0, 0), lg = lf;
+#pragma unroll 4
     for (int64_t p = __ldg(A.voff + j); p < __ldg(A.voff + j + 1); ++p) {
         const double a = __ldg(A.wf + p), b = __ldg(A.wg + p);
         const dbl4 l = ld4v(A.lam, __ldg(A.vid + p));
@@ -506,6 +515,7 @@ __global__ void adj_vertex_kernel(AdjVertexArgs A) {
         lg.w = fma(b, l.w, lg.w);
     }
     dbl4 g = vertex_flux_vjp(ld4v(A.w, j), A.gm1, lf, lg);
+#pragma unroll 4
     for (int64_t p = __ldg(A.soff + j); p < __ldg(A.soff + j + 1); ++p) add_to(g, ld4v(A.G, __ldg(A.slot + p)));
     st4(A.grad, j, g);
 }
@@ -549,7 +559,8 @@ void launch_ghost_fold(double *x, const int32_t *donor, const int64_t *off, cons
 
 void launch_residual_vjp(const AdjEdgeArgs &ea, const AdjTables &t, const AdjVertexArgs &va, cudaStream_t s) {
     if (ea.ne > 0) {
-        adj_edge_lambda_kernel<<<nblk(ea.ne, 256), 256, 0, s>>>(t.eoff, t.evid, t.ewt, va.lam, ea.lam_r_mut, ea.ne);
+        adj_edge_lambda_kernel<<<nblk(ea.ne, 256), 256, 0, s>>>(t.eoff, t.evid, t.ewt, t.eperm, va.lam, ea.lam_r_mut,
+                                                               ea.ne);
         if (ea.prec == 48) launch_edge_flux_vjp_dw(ea, s);
         else edge_flux_vjp_kernel<<<nblk(ea.ne, kVjpBlock), kVjpBlock, 0, s>>>(ea);
     }

@@ -29,6 +29,7 @@ struct AdjTables {
     const int64_t *eoff;  // [ne+1]
     const int32_t *evid;
     const double *ewt;    // -w_k: the residual's minus sign carried by the weights
+    const int32_t *eperm; // [ne] edge of each thread (list-length order inside windows)
 };
 
 // Per-vertex part: vertex transpose (wf, wg of every stencil that holds the
@@ -45,6 +46,7 @@ struct AdjVertexArgs {
     const int64_t *slot;  // index slot * ne + k into G
     const double *G;
     double *grad;         // [nv][4] output
+    const int32_t *perm;  // [nv] vertex of each thread (list-length order inside windows)
 };
 
 // The double-word edge-flux VJP (precision 48) of the same edge flux.

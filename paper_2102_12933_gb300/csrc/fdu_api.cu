@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <new>
 #include <tuple>
@@ -107,6 +108,7 @@ struct fdu_mesh {
     int adj_prec = 64;                // adjoint precision: 64, or 48 (double-word VJP, precision-48 steps)
     int64_t *adj_eoff = nullptr, *adj_voff = nullptr, *adj_soff = nullptr, *adj_slot = nullptr;
     int32_t *adj_evid = nullptr, *adj_vvid = nullptr;
+    int32_t *adj_eperm = nullptr, *adj_vperm = nullptr;  // thread -> edge / vertex of the transpose kernels
     double *adj_ewt = nullptr, *adj_wf = nullptr, *adj_wg = nullptr;
     double *adj_lam_r = nullptr, *adj_G = nullptr;
     double *adj_S1 = nullptr, *adj_buf[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -631,6 +633,24 @@ fdu_status adjoint_setup(fdu_mesh *m) {
     if ((st = m->upload(m->adj_wg, wg))) return st;
     if ((st = m->upload(m->adj_soff, scnt))) return st;
     if ((st = m->upload(m->adj_slot, slot))) return st;
+    // the transpose kernels give one thread a list (edges: the stencils that
+    // hold the edge; vertices: the stencils and stencil slots that hold the
+    // vertex); inside windows of 256 consecutive ids the threads are ordered
+    // by list length, so the lanes of a warp walk lists of about one length
+    auto window_order = [](int64_t n, const std::function<int64_t(int64_t)> &len) {
+        std::vector<int32_t> perm(std::max<int64_t>(n, 1));
+        std::iota(perm.begin(), perm.begin() + n, 0);
+        for (int64_t w0 = 0; w0 < n; w0 += 256)
+            std::stable_sort(perm.begin() + w0, perm.begin() + std::min<int64_t>(n, w0 + 256),
+                             [&](int32_t a, int32_t b) { return len(a) > len(b); });
+        return perm;
+    };
+    if ((st = m->upload(m->adj_eperm, window_order(ne, [&](int64_t k) { return ecnt[k + 1] - ecnt[k]; }))))
+        return st;
+    if ((st = m->upload(m->adj_vperm, window_order(nv, [&](int64_t v) {
+             return (vcnt[v + 1] - vcnt[v]) * 8 + (scnt[v + 1] - scnt[v]) * 4;  // FP64 work of each list
+         }))))
+        return st;
     if ((st = m->alloc(m->adj_lam_r, 4 * ne))) return st;
     if ((st = m->alloc(m->adj_G, 6 * 4 * ne))) return st;
     if ((st = m->alloc(m->adj_S1, 4 * nv))) return st;
@@ -694,7 +714,7 @@ void enqueue_residual_vjp(fdu_mesh *m, const double *w, const double *lam, doubl
         }
         ea.dw_eps_e = e48.dw_eps_e;
     }
-    AdjTables t{m->adj_eoff, m->adj_evid, m->adj_ewt};
+    AdjTables t{m->adj_eoff, m->adj_evid, m->adj_ewt, m->adj_eperm};
     AdjVertexArgs va{};
     va.nv = m->nv;
     va.voff = m->adj_voff;
@@ -708,6 +728,7 @@ void enqueue_residual_vjp(fdu_mesh *m, const double *w, const double *lam, doubl
     va.slot = m->adj_slot;
     va.G = m->adj_G;
     va.grad = out;
+    va.perm = m->adj_vperm;
     launch_residual_vjp(ea, t, va, s);
 }
 

@@ -172,6 +172,15 @@ __device__ __forceinline__ dbl4 forward_euler(const dbl4 &ws, const dbl4 &L, dou
     return fe;
 }
 
+// Two adjacent float4 (record j of a [n][2] float4 buffer: FP32 vertex fluxes
+// (f, g), or an edge's double-word increments) as one 32-byte load; the
+// buffers are 32-byte aligned and read-only in the kernel.
+__device__ __forceinline__ void ld_fg32(const float4 *F, int64_t j, float4 &f, float4 &g) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(f.x), "=f"(f.y), "=f"(f.z), "=f"(f.w), "=f"(g.x), "=f"(g.y), "=f"(g.z), "=f"(g.w)
+        : "l"(F + 2 * j));
+}
+
 // ------------------------------------------------------------------ FP64 divergence (+ RK stage)
 // Position i of the SELL tables; the vertex it holds is A.perm[i].  With
 // DWE (precision 48) the edge entries are double-word increments
@@ -213,7 +222,8 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) 
             const int32_t k = __ldg(A.eid + p);
             const float2 wq = __ldg(we2 + p);
             const dw a = dw_make(wq.x, wq.y);
-            const float4 q0 = __ldg(rd + 2 * (int64_t)k), q1 = __ldg(rd + 2 * (int64_t)k + 1);
+            float4 q0, q1;
+            ld_fg32(rd, k, q0, q1);  // the edge's two double-word float4, one 32-byte load
             dot2_add(sx, a, dw_make(q0.x, q0.y));
             dot2_add(sy, a, dw_make(q0.z, q0.w));
             dot2_add(sz, a, dw_make(q1.x, q1.y));
@@ -514,14 +524,6 @@ __device__ __forceinline__ float ld_stream(const float *p) {
     asm("ld.global.nc.L1::no_allocate.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
-// Vertex fluxes (f, g) of vertex j from the FP32 [nv][2] float4 buffer as one
-// 32-byte load (the buffer is 32-byte aligned and read-only in the kernel).
-__device__ __forceinline__ void ld_fg32(const float4 *F, int64_t j, float4 &f, float4 &g) {
-    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=f"(f.x), "=f"(f.y), "=f"(f.z), "=f"(f.w), "=f"(g.x), "=f"(g.y), "=f"(g.z), "=f"(g.w)
-        : "l"(F + 2 * j));
-}
-
 // Table loads of the FP32 divergence: streaming loads in the fused stage
 // (modes 1..3: 0.066 -> 0.062 ms at 250k vertices), plain cached loads for
 // the residual alone (mode 0, where the streaming form measured slower).

@@ -440,7 +440,7 @@ def run_ours(args):
     vnnz, ennz = info["div_vert_nnz"], info["div_edge_nnz"]
     div_flops = FLOP_DIV64_PER_VENTRY * vnnz + FLOP_DIV64_PER_EENTRY * ennz + FLOP_DIV64_FIXED * nv
     # FP32 kernels are HBM-bound.  Bytes per launch of the kernels' own tables:
-    edge32_bytes = ne * (24 + 26 * 4 + 16) + nv * 16  # ids, 26 coefficients, flux; FP32 state once
+    edge32_bytes = ne * (24 + 4 * 4 + 8 + 16) + nv * 16  # ids, 4 stencil gaps, normal, flux; FP32 state once
     div32_bytes = (vnnz * 12 + ennz * 8 + nv * 8) + nv * (32 + 32 + 32 + 32 + 16) + ne * 16 + nv * 32
     # and the method's algorithmic bytes at p = 4 (compact edge form: 6 ids, 4
     # curve coordinates and n per edge; divergence tables (2J+K+2) p + 4 (J+K)
@@ -529,7 +529,8 @@ def run_ours(args):
             "stage": {"avg_ms": round(stage32_ms, 4), "algorithmic_bytes": int(edge32_alg + div32_alg),
                       "frac_hbm_algorithmic": round((edge32_alg + div32_alg) / (stage32_ms / 1e3) / 1e9 / hbm, 4)},
             "frac_hbm_note": "frac_hbm divides the kernel's own table bytes; frac_hbm_algorithmic the method's "
-                             "compact bytes (edge: 64 B per edge + 16 B per vertex; divergence: its stencil "
+                             "compact bytes (edge: 64 B per edge + 16 B per vertex, which the edge kernel's "
+                             "tables now are: ids, 4 stencil gaps and the normal; divergence: its stencil "
                              "tables, flux read, residual write and the stage's 80 B per vertex)",
         },
         "e2e": {"value": round(e2e_value, 3), "unit": "Mvertex/s", "h2d_bytes_per_step": nv * 32,

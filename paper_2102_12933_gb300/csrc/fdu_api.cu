@@ -60,7 +60,7 @@ struct fdu_mesh {
     // tables
     int32_t *sten = nullptr;          // [6][ne_act]
     double *coef64 = nullptr;         // [32][ne_act]
-    float *coef32 = nullptr;          // [6][ne_act] float4, then [ne_act] float2 (n_x, n_y)
+    float *coef32 = nullptr;          // [ne_act] float4 of stencil gaps, then [ne_act] float2 (n_x, n_y)
     // precision 48 (built on first use): double-word coefficient block
     // [kEdgeCoef][ne_act]; FP64 divergence tables with the left vertex flux
     // of each edge folded into the vertex weights; edge weights as double words
@@ -243,16 +243,14 @@ fdu_status upload_tables(fdu_mesh *m) {
     for (int64_t e = 0; e < ne; ++e) {
         const int64_t o = T.e_new2old[e];
         for (int i = 0; i < 6; ++i) sten[i * ne + e] = T.v_old2new[T.sten[6 * o + i]];
-        for (int c = 0; c < kEdgeCoef; ++c) {
-            coef[(size_t)c * ne + e] = T.coef[(size_t)kEdgeCoef * o + c];
-            // FP32 block: values 0..23 as float4 vectors [c/4][ne][c%4], then
-            // the normal as float2 vectors [ne][2] after the 6 x 4 x ne floats
-            const float v = (float)T.coef[(size_t)kEdgeCoef * o + c];
-            if (c < 4 * kEdgeCoef32Vec)
-                coef32[((size_t)(c / 4) * ne + e) * 4 + c % 4] = v;
-            else
-                coef32[(size_t)4 * kEdgeCoef32Vec * ne + 2 * e + (c - 4 * kEdgeCoef32Vec)] = v;
-        }
+        for (int c = 0; c < kEdgeCoef; ++c) coef[(size_t)c * ne + e] = T.coef[(size_t)kEdgeCoef * o + c];
+        // FP32 form: the gaps between consecutive stencil coordinates (the
+        // coordinates put L1 at -1/2 and R1 at 1/2), differenced in FP64, as
+        // one float4 [ne][4], then the normal as float2 [ne][2]
+        const double *xi = &T.xi[6 * (size_t)o];
+        const double gap[4] = {-0.5 - xi[1], xi[1] - xi[0], xi[4] - 0.5, xi[5] - xi[4]};
+        for (int c = 0; c < 4; ++c) coef32[4 * (size_t)e + c] = (float)gap[c];
+        for (int c = 0; c < 2; ++c) coef32[4 * (size_t)ne + 2 * e + c] = (float)T.coef[(size_t)kEdgeCoef * o + kCoefN + c];
     }
     if ((st = m->upload(m->sten, sten))) return st;
     if ((st = m->upload(m->coef64, coef))) return st;

@@ -34,10 +34,11 @@ constexpr int kCoefCL = 20;
 constexpr int kCoefCR = 22;
 constexpr int kCoefN = 24;
 constexpr int kEdgeCoef = 26;
-// FP32 copy: values 0..23 as six float4 per edge ([6][ne] float4), then
-// (n_x, n_y) as one float2 per edge ([ne] float2): 104 bytes, no padding
-constexpr int kEdgeCoef32 = 26;
-constexpr int kEdgeCoef32Vec = 6;  // float4 blocks before the normals
+// FP32 form: the edge's four stencil gaps as one float4 per edge ([ne]
+// float4: L1-L2, L2-L3, R1-R2, R2-R3 along the curve, each divided by the
+// arc length L1-R1), then (n_x, n_y) as one float2 per edge ([ne] float2):
+// 24 bytes.  The FP32 edge flux forms values 0..23 from the gaps.
+constexpr int kEdgeCoef32 = 6;  // floats per edge
 
 struct HostTables {
     int64_t nv = 0, nt = 0, ne = 0, n_real = 0;

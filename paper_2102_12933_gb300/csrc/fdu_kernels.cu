@@ -288,10 +288,11 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) 
 }
 
 // ================================================================== FP32 path
-// The FP32 residual reads an FP32 copy of the state and an FP32 copy of the
-// edge coefficient block (seven float4 per edge); weights, fluxes and sums
-// are FP32.  Reciprocals use the hardware approximation (rcp.approx, about
-// one ulp), well inside the FP32 path's error against FP64.
+// The FP32 residual reads an FP32 copy of the state and, per edge, its four
+// stencil gaps and normal (24 bytes), from which it forms the NU-WENO5
+// coefficients in registers; weights, fluxes and sums are FP32.  Reciprocals
+// use the hardware approximation (rcp.approx, about one ulp), well inside
+// the FP32 path's error against FP64.
 __device__ __forceinline__ float rcp32(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -369,6 +370,71 @@ __device__ __forceinline__ void weno_pair32(const float *k, float a, float b, fl
     dr = fmaf(r0, vd + c, fmaf(r1, vc, r2 * vb)) * rcp32(r0 + r1 + r2);
 }
 
+// NU-WENO5 coefficients of one edge in FP32 (Appendix: the sub-stencil
+// interpolants' values at the midpoint, their smoothness indicators, and
+// the linear weights that make the combination the degree-4 interpolant,
+// Eq. S5), in the order of the coefficient block (fdu_internal.h), from
+// the four gaps between consecutive stencil points along the curve, each
+// divided by the arc length L1-R1:
+//   a = L1-L2, b = L2-L3, c = R1-R2, d = R2-R3,
+// so that the left side's points are -(1/2+a+b), -(1/2+a), -1/2, 1/2,
+// 1/2+c and the right side's (mirrored) the same with (a, b, c) -> (c, d,
+// a).  A sub-stencil's Lagrange basis value at 0 of a point x_j is
+// x_a x_b / ((x_j - x_a)(x_j - x_b)) over its other two points, its slope
+// -(x_a + x_b) / (...) and its curvature 2 / (...); the smoothness
+// indicator (slope)^2 + (13/12)(2 curvature)^2 (unit spacing between L1
+// and R1) is kept as the quadratic form of the two differences.  The
+// linear weights have the closed forms
+//   C_0 = (1/2)(1/2+c) / ((1+a+b)(1+a+b+c)),
+//   C_2 = (1/2+a+b)(1/2+a) / ((1+a+b+c)(1+a+c)),   C_1 = 1 - C_0 - C_2
+// (ratios of degree-4 and sub-stencil Lagrange values), of which the block
+// keeps C_0/C_1 and C_2/C_1.  Every factor is a sum of positive gaps, so
+// no step cancels.
+constexpr float kT3 = 13.0f / 3.0f;  // (13/12) x 2^2
+// outer sub-stencil of a side (points -(1/2+a+b), -(1/2+a), -1/2): values
+// of its two outer points' differences and the indicator's form
+__device__ __forceinline__ void weno_outer32(float a, float b, float *k) {
+    const float ab = a + b;
+    const float r0 = rcp32(b * ab), r1 = -rcp32(a * b);
+    const float s0 = 1.0f + a, s1 = 1.0f + ab;
+    k[0] = 0.5f * (0.5f + a) * r0;
+    k[1] = 0.5f * (0.5f + ab) * r1;
+    k[2] = r0 * r0 * fmaf(s0, s0, kT3);
+    k[3] = 2.0f * r0 * r1 * fmaf(s0, s1, kT3);
+    k[4] = r1 * r1 * fmaf(s1, s1, kT3);
+}
+// C_0/C_1 and C_2/C_1 of a side from its gaps (a, b) and the far side's c
+__device__ __forceinline__ void weno_ratios32(float a, float b, float c, float *k) {
+    const float p = 1.0f + a + b, r = 1.0f + a + c;
+    const float n0r = 0.5f * (0.5f + c) * r, n2p = (0.5f + a + b) * (0.5f + a) * p;
+    const float ir = rcp32((p + c) * p * r - n0r - n2p);
+    k[0] = n0r * ir;
+    k[1] = n2p * ir;
+}
+__device__ __forceinline__ void weno_coef32(const float4 g, float *k) {
+    const float a = g.x, b = g.y, c = g.z, d = g.w;
+    weno_outer32(a, b, k);  // S_a
+    {                       // S_b: points -(1/2+a), -1/2, 1/2
+        const float r2 = rcp32(1.0f + a), r0 = rcp32(a * (1.0f + a));
+        k[5] = -0.25f * r0;
+        k[6] = 0.5f * (0.5f + a) * r2;
+        k[7] = kT3 * r0 * r0;
+        k[8] = 2.0f * kT3 * r0 * r2;
+        k[9] = fmaf(kT3 * r2, r2, 1.0f);
+    }
+    {  // S_c: points -1/2, 1/2, 1/2+c
+        const float r1 = -rcp32(c), r2 = rcp32(c * (1.0f + c));
+        k[10] = -0.5f * (0.5f + c) * r1;
+        k[11] = -0.25f * r2;
+        k[12] = fmaf(kT3 * r1, r1, 1.0f);
+        k[13] = 2.0f * kT3 * r1 * r2;
+        k[14] = kT3 * r2 * r2;
+    }
+    weno_outer32(c, d, k + 15);  // S_d
+    weno_ratios32(a, b, c, k + kCoefCL);
+    weno_ratios32(c, d, a, k + kCoefCR);
+}
+
 __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int64_t e) {
     const float4 *__restrict__ w = static_cast<const float4 *>(A.w);
     const float *__restrict__ g = static_cast<const float *>(A.coef);
@@ -378,24 +444,11 @@ __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int6
     int32_t s[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
-    // coefficient block: six float4 per edge ([c/4][ne] float4, component
-    // c%4) and the normal as one float2 ([ne] float2 after them)
-    const float4 *__restrict__ g4 = reinterpret_cast<const float4 *>(g);
-    float k[kEdgeCoef32];
-#pragma unroll
-    for (int i = 0; i < kEdgeCoef32Vec; ++i) {
-        const float4 q = __ldg(g4 + (int64_t)i * ne + e);
-        k[4 * i] = q.x;
-        k[4 * i + 1] = q.y;
-        k[4 * i + 2] = q.z;
-        k[4 * i + 3] = q.w;
-    }
-    {
-        const float2 q = __ldg(reinterpret_cast<const float2 *>(g + (int64_t)4 * kEdgeCoef32Vec * ne) + e);
-        k[kCoefN] = q.x;
-        k[kCoefN + 1] = q.y;
-    }
-    const float nx = k[kCoefN], ny = k[kCoefN + 1];
+    // the edge's stencil gaps ([ne] float4) and normal ([ne] float2 after them)
+    const float2 nq = __ldg(reinterpret_cast<const float2 *>(g + (int64_t)4 * ne) + e);
+    const float nx = nq.x, ny = nq.y;
+    float k[kCoefN];
+    weno_coef32(__ldg(reinterpret_cast<const float4 *>(g) + e), k);
     const float4 L1 = __ldg(w + s[2]), R1 = __ldg(w + s[3]);
     const Prim32 pL1 = prim32(L1, gm1), pR1 = prim32(R1, gm1);
     const Roe32 C = roe32(L1, pL1, R1, pR1, nx, ny, gm1);

@@ -368,6 +368,19 @@ fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n);
  * Roe weights): y[i] = 1/sqrt(x[i]) by Newton-Raphson refinement of the
  * hardware approximation, for host arrays of positive normal doubles. */
 fdu_status fdu_check_rsqrt64(int device, const double *x, double *y, int64_t n);
+/* Accuracy check of the FP32 path's NU-WENO5 coefficients (Appendix, Eqs.
+ * u0-u2, the smoothness indicators and the linear weights C_K; no
+ * counterpart in the paper as an entry point).  xi: host [n][6] stencil
+ * coordinates of n edges as fdu_get_edge_stencils returns them (L3, L2, L1,
+ * R1, R2, R3 along the curve, L1 = -1/2, R1 = 1/2, strictly increasing);
+ * k: host [n][24] output, the coefficient block the FP32 edge kernel forms
+ * in FP32 from the edge's four gaps, widened to double: per sub-stencil
+ * S_a (L3, L2 against L1), S_b (L2, R1 against L1), S_c (R1, R2 against L1)
+ * and S_d (R3, R2 against R1) its two value coefficients and the quadratic
+ * form (m0, m1, m2) of its smoothness indicator in the same two
+ * differences; then C_0/C_1 and C_2/C_1 of the left and of the right state.
+ * FDU_ERR_ARG for null pointers, n < 0 or coordinates out of order. */
+fdu_status fdu_check_weno_coef32(int device, const double *xi, double *k, int64_t n);
 /* Accuracy check of the double-word primitives of precision 48 (no
  * counterpart in the paper).  Host arrays x[n], y[n]; each value is split
  * into a double word as the precision-48 kernels split FP64 inputs, `op`

@@ -231,6 +231,14 @@ void sell_tables(const fdu_mesh *m, const std::vector<int32_t> &order, const dou
     }
 }
 
+// The FP32 edge form's four gaps from an edge's stencil coordinates (L1 at
+// -1/2, R1 at 1/2): L1-L2, L2-L3, R1-R2, R2-R3 as positive lengths,
+// differenced in FP64 and rounded once.
+void stencil_gaps(const double xi[6], float g[4]) {
+    const double d[4] = {-0.5 - xi[1], xi[1] - xi[0], xi[4] - 0.5, xi[5] - xi[4]};
+    for (int c = 0; c < 4; ++c) g[c] = (float)d[c];
+}
+
 // Pack host tables into device layouts.
 fdu_status upload_tables(fdu_mesh *m) {
     const HostTables &T = m->T;
@@ -247,9 +255,7 @@ fdu_status upload_tables(fdu_mesh *m) {
         // FP32 form: the gaps between consecutive stencil coordinates (the
         // coordinates put L1 at -1/2 and R1 at 1/2), differenced in FP64, as
         // one float4 [ne][4], then the normal as float2 [ne][2]
-        const double *xi = &T.xi[6 * (size_t)o];
-        const double gap[4] = {-0.5 - xi[1], xi[1] - xi[0], xi[4] - 0.5, xi[5] - xi[4]};
-        for (int c = 0; c < 4; ++c) coef32[4 * (size_t)e + c] = (float)gap[c];
+        stencil_gaps(&T.xi[6 * (size_t)o], &coef32[4 * (size_t)e]);
         for (int c = 0; c < 2; ++c) coef32[4 * (size_t)ne + 2 * e + c] = (float)T.coef[(size_t)kEdgeCoef * o + kCoefN + c];
     }
     if ((st = m->upload(m->sten, sten))) return st;
@@ -1705,6 +1711,35 @@ fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n) 
 
 fdu_status fdu_check_rsqrt64(int device, const double *x, double *y, int64_t n) {
     return check_special(device, x, y, n, 1);
+}
+
+fdu_status fdu_check_weno_coef32(int device, const double *xi, double *k, int64_t n) {
+    if (!xi || !k || n < 0) return set_err(FDU_ERR_ARG, "bad arguments");
+    std::vector<float> g(4 * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const double *x = xi + 6 * i;
+        if (x[2] != -0.5 || x[3] != 0.5 || !(x[0] < x[1] && x[1] < x[2] && x[3] < x[4] && x[4] < x[5]))
+            return set_err(FDU_ERR_ARG, "stencil coordinates of row " + std::to_string(i) +
+                                            " are not increasing with L1 = -1/2 and R1 = 1/2");
+        stencil_gaps(x, &g[4 * (size_t)i]);
+    }
+    if (n == 0) return FDU_OK;
+    CK(cudaSetDevice(device));
+    void *d = nullptr;
+    CK(cudaMalloc(&d, (size_t)n * (4 + kCoefN) * sizeof(float)));
+    float4 *dg = static_cast<float4 *>(d);
+    float *dk = reinterpret_cast<float *>(dg + n);
+    std::vector<float> kf((size_t)kCoefN * n);
+    cudaError_t e = cudaMemcpy(dg, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch_weno_coef32_check(dg, dk, n, nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(kf.data(), dk, kf.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return set_err(FDU_ERR_CUDA, std::string("coefficient check: ") + cudaGetErrorString(e));
+    for (size_t i = 0; i < kf.size(); ++i) k[i] = kf[i];
+    return FDU_OK;
 }
 
 fdu_status fdu_set_adjoint_precision(fdu_mesh *m, int precision) {

@@ -851,6 +851,16 @@ __global__ void recip_check_kernel(const double *x, double *y, int64_t n, int wh
     if (i < n) y[i] = which == 1 ? rsqrt64(x[i]) : recip64(x[i]);
 }
 
+// the FP32 edge kernel's coefficient block of n edges from their gaps
+__global__ void weno_coef32_check_kernel(const float4 *g, float *k, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float c[kCoefN];
+    weno_coef32(g[i], c);
+#pragma unroll
+    for (int j = 0; j < kCoefN; ++j) k[(int64_t)kCoefN * i + j] = c[j];
+}
+
 inline unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
@@ -999,6 +1009,10 @@ double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s) {
 
 void launch_recip_check(const double *x, double *y, int64_t n, int which, cudaStream_t s) {
     if (n > 0) recip_check_kernel<<<blocks(n, 256), 256, 0, s>>>(x, y, n, which);
+}
+
+void launch_weno_coef32_check(const float4 *g, float *k, int64_t n, cudaStream_t s) {
+    if (n > 0) weno_coef32_check_kernel<<<blocks(n, 256), 256, 0, s>>>(g, k, n);
 }
 
 void launch_dt_finalize(unsigned long long *slot, double *tstate, double cfl, double t_end,

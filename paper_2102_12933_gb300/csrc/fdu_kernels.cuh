@@ -88,6 +88,8 @@ double fma_probe_tflops(int precision, int sms, void *scratch, cudaStream_t s);
 // y[i] = the kernels' FP64 reciprocal (which = 0) or reciprocal square root
 // (which = 1) of x[i] (device pointers; accuracy check)
 void launch_recip_check(const double *x, double *y, int64_t n, int which, cudaStream_t s);
+// k[24 i + j] = value j of the FP32 edge kernel's NU-WENO5 block formed from gaps g[i]
+void launch_weno_coef32_check(const float4 *g, float *k, int64_t n, cudaStream_t s);
 // Adaptive step: dt = min(cfl * bound, t_end - t) from the reduced bound in
 // *slot (bit pattern of a positive double); tstate = (t, dt, nonphysical);
 // the slot is reset to +inf for the next reduction; *nsteps counts steps

@@ -33,7 +33,7 @@ EXPORTS = (
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
     "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
-    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_check_dw", "fdu_set_adjoint_precision", "fdu_mesh_create_cells", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
+    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_check_weno_coef32", "fdu_check_dw", "fdu_set_adjoint_precision", "fdu_mesh_create_cells", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
     "fdu_batch_max_dt", "fdu_batch_set_dt", "fdu_batch_rk_steps", "fdu_batch_set_launch", "fdu_batch_autotune",
     "fdu_batch_barrier_selftest", "fdu_residual_vjp", "fdu_rk_step_vjp", "fdu_adjoint_rk",
 )
@@ -108,6 +108,7 @@ def load():
         L.fdu_residual_noalloc.argtypes = [P, P, P, P]
         L.fdu_check_recip64.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_check_rsqrt64.argtypes = [C.c_int, dp, dp, i64]
+        L.fdu_check_weno_coef32.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_check_dw.argtypes = [C.c_int, C.c_int, dp, dp, dp, i64]
         L.fdu_set_adjoint_precision.argtypes = [C.c_void_p, C.c_int]
         L.fdu_mesh_create_cells.argtypes = [dp, i64, lp, ip, i64, C.c_int, C.POINTER(MeshOpts), C.POINTER(P)]
@@ -210,6 +211,15 @@ def check_recip64(x, device=0):
     y = np.zeros_like(x)
     _check(load().fdu_check_recip64(int(device), _dp(x), _dp(y), x.size))
     return y
+
+
+def check_weno_coef32(xi, device=0):
+    """The FP32 edge kernel's NU-WENO5 coefficient block [n, 24] formed from
+    stencil coordinates xi [n, 6] (accuracy check)."""
+    xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(-1, 6)
+    k = np.zeros((xi.shape[0], 24))
+    _check(load().fdu_check_weno_coef32(int(device), _dp(xi), _dp(k), xi.shape[0]))
+    return k
 
 
 DW_OPS = {"split": 0, "add": 1, "add_sloppy": 2, "mul": 3, "mul_unnormalised": 4, "recip": 5, "rsqrt": 6,

@@ -62,6 +62,12 @@ NCU_EDGE48_FMA_PIPE = 0.585
 NCU_EDGE48_FP64_PIPE = 0.141
 NCU_EDGE48_THREAD_INSTR_PER_EDGE = 97722617 * 32 / 480000
 TRAFFIC_EDGE48_B_PER_EDGE = (121.78432 + 6.677504) * 1e6 / 480000
+# edge_flux_f32 from one ncu capture on the 480k-edge case: issue slots busy,
+# FMA pipe busy, DRAM throughput (% of peak), DRAM bytes per edge.
+NCU_EDGE32_ISSUE_ACTIVE = 0.614
+NCU_EDGE32_FMA_PIPE = 0.505
+NCU_EDGE32_DRAM = 0.184
+TRAFFIC_EDGE32_B_PER_EDGE = (25.614336 + 0.0) * 1e6 / 480000
 
 
 def _peaks():
@@ -517,6 +523,10 @@ def run_ours(args):
             "value": round(value32, 3), "unit": "Mvertex/s", "speedup_vs_f64": round(value32 / value, 3),
             "error_vs_f64": err32,
             "edge_kernel": {"avg_launch_ms": round(e32_avg, 4),
+                            "bound": "FP32 issue (NU-WENO5 coefficients formed in registers)",
+                            "ncu_issue_active": NCU_EDGE32_ISSUE_ACTIVE, "ncu_fma_pipe": NCU_EDGE32_FMA_PIPE,
+                            "ncu_dram_throughput": NCU_EDGE32_DRAM,
+                            "traffic": round(TRAFFIC_EDGE32_B_PER_EDGE * ne), "traffic_unit": "bytes per launch",
                             "achieved_gbs": round(edge32_bytes / (e32_avg / 1e3) / 1e9, 1),
                             "frac_hbm": round(edge32_bytes / (e32_avg / 1e3) / 1e9 / hbm, 4),
                             "algorithmic_bytes": int(edge32_alg),

@@ -46,21 +46,23 @@ __device__ __forceinline__ bool pos64(double x) {
     return b > 0 && b <= 0x7FF0000000000000LL;
 }
 
-// Reciprocal of a positive normal double by Newton-Raphson iteration
-// y <- y + y (1 - x y), started from the hardware's approximate FP64
-// reciprocal (PTX rcp.approx.ftz.f64); two iterations bring the relative
-// error to the rounding level (checked against IEEE division by the tests).
+// Reciprocal of a positive normal double from the hardware's approximate
+// FP64 reciprocal y (PTX rcp.approx.ftz.f64) and one correction of third
+// order in its residual e = 1 - x y: 1/x = y / (1 - e) = y (1 + e + e^2) +
+// O(e^3), three FP64 operations.  With the approximation's relative error
+// e the truncation is below e^3, far under the rounding level for the
+// approximation's accuracy (the tests hold the result to 2 ulp of IEEE
+// division).
 __device__ __forceinline__ double recip64(double x) {
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    double e = fma(-x, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-x, y, 1.0);
-    return fma(y, e, y);
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 }
 
 // One Newton-Raphson step from the hardware approximation: relative error
-// near 2^-44, ample for quotients whose error is damped by a small
+// the square of the approximation's (about 2^-20 on GB300), so near 2^-40,
+// ample for quotients whose error is damped by a small
 // multiplier (the nonlinear WENO weights: an error d omega moves the
 // interpolant by d omega (v_k - v), and v_k - v is O(h^3)).
 __device__ __forceinline__ double recip64_fast(double x) {
@@ -70,19 +72,30 @@ __device__ __forceinline__ double recip64_fast(double x) {
     return fma(y, e, y);
 }
 
-// 1/sqrt(x) of a positive normal double by Newton-Raphson iteration for the
-// reciprocal square root, y <- y (3 - x y^2) / 2 = y + y (1/2 - (x/2) y^2),
-// started from the hardware's approximate FP64 reciprocal square root (PTX
-// rsqrt.approx.ftz.f64); two iterations bring the relative error to the
-// rounding level (checked against a quad-precision reference by the tests).
+// 1/sqrt(x) of a positive normal double from the hardware's approximate
+// FP64 reciprocal square root y (PTX rsqrt.approx.ftz.f64) and one
+// correction of third order in its residual e = 1 - x y^2, from the series
+// (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + O(e^3):
+//   1/sqrt(x) = y + (y e) (1/2 + 3e/8) + O(e^3),
+// five FP64 operations (checked against 1/sqrt(x) in extended precision by
+// the tests).
 __device__ __forceinline__ double rsqrt64(double x) {
     double y;
     asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-    const double h = 0.5 * x;
-    double e = fma(-h, y * y, 0.5);
-    y = fma(y, e, y);
-    e = fma(-h, y * y, 0.5);
-    return fma(y, e, y);
+    const double e = fma(-x, y * y, 1.0);
+    return fma(y * e, fma(0.375, e, 0.5), y);
+}
+
+// x / 2, exact, on the integer pipe where the exponent allows it: for a
+// normal x whose result is normal the exponent field drops by one; zero,
+// infinities and NaN are returned as they are (x / 2 is the same value);
+// only results below the normal range take the FP64 product.
+__device__ __forceinline__ double half64(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned ex = ((unsigned)hi >> 20) & 0x7FFu;
+    if (ex > 1u && ex < 0x7FFu) return __hiloint2double(hi - 0x00100000, lo);
+    if (ex == 0x7FFu || ((hi & 0x7FFFFFFF) | lo) == 0) return x;
+    return 0.5 * x;
 }
 
 // Per-state quantities reused by the Roe average and the physical flux.
@@ -124,14 +137,14 @@ __device__ __forceinline__ Roe64 roe64_from_records(const dbl4 &qa, const dbl4 &
     R.u = (qa.y + qb.y) * inv;
     R.v = (qa.z + qb.z) * inv;
     R.H = (qa.w + qb.w) * inv;
-    R.hq2 = 0.5 * (R.u * R.u + R.v * R.v);
+    R.hq2 = half64(R.u * R.u + R.v * R.v);
     const double c2 = gm1 * (R.H - R.hq2);
     R.ic = rsqrt64(c2);
     R.c = c2 * R.ic;
     const double ic2 = R.ic * R.ic;
     R.b1 = gm1 * ic2;
     R.b1h = hgm1 * ic2;  // hgm1 = (gamma - 1) / 2
-    R.ich = 0.5 * R.ic;
+    R.ich = half64(R.ic);
     R.nx = nx;
     R.ny = ny;
     R.qn = R.u * nx + R.v * ny;
@@ -148,14 +161,14 @@ __device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const db
     R.u = (a.y * pa.r + b.y * pb.r) * inv;
     R.v = (a.z * pa.r + b.z * pb.r) * inv;
     R.H = ((a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r) * inv;
-    R.hq2 = 0.5 * (R.u * R.u + R.v * R.v);
+    R.hq2 = half64(R.u * R.u + R.v * R.v);
     const double c2 = gm1 * (R.H - R.hq2);
     R.ic = rsqrt64(c2);
     R.c = c2 * R.ic;
     const double ic2 = R.ic * R.ic;
     R.b1 = gm1 * ic2;
     R.b1h = hgm1 * ic2;  // hgm1 = (gamma - 1) / 2
-    R.ich = 0.5 * R.ic;
+    R.ich = half64(R.ic);
     R.nx = nx;
     R.ny = ny;
     R.qn = R.u * nx + R.v * ny;

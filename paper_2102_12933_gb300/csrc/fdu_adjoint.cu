@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     const dbl4 lam = ld4v(A.lam_r, e);
 
     // ---------------- forward
-    const Prim64 pL1 = prim64(L1, gm1, hgm1), pR1 = prim64(R1, gm1, hgm1);
+    const Prim64 pL1 = prim64(L1, gm1), pR1 = prim64(R1, gm1);
     const Roe64 C = roe64(L1, pL1, R1, pR1, nx, ny, gm1, hgm1);
     const dbl4 dM = sub4(R1, L1), dL2 = sub4(W1, L1), dL3 = sub4(W0, L1), dR2 = sub4(W4, R1), dR3 = sub4(W5, R1);
     const dbl4 cM = project64(C, dM), cL2 = project64(C, dL2), cL3 = project64(C, dL3), cR2 = project64(C, dR2),
@@ -357,8 +357,8 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     Prim64 pl, pr;
     bool ok = pos64(wl.x) && pos64(wr.x);
     if (ok) {
-        pl = prim64(wl, gm1, hgm1);
-        pr = prim64(wr, gm1, hgm1);
+        pl = prim64(wl, gm1);
+        pr = prim64(wr, gm1);
         ok = pos64(pl.p) && pos64(pr.p);
     }
     if (!ok) {

@@ -86,16 +86,15 @@ __device__ __forceinline__ double rsqrt64(double x) {
     return fma(y * e, fma(0.375, e, 0.5), y);
 }
 
-// x / 2, exact, on the integer pipe where the exponent allows it: for a
-// normal x whose result is normal the exponent field drops by one; zero,
-// infinities and NaN are returned as they are (x / 2 is the same value);
-// only results below the normal range take the FP64 product.
+// x / 2 on the integer pipe, without a branch: for a normal x whose half is
+// normal the exponent field drops by one (exact); infinities and NaN are
+// returned as they are; zero, and the halves below the normal range
+// (|x| < 2^-1021), become a zero of x's sign.
 __device__ __forceinline__ double half64(double x) {
     const int hi = __double2hiint(x), lo = __double2loint(x);
     const unsigned ex = ((unsigned)hi >> 20) & 0x7FFu;
-    if (ex > 1u && ex < 0x7FFu) return __hiloint2double(hi - 0x00100000, lo);
-    if (ex == 0x7FFu || ((hi & 0x7FFFFFFF) | lo) == 0) return x;
-    return 0.5 * x;
+    const int h2 = ex > 1u ? (ex < 0x7FFu ? hi - 0x00100000 : hi) : (int)((unsigned)hi & 0x80000000u);
+    return __hiloint2double(h2, ex > 1u ? lo : 0);
 }
 
 // Per-state quantities reused by the Roe average and the physical flux.
@@ -104,20 +103,12 @@ struct Prim64 {
     double ir;  // 1/rho
     double p;   // pressure
 };
+// p = (gamma - 1) (E - (|m|^2 / 2) / rho), the halving on the integer pipe.
 __device__ __forceinline__ Prim64 prim64(const dbl4 &w, double gm1) {
     Prim64 q;
     q.r = rsqrt64(w.x);
     q.ir = q.r * q.r;
-    q.p = gm1 * (w.w - 0.5 * (w.y * w.y + w.z * w.z) * q.ir);
-    return q;
-}
-// The same with hgm1 = (gamma - 1) / 2 given: p = (gamma - 1) E - hgm1 |m|^2 / rho,
-// one product fewer.
-__device__ __forceinline__ Prim64 prim64(const dbl4 &w, double gm1, double hgm1) {
-    Prim64 q;
-    q.r = rsqrt64(w.x);
-    q.ir = q.r * q.r;
-    q.p = fma(-(hgm1 * fma(w.z, w.z, w.y * w.y)), q.ir, gm1 * w.w);
+    q.p = gm1 * fma(-half64(fma(w.z, w.z, w.y * w.y)), q.ir, w.w);
     return q;
 }
 
@@ -158,9 +149,11 @@ __device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const db
     const double sa = a.x * pa.r, sb = b.x * pb.r;
     const double inv = recip64(sa + sb);
     R.inv = inv;
-    R.u = (a.y * pa.r + b.y * pb.r) * inv;
-    R.v = (a.z * pa.r + b.z * pb.r) * inv;
-    R.H = ((a.w + pa.p) * pa.r + (b.w + pb.p) * pb.r) * inv;
+    // the sides' weights r / (sqrt(rho_a) + sqrt(rho_b)) formed once
+    const double ra = pa.r * inv, rb = pb.r * inv;
+    R.u = fma(a.y, ra, b.y * rb);
+    R.v = fma(a.z, ra, b.z * rb);
+    R.H = fma(a.w + pa.p, ra, (b.w + pb.p) * rb);
     R.hq2 = half64(R.u * R.u + R.v * R.v);
     const double c2 = gm1 * (R.H - R.hq2);
     R.ic = rsqrt64(c2);
@@ -182,7 +175,8 @@ __device__ __forceinline__ Roe64 roe64(const dbl4 &a, const Prim64 &pa, const db
 // phi/2 and psi/2 are formed directly (factors b1/2, ic/2), so the four
 // fields cost no separate halving.
 __device__ __forceinline__ dbl4 project64(const Roe64 &R, const dbl4 &d) {
-    const double phh = R.b1h * (R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w);
+    // d.w starts the chain, so the four terms take three fused multiply-adds
+    const double phh = R.b1h * fma(-R.v, d.z, fma(-R.u, d.y, fma(R.hq2, d.x, d.w)));
     const double psh = (R.qn * d.x - R.nx * d.y - R.ny * d.z) * R.ich;
     return dbl4_make(phh + psh, fma(-2.0, phh, d.x), R.nx * d.z - R.ny * d.y - R.qt * d.x, phh - psh);
 }

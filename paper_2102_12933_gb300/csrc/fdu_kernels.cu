@@ -46,7 +46,7 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
     // characteristic decomposition at the Roe average of the end states
     // (per-vertex Roe records when the stage kernel provided them)
     const Roe64 C = A.Q ? roe64_from_records(ld4v(A.Q, s[2]), ld4v(A.Q, s[3]), nx, ny, gm1, hgm1)
-                        : roe64(L1, prim64(L1, gm1, hgm1), R1, prim64(R1, gm1, hgm1), nx, ny, gm1, hgm1);
+                        : roe64(L1, prim64(L1, gm1), R1, prim64(R1, gm1), nx, ny, gm1, hgm1);
     const dbl4 cM = project64(C, sub4(R1, L1));               // R1 - L1
     const dbl4 cL2 = project64(C, sub4(ld4v(w, s[1]), L1));    // L2 - L1
     const dbl4 cL3 = project64(C, sub4(ld4v(w, s[0]), L1));    // L3 - L1
@@ -69,15 +69,15 @@ __device__ __forceinline__ void edge_flux_f64_body(const EdgeArgs &A, const int6
     Prim64 pl, pr;
     bool ok = pos64(wl.x) && pos64(wr.x);
     if (ok) {
-        pl = prim64(wl, gm1, hgm1);
-        pr = prim64(wr, gm1, hgm1);
+        pl = prim64(wl, gm1);
+        pr = prim64(wr, gm1);
         ok = pos64(pl.p) && pos64(pr.p);
     }
     if (!ok) {  // positivity fallback: first-order end states
         wl = L1;
         wr = R1;
-        pl = prim64(L1, gm1, hgm1);
-        pr = prim64(R1, gm1, hgm1);
+        pl = prim64(L1, gm1);
+        pr = prim64(R1, gm1);
         atomicAdd(A.fallback, 1ull);
     }
 

@@ -25,8 +25,14 @@ namespace fdu {
 namespace {
 using namespace dev;
 
+// Cotangent accumulators start at -0.0, the additive identity of IEEE
+// arithmetic (-0 + x = x for every x, while +0 + -0 = +0), so the compiler
+// drops the first addition into each instead of issuing it on the FP64 pipe.
+constexpr double kNZ = -0.0;
+__device__ __forceinline__ dbl4 nz4() { return dbl4_make(kNZ, kNZ, kNZ, kNZ); }
+
 struct Prim64Bar {
-    double r = 0, ir = 0, p = 0;
+    double r = kNZ, ir = kNZ, p = kNZ;
 };
 // Cotangents of a Roe64.  The projections' parts through b1h and ich are
 // kept as the raw sums sphi = sum phh_bar (c.x + c.w) and spsi = sum psh_bar
@@ -35,7 +41,7 @@ struct Prim64Bar {
 // ich = ic / 2, sum phh_bar phh / b1h * d b1h / d ic = c sphi and sum psh_bar
 // psh / ich * d ich / d ic = c spsi / 2.
 struct Roe64Bar {
-    double u = 0, v = 0, H = 0, c = 0, qn = 0, qt = 0, hq2 = 0, sphi = 0, spsi = 0;
+    double u = kNZ, v = kNZ, H = kNZ, c = kNZ, qn = kNZ, qt = kNZ, hq2 = kNZ, sphi = kNZ, spsi = kNZ;
 };
 
 __device__ __forceinline__ void add_to(dbl4 &a, const dbl4 &b) {
@@ -245,8 +251,8 @@ __device__ __forceinline__ dbl4 vertex_flux_vjp(const dbl4 &w, double gm1, const
     const double ir = recip64(w.x);  // within 2 ulp of 1 / rho, without the FP64 division sequence
     const double u = w.y * ir, v = w.z * ir;
     const double p = gm1 * (w.w - 0.5 * (w.y * u + w.z * v));
-    dbl4 wb = dbl4_make(0, 0, 0, 0);
-    double ub = 0, vb = 0, pb = 0;
+    dbl4 wb = nz4();
+    double ub = kNZ, vb = kNZ, pb = kNZ;
     // f = (m_x, m_x u + p, m_y u, (E + p) u)
     wb.y += fb.x + fb.y * u;
     ub += fb.y * w.y + fb.z * w.z + fb.w * (w.w + p);
@@ -398,11 +404,11 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     const dbl4 sv = dbl4_make(nu_m * a.x, nu_u * a.y, nu_u * a.z, nu_p * a.w);
 
     // ---------------- reverse
-    dbl4 wlb = dbl4_make(0, 0, 0, 0), wrb = dbl4_make(0, 0, 0, 0);
+    dbl4 wlb = nz4(), wrb = nz4();
     Prim64Bar plb, prb;
     fluxn_vjp(wl, pl, nx, ny, lam, wlb, plb);
     Roe64Bar Qb;
-    dbl4 svb = dbl4_make(0, 0, 0, 0);
+    dbl4 svb = nz4();
     unproject64_vjp(Q, sv, lam, svb, Qb);
     const dbl4 ab = dbl4_make(nu_m * svb.x, nu_u * svb.y, nu_u * svb.z, nu_p * svb.w);
     const double nmb = a.x * svb.x, nub = a.y * svb.y + a.z * svb.z, npb = a.w * svb.w;
@@ -410,7 +416,7 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     const double deltab = nub * hu + nmb * hm + npb * hp;
     Qb.qn += lub + lmb + lpb;
     Qb.c += lpb - lmb + 0.1 * deltab;
-    dbl4 dwb = dbl4_make(0, 0, 0, 0);
+    dbl4 dwb = nz4();
     project64_vjp(Q, dw, a, ab, dwb, Qb);
     add_to(wrb, dwb);
     wlb = sub4(wlb, dwb);
@@ -418,10 +424,10 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     prim64_vjp(wl, pl, plb, gm1, wlb);
     prim64_vjp(wr, pr, prb, gm1, wrb);
 
-    dbl4 G0 = dbl4_make(0, 0, 0, 0), G1 = G0, GL1 = wlb, GR1 = wrb, G4 = G0, G5 = G0;
+    dbl4 G0 = nz4(), G1 = G0, GL1 = wlb, GR1 = wrb, G4 = G0, G5 = G0;
     if (ok) {
         Roe64Bar Cb;
-        dbl4 dlb = dbl4_make(0, 0, 0, 0), drb = dbl4_make(0, 0, 0, 0);
+        dbl4 dlb = nz4(), drb = nz4();
         unproject64_vjp(C, dl, wlb, dlb, Cb);
         unproject64_vjp(C, dr, wrb, drb, Cb);
         dbl4 cL3b, cL2b, cMb, cR2Lb, cR3b, cR2b;
@@ -442,7 +448,7 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
                         cR2Lb.w, cR3b.w, cR2b.w);
         add_to(cR2b, cR2Lb);
         add_to(cMb, cR2Lb);
-        dbl4 dMb = dbl4_make(0, 0, 0, 0), dL2b = dMb, dL3b = dMb, dR2b = dMb, dR3b = dMb;
+        dbl4 dMb = nz4(), dL2b = dMb, dL3b = dMb, dR2b = dMb, dR3b = dMb;
         project64_vjp(C, dM, cM, cMb, dMb, Cb);
         project64_vjp(C, dL2, cL2, cL2b, dL2b, Cb);
         project64_vjp(C, dL3, cL3, cL3b, dL3b, Cb);

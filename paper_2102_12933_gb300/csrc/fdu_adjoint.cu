@@ -53,10 +53,11 @@ __device__ __forceinline__ void add_to(dbl4 &a, const dbl4 &b) {
 
 // w -> (r = rho^-1/2, ir = 1/rho = r^2, p = (gamma - 1) E - (gamma - 1)/2 |m|^2 ir)
 __device__ __forceinline__ void prim64_vjp(const dbl4 &w, const Prim64 &P, const Prim64Bar &B, double gm1, dbl4 &wb) {
+    // the factors 1/2 and 2 are applied to the exponent field (half64, twice64)
     const double pg = B.p * gm1;
-    const double irb = fma(-0.5 * pg, fma(w.y, w.y, w.z * w.z), B.ir);
-    const double rb = fma(2.0 * P.r, irb, B.r);
-    wb.x = fma(rb, -0.5 * P.ir * P.r, wb.x);  // d r / d rho = -r^3 / 2
+    const double irb = fma(-half64(pg), fma(w.y, w.y, w.z * w.z), B.ir);
+    const double rb = fma(twice64(P.r), irb, B.r);
+    wb.x = fma(rb, -(half64(P.ir) * P.r), wb.x);  // d r / d rho = -r^3 / 2
     const double t = pg * P.ir;
     wb.y = fma(-t, w.y, wb.y);
     wb.z = fma(-t, w.z, wb.z);
@@ -75,7 +76,7 @@ __device__ __forceinline__ void roe64_vjp(const dbl4 &a, const Prim64 &pa, const
     double ub = Rb.u + Rb.qn * R.nx - Rb.qt * R.ny;
     double vb = Rb.v + Rb.qn * R.ny + Rb.qt * R.nx;
     const double icb = R.c * fma(0.5, Rb.spsi, Rb.sphi);
-    const double c2b = 0.5 * R.ic * fma(-icb, R.ic * R.ic, Rb.c);
+    const double c2b = R.ich * fma(-icb, R.ic * R.ic, Rb.c);  // ich = ic / 2
     const double Hb = Rb.H + c2b * gm1;
     const double hq2b = Rb.hq2 - c2b * gm1;
     ub += hq2b * R.u;
@@ -250,7 +251,7 @@ __device__ __forceinline__ void fluxn_vjp(const dbl4 &w, const Prim64 &P, double
 __device__ __forceinline__ dbl4 vertex_flux_vjp(const dbl4 &w, double gm1, const dbl4 &fb, const dbl4 &gb) {
     const double ir = recip64(w.x);  // within 2 ulp of 1 / rho, without the FP64 division sequence
     const double u = w.y * ir, v = w.z * ir;
-    const double p = gm1 * (w.w - 0.5 * (w.y * u + w.z * v));
+    const double p = gm1 * (w.w - half64(w.y * u + w.z * v));
     dbl4 wb = nz4();
     double ub = kNZ, vb = kNZ, pb = kNZ;
     // f = (m_x, m_x u + p, m_y u, (E + p) u)
@@ -266,7 +267,7 @@ __device__ __forceinline__ dbl4 vertex_flux_vjp(const dbl4 &w, double gm1, const
     pb += gb.z + gb.w * v;
     wb.w += gb.w * v;
     // p = gm1 (E - |m|^2 / (2 rho))
-    wb.x += pb * gm1 * 0.5 * (u * u + v * v);
+    wb.x += pb * gm1 * half64(u * u + v * v);
     wb.y += -pb * gm1 * u;
     wb.z += -pb * gm1 * v;
     wb.w += pb * gm1;

@@ -97,6 +97,21 @@ __device__ __forceinline__ double half64(double x) {
     return __hiloint2double(h2, ex > 1u ? lo : 0);
 }
 
+// 2 x on the integer pipe, exact, without a branch: a normal x below the top
+// binade gains one in its exponent field; a subnormal x (exponent field 0)
+// doubles by shifting its significand; the top binade overflows to
+// infinity; infinities and NaN are returned as they are.
+__device__ __forceinline__ double twice64(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFULL;
+    const unsigned ex = (unsigned)(mag >> 52);
+    const unsigned long long r = ex == 0u      ? mag << 1
+                                 : ex < 0x7FEu ? mag + (1ULL << 52)
+                                 : ex == 0x7FEu ? 0x7FF0000000000000ULL
+                                                : mag;
+    return __longlong_as_double((long long)(r | (b & 0x8000000000000000ULL)));
+}
+
 // Per-state quantities reused by the Roe average and the physical flux.
 struct Prim64 {
     double r;   // rho^-1/2

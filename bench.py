@@ -46,14 +46,14 @@ FLOP_DIV64_PER_EENTRY = 8
 FLOP_DIV64_FIXED = 70
 FP64_PEAK_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor), NVIDIA datasheet figure
 # DRAM bytes per edge of edge_flux_f64 from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum = 121.7 + 7.4 MB on the 480k-edge case of the same
+# dram__bytes_write.sum = 121.7 + 7.3 MB on the 480k-edge case of the same
 # workload, scaled per edge); None once the kernel changes after the capture.
-TRAFFIC_EDGE64_B_PER_EDGE = (121.73824 + 7.38688) * 1e6 / 480000
+TRAFFIC_EDGE64_B_PER_EDGE = (121.745408 + 7.27552) * 1e6 / 480000
 # From the same capture: FP64 pipe busy (sm__pipe_fp64_cycles_active, % of
 # active cycles) and executed FP64 thread instructions (DADD + DFMA + DMUL)
 # per edge of edge_flux_f64.
-NCU_EDGE64_FP64_PIPE_BUSY = 0.8964
-NCU_EDGE64_FP64_INSTR_PER_EDGE = (27980077 + 113280000 + 76120154) / 480000
+NCU_EDGE64_FP64_PIPE_BUSY = 0.8983
+NCU_EDGE64_FP64_INSTR_PER_EDGE = 448.9  # 54.3 DADD + 240.0 DFMA + 154.6 DMUL
 # edge_flux_dw (precision 48) from one ncu capture on the 480k-edge case:
 # issue slots busy, FMA (FP32) pipe busy, FP64 pipe busy (% of active
 # cycles), thread instructions per edge, DRAM bytes per edge.

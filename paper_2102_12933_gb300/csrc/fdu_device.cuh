@@ -267,11 +267,13 @@ __device__ __forceinline__ void weno_pair64_l1(const double *k, double a, double
     // left: (C0 bb bc va + ba bc vb + C2 ba bb vc) / (C0 bb bc + ba bc + C2 ba bb)
     // with bc factored from the first two terms; right: (D0 bb bc vd' + bd bb vc
     // + D2 bd bc vb) / (D0 bb bc + bd bb + D2 bd bc) with bb factored from the
-    // first two (one product fewer per field than the term-by-term sums)
+    // first two (one product fewer per field than the term-by-term sums); vd' =
+    // vd + c is formed with c inside its fused multiply-adds (W.vd is not used)
     const double g = k[20] * W.bb, m = k[21] * (W.ba * W.bb);
     dl = fma(W.bc, fma(g, W.va, W.ba * W.vb), m * W.vc) * recip64_fast(fma(W.bc, g + W.ba, m));
     const double s = k[22] * W.bc, q = k[23] * (W.bd * W.bc);
-    dr = fma(W.bb, fma(s, W.vd + c, W.bd * W.vc), q * W.vb) * recip64_fast(fma(W.bb, s + W.bd, q));
+    const double vdc = fma(k[15], e, fma(k[16], f, c));
+    dr = fma(W.bb, fma(s, vdc, W.bd * W.vc), q * W.vb) * recip64_fast(fma(W.bb, s + W.bd, q));
 }
 
 }  // namespace dev

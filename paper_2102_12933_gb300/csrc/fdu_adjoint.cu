@@ -20,6 +20,7 @@
 #include "fdu_adjoint.cuh"
 #include "fdu_device.cuh"
 #include "fdu_internal.h"
+#include "fdu_kernels.cuh"
 
 namespace fdu {
 namespace {
@@ -479,16 +480,20 @@ __global__ void __launch_bounds__(kVjpBlock) edge_flux_vjp_kernel(AdjEdgeArgs A)
     st4(G, 5 * ne + e, G5);
 }
 
-// lam_r[k] = -sum_v we_vk lam_v (CSR over edges; the table holds -we)
+// lam_r[k] = -sum_v we_vk lam_v (the table holds -we).  Thread i serves edge
+// perm[i]; its list is lane i % 32 of SELL-32 slice i / 32 (entry j at
+// off[slice] + 32 j + lane, padding with weight 0).
 __global__ void adj_edge_lambda_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ vid,
                                        const double *__restrict__ wt, const int32_t *__restrict__ perm,
                                        const double *__restrict__ lam, double *__restrict__ lam_r, int64_t ne) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
-    const int64_t k = perm ? (int64_t)__ldg(perm + i) : i;
+    const int64_t k = __ldg(perm + i);
+    const int64_t sl = i / kSell;
     dbl4 acc = dbl4_make(0, 0, 0, 0);
+    const int64_t end = __ldg(off + sl + 1);
 #pragma unroll 4
-    for (int64_t p = __ldg(off + k); p < __ldg(off + k + 1); ++p) {
+    for (int64_t p = __ldg(off + sl) + i % kSell; p < end; p += kSell) {
         const double a = __ldg(wt + p);
         const dbl4 l = ld4v(lam, __ldg(vid + p));
         acc.x = fma(a, l.x, acc.x);
@@ -501,29 +506,39 @@ __global__ void adj_edge_lambda_kernel(const int64_t *__restrict__ off, const in
 
 // grad[j] = (df/dw)^T lam_f + (dg/dw)^T lam_g with lam_f = -sum_v wf_vj lam_v
 // (the table holds -wf, -wg; the centre weights are included as the entry
-// v = j), then + sum of the edge-flux
-// slot cotangents G[slot][k] over the stencil slots that hold j.
+// v = j), then + sum of the edge-flux slot cotangents G[slot][k] over the
+// stencil slots that hold j.  Thread i serves vertex perm[i]; both lists are
+// SELL-32 like the edge transpose's (padding: weight 0 on j itself, and the
+// zero record of G).
 __global__ void adj_vertex_kernel(AdjVertexArgs A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.nv) return;
-    const int64_t j = A.perm ? (int64_t)__ldg(A.perm + i) : i;
+    const int64_t j = __ldg(A.perm + i);
+    const int64_t sl = i / kSell;
+    const int lane = (int)(i % kSell);
     dbl4 lf = dbl4_make(0, 0, 0, 0), lg = lf;
+    {
+        const int64_t end = __ldg(A.voff + sl + 1);
 #pragma unroll 4
-    for (int64_t p = __ldg(A.voff + j); p < __ldg(A.voff + j + 1); ++p) {
-        const double a = __ldg(A.wf + p), b = __ldg(A.wg + p);
-        const dbl4 l = ld4v(A.lam, __ldg(A.vid + p));
-        lf.x = fma(a, l.x, lf.x);
-        lf.y = fma(a, l.y, lf.y);
-        lf.z = fma(a, l.z, lf.z);
-        lf.w = fma(a, l.w, lf.w);
-        lg.x = fma(b, l.x, lg.x);
-        lg.y = fma(b, l.y, lg.y);
-        lg.z = fma(b, l.z, lg.z);
-        lg.w = fma(b, l.w, lg.w);
+        for (int64_t p = __ldg(A.voff + sl) + lane; p < end; p += kSell) {
+            const double a = __ldg(A.wf + p), b = __ldg(A.wg + p);
+            const dbl4 l = ld4v(A.lam, __ldg(A.vid + p));
+            lf.x = fma(a, l.x, lf.x);
+            lf.y = fma(a, l.y, lf.y);
+            lf.z = fma(a, l.z, lf.z);
+            lf.w = fma(a, l.w, lf.w);
+            lg.x = fma(b, l.x, lg.x);
+            lg.y = fma(b, l.y, lg.y);
+            lg.z = fma(b, l.z, lg.z);
+            lg.w = fma(b, l.w, lg.w);
+        }
     }
     dbl4 g = vertex_flux_vjp(ld4v(A.w, j), A.gm1, lf, lg);
+    {
+        const int64_t end = __ldg(A.soff + sl + 1);
 #pragma unroll 4
-    for (int64_t p = __ldg(A.soff + j); p < __ldg(A.soff + j + 1); ++p) add_to(g, ld4v(A.G, __ldg(A.slot + p)));
+        for (int64_t p = __ldg(A.soff + sl) + lane; p < end; p += kSell) add_to(g, ld4v(A.G, __ldg(A.slot + p)));
+    }
     st4(A.grad, j, g);
 }
 

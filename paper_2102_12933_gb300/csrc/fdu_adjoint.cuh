@@ -13,7 +13,7 @@ struct AdjEdgeArgs {
     const double *w;      // [nv][4] state the residual is linearised at
     const double *lam_r;  // [ne][4] cotangent of the edge fluxes (read by the VJP kernel)
     double *lam_r_mut;    // the same buffer, written by the transpose gather
-    double *G;            // [6][ne][4] cotangents of the stencil states, per slot
+    double *G;            // [6][ne][4] cotangents of the stencil states, per slot, then one zero record
     int64_t ne;
     double gm1, eps;
     // precision 48 (double-word edge VJP, fdu_adjoint_dw.cu)
@@ -24,29 +24,33 @@ struct AdjEdgeArgs {
 };
 
 // Edge transpose: for each active edge, the vertices whose divergence
-// stencil holds it and the weights w_k.
+// stencil holds it and the weights w_k, in SELL-32 form over the threads:
+// thread i serves edge eperm[i], its entry j sits at eoff[i / 32] + 32 j +
+// i % 32, and a slice's lists are padded to its longest with weight 0.
 struct AdjTables {
-    const int64_t *eoff;  // [ne+1]
+    const int64_t *eoff;  // [ceil(ne / 32) + 1] slice offsets
     const int32_t *evid;
     const double *ewt;    // -w_k: the residual's minus sign carried by the weights
-    const int32_t *eperm; // [ne] edge of each thread (list-length order inside windows)
+    const int32_t *eperm; // [ne] edge of each thread (list-length order inside windows of 256)
 };
 
 // Per-vertex part: vertex transpose (wf, wg of every stencil that holds the
-// vertex, centre weights as the vertex's own entry) and stencil incidence.
+// vertex, centre weights as the vertex's own entry) and stencil incidence,
+// both in SELL-32 form over the threads like AdjTables (padding: weight 0 on
+// the vertex itself; slot 6 ne, the zero record of G).
 struct AdjVertexArgs {
     int64_t nv;
-    const int64_t *voff;  // [nv+1]
+    const int64_t *voff;  // [ceil(nv / 32) + 1] slice offsets
     const int32_t *vid;
     const double *wf, *wg;  // -wf, -wg (and minus the centre weights at v = j)
     const double *lam;    // [nv][4] cotangent of the residual
     const double *w;      // [nv][4] state
     double gm1;
-    const int64_t *soff;  // [nv+1] stencil incidence
+    const int64_t *soff;  // [ceil(nv / 32) + 1] slice offsets of the stencil incidence
     const int64_t *slot;  // index slot * ne + k into G
     const double *G;
     double *grad;         // [nv][4] output
-    const int32_t *perm;  // [nv] vertex of each thread (list-length order inside windows)
+    const int32_t *perm;  // [nv] vertex of each thread (list-length order inside windows of 256)
 };
 
 // The double-word edge-flux VJP (precision 48) of the same edge flux.

@@ -628,15 +628,6 @@ fdu_status adjoint_setup(fdu_mesh *m) {
     for (int64_t k = 0; k < ne; ++k)
         for (int i = 0; i < 6; ++i) slot[sf[T.v_old2new[T.sten[6 * (int64_t)T.e_new2old[k] + i]]]++] = i * ne + k;
     fdu_status st;
-    if ((st = m->upload(m->adj_eoff, ecnt))) return st;
-    if ((st = m->upload(m->adj_evid, evid))) return st;
-    if ((st = m->upload(m->adj_ewt, ewt))) return st;
-    if ((st = m->upload(m->adj_voff, vcnt))) return st;
-    if ((st = m->upload(m->adj_vvid, vvid))) return st;
-    if ((st = m->upload(m->adj_wf, wf))) return st;
-    if ((st = m->upload(m->adj_wg, wg))) return st;
-    if ((st = m->upload(m->adj_soff, scnt))) return st;
-    if ((st = m->upload(m->adj_slot, slot))) return st;
     // the transpose kernels give one thread a list (edges: the stencils that
     // hold the edge; vertices: the stencils and stencil slots that hold the
     // vertex); inside windows of 256 consecutive ids the threads are ordered
@@ -649,14 +640,79 @@ fdu_status adjoint_setup(fdu_mesh *m) {
                              [&](int32_t a, int32_t b) { return len(a) > len(b); });
         return perm;
     };
-    if ((st = m->upload(m->adj_eperm, window_order(ne, [&](int64_t k) { return ecnt[k + 1] - ecnt[k]; }))))
-        return st;
-    if ((st = m->upload(m->adj_vperm, window_order(nv, [&](int64_t v) {
-             return (vcnt[v + 1] - vcnt[v]) * 8 + (scnt[v + 1] - scnt[v]) * 4;  // FP64 work of each list
-         }))))
-        return st;
+    const std::vector<int32_t> eperm = window_order(ne, [&](int64_t k) { return ecnt[k + 1] - ecnt[k]; });
+    const std::vector<int32_t> vperm = window_order(nv, [&](int64_t v) {
+        return (vcnt[v + 1] - vcnt[v]) * 8 + (scnt[v + 1] - scnt[v]) * 4;  // FP64 work of each list
+    });
+    // The lists in SELL-32 form, in thread order: slice s holds the lists of
+    // threads 32 s .. 32 s + 31, entry j of lane l at off[s] + 32 j + l, every
+    // list of a slice padded to the slice's longest (a warp's table loads are
+    // then contiguous).  sell_fill calls put(dst, thread item, entry index, or
+    // -1 for padding).
+    auto sell_offsets = [](int64_t n, const std::vector<int32_t> &perm, const std::vector<int64_t> &csr) {
+        const int64_t ns = (n + kSell - 1) / kSell;
+        std::vector<int64_t> off(ns + 1, 0);
+        for (int64_t sl = 0; sl < ns; ++sl) {
+            int64_t mx = 0;
+            for (int64_t i = sl * kSell; i < std::min(n, (sl + 1) * kSell); ++i)
+                mx = std::max(mx, csr[perm[i] + 1] - csr[perm[i]]);
+            off[sl + 1] = off[sl] + mx * kSell;
+        }
+        return off;
+    };
+    auto sell_fill = [](int64_t n, const std::vector<int32_t> &perm, const std::vector<int64_t> &csr,
+                        const std::vector<int64_t> &off, const std::function<void(int64_t, int32_t, int64_t)> &put) {
+        for (int64_t sl = 0; sl + 1 < (int64_t)off.size(); ++sl) {
+            const int64_t len = (off[sl + 1] - off[sl]) / kSell;
+            for (int64_t lane = 0; lane < kSell; ++lane) {
+                const int64_t i = sl * kSell + lane;
+                const int32_t item = i < n ? perm[i] : 0;
+                const int64_t cnt = i < n ? csr[item + 1] - csr[item] : 0;
+                for (int64_t j = 0; j < len; ++j) put(off[sl] + j * kSell + lane, item, j < cnt ? csr[item] + j : -1);
+            }
+        }
+    };
+    {
+        const std::vector<int64_t> off = sell_offsets(ne, eperm, ecnt);
+        std::vector<int32_t> sid(off.back(), 0);
+        std::vector<double> swt(off.back(), 0.0);
+        sell_fill(ne, eperm, ecnt, off, [&](int64_t d, int32_t, int64_t q) {
+            if (q < 0) return;  // padding: weight 0 on vertex 0
+            sid[d] = evid[q];
+            swt[d] = ewt[q];
+        });
+        if ((st = m->upload(m->adj_eoff, off))) return st;
+        if ((st = m->upload(m->adj_evid, sid))) return st;
+        if ((st = m->upload(m->adj_ewt, swt))) return st;
+    }
+    {
+        const std::vector<int64_t> off = sell_offsets(nv, vperm, vcnt), soff = sell_offsets(nv, vperm, scnt);
+        std::vector<int32_t> sid(off.back(), 0);
+        std::vector<double> swf(off.back(), 0.0), swg(off.back(), 0.0);
+        std::vector<int64_t> sslot(soff.back(), 6 * ne);  // padding: the zero record after the 6 ne slot records
+        sell_fill(nv, vperm, vcnt, off, [&](int64_t d, int32_t v, int64_t q) {
+            sid[d] = q >= 0 ? vvid[q] : v;  // padding: weight 0 on the vertex itself
+            if (q < 0) return;
+            swf[d] = wf[q];
+            swg[d] = wg[q];
+        });
+        sell_fill(nv, vperm, scnt, soff, [&](int64_t d, int32_t, int64_t q) {
+            if (q >= 0) sslot[d] = slot[q];
+        });
+        if ((st = m->upload(m->adj_voff, off))) return st;
+        if ((st = m->upload(m->adj_vvid, sid))) return st;
+        if ((st = m->upload(m->adj_wf, swf))) return st;
+        if ((st = m->upload(m->adj_wg, swg))) return st;
+        if ((st = m->upload(m->adj_soff, soff))) return st;
+        if ((st = m->upload(m->adj_slot, sslot))) return st;
+    }
+    if ((st = m->upload(m->adj_eperm, eperm))) return st;
+    if ((st = m->upload(m->adj_vperm, vperm))) return st;
     if ((st = m->alloc(m->adj_lam_r, 4 * ne))) return st;
-    if ((st = m->alloc(m->adj_G, 6 * 4 * ne))) return st;
+    // 6 ne slot records and one zero record that padded slot entries point at
+    // (the edge-flux VJP writes only the first 6 ne)
+    if ((st = m->alloc(m->adj_G, 6 * 4 * ne + 4))) return st;
+    CK(cudaMemset(m->adj_G, 0, (6 * 4 * ne + 4) * sizeof(double)));
     if ((st = m->alloc(m->adj_S1, 4 * nv))) return st;
     for (int i = 0; i < 5; ++i)
         if ((st = m->alloc(m->adj_buf[i], 4 * nv))) return st;

@@ -368,6 +368,14 @@ fdu_status fdu_check_recip64(int device, const double *x, double *y, int64_t n);
  * Roe weights): y[i] = 1/sqrt(x[i]) by Newton-Raphson refinement of the
  * hardware approximation, for host arrays of positive normal doubles. */
 fdu_status fdu_check_rsqrt64(int device, const double *x, double *y, int64_t n);
+/* The kernels' exact scalings by 2 and 1/2 on the integer pipe (no
+ * counterpart in the paper): y[i] = 2 x[i] (up != 0) or x[i] / 2 (up == 0)
+ * for host arrays of doubles.  Doubling is exact for every input (the top
+ * binade overflows to infinity; infinities and NaN are unchanged); halving
+ * is exact where the half is a normal double, leaves infinities and NaN
+ * unchanged, and gives a zero of x's sign where the half is below the
+ * normal range (|x| < 2^-1021). */
+fdu_status fdu_check_scale2(int device, const double *x, double *y, int64_t n, int up);
 /* Accuracy check of the FP32 path's NU-WENO5 coefficients (Appendix, Eqs.
  * u0-u2, the smoothness indicators and the linear weights C_K; no
  * counterpart in the paper as an entry point).  xi: host [n][6] stencil

@@ -1769,6 +1769,10 @@ fdu_status fdu_check_rsqrt64(int device, const double *x, double *y, int64_t n) 
     return check_special(device, x, y, n, 1);
 }
 
+fdu_status fdu_check_scale2(int device, const double *x, double *y, int64_t n, int up) {
+    return check_special(device, x, y, n, up ? 3 : 2);
+}
+
 fdu_status fdu_check_weno_coef32(int device, const double *xi, double *k, int64_t n) {
     if (!xi || !k || n < 0) return set_err(FDU_ERR_ARG, "bad arguments");
     std::vector<float> g(4 * (size_t)n);

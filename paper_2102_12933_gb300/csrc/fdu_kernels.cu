@@ -846,9 +846,12 @@ __global__ void dt_finalize_kernel(unsigned long long *slot, double *tstate, dou
     *slot = 0x7FF0000000000000ull;
 }
 
+// which: 0 recip64, 1 rsqrt64, 2 half64, 3 twice64
 __global__ void recip_check_kernel(const double *x, double *y, int64_t n, int which) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = which == 1 ? rsqrt64(x[i]) : recip64(x[i]);
+    if (i >= n) return;
+    const double v = x[i];
+    y[i] = which == 0 ? recip64(v) : which == 1 ? rsqrt64(v) : which == 2 ? half64(v) : twice64(v);
 }
 
 // the FP32 edge kernel's coefficient block of n edges from their gaps

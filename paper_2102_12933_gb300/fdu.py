@@ -33,7 +33,7 @@ EXPORTS = (
     "fdu_mesh_info_get", "fdu_get_edges", "fdu_get_edge_stencils", "fdu_get_div_sizes", "fdu_get_div_stencils",
     "fdu_set_state", "fdu_get_state", "fdu_residual", "fdu_max_dt", "fdu_rk_step", "fdu_rk_steps",
     "fdu_fallback_count", "fdu_profile", "fdu_profile_read", "fdu_probe_fma", "fdu_residual_noalloc",
-    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_check_weno_coef32", "fdu_check_dw", "fdu_set_adjoint_precision", "fdu_mesh_create_cells", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
+    "fdu_check_recip64", "fdu_check_rsqrt64", "fdu_check_scale2", "fdu_check_weno_coef32", "fdu_check_dw", "fdu_set_adjoint_precision", "fdu_mesh_create_cells", "fdu_advance", "fdu_limited_count", "fdu_batch_create", "fdu_batch_info",
     "fdu_batch_max_dt", "fdu_batch_set_dt", "fdu_batch_rk_steps", "fdu_batch_set_launch", "fdu_batch_autotune",
     "fdu_batch_barrier_selftest", "fdu_residual_vjp", "fdu_rk_step_vjp", "fdu_adjoint_rk",
 )
@@ -109,6 +109,7 @@ def load():
         L.fdu_check_recip64.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_check_rsqrt64.argtypes = [C.c_int, dp, dp, i64]
         L.fdu_check_weno_coef32.argtypes = [C.c_int, dp, dp, i64]
+        L.fdu_check_scale2.argtypes = [C.c_int, dp, dp, i64, C.c_int]
         L.fdu_check_dw.argtypes = [C.c_int, C.c_int, dp, dp, dp, i64]
         L.fdu_set_adjoint_precision.argtypes = [C.c_void_p, C.c_int]
         L.fdu_mesh_create_cells.argtypes = [dp, i64, lp, ip, i64, C.c_int, C.POINTER(MeshOpts), C.POINTER(P)]
@@ -210,6 +211,15 @@ def check_recip64(x, device=0):
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.zeros_like(x)
     _check(load().fdu_check_recip64(int(device), _dp(x), _dp(y), x.size))
+    return y
+
+
+def check_scale2(x, up, device=0):
+    """The kernels' exact scaling of x by 2 (up) or 1/2 on the integer pipe
+    (accuracy check)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x)
+    _check(load().fdu_check_scale2(int(device), _dp(x), _dp(y), x.size, 1 if up else 0))
     return y
 
 

@@ -265,6 +265,33 @@ def test_fast_rsqrt_within_two_ulp_of_exact():
     assert ulp.max() <= 2.0
 
 
+def test_exact_scalings_by_two():
+    """The integer-pipe scalings of the FP64 kernels (Roe averages' |u|^2 / 2
+    and 1 / (2c), the pressure's |m|^2 / 2, the adjoint's factors 2 and 1/2)
+    against IEEE multiplication: doubling bit-exact for every double
+    (subnormals included; the top binade overflows to infinity), halving
+    bit-exact wherever the half is normal and a zero of the input's sign
+    below that; infinities and NaN unchanged."""
+    rng = np.random.default_rng(6)
+    n = 40000
+    x = np.ldexp(rng.uniform(1.0, 2.0, n), rng.integers(-1074, 1024, n)) * rng.choice([-1.0, 1.0], n)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 2.0 ** -1022, -2.0 ** -1022, 2.0 ** -1021,
+                        2.0 ** -1074, -2.0 ** -1074, np.finfo(np.float64).max, 2.0 ** 1023,
+                        np.nextafter(2.0 ** 1023, 0.0), 1.0, 3.0])
+    x = np.concatenate([x, special])
+    with np.errstate(over="ignore"):
+        want_up = x * 2.0
+    up = fdu.check_scale2(x, True)
+    assert np.array_equal(up, want_up, equal_nan=True)
+    assert np.array_equal(np.signbit(up), np.signbit(want_up))
+    dn = fdu.check_scale2(x, False)
+    normal_half = ~np.isfinite(x) | (np.abs(x) >= 2.0 ** -1021)
+    assert np.array_equal(dn[normal_half], (x * 0.5)[normal_half], equal_nan=True)
+    assert np.all(dn[~normal_half] == 0.0)
+    assert np.array_equal(np.signbit(dn[~normal_half]), np.signbit(x[~normal_half]))
+    assert np.count_nonzero(~normal_half) > 100  # the flushed range is exercised
+
+
 def test_four_million_vertex_mesh_sampled_parity_and_free_stream():
     """The largest case of the suite: a 2000 x 2000 torus lattice (4M vertices,
     12M edges, ~290M divergence entries with 64-bit offsets).  Sampled FP64

@@ -64,10 +64,10 @@ NCU_EDGE48_THREAD_INSTR_PER_EDGE = 97722617 * 32 / 480000
 TRAFFIC_EDGE48_B_PER_EDGE = (121.78432 + 6.677504) * 1e6 / 480000
 # edge_flux_f32 from one ncu capture on the 480k-edge case: issue slots busy,
 # FMA pipe busy, DRAM throughput (% of peak), DRAM bytes per edge.
-NCU_EDGE32_ISSUE_ACTIVE = 0.614
-NCU_EDGE32_FMA_PIPE = 0.505
-NCU_EDGE32_DRAM = 0.184
-TRAFFIC_EDGE32_B_PER_EDGE = (25.614336 + 0.0) * 1e6 / 480000
+NCU_EDGE32_ISSUE_ACTIVE = 0.628
+NCU_EDGE32_FMA_PIPE = 0.514
+NCU_EDGE32_DRAM = 0.193
+TRAFFIC_EDGE32_B_PER_EDGE = (25.61408 + 0.0) * 1e6 / 480000
 
 
 def _peaks():

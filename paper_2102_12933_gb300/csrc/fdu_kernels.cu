@@ -316,7 +316,7 @@ __device__ __forceinline__ Prim32 prim32(const float4 &w, float gm1) {
     return q;
 }
 struct Roe32 {
-    float u, v, H, c, ic, b1, qn, qt, hq2, nx, ny;
+    float u, v, H, c, ic, b1h, ich, qn, qt, hq2, nx, ny;  // b1h = b1 / 2, ich = ic / 2
 };
 __device__ __forceinline__ Roe32 roe32(const float4 &a, const Prim32 &pa, const float4 &b, const Prim32 &pb, float nx,
                                       float ny, float gm1) {
@@ -330,23 +330,34 @@ __device__ __forceinline__ Roe32 roe32(const float4 &a, const Prim32 &pa, const 
     const float c2 = gm1 * (R.H - R.hq2);
     R.ic = rsqrtf(c2);
     R.c = c2 * R.ic;
-    R.b1 = gm1 * R.ic * R.ic;
+    R.b1h = 0.5f * gm1 * R.ic * R.ic;
+    R.ich = 0.5f * R.ic;
     R.nx = nx;
     R.ny = ny;
     R.qn = R.u * nx + R.v * ny;
     R.qt = R.v * nx - R.u * ny;
     return R;
 }
+// pre-halved factors (phi/2, psi/2) and the sum started from d.w
 __device__ __forceinline__ float4 project32(const Roe32 &R, const float4 &d) {
-    const float phi = R.b1 * (R.hq2 * d.x - R.u * d.y - R.v * d.z + d.w);
-    const float psi = (R.qn * d.x - R.nx * d.y - R.ny * d.z) * R.ic;
-    return make_float4(0.5f * (phi + psi), d.x - phi, R.nx * d.z - R.ny * d.y - R.qt * d.x, 0.5f * (phi - psi));
+    const float phh = R.b1h * fmaf(-R.v, d.z, fmaf(-R.u, d.y, fmaf(R.hq2, d.x, d.w)));
+    const float psh = (R.qn * d.x - R.nx * d.y - R.ny * d.z) * R.ich;
+    return make_float4(phh + psh, fmaf(-2.0f, phh, d.x), R.nx * d.z - R.ny * d.y - R.qt * d.x, phh - psh);
 }
 __device__ __forceinline__ float4 unproject32(const Roe32 &R, const float4 &c) {
     const float rho = c.x + c.y + c.w;
     const float dd = R.c * (c.w - c.x);
     return make_float4(rho, R.u * rho + R.nx * dd - R.ny * c.z, R.v * rho + R.ny * dd + R.nx * c.z,
                        R.H * (c.x + c.w) + R.hq2 * c.y + R.qn * dd + R.qt * c.z);
+}
+// base + unproject32(R, c), with base taken into the fused multiply-adds
+__device__ __forceinline__ float4 unproject_add32(const Roe32 &R, const float4 &c, const float4 &base) {
+    const float ac = c.x + c.w;
+    const float rho = ac + c.y;
+    const float dd = R.c * (c.w - c.x);
+    return make_float4(base.x + rho, fmaf(R.u, rho, fmaf(R.nx, dd, fmaf(-R.ny, c.z, base.y))),
+                       fmaf(R.v, rho, fmaf(R.ny, dd, fmaf(R.nx, c.z, base.z))),
+                       fmaf(R.H, ac, fmaf(R.hq2, c.y, fmaf(R.qn, dd, fmaf(R.qt, c.z, base.w)))));
 }
 
 // FP32 NU-WENO5 increments of one field, both sides (same sub-stencil
@@ -464,8 +475,8 @@ __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int6
     weno_pair32(k, cL3.z, cL2.z, cM.z, cR2L.z, cR3.z, cR2.z, eps, dl.z, dr.z);
     weno_pair32(k, cL3.w, cL2.w, cM.w, cR2L.w, cR3.w, cR2.w, eps, dl.w, dr.w);
 
-    float4 wl = add4f(L1, unproject32(C, dl));
-    float4 wr = add4f(L1, unproject32(C, dr));
+    float4 wl = unproject_add32(C, dl, L1);
+    float4 wr = unproject_add32(C, dr, L1);
     Prim32 pl, pr;
     bool ok = wl.x > 0.f && wr.x > 0.f;
     if (ok) {

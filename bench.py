@@ -62,12 +62,18 @@ NCU_EDGE48_FMA_PIPE = 0.585
 NCU_EDGE48_FP64_PIPE = 0.141
 NCU_EDGE48_THREAD_INSTR_PER_EDGE = 97722617 * 32 / 480000
 TRAFFIC_EDGE48_B_PER_EDGE = (121.78432 + 6.677504) * 1e6 / 480000
-# edge_flux_f32 from one ncu capture on the 480k-edge case: issue slots busy,
-# FMA pipe busy, DRAM throughput (% of peak), DRAM bytes per edge.
-NCU_EDGE32_ISSUE_ACTIVE = 0.628
-NCU_EDGE32_FMA_PIPE = 0.514
-NCU_EDGE32_DRAM = 0.193
-TRAFFIC_EDGE32_B_PER_EDGE = (25.61408 + 0.0) * 1e6 / 480000
+# edge_flux_f32 from one ncu capture each on the 480k-edge case: issue slots
+# busy, FMA pipe busy, DRAM throughput (% of peak), DRAM bytes per edge; the
+# default form (FP64-built block streamed in FP32) and the compact form
+# (values formed in the kernel from the stencil gaps, mesh option f32_coef = 1).
+NCU_EDGE32_ISSUE_ACTIVE = 0.438
+NCU_EDGE32_FMA_PIPE = 0.345
+NCU_EDGE32_DRAM = 0.414
+TRAFFIC_EDGE32_B_PER_EDGE = (64.013312 + 0.81536) * 1e6 / 480000
+NCU_EDGE32G_ISSUE_ACTIVE = 0.628
+NCU_EDGE32G_FMA_PIPE = 0.514
+NCU_EDGE32G_DRAM = 0.193
+TRAFFIC_EDGE32G_B_PER_EDGE = (25.61408 + 0.0) * 1e6 / 480000
 
 
 def _peaks():
@@ -323,14 +329,15 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    def timed_steps(prec, k):
+    def timed_steps(prec, k, mesh_=None):
+        mesh_ = M if mesh_ is None else mesh_
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(k):
-            M.rk_step(dt, prec, stream=stream)
+            mesh_.rk_step(dt, prec, stream=stream)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -396,6 +403,27 @@ def run_ours(args):
     err48 = {"rho": _rel_l2(w48b[:, 0], w64b[:, 0]), "rhoE": _rel_l2(w48b[:, 3], w64b[:, 3]),
              "steps": err_steps}
 
+    # ---------------- FP32 with the compact coefficient form: a second mesh
+    # with f32_coef = 1 (NU-WENO5 values formed in FP32 in the edge kernel from
+    # the FP64-built stencil gaps instead of streaming the FP64-built block),
+    # the same steps from w0 and the same FP64 reference
+    Mc = fdu.Mesh(mesh.xy, mesh.tri, mesh.Lx, mesh.Ly, device=local, f32_coef=1,
+                  **({"artificial_edges": 1} if hybrid else {}))
+    Mc.set_state(w0)
+    for _ in range(args.warmup):
+        Mc.rk_step(dt, 32, stream=stream)
+    Mc.set_state(w0)
+    Mc.profile(True)
+    Mc.profile_read("edge", 32)
+    msc = timed_steps(32, args.warmup + args.steps, Mc)
+    ec_ms, ec_n = Mc.profile_read("edge", 32)
+    Mc.profile(False)
+    Mc.set_state(w0)
+    Mc.rk_steps(dt, err_steps, 32, stream=stream)
+    wcb = Mc.get_state()
+    errc = {"rho": _rel_l2(wcb[:, 0], w64b[:, 0]), "rhoE": _rel_l2(wcb[:, 3], w64b[:, 3]), "steps": err_steps}
+    Mc.close()
+
     # ---------------- end to end through the C-ABI with host buffers
     # pinned host buffers: the copies are DMA transfers of the caller's rows
     host_in = torch.from_numpy(np.ascontiguousarray(w0)).pin_memory().numpy()
@@ -446,7 +474,8 @@ def run_ours(args):
     vnnz, ennz = info["div_vert_nnz"], info["div_edge_nnz"]
     div_flops = FLOP_DIV64_PER_VENTRY * vnnz + FLOP_DIV64_PER_EENTRY * ennz + FLOP_DIV64_FIXED * nv
     # FP32 kernels are HBM-bound.  Bytes per launch of the kernels' own tables:
-    edge32_bytes = ne * (24 + 4 * 4 + 8 + 16) + nv * 16  # ids, 4 stencil gaps, normal, flux; FP32 state once
+    edge32_bytes = ne * (24 + 26 * 4 + 16) + nv * 16  # ids, 24 coefficients and the normal, flux; FP32 state once
+    edge32c_bytes = ne * (24 + 4 * 4 + 8 + 16) + nv * 16  # compact form: ids, 4 stencil gaps, normal, flux
     div32_bytes = (vnnz * 12 + ennz * 8 + nv * 8) + nv * (32 + 32 + 32 + 32 + 16) + ne * 16 + nv * 32
     # and the method's algorithmic bytes at p = 4 (compact edge form: 6 ids, 4
     # curve coordinates and n per edge; divergence tables (2J+K+2) p + 4 (J+K)
@@ -522,11 +551,13 @@ def run_ours(args):
         "fp32": {
             "value": round(value32, 3), "unit": "Mvertex/s", "speedup_vs_f64": round(value32 / value, 3),
             "error_vs_f64": err32,
+            "coefficients": "NU-WENO5 block built in FP64 on the host, streamed rounded to FP32 (104 B per edge)",
             "edge_kernel": {"avg_launch_ms": round(e32_avg, 4),
-                            "bound": "FP32 issue (NU-WENO5 coefficients formed in registers)",
+                            "bound": "coefficient stream and gather latency (neither DRAM nor issue saturated)",
                             "ncu_issue_active": NCU_EDGE32_ISSUE_ACTIVE, "ncu_fma_pipe": NCU_EDGE32_FMA_PIPE,
                             "ncu_dram_throughput": NCU_EDGE32_DRAM,
-                            "traffic": round(TRAFFIC_EDGE32_B_PER_EDGE * ne), "traffic_unit": "bytes per launch",
+                            "traffic": (round(TRAFFIC_EDGE32_B_PER_EDGE * ne) if TRAFFIC_EDGE32_B_PER_EDGE else None),
+                            "traffic_unit": "bytes per launch",
                             "achieved_gbs": round(edge32_bytes / (e32_avg / 1e3) / 1e9, 1),
                             "frac_hbm": round(edge32_bytes / (e32_avg / 1e3) / 1e9 / hbm, 4),
                             "algorithmic_bytes": int(edge32_alg),
@@ -539,9 +570,23 @@ def run_ours(args):
             "stage": {"avg_ms": round(stage32_ms, 4), "algorithmic_bytes": int(edge32_alg + div32_alg),
                       "frac_hbm_algorithmic": round((edge32_alg + div32_alg) / (stage32_ms / 1e3) / 1e9 / hbm, 4)},
             "frac_hbm_note": "frac_hbm divides the kernel's own table bytes; frac_hbm_algorithmic the method's "
-                             "compact bytes (edge: 64 B per edge + 16 B per vertex, which the edge kernel's "
-                             "tables now are: ids, 4 stencil gaps and the normal; divergence: its stencil "
-                             "tables, flux read, residual write and the stage's 80 B per vertex)",
+                             "compact bytes (edge: 64 B per edge + 16 B per vertex, which the compact "
+                             "coefficient form's tables are; divergence: its stencil tables, flux read, "
+                             "residual write and the stage's 80 B per vertex)",
+            "compact_coefficients": {
+                "note": "mesh option f32_coef = 1: NU-WENO5 values formed in FP32 in the edge kernel from the "
+                        "stencil gaps (built in FP64 on the host) instead of the streamed FP64-built block; "
+                        "same mesh, initial state, steps and FP64 reference",
+                "value": round(replica_throughput(nv * stages * (args.warmup + args.steps), ws_, msc / 1e3) / 1e6, 3),
+                "unit": "Mvertex/s", "error_vs_f64": errc,
+                "edge_kernel": {"avg_launch_ms": round(ec_ms / max(ec_n, 1), 4),
+                                "bound": "FP32 issue",
+                                "ncu_issue_active": NCU_EDGE32G_ISSUE_ACTIVE, "ncu_fma_pipe": NCU_EDGE32G_FMA_PIPE,
+                                "ncu_dram_throughput": NCU_EDGE32G_DRAM,
+                                "traffic": round(TRAFFIC_EDGE32G_B_PER_EDGE * ne), "traffic_unit": "bytes per launch",
+                                "frac_hbm_algorithmic": round(edge32c_bytes / (ec_ms / max(ec_n, 1) / 1e3) / 1e9 / hbm,
+                                                              4)},
+            },
         },
         "e2e": {"value": round(e2e_value, 3), "unit": "Mvertex/s", "h2d_bytes_per_step": nv * 32,
                 "d2h_bytes_per_step": nv * 32, "steps": e2e_steps, "blocks": e2e_blocks, "statistic": "median block",

@@ -77,6 +77,10 @@ typedef struct fdu_mesh_opts {
                                    forward-Euler part ws + theta dt L of each vertex's RK stage uses the
                                    largest theta in {1, 1/2, ..., 2^-20, 0} keeping rho and p at least alpha
                                    times the stage input's (the paper has no such safeguard) */
+    int f32_coef;               /* NU-WENO5 coefficients of the FP32 path: 0 = the block built in FP64 on the host,
+                                   rounded to FP32 and streamed (104 bytes per edge; the default); 1 = formed in
+                                   FP32 by the FP32 edge kernel from the edge's four stencil gaps (24 bytes per
+                                   edge with the normal; the gaps are built in FP64 on the host) */
 } fdu_mesh_opts;
 
 typedef struct fdu_mesh fdu_mesh;

@@ -60,7 +60,7 @@ struct fdu_mesh {
     // tables
     int32_t *sten = nullptr;          // [6][ne_act]
     double *coef64 = nullptr;         // [32][ne_act]
-    float *coef32 = nullptr;          // [ne_act] float4 of stencil gaps, then [ne_act] float2 (n_x, n_y)
+    float *coef32 = nullptr;          // FP32 block: [6][ne_act] float4, or (f32_coef = 1) [ne_act] float4 of gaps; then [ne_act] float2 (n_x, n_y)
     // precision 48 (built on first use): double-word coefficient block
     // [kEdgeCoef][ne_act]; FP64 divergence tables with the left vertex flux
     // of each edge folded into the vertex weights; edge weights as double words
@@ -247,16 +247,30 @@ fdu_status upload_tables(fdu_mesh *m) {
     // 1D stencils and coefficient blocks, SoA over internal active edges
     std::vector<int32_t> sten(6 * ne);
     std::vector<double> coef((size_t)kEdgeCoef * ne);
-    std::vector<float> coef32((size_t)kEdgeCoef32 * ne, 0.0f);
+    const bool gaps32 = m->opts.f32_coef == 1;
+    std::vector<float> coef32((size_t)(gaps32 ? kEdgeCoef32Gaps : kEdgeCoef32) * ne, 0.0f);
     for (int64_t e = 0; e < ne; ++e) {
         const int64_t o = T.e_new2old[e];
         for (int i = 0; i < 6; ++i) sten[i * ne + e] = T.v_old2new[T.sten[6 * o + i]];
         for (int c = 0; c < kEdgeCoef; ++c) coef[(size_t)c * ne + e] = T.coef[(size_t)kEdgeCoef * o + c];
-        // FP32 form: the gaps between consecutive stencil coordinates (the
-        // coordinates put L1 at -1/2 and R1 at 1/2), differenced in FP64, as
-        // one float4 [ne][4], then the normal as float2 [ne][2]
-        stencil_gaps(&T.xi[6 * (size_t)o], &coef32[4 * (size_t)e]);
-        for (int c = 0; c < 2; ++c) coef32[4 * (size_t)ne + 2 * e + c] = (float)T.coef[(size_t)kEdgeCoef * o + kCoefN + c];
+        if (gaps32) {
+            // compact FP32 form: the gaps between consecutive stencil coordinates
+            // (the coordinates put L1 at -1/2 and R1 at 1/2), differenced in FP64,
+            // as one float4 [ne][4], then the normal as float2 [ne][2]
+            stencil_gaps(&T.xi[6 * (size_t)o], &coef32[4 * (size_t)e]);
+            for (int c = 0; c < 2; ++c)
+                coef32[4 * (size_t)ne + 2 * e + c] = (float)T.coef[(size_t)kEdgeCoef * o + kCoefN + c];
+        } else {
+            // default FP32 form: the FP64 block rounded to FP32, values 0..23 as
+            // float4 vectors [c/4][ne][c%4], then the normal as float2 [ne][2]
+            for (int c = 0; c < kEdgeCoef; ++c) {
+                const float v = (float)T.coef[(size_t)kEdgeCoef * o + c];
+                if (c < 4 * kEdgeCoef32Vec)
+                    coef32[((size_t)(c / 4) * ne + e) * 4 + c % 4] = v;
+                else
+                    coef32[(size_t)4 * kEdgeCoef32Vec * ne + 2 * e + (c - 4 * kEdgeCoef32Vec)] = v;
+            }
+        }
     }
     if ((st = m->upload(m->sten, sten))) return st;
     if ((st = m->upload(m->coef64, coef))) return st;
@@ -446,6 +460,7 @@ EdgeArgs edge_args(fdu_mesh *m, int prec, const void *w) {
     EdgeArgs a{};
     a.sten = m->sten;
     a.coef = fp64_state(prec) ? (const void *)m->coef64 : (const void *)m->coef32;
+    a.coef_gaps = !fp64_state(prec) && m->opts.f32_coef == 1;
     a.w = w;
     a.r = fp64_state(prec) ? (void *)m->r64 : (void *)m->r32;
     if (prec == 48) {
@@ -910,6 +925,7 @@ fdu_status fdu_default_opts(fdu_mesh_opts *o) {
     o->host_threads = 0;
     o->ghost_donor = nullptr;
     o->positivity_alpha = 0.0;
+    o->f32_coef = 0;
     return FDU_OK;
 }
 
@@ -923,6 +939,7 @@ static fdu_status mesh_create(const double *xy, int64_t nv, const CellList &cell
         return set_err(FDU_ERR_ARG, "lsq_degree must be 1..6 and lsq_levels 1..2");
     if (!(opts->positivity_alpha >= 0.0 && opts->positivity_alpha < 1.0))
         return set_err(FDU_ERR_ARG, "positivity_alpha must be in [0, 1)");
+    if (opts->f32_coef != 0 && opts->f32_coef != 1) return set_err(FDU_ERR_ARG, "f32_coef must be 0 or 1");
     if (!(opts->gamma > 1.0) || !(opts->weno_eps > 0) || !(opts->weno_eps32 > 0))
         return set_err(FDU_ERR_ARG, "gamma must be > 1 and the WENO epsilons > 0");
     if (opts->bc == FDU_BC_PERIODIC && !(opts->Lx > 0 && opts->Ly > 0))
@@ -1295,6 +1312,7 @@ fdu_status fdu_batch_create(int32_t n_meshes, const double *const *xy, const int
     if (opts->ghost_donor || opts->bc != FDU_BC_PERIODIC)
         return set_err(FDU_ERR_ARG, "batches hold periodic meshes (without ghost vertices)");
     if (opts->device < 0) return set_err(FDU_ERR_ARG, "batches need a device");
+    if (opts->f32_coef != 0 && opts->f32_coef != 1) return set_err(FDU_ERR_ARG, "f32_coef must be 0 or 1");
     int64_t V = 0, T = 0;
     for (int i = 0; i < n_meshes; ++i) {
         if (!xy[i] || !tri[i] || nv[i] < 3 || nt[i] < 1) return set_err(FDU_ERR_ARG, "bad mesh " + std::to_string(i));

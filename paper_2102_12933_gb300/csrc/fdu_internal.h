@@ -34,11 +34,18 @@ constexpr int kCoefCL = 20;
 constexpr int kCoefCR = 22;
 constexpr int kCoefN = 24;
 constexpr int kEdgeCoef = 26;
-// FP32 form: the edge's four stencil gaps as one float4 per edge ([ne]
-// float4: L1-L2, L2-L3, R1-R2, R2-R3 along the curve, each divided by the
-// arc length L1-R1), then (n_x, n_y) as one float2 per edge ([ne] float2):
-// 24 bytes.  The FP32 edge flux forms values 0..23 from the gaps.
-constexpr int kEdgeCoef32 = 6;  // floats per edge
+// FP32 path, default form: the FP64-built block rounded to FP32, values
+// 0..23 as six float4 per edge ([6][ne] float4, value c at block c / 4,
+// component c % 4), then (n_x, n_y) as one float2 per edge ([ne] float2
+// after them): 104 bytes per edge.
+constexpr int kEdgeCoef32 = 26;
+constexpr int kEdgeCoef32Vec = 6;  // float4 blocks before the normals
+// FP32 path, compact form (mesh option f32_coef = 1): the edge's four stencil
+// gaps as one float4 per edge ([ne] float4: L1-L2, L2-L3, R1-R2, R2-R3 along
+// the curve, each divided by the arc length L1-R1, differenced in FP64),
+// then the float2 normals: 24 bytes per edge.  The FP32 edge flux forms
+// values 0..23 from the gaps in FP32.
+constexpr int kEdgeCoef32Gaps = 6;
 
 struct HostTables {
     int64_t nv = 0, nt = 0, ne = 0, n_real = 0;

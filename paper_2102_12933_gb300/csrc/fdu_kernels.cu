@@ -288,11 +288,13 @@ __device__ __forceinline__ void div_f64_body(const DivArgs &A, const int64_t i) 
 }
 
 // ================================================================== FP32 path
-// The FP32 residual reads an FP32 copy of the state and, per edge, its four
-// stencil gaps and normal (24 bytes), from which it forms the NU-WENO5
-// coefficients in registers; weights, fluxes and sums are FP32.  Reciprocals
-// use the hardware approximation (rcp.approx, about one ulp), well inside
-// the FP32 path's error against FP64.
+// The FP32 residual reads an FP32 copy of the state and, per edge, the
+// FP64-built NU-WENO5 block rounded to FP32 (104 bytes), or in the compact
+// form (mesh option f32_coef = 1) the edge's four stencil gaps and normal
+// (24 bytes), from which it forms the coefficients in registers; weights,
+// fluxes and sums are FP32.  Reciprocals use the hardware approximation
+// (rcp.approx, about one ulp), well inside the FP32 path's error against
+// FP64.
 __device__ __forceinline__ float rcp32(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -446,6 +448,9 @@ __device__ __forceinline__ void weno_coef32(const float4 g, float *k) {
     weno_ratios32(c, d, a, k + kCoefCR);
 }
 
+// GAPS: the compact coefficient form (the values formed here from the
+// edge's stencil gaps); otherwise the FP64-built block rounded to FP32.
+template <bool GAPS>
 __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int64_t e) {
     const float4 *__restrict__ w = static_cast<const float4 *>(A.w);
     const float *__restrict__ g = static_cast<const float *>(A.coef);
@@ -455,11 +460,30 @@ __device__ __forceinline__ void edge_flux_f32_body(const EdgeArgs &A, const int6
     int32_t s[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) s[i] = __ldg(A.sten + (int64_t)i * ne + e);
-    // the edge's stencil gaps ([ne] float4) and normal ([ne] float2 after them)
-    const float2 nq = __ldg(reinterpret_cast<const float2 *>(g + (int64_t)4 * ne) + e);
-    const float nx = nq.x, ny = nq.y;
     float k[kCoefN];
-    weno_coef32(__ldg(reinterpret_cast<const float4 *>(g) + e), k);
+    float nx, ny;
+    if (GAPS) {
+        // the edge's stencil gaps ([ne] float4) and normal ([ne] float2 after them)
+        const float2 nq = __ldg(reinterpret_cast<const float2 *>(g + (int64_t)4 * ne) + e);
+        nx = nq.x;
+        ny = nq.y;
+        weno_coef32(__ldg(reinterpret_cast<const float4 *>(g) + e), k);
+    } else {
+        // six float4 of values ([c/4][ne] float4, component c%4), then the
+        // normal as one float2 ([ne] float2 after them)
+        const float4 *__restrict__ g4 = reinterpret_cast<const float4 *>(g);
+#pragma unroll
+        for (int i = 0; i < kEdgeCoef32Vec; ++i) {
+            const float4 q = __ldg(g4 + (int64_t)i * ne + e);
+            k[4 * i] = q.x;
+            k[4 * i + 1] = q.y;
+            k[4 * i + 2] = q.z;
+            k[4 * i + 3] = q.w;
+        }
+        const float2 nq = __ldg(reinterpret_cast<const float2 *>(g + (int64_t)4 * kEdgeCoef32Vec * ne) + e);
+        nx = nq.x;
+        ny = nq.y;
+    }
     const float4 L1 = __ldg(w + s[2]), R1 = __ldg(w + s[3]);
     const Prim32 pL1 = prim32(L1, gm1), pR1 = prim32(R1, gm1);
     const Roe32 C = roe32(L1, pL1, R1, pR1, nx, ny, gm1);
@@ -644,11 +668,14 @@ __global__ void __launch_bounds__(kEdgeBlock) edge_flux_f64_kernel(EdgeArgs A) {
     if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
     edge_flux_f64_body(A, e);
 }
-__global__ void __launch_bounds__(kEdgeBlock, 6) edge_flux_f32_kernel(EdgeArgs A) {
+// compact form: 80 registers, 24 warps per SM; the streamed block: 95 registers
+// and 20 warps (at 80 it spills)
+template <bool GAPS>
+__global__ void __launch_bounds__(kEdgeBlock, GAPS ? 6 : 5) edge_flux_f32_kernel(EdgeArgs A) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= A.ne) return;
     if (A.dt_dev && *A.dt_dev == 0.0) return;  // adaptive run already at t_end
-    edge_flux_f32_body(A, e);
+    edge_flux_f32_body<GAPS>(A, e);
 }
 template <int MODE, bool DWE>
 __global__ void __launch_bounds__(kDivBlock) div_f64_kernel(DivArgs A) {
@@ -728,7 +755,8 @@ __global__ void stage_persistent_kernel(EdgeArgs EA, DivArgs DA, unsigned int *b
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t e = t0; e < EA.ne; e += stride) {
         if (PREC == 64) edge_flux_f64_body(EA, e);
-        else edge_flux_f32_body(EA, e);
+        else if (EA.coef_gaps) edge_flux_f32_body<true>(EA, e);
+        else edge_flux_f32_body<false>(EA, e);
     }
     __threadfence();
     if (!grid_barrier(bar_count, bar_gen, nblocks_expected, spin_limit, err)) return;
@@ -889,7 +917,9 @@ void launch_edge_flux_f64(const EdgeArgs &a, cudaStream_t s) {
     if (a.ne > 0) edge_flux_f64_kernel<<<blocks(a.ne, kEdgeBlock), kEdgeBlock, 0, s>>>(a);
 }
 void launch_edge_flux_f32(const EdgeArgs &a, cudaStream_t s) {
-    if (a.ne > 0) edge_flux_f32_kernel<<<blocks(a.ne, kEdgeBlock), kEdgeBlock, 0, s>>>(a);
+    if (a.ne <= 0) return;
+    if (a.coef_gaps) edge_flux_f32_kernel<true><<<blocks(a.ne, kEdgeBlock), kEdgeBlock, 0, s>>>(a);
+    else edge_flux_f32_kernel<false><<<blocks(a.ne, kEdgeBlock), kEdgeBlock, 0, s>>>(a);
 }
 template <bool DWE>
 void launch_div_f64_t(const DivArgs &a, int mode, cudaStream_t s) {

@@ -13,7 +13,9 @@ constexpr int kDivBlock = 128;   // threads per block, divergence kernels
 // Edge-flux inputs (internal ids, SoA over the active edges).
 struct EdgeArgs {
     const int32_t *sten;  // [6][ne]  L3 L2 L1 R1 R2 R3
-    const void *coef;     // FP64: [kEdgeCoef][ne]; FP32: [ne] float4 of stencil gaps, then [ne] float2 (n_x, n_y)
+    const void *coef;     // FP64: [kEdgeCoef][ne]; FP32: [6][ne] float4 of values 0..23, or (coef_gaps) [ne]
+                          // float4 of stencil gaps; then [ne] float2 (n_x, n_y)
+    bool coef_gaps;       // FP32: the block is the compact gaps form (values formed in the kernel)
     const void *w;        // FP64: [nv][4] double; FP32: [nv] float4
     void *r;              // FP64: [ne][4] double; FP32: [ne] float4
     int64_t ne;

@@ -50,7 +50,7 @@ class MeshOpts(C.Structure):
         ("Lx", C.c_double), ("Ly", C.c_double), ("weno_eps", C.c_double), ("weno_eps32", C.c_double),
         ("gamma", C.c_double), ("lsq_degree", C.c_int), ("lsq_levels", C.c_int), ("bc", C.c_int),
         ("renumber", C.c_int), ("device", C.c_int), ("host_threads", C.c_int),
-        ("ghost_donor", C.POINTER(C.c_int32)), ("positivity_alpha", C.c_double),
+        ("ghost_donor", C.POINTER(C.c_int32)), ("positivity_alpha", C.c_double), ("f32_coef", C.c_int),
     ]
 
 
@@ -260,11 +260,13 @@ class Mesh:
 
     def __init__(self, xy, tri, Lx=0.0, Ly=0.0, *, lsq_degree=2, lsq_levels=2, device=0, renumber=1,
                  ghost_donor=None, weno_eps=1e-40, weno_eps32=1e-30, gamma=1.4, host_threads=0,
-                 positivity_alpha=0.0, artificial_edges=None):
+                 positivity_alpha=0.0, artificial_edges=None, f32_coef=0):
         """`tri` is an (nt, 3) array of triangles, or a pair (cell_off,
         cell_vtx) of a hybrid triangle / quadrilateral mesh in CSR form; then
         `artificial_edges` (0, 1 or 2, default 1) selects the artificial
-        edges of fdu_mesh_create_cells."""
+        edges of fdu_mesh_create_cells.  `f32_coef` selects the FP32 path's
+        NU-WENO5 coefficients: 0 the FP64-built block streamed in FP32, 1
+        formed in the FP32 edge kernel from the stencil gaps."""
         L = load()
         self._h = None
         xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
@@ -284,7 +286,7 @@ class Mesh:
             bc = FDU_BC_TRANSMISSIVE
         o = default_opts(Lx=float(Lx), Ly=float(Ly), lsq_degree=lsq_degree, lsq_levels=lsq_levels, device=device,
                          renumber=renumber, weno_eps=weno_eps, weno_eps32=weno_eps32, gamma=gamma, bc=bc,
-                         host_threads=host_threads, positivity_alpha=float(positivity_alpha))
+                         host_threads=host_threads, positivity_alpha=float(positivity_alpha), f32_coef=int(f32_coef))
         if gp is not None:
             o.ghost_donor = gp
         h = C.c_void_p()
@@ -483,7 +485,7 @@ class Batch(Mesh):
     launch per RK stage).  States are the meshes' rows concatenated."""
 
     def __init__(self, meshes, L, *, lsq_degree=2, lsq_levels=2, device=0, renumber=1, gamma=1.4,
-                 weno_eps=1e-40, weno_eps32=1e-30, host_threads=0):
+                 weno_eps=1e-40, weno_eps32=1e-30, host_threads=0, f32_coef=0):
         Lib = load()
         self._h = None
         xys = [np.ascontiguousarray(m[0], dtype=np.float64).reshape(-1, 2) for m in meshes]
@@ -496,7 +498,7 @@ class Batch(Mesh):
         nt = np.array([a.shape[0] for a in tris], np.int64)
         o = default_opts(Lx=float(L), Ly=float(L), lsq_degree=lsq_degree, lsq_levels=lsq_levels, device=device,
                          renumber=renumber, weno_eps=weno_eps, weno_eps32=weno_eps32, gamma=gamma,
-                         host_threads=host_threads)
+                         host_threads=host_threads, f32_coef=int(f32_coef))
         h = C.c_void_p()
         _check(Lib.fdu_batch_create(n, xp, _lp(nv), tp, _lp(nt), C.byref(o), C.byref(h)))
         self._h = h

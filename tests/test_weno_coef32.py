@@ -97,3 +97,74 @@ def test_coefficient_check_rejects_bad_coordinates():
             fdu.check_weno_coef32(bad)
         assert e.value.status == -1  # FDU_ERR_ARG
     assert fdu.check_weno_coef32(np.zeros((0, 6))).shape == (0, 24)
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.gpu
+@needs_gpu
+def test_compact_form_fp32_parity_with_the_oracle():
+    """The FP32 path with the compact coefficient form (mesh option f32_coef =
+    1) under the FP32 path's bounds against the oracle: residual within 1e-4
+    relative L2 per component, density and energy after 20 RK3 steps within
+    1e-5; and within FP32 rounding of the default form (the FP64-built block
+    streamed in FP32)."""
+    m, w0 = inputs.vortex_case(40, seed=1001)
+    om = oracle.OracleMesh(m.xy, m.tri, m.Lx, m.Ly)
+    Mc = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0, f32_coef=1)
+    Md = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0)
+    Mc.set_state(w0)
+    Md.set_state(w0)
+    got, dflt = Mc.residual(32), Md.residual(32)
+    want = om.residual(w0)
+    for k in range(4):
+        assert _rel_l2(got[:, k], want[:, k]) <= 1e-4
+        assert _rel_l2(got[:, k], dflt[:, k]) <= 2e-5
+    dt = om.max_dt(w0, 0.5)
+    Mc.rk_steps(dt, 20, 32)
+    wc = Mc.get_state()
+    wo = w0.copy()
+    for _ in range(20):
+        wo = om.rk3_step(wo, dt)
+    assert _rel_l2(wc[:, 0], wo[:, 0]) <= 1e-5
+    assert _rel_l2(wc[:, 3], wo[:, 3]) <= 1e-5
+    Mc.close()
+    Md.close()
+
+
+@pytest.mark.gpu
+@needs_gpu
+def test_compact_form_batch_matches_single_meshes():
+    """The batched persistent stage takes the compact form's branch when the
+    batch is built with f32_coef = 1: four FP32 steps of each mesh in the batch
+    against the same mesh alone with the same option (the tolerance of the
+    batch tests for FP32)."""
+    cases = [inputs.vortex_case(n, seed=s) for n, s in ((16, 7101), (23, 7102), (29, 7103))]
+    B = fdu.Batch([(m.xy, m.tri) for m, _ in cases], L=10.0, device=0, f32_coef=1)
+    w0 = np.concatenate([w for _, w in cases])
+    B.set_state(w0)
+    dts = B.batch_max_dt(0.5)
+    B.set_dt(dts)
+    B.batch_rk_steps(4, 32)
+    got = B.get_state()
+    for i, ((m, w), dt) in enumerate(zip(cases, dts)):
+        M = fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=0, f32_coef=1)
+        M.set_state(w)
+        for _ in range(4):
+            M.rk_step(dt, 32)
+        want = M.get_state()
+        M.close()
+        sl = slice(B.offsets[i], B.offsets[i + 1])
+        for k in range(4):
+            assert _rel_l2(got[sl, k] - w[:, k], want[:, k] - w[:, k]) <= 1e-6
+    B.close()
+
+
+def test_f32_coef_option_is_checked():
+    """Checked on the host before any device use."""
+    m, _ = inputs.vortex_case(8, seed=7104)
+    with pytest.raises(fdu.FduError) as e:
+        fdu.Mesh(m.xy, m.tri, m.Lx, m.Ly, device=-1, f32_coef=2)
+    assert e.value.status == -1  # FDU_ERR_ARG

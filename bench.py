@@ -66,14 +66,14 @@ TRAFFIC_EDGE48_B_PER_EDGE = (121.78432 + 6.677504) * 1e6 / 480000
 # busy, FMA pipe busy, DRAM throughput (% of peak), DRAM bytes per edge; the
 # default form (FP64-built block streamed in FP32) and the compact form
 # (values formed in the kernel from the stencil gaps, mesh option f32_coef = 1).
-NCU_EDGE32_ISSUE_ACTIVE = 0.438
-NCU_EDGE32_FMA_PIPE = 0.345
-NCU_EDGE32_DRAM = 0.414
-TRAFFIC_EDGE32_B_PER_EDGE = (64.013312 + 0.81536) * 1e6 / 480000
-NCU_EDGE32G_ISSUE_ACTIVE = 0.628
-NCU_EDGE32G_FMA_PIPE = 0.514
-NCU_EDGE32G_DRAM = 0.193
-TRAFFIC_EDGE32G_B_PER_EDGE = (25.61408 + 0.0) * 1e6 / 480000
+NCU_EDGE32_ISSUE_ACTIVE = 0.441
+NCU_EDGE32_FMA_PIPE = 0.344
+NCU_EDGE32_DRAM = 0.418
+TRAFFIC_EDGE32_B_PER_EDGE = (64.013056 + 0.72192) * 1e6 / 480000
+NCU_EDGE32G_ISSUE_ACTIVE = 0.644
+NCU_EDGE32G_FMA_PIPE = 0.516
+NCU_EDGE32G_DRAM = 0.194
+TRAFFIC_EDGE32G_B_PER_EDGE = (25.61408 + 0.000512) * 1e6 / 480000
 
 
 def _peaks():
